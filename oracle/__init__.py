@@ -1,0 +1,250 @@
+"""FP64 CPU oracle for the MPPI + contact-rollout path (test infrastructure).
+
+Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
+leg may import this package.  It wraps ``mppi_oracle.c`` (plain C, FP64),
+which shares no code with the CUDA path.  ``build()`` compiles it with gcc.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mppi_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "liboracle.so")
+_lib = None
+
+MAXL, MAXB, MAXC, MAXNV, MAXNQ = 7, 16, 16, 20, 21
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into oracle/_build/liboracle.so (gcc, -O2)."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-fno-fast-math",
+           "-ffp-contract=off", "-o", tmp, _SRC, "-lm", "-lpthread"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+class StepInfo(C.Structure):
+    _fields_ = [("ncon", C.c_int), ("nactive", C.c_int), ("pen_all", C.c_double),
+                ("pen_box", C.c_double), ("chol_fail", C.c_int)]
+
+
+class Contact(C.Structure):
+    _fields_ = [("dist", C.c_double), ("p", C.c_double * 3), ("n", C.c_double * 3),
+                ("bodyA", C.c_int), ("bodyB", C.c_int), ("box", C.c_int)]
+
+
+class FK(C.Structure):
+    _fields_ = [(name, C.c_double * (2 * MAXL * k)) for name, k in
+                (("R", 9), ("p", 3), ("z", 3), ("o", 3), ("c", 3), ("a0", 3), ("a1", 3), ("Iw", 9))]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = build()
+        L = C.CDLL(path)
+        d, i, u32p, dp = C.c_double, C.c_int, C.POINTER(C.c_uint32), C.POINTER(C.c_double)
+        vp = C.c_void_p
+        L.or_model_size.restype = i
+        L.or_model_parse.argtypes = [vp, C.c_size_t, vp]
+        L.or_model_parse.restype = i
+        L.or_forward_kinematics.argtypes = [vp, dp, C.POINTER(FK)]
+        L.or_mass_matrix.argtypes = [vp, dp, dp]
+        L.or_bias.argtypes = [vp, dp, dp, dp]
+        L.or_rnea.argtypes = [vp, dp, dp, dp, dp]
+        L.or_sphere_capsule.argtypes = [dp, d, dp, dp, d, dp, dp, dp]
+        L.or_box_sdf.argtypes = [dp, dp, dp, dp, dp, dp]
+        L.or_sphere_box.argtypes = [dp, d, dp, dp, dp, dp, dp]
+        L.or_capsule_box.argtypes = [dp, dp, d, dp, dp, dp, dp, dp, dp]
+        L.or_step_ex.argtypes = [vp, dp, dp, dp, C.POINTER(StepInfo), dp, C.POINTER(Contact)]
+        L.or_step_ex.restype = i
+        L.or_stage_cost.argtypes = [vp, dp, dp, C.POINTER(StepInfo)]
+        L.or_stage_cost.restype = d
+        L.or_rollout.argtypes = [vp, dp, dp, i, dp]
+        L.or_rollout.restype = d
+        L.or_rollout_many.argtypes = [vp, dp, i, dp, i, i, dp, i]
+        L.or_philox4x32_10.argtypes = [u32p, u32p, u32p]
+        L.or_normals4.argtypes = [u32p, dp]
+        L.or_noise.argtypes = [C.c_uint64, C.c_uint64, i, i, i, dp, dp]
+        L.or_mppi_update.argtypes = [i, i, i, dp, dp, d, dp, dp, dp]
+        L.or_mppi_update.restype = i
+        L.or_mppi_iteration.argtypes = [vp, dp, dp, i, i, d, dp, C.c_uint64, C.c_uint64, dp, dp, dp, i]
+        L.or_mppi_iteration.restype = i
+        _lib = L
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+class Model:
+    """A parsed scene in the oracle's own representation."""
+
+    def __init__(self, blob: bytes):
+        L = lib()
+        self._buf = C.create_string_buffer(L.or_model_size())
+        self._blob = C.create_string_buffer(blob, len(blob))
+        rc = L.or_model_parse(self._blob, len(blob), self._buf)
+        if rc != 0:
+            raise ValueError(f"oracle: malformed scene blob ({rc})")
+        hdr = np.frombuffer(blob[16:16 + 8 * 3], dtype="<f8")
+        self.na = int(hdr[0])
+        self.nq, self.nv, self.nu = 2 * self.na + 7, 2 * self.na + 6, 2 * self.na
+
+    @property
+    def ptr(self):
+        return C.cast(self._buf, C.c_void_p)
+
+    # -- kinematics and dynamics ------------------------------------------
+    def fk(self, q):
+        f = FK()
+        q = _f64(q)
+        lib().or_forward_kinematics(self.ptr, _dp(q), C.byref(f))
+        na = self.na
+
+        def arr(name, k):
+            return np.array(getattr(f, name)).reshape(2, MAXL, k)[:, :na]
+        return {n: arr(n, k) for n, k in (("R", 9), ("p", 3), ("z", 3), ("o", 3), ("c", 3),
+                                           ("a0", 3), ("a1", 3), ("Iw", 9))}
+
+    def mass_matrix(self, q):
+        M = np.zeros((self.nv, self.nv))
+        lib().or_mass_matrix(self.ptr, _dp(_f64(q)), _dp(M))
+        return M
+
+    def bias(self, q, qd):
+        c = np.zeros(self.nv)
+        lib().or_bias(self.ptr, _dp(_f64(q)), _dp(_f64(qd)), _dp(c))
+        return c
+
+    def rnea(self, q, qd, qdd):
+        t = np.zeros(self.nv)
+        lib().or_rnea(self.ptr, _dp(_f64(q)), _dp(_f64(qd)), _dp(_f64(qdd)), _dp(t))
+        return t
+
+    # -- stepping ----------------------------------------------------------
+    def step(self, x, u, want_contacts=False):
+        x = _f64(x)
+        u = _f64(u)
+        xo = np.zeros(self.nq + self.nv)
+        info = StepInfo()
+        lam = np.zeros(3 * MAXC)
+        cons = (Contact * MAXC)()
+        rc = lib().or_step_ex(self.ptr, _dp(x), _dp(u), _dp(xo), C.byref(info), _dp(lam), cons)
+        if rc != 0:
+            raise FloatingPointError("oracle: mass matrix not positive definite")
+        if not want_contacts:
+            return xo, info
+        clist = [dict(dist=c.dist, p=np.array(c.p), n=np.array(c.n), bodyA=c.bodyA, bodyB=c.bodyB,
+                      box=c.box) for c in cons[:info.ncon]]
+        return xo, info, lam[:3 * info.ncon].copy(), clist
+
+    def stage_cost(self, x_next, u, info):
+        return lib().or_stage_cost(self.ptr, _dp(_f64(x_next)), _dp(_f64(u)), C.byref(info))
+
+    def rollout(self, x, U, traj=False):
+        U = _f64(U)
+        H = U.shape[0]
+        T = np.zeros((H + 1, self.nq + self.nv)) if traj else None
+        c = lib().or_rollout(self.ptr, _dp(_f64(x)), _dp(U), H, _dp(T) if traj else None)
+        return (c, T) if traj else c
+
+    def rollout_many(self, x, U, per_sample_state=False, nthreads=1):
+        U = _f64(U)
+        K, H = U.shape[0], U.shape[1]
+        costs = np.zeros(K)
+        lib().or_rollout_many(self.ptr, _dp(_f64(x)), int(per_sample_state), _dp(U), K, H,
+                              _dp(costs), nthreads)
+        return costs
+
+    def mppi_iteration(self, x, u_nom, K, lam, sigma, seed, iteration, nthreads=1,
+                       want_samples=False):
+        u_nom = _f64(u_nom)
+        H = u_nom.shape[0]
+        u_out = np.zeros_like(u_nom)
+        costs = np.zeros(K)
+        U = np.zeros((K, H, self.nu)) if want_samples else None
+        st = lib().or_mppi_iteration(self.ptr, _dp(_f64(x)), _dp(u_nom), K, H, float(lam),
+                                     _dp(_f64(sigma)), C.c_uint64(seed), C.c_uint64(iteration),
+                                     _dp(u_out), _dp(costs), _dp(U) if want_samples else None,
+                                     nthreads)
+        out = dict(u_nom=u_out, costs=costs, status=st)
+        if want_samples:
+            out["U"] = U
+        return out
+
+
+# -- narrow phase (module level, for brute-force tests) --------------------
+def sphere_capsule(c, r, a, b, rc):
+    dist, p, n = C.c_double(), np.zeros(3), np.zeros(3)
+    lib().or_sphere_capsule(_dp(_f64(c)), r, _dp(_f64(a)), _dp(_f64(b)), rc, C.byref(dist), _dp(p), _dp(n))
+    return dist.value, p, n
+
+
+def box_sdf(x, bc, bh):
+    s, n, surf = C.c_double(), np.zeros(3), np.zeros(3)
+    lib().or_box_sdf(_dp(_f64(x)), _dp(_f64(bc)), _dp(_f64(bh)), C.byref(s), _dp(n), _dp(surf))
+    return s.value, n, surf
+
+
+def sphere_box(c, r, bc, bh):
+    dist, p, n = C.c_double(), np.zeros(3), np.zeros(3)
+    lib().or_sphere_box(_dp(_f64(c)), r, _dp(_f64(bc)), _dp(_f64(bh)), C.byref(dist), _dp(p), _dp(n))
+    return dist.value, p, n
+
+
+def capsule_box(a, b, rc, bc, bh):
+    dist, p, n, t = C.c_double(), np.zeros(3), np.zeros(3), C.c_double()
+    lib().or_capsule_box(_dp(_f64(a)), _dp(_f64(b)), rc, _dp(_f64(bc)), _dp(_f64(bh)), C.byref(dist),
+                         _dp(p), _dp(n), C.byref(t))
+    return dist.value, p, n, t.value
+
+
+# -- random numbers ---------------------------------------------------------
+def philox4x32_10(ctr, key):
+    c = (C.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
+    k = (C.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
+    o = (C.c_uint32 * 4)()
+    lib().or_philox4x32_10(c, k, o)
+    return [int(v) for v in o]
+
+
+def normals4(words):
+    w = (C.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in words])
+    z = np.zeros(4)
+    lib().or_normals4(w, _dp(z))
+    return z
+
+
+def noise(seed, iteration, K, H, nu, sigma):
+    eps = np.zeros((K, H, nu))
+    lib().or_noise(C.c_uint64(seed), C.c_uint64(iteration), K, H, nu, _dp(_f64(sigma)), _dp(eps))
+    return eps
+
+
+def mppi_update(costs, U, lam, u_nom):
+    costs = _f64(costs)
+    U = _f64(U)
+    K, H, nu = U.shape
+    u_out = np.zeros((H, nu))
+    w = np.zeros(K)
+    st = lib().or_mppi_update(K, H, nu, _dp(costs), _dp(U), float(lam), _dp(_f64(u_nom)), _dp(u_out), _dp(w))
+    return u_out, w, st
