@@ -880,8 +880,10 @@ void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
-/* Uniform in (0,1): ((x >> 8) + 1/2) 2^-24, exactly representable, never 0. */
-static double u01(uint32_t x) { return ((double)(x >> 8) + 0.5) * (1.0 / 16777216.0); }
+/* Uniform in (0,1) from the top 23 bits: ((x >> 9) + 1/2) 2^-23.  Never 0
+ * or 1, and exactly representable in FP32 as well as FP64, so an FP32
+ * implementation draws the very same uniforms. */
+static double u01(uint32_t x) { return ((double)(x >> 9) + 0.5) * (1.0 / 8388608.0); }
 
 /* Four standard normals from one Philox block by Box-Muller on the word
  * pairs (0,1) and (2,3): z0 = r cos(2 pi u1), z1 = r sin(2 pi u1). */

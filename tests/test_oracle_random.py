@@ -28,21 +28,26 @@ def test_philox_known_answers(ctr, key, expect):
 
 
 def test_uniform_mapping_bounds():
-    # ((x >> 8) + 1/2) 2^-24 never reaches 0 or 1: the extreme words give
+    # ((x >> 9) + 1/2) 2^-23 never reaches 0 or 1: the extreme words give
     # finite normals
     z = oracle.normals4([0, 0, 0xFFFFFFFF, 0xFFFFFFFF])
     assert np.all(np.isfinite(z))
-    # word 0 = 0 -> u = 2^-25 -> r = sqrt(2 * 25 ln 2)
-    r = np.sqrt(-2.0 * np.log(0.5 / 16777216.0))
-    assert z[0] == pytest.approx(r * np.cos(2 * np.pi * 0.5 / 16777216.0), rel=1e-15)
+    # word 0 = 0 -> u = 2^-24 -> r = sqrt(2 * 24 ln 2)
+    r = np.sqrt(-2.0 * np.log(0.5 / 8388608.0))
+    assert z[0] == pytest.approx(r * np.cos(2 * np.pi * 0.5 / 8388608.0), rel=1e-15)
+    # every uniform is exactly representable in FP32 (24-bit significand)
+    xs = np.array([0, 1, 511, 512, 0x7FFFFFFF, 0xFFFFFE00, 0xFFFFFFFF], dtype=np.uint64)
+    u = ((xs >> 9).astype(np.float64) + 0.5) / 2 ** 23
+    assert np.all(u.astype(np.float32).astype(np.float64) == u)
+    assert np.all((u > 0) & (u < 1))
 
 
 def test_box_muller_pairs_closed_form():
     # u0 = 1/2 + 1/2^25 (x = 0x80000000), u1 = 1/4 + ... : angle 90 degrees
     w = [0x80000000, 0x40000000, 0x80000000, 0x00000000]
     z = oracle.normals4(w)
-    u0 = ((0x80000000 >> 8) + 0.5) / 2 ** 24
-    u1 = ((0x40000000 >> 8) + 0.5) / 2 ** 24
+    u0 = ((0x80000000 >> 9) + 0.5) / 2 ** 23
+    u1 = ((0x40000000 >> 9) + 0.5) / 2 ** 23
     r = np.sqrt(-2 * np.log(u0))
     assert z[0] == pytest.approx(r * np.cos(2 * np.pi * u1), abs=1e-15)
     assert z[1] == pytest.approx(r * np.sin(2 * np.pi * u1), rel=1e-14)
