@@ -1,0 +1,157 @@
+/*
+ * mppi.h -- C ABI of libmppi: GPU (sm_103a) sampling-based optimisation of
+ * bimanual ball manipulation with a parallel rigid-body contact simulator.
+ *
+ * The optimiser is the MPPI loop of the paper's Algorithm 1 (sample control
+ * sequences from N(nu, Sigma), roll each out through the world model, sum the
+ * stage costs, weight the samples with s_j = exp(-c_j / beta) and move the
+ * mean to the weighted average, Eq. 8a and 8d) with the learning rate
+ * eta = 1, the elite set equal to all K samples, beta = lambda and a fixed
+ * diagonal Sigma = diag(sigma^2).  The world model is a MuJoCo-style
+ * simulator of two revolute arms with capsule links, a free ball, static
+ * boxes and a floor (Sec. III, Eq. 1b; joint-space dynamics, soft frictional
+ * contact by projected Gauss-Seidel, semi-implicit Euler).
+ *
+ * Conventions
+ *  - Every tensor argument is a caller-owned DEVICE pointer to float32 in
+ *    row-major order (last index fastest) unless stated otherwise.  The
+ *    library never frees caller memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls enqueue work and return without synchronising, except
+ *    where stated.
+ *  - Return codes are the MPPI_* values below; no exception crosses the ABI.
+ *    Errors detected on the device (non-finite costs, a failed Cholesky
+ *    pivot, a bounded wait that ran out) are recorded in the handle's error
+ *    word and returned by mppi_sync() / mppi_batch_sync().
+ *  - One handle per stream; a handle is not thread-safe.
+ *  - Dimensions for a model with n_a joints per arm: nq = 2 n_a + 7
+ *    (left arm, right arm, ball position, ball quaternion w-first),
+ *    nv = 2 n_a + 6 (arm joint rates, ball linear and angular velocity in
+ *    world axes), nu = 2 n_a (one control per arm joint), state
+ *    x = (q, qdot) of nx = nq + nv floats.  Supported n_a: 3 and 7.
+ */
+#ifndef MPPI_H
+#define MPPI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    MPPI_OK = 0,
+    MPPI_ERR_INVALID_ARG = 1, /* bad pointer, size or blob                   */
+    MPPI_ERR_OOM = 2,         /* device or host allocation failed            */
+    MPPI_ERR_CUDA = 3,        /* a CUDA runtime call or launch failed        */
+    MPPI_ERR_NONFINITE = 4,   /* every sample cost was NaN/inf, or a state
+                                 went non-finite; u_nom was left unchanged   */
+    MPPI_ERR_TIMEOUT = 5,     /* a bounded device wait gave up               */
+    MPPI_ERR_ADMISSION = 6,   /* server: request does not fit the budget     */
+    MPPI_ERR_CHOLESKY = 7,    /* (M + dt D) lost positive definiteness       */
+    MPPI_ERR_UNSUPPORTED = 8  /* model outside the compiled variants         */
+};
+
+typedef struct mppi_model mppi_model;
+typedef struct mppi_ctx mppi_ctx;
+
+/* Human-readable name of a return code (static string). */
+const char *mppi_strerror(int code);
+
+/* ---------------------------------------------------------------- model */
+/* Parse a scene blob (host memory, `len` bytes; layout: u32 magic
+ * 0x4950504D, u32 version 1, u32 count, u32 0, then `count` float64 values
+ * -- kinematics, inertias, capsule geometry, contact constants, boxes, cost
+ * weights, home state) and upload it to the current device.  The blob is
+ * copied; the caller keeps ownership of it.  *out receives an immutable
+ * model that may be shared by many handles. */
+int mppi_model_load(const void *blob, size_t len, mppi_model **out);
+void mppi_model_free(mppi_model *m);
+/* Dimensions of a loaded model (any output pointer may be NULL). */
+int mppi_model_dims(const mppi_model *m, int *nq, int *nv, int *nu, int *n_boxes);
+/* Home state x0 of the scene into host memory (nx floats). */
+int mppi_model_home(const mppi_model *m, float *x0_host);
+
+/* ------------------------------------------------------------- controller */
+/* One MPPI controller (paper Alg. 1, Eq. 8).  K samples per iteration,
+ * horizon H steps, temperature lambda > 0, sigma = nu per-control standard
+ * deviations (HOST pointer, copied), 64-bit Philox key `seed`.  Allocates
+ * the handle's device workspace (K costs, error word, iteration counter).
+ * 1 <= K <= 1<<20, 1 <= H <= 1024. */
+int mppi_create(const mppi_model *m, int K, int H, float lambda, const float *sigma, uint64_t seed,
+                mppi_ctx **out);
+int mppi_destroy(mppi_ctx *c);
+
+/* One optimisation iteration (Alg. 1 loop body without the QP projection):
+ *   eps[k,h,j] = sigma_j N(0,1) from Philox4x32-10, key = seed, counter =
+ *                (j/4, h, k, iteration), Box-Muller on the word pairs;
+ *   U_k = clamp(u_nom + eps_k, u_lo, u_hi) per control;
+ *   c_k = sum_h stage cost along the rollout of U_k from `state`;
+ *   w_k = exp(-(c_k - min c)/lambda) (non-finite c_k -> 0);
+ *   u_nom_out = sum_k w_k U_k / sum_k w_k        (Eq. 8a, 8d).
+ * state: nx floats; u_nom, u_nom_out: H x nu, may alias.  Advances the
+ * handle's iteration counter (on the device) by one. */
+int mppi_step(mppi_ctx *c, const float *state, const float *u_nom, float *u_nom_out, void *stream);
+
+/* `iters` iterations of mppi_step in place on u_nom_inout (Alg. 1, M =
+ * iters).  best_cost_out (optional, 2 floats): lowest sample cost of the
+ * last iteration and its sample index (as float).  After the first call
+ * with a given (state, u_nom_inout, iters, stream), the iterations are
+ * replayed from a captured CUDA graph. */
+int mppi_solve(mppi_ctx *c, const float *state, float *u_nom_inout, int iters, float *best_cost_out,
+               void *stream);
+
+/* Weighted-mean update alone (Eq. 8a, 8d) for host- or test-supplied
+ * costs: costs (K), u_nom, u_out (H x nu, may alias).  The samples are the
+ * Philox samples of the handle's current iteration counter.  Does not
+ * advance the counter. */
+int mppi_update(mppi_ctx *c, const float *costs, const float *u_nom, float *u_out, void *stream);
+
+/* Roll out n explicit control sequences: states (n x nx), U (n x H x nu),
+ * costs (n) -- the same simulator and stage costs as mppi_step with the
+ * controls given instead of sampled.  states_out (optional, n x nx): the
+ * state after the last step.  n <= K of the handle. */
+int rollout_batch(mppi_ctx *c, int n, const float *states, const float *U, float *costs,
+                  float *states_out, void *stream);
+
+/* One simulator step for n states in place: states_inout (n x nx), U1
+ * (n x nu).  n <= K. */
+int sim_step(mppi_ctx *c, int n, float *states_inout, const float *U1, void *stream);
+
+/* Materialise the Philox noise of iteration `iteration`: eps_out
+ * (K x H x nu).  For tests. */
+int mppi_debug_noise(mppi_ctx *c, uint64_t iteration, float *eps_out, void *stream);
+
+/* Raw Philox4x32-10 words for n counters (tests of the integer stream):
+ * ctr (device, n x 4 uint32), key = the 64-bit key, out (device, n x 4). */
+int mppi_debug_philox(int n, const uint32_t *ctr, uint64_t key, uint32_t *out, void *stream);
+
+/* Iteration counter (checkpoint / resume).  get synchronises `stream`. */
+int mppi_get_iteration(mppi_ctx *c, uint64_t *iteration, void *stream);
+int mppi_set_iteration(mppi_ctx *c, uint64_t iteration, void *stream);
+
+/* Synchronise `stream`, then return and clear the handle's device error
+ * word: MPPI_OK, MPPI_ERR_NONFINITE, MPPI_ERR_CHOLESKY or MPPI_ERR_TIMEOUT. */
+int mppi_sync(mppi_ctx *c, void *stream);
+
+/* Profiling.  mppi_profile(c, n) records CUDA events around the rollout
+ * and update kernels of the next n iterations (mppi_step / mppi_solve
+ * eager path) on the launching stream and counts, on the device, the active
+ * contacts and the capsule-box pairs that pass the bounding-sphere cull;
+ * n = 0 turns it off.  mppi_profile_read synchronises the recorded events
+ * and returns: iterations recorded, total rollout and update kernel time
+ * (ms), mean active contacts per sample-step and mean exact capsule-box
+ * tests per sample-step.  Any output pointer may be NULL. */
+int mppi_profile(mppi_ctx *c, int n);
+int mppi_profile_read(mppi_ctx *c, int *n, float *rollout_ms, float *update_ms, double *contacts_per_step,
+                      double *box_tests_per_step);
+
+/* Launch shape: samples (warps) per CTA for the rollout kernels, 1..16
+ * (0 = the library default).  Used by the autotuner. */
+int mppi_set_launch(mppi_ctx *c, int samples_per_cta);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MPPI_H */

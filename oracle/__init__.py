@@ -75,6 +75,8 @@ def lib():
         L.or_rollout.argtypes = [vp, dp, dp, i, dp]
         L.or_rollout.restype = d
         L.or_rollout_many.argtypes = [vp, dp, i, dp, i, i, dp, i]
+        L.or_min_abs_dist.argtypes = [vp, dp]
+        L.or_min_abs_dist.restype = d
         L.or_philox4x32_10.argtypes = [u32p, u32p, u32p]
         L.or_normals4.argtypes = [u32p, dp]
         L.or_noise.argtypes = [C.c_uint64, C.c_uint64, i, i, i, dp, dp]
@@ -156,6 +158,10 @@ class Model:
         clist = [dict(dist=c.dist, p=np.array(c.p), n=np.array(c.n), bodyA=c.bodyA, bodyB=c.bodyB,
                       box=c.box) for c in cons[:info.ncon]]
         return xo, info, lam[:3 * info.ncon].copy(), clist
+
+    def min_abs_dist(self, x):
+        """Smallest |signed distance| over all candidate pairs at x."""
+        return lib().or_min_abs_dist(self.ptr, _dp(_f64(x)))
 
     def stage_cost(self, x_next, u, info):
         return lib().or_stage_cost(self.ptr, _dp(_f64(x_next)), _dp(_f64(u)), C.byref(info))

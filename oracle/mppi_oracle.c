@@ -49,6 +49,7 @@
 #define OR_MAXNV 20
 #define OR_MAXNQ 21
 #define OR_MAXR (3 * OR_MAXC)
+#define OR_FACE_TIE 1e-5   /* m: face distances this close count as tied */
 
 typedef struct {
     double FR[9], Fp[3];
@@ -456,8 +457,8 @@ void or_sphere_capsule(const double *c, double r, const double *a, const double 
 }
 
 /* Signed distance from point x to an axis-aligned box, its outward normal
- * and the closest surface point.  Inside: nearest face, ties -> lowest axis,
- * + face before - face. */
+ * and the closest surface point.  Inside: nearest face, faces within 1e-5 m
+ * of the nearest are tied, ties -> lowest axis, + face before - face. */
 void or_box_sdf(const double *x, const double *bc, const double *bh, double *sdf, double *n, double *surf) {
     double q[3], cl[3];
     int inside = 1;
@@ -474,14 +475,19 @@ void or_box_sdf(const double *x, const double *bc, const double *bh, double *sdf
         memcpy(surf, cl, sizeof cl);
         return;
     }
-    double best = INFINITY;
-    int ax = 0, sg = 1;
+    /* nearest face; faces within OR_FACE_TIE of the nearest count as tied
+     * (the deepest point of a segment crossing a box lies where two faces
+     * are equidistant), ties -> lowest axis, + face before - face */
+    double fd[6], best = INFINITY;
     for (int k = 0; k < 3; k++) {
-        double dp = (bc[k] + bh[k]) - x[k];  /* distance to + face */
-        double dm = x[k] - (bc[k] - bh[k]);  /* distance to - face */
-        if (dp < best) { best = dp; ax = k; sg = 1; }
-        if (dm < best) { best = dm; ax = k; sg = -1; }
+        fd[2 * k] = (bc[k] + bh[k]) - x[k];      /* distance to + face */
+        fd[2 * k + 1] = x[k] - (bc[k] - bh[k]);  /* distance to - face */
+        if (fd[2 * k] < best) best = fd[2 * k];
+        if (fd[2 * k + 1] < best) best = fd[2 * k + 1];
     }
+    int f = 0;
+    while (fd[f] > best + OR_FACE_TIE) f++;
+    int ax = f / 2, sg = (f % 2) ? -1 : 1;
     *sdf = -best;
     n[0] = n[1] = n[2] = 0.0;
     n[ax] = (double)sg;
@@ -592,6 +598,20 @@ int or_collide(const or_model *m, const or_fk *f, const double *ballp, or_contac
     *pen_all = pa;
     *pen_box = pb;
     return 0;
+}
+
+/* Smallest |signed distance| over all candidate pairs at state x (used to
+ * keep parity scenes away from contact activation boundaries). */
+double or_min_abs_dist(const or_model *m, const double *x) {
+    or_fk f;
+    or_forward_kinematics(m, x, &f);
+    or_contact all[1 + 2 * OR_MAXL + OR_MAXB + 2 * OR_MAXL * OR_MAXB], act[OR_MAXC];
+    int nall, nact;
+    double pa, pb;
+    or_collide(m, &f, x + 2 * m->na, all, &nall, act, &nact, &pa, &pb);
+    double best = INFINITY;
+    for (int j = 0; j < nall; j++) if (fabs(all[j].dist) < best) best = fabs(all[j].dist);
+    return best;
 }
 
 /* Contact frame rows: n, t1 = normalise(n x e) with e the world axis of

@@ -1,0 +1,809 @@
+// Kernels and C ABI of libmppi (see include/mppi.h).
+//
+// Kernels
+//   rollout_kernel<NA, MODE>  one warp per sample: H simulator steps with the
+//                             state resident in shared memory, stage costs,
+//                             cost[k].  MODE 0 reads explicit controls, MODE 1
+//                             samples them in-kernel from Philox (Alg. 1,
+//                             sampling + rollout + cost).
+//   update_kernel<NU>         one CTA per horizon step h: min cost, weights
+//                             exp(-(c - c_min)/lambda), sum_k w_k U_k[h,:]
+//                             with the samples regenerated from Philox,
+//                             fixed-order tree reductions (Eq. 8a, 8d).
+//   noise_kernel<NU>          materialises the Philox noise (tests).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/mppi.h"
+#include "mppi_device.cuh"
+#include "mppi_internal.h"
+
+using namespace mppi;
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+namespace mppi {
+
+template <int NA, int MODE>
+__global__ void __launch_bounds__(512) rollout_kernel(RolloutArgs args) {
+    using d = Dims<NA>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    DevModel& M = *reinterpret_cast<DevModel*>(smem);
+    float* unom_s = reinterpret_cast<float*>(smem + sizeof(DevModel));
+    const int unom_n = (MODE == 1 && args.stage_unom) ? args.H * d::NU : 0;
+    const size_t ws_off = sizeof(DevModel) + ((size_t)unom_n * sizeof(float) + 15) / 16 * 16;
+    WarpWS<NA>* wsb = reinterpret_cast<WarpWS<NA>*>(smem + ws_off);
+
+    {  // stage the model (and u_nom) in shared memory
+        const float4* src = reinterpret_cast<const float4*>(args.model);
+        float4* dst = reinterpret_cast<float4*>(smem);
+        for (int t = threadIdx.x; t < (int)(sizeof(DevModel) / 16); t += blockDim.x) dst[t] = src[t];
+        for (int t = threadIdx.x; t < unom_n; t += blockDim.x) unom_s[t] = args.u_nom[t];
+    }
+    __syncthreads();
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int k = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (k >= args.n) return;
+    WarpWS<NA>& w = wsb[warp];
+    const float* x = args.states + (size_t)k * args.state_stride;
+    if (lane < d::NQ) w.q[lane] = x[lane];
+    if (lane < d::NV) w.qd[lane] = x[d::NQ + lane];
+    uint32_t iter = 0;
+    uint2 key = make_uint2(0, 0);
+    float sig = 0.0f, lo = 0.0f, hi = 0.0f;
+    if (MODE == 1) {
+        iter = (uint32_t)(args.iter_ptr ? *args.iter_ptr : args.iter_val);
+        key = make_uint2((uint32_t)args.seed, (uint32_t)(args.seed >> 32));
+        if (lane < d::NU) {
+            sig = args.sigma[lane];
+            lo = M.link[lane / NA][lane % NA].u_lo;
+            hi = M.link[lane / NA][lane % NA].u_hi;
+        }
+    }
+    __syncwarp();
+    float cost = 0.0f;
+    const float* gb = M.goal;
+    unsigned n_exact = 0, n_con = 0;
+    for (int h = 0; h < args.H; ++h) {
+        if (lane < d::NU) {
+            if (MODE == 1) {
+                const float un = unom_n ? unom_s[h * d::NU + lane] : args.u_nom[h * d::NU + lane];
+                w.u[lane] = sample_control(key, iter, k, h, lane, un, sig, lo, hi);
+            } else {
+                w.u[lane] = args.U[((size_t)k * args.H + h) * d::NU + lane];
+            }
+        }
+        forward_kinematics<NA>(M, w, lane);
+        __syncwarp();
+        if (h > 0 && lane == 0 && M.w_grasp != 0.0f) cost += M.w_grasp * grasp_term<NA>(w);
+        n_exact += collide<NA>(M, w, lane);
+        __syncwarp();
+        n_con += w.ncon;
+        dynamics<NA>(M, w, lane, args.err);
+        contacts<NA>(M, w, lane);
+        integrate<NA>(M, w, lane);
+        if (lane == 0) {
+            const float* pb = &w.q[d::B];
+            const float e0 = pb[0] - gb[0], e1 = pb[1] - gb[1], e2 = pb[2] - gb[2];
+            float uu = 0.0f;
+#pragma unroll
+            for (int j = 0; j < d::NU; ++j) uu += w.u[j] * w.u[j];
+            cost += M.w_goal * (e0 * e0 + e1 * e1 + e2 * e2) + M.w_u * uu + M.w_pen * w.pen_all +
+                    M.w_obst * w.pen_box;
+        }
+        __syncwarp();
+    }
+    if (M.w_grasp != 0.0f) {
+        forward_kinematics<NA>(M, w, lane);
+        __syncwarp();
+        if (lane == 0) cost += M.w_grasp * grasp_term<NA>(w);
+    }
+    if (lane == 0) {
+        args.costs[k] = cost;
+        if (!isfinite(cost)) atomicOr(args.err, ERRB_NONFINITE);
+    }
+    if (args.stats) {
+        n_exact = __reduce_add_sync(FULL, n_exact);
+        if (lane == 0) {
+            atomicAdd(&args.stats[0], (unsigned long long)args.H);
+            atomicAdd(&args.stats[1], (unsigned long long)n_con);
+            atomicAdd(&args.stats[2], (unsigned long long)n_exact);
+        }
+    }
+    if (args.states_out) {
+        float* xo = args.states_out + (size_t)k * d::NX;
+        if (lane < d::NQ) xo[lane] = w.q[lane];
+        if (lane < d::NV) xo[d::NQ + lane] = w.qd[lane];
+    }
+}
+
+template <int NU>
+__global__ void __launch_bounds__(256) update_kernel(UpdateArgs a) {
+    constexpr int T = 256;
+    __shared__ float red[NU + 1][T];
+    __shared__ float rmin[T];
+    __shared__ int ridx[T];
+    __shared__ int is_last;
+    const int h = blockIdx.x, tid = threadIdx.x;
+    const uint32_t iter = (uint32_t)(a.iter_ptr ? *a.iter_ptr : a.iter_val);
+    const uint2 key = make_uint2((uint32_t)a.seed, (uint32_t)(a.seed >> 32));
+    // (1) lowest finite cost (first index among equals)
+    float cm = INFINITY;
+    int ci = 0x7fffffff;
+    for (int k = tid; k < a.K; k += T) {
+        const float c = a.costs[k];
+        if (isfinite(c) && (c < cm)) {
+            cm = c;
+            ci = k;
+        }
+    }
+    rmin[tid] = cm;
+    ridx[tid] = ci;
+    __syncthreads();
+    for (int s = T / 2; s > 0; s >>= 1) {
+        if (tid < s) {
+            const float o = rmin[tid + s];
+            const int oi = ridx[tid + s];
+            if (o < rmin[tid] || (o == rmin[tid] && oi < ridx[tid])) {
+                rmin[tid] = o;
+                ridx[tid] = oi;
+            }
+        }
+        __syncthreads();
+    }
+    const float cmin = rmin[0];
+    const int cidx = ridx[0];
+    __syncthreads();
+    const bool any = isfinite(cmin);
+    // (2) weighted sums with regenerated samples
+    float acc[NU];
+#pragma unroll
+    for (int j = 0; j < NU; ++j) acc[j] = 0.0f;
+    float Z = 0.0f;
+    float un[NU], sg[NU], lo[NU], hi[NU];
+#pragma unroll
+    for (int j = 0; j < NU; ++j) {
+        un[j] = a.u_nom[h * NU + j];
+        sg[j] = a.sigma[j];
+        lo[j] = a.u_lo[j];
+        hi[j] = a.u_hi[j];
+    }
+    if (any) {
+        const float inv_lam = 1.0f / a.lambda;
+        for (int k = tid; k < a.K; k += T) {
+            const float c = a.costs[k];
+            const float wk = isfinite(c) ? expf(-(c - cmin) * inv_lam) : 0.0f;
+            Z += wk;
+#pragma unroll
+            for (int jb = 0; jb < (NU + 3) / 4; ++jb) {
+                const uint4 wv = philox4x32_10(make_uint4((uint32_t)jb, (uint32_t)h, (uint32_t)k, iter), key);
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int j = 4 * jb + t;
+                    if (j < NU) {
+                        const float z = block_normal(wv, t);
+                        const float u = fminf(fmaxf(__fmaf_rn(sg[j], z, un[j]), lo[j]), hi[j]);
+                        acc[j] += wk * u;
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < NU; ++j) red[j][tid] = acc[j];
+    red[NU][tid] = Z;
+    __syncthreads();
+    for (int s = T / 2; s > 0; s >>= 1) {
+        if (tid < s) {
+#pragma unroll
+            for (int j = 0; j <= NU; ++j) red[j][tid] += red[j][tid + s];
+        }
+        __syncthreads();
+    }
+    if (tid < NU) a.u_out[h * NU + tid] = any ? red[tid][0] / red[NU][0] : un[tid];
+    if (h == 0 && tid == 0) {
+        if (!any) atomicOr(a.err, ERRB_NONFINITE);
+        if (a.best) {
+            a.best[0] = cmin;
+            a.best[1] = (float)cidx;
+        }
+    }
+    // last CTA to finish advances the iteration counter (no waiting)
+    if (a.advance) {
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            const unsigned t = atomicAdd(a.done, 1u);
+            is_last = (t == gridDim.x - 1);
+        }
+        __syncthreads();
+        if (is_last && tid == 0) {
+            *a.done = 0u;
+            *a.iter_ptr += 1ull;
+            __threadfence();
+        }
+    }
+}
+
+template <int NU>
+__global__ void noise_kernel(NoiseArgs a) {
+    const size_t n = (size_t)a.K * a.H * NU;
+    const uint2 key = make_uint2((uint32_t)a.seed, (uint32_t)(a.seed >> 32));
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(i % NU);
+        const int h = (int)((i / NU) % a.H);
+        const int k = (int)(i / ((size_t)NU * a.H));
+        const uint4 wv = philox4x32_10(make_uint4((uint32_t)(j >> 2), (uint32_t)h, (uint32_t)k, (uint32_t)a.iter), key);
+        a.eps[i] = __fmul_rn(a.sigma[j], block_normal(wv, j & 3));
+    }
+}
+
+__global__ void philox_kernel(int n, const uint4* ctr, uint2 key, uint4* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = philox4x32_10(ctr[i], key);
+}
+
+}  // namespace mppi
+
+// ---------------------------------------------------------------------------
+// host helpers
+// ---------------------------------------------------------------------------
+namespace {
+
+int cuda_fail(cudaError_t e) {
+    if (e == cudaSuccess) return MPPI_OK;
+    if (e == cudaErrorMemoryAllocation) return MPPI_ERR_OOM;
+    return MPPI_ERR_CUDA;
+}
+
+template <int NA>
+size_t rollout_smem(int spc, int unom_floats) {
+    return sizeof(DevModel) + ((size_t)unom_floats * sizeof(float) + 15) / 16 * 16 + (size_t)spc * sizeof(WarpWS<NA>);
+}
+
+template <int NA, int MODE>
+int launch_rollout_t(const RolloutArgs& a, int spc, cudaStream_t s) {
+    const int unom = (MODE == 1 && a.stage_unom) ? a.H * Dims<NA>::NU : 0;
+    const size_t sm = rollout_smem<NA>(spc, unom);
+    static int max_set[17] = {0};
+    auto fn = rollout_kernel<NA, MODE>;
+    if (sm > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    (void)max_set;
+    const int grid = (a.n + spc - 1) / spc;
+    fn<<<grid, spc * 32, sm, s>>>(a);
+    return cuda_fail(cudaGetLastError());
+}
+
+}  // namespace
+
+namespace mppi {
+
+int launch_rollout(int na, int mode, const RolloutArgs& a, int spc, cudaStream_t s) {
+    if (a.n <= 0) return MPPI_OK;
+    if (na == 3) return mode ? launch_rollout_t<3, 1>(a, spc, s) : launch_rollout_t<3, 0>(a, spc, s);
+    if (na == 7) return mode ? launch_rollout_t<7, 1>(a, spc, s) : launch_rollout_t<7, 0>(a, spc, s);
+    return MPPI_ERR_UNSUPPORTED;
+}
+
+int launch_update(int nu, const UpdateArgs& a, int H, cudaStream_t s) {
+    if (nu == 6) update_kernel<6><<<H, 256, 0, s>>>(a);
+    else if (nu == 14) update_kernel<14><<<H, 256, 0, s>>>(a);
+    else return MPPI_ERR_UNSUPPORTED;
+    return cuda_fail(cudaGetLastError());
+}
+
+int launch_noise(int nu, const NoiseArgs& a, cudaStream_t s) {
+    const size_t n = (size_t)a.K * a.H * nu;
+    const int grid = (int)std::min<size_t>((n + 255) / 256, 4096);
+    if (nu == 6) noise_kernel<6><<<grid, 256, 0, s>>>(a);
+    else if (nu == 14) noise_kernel<14><<<grid, 256, 0, s>>>(a);
+    else return MPPI_ERR_UNSUPPORTED;
+    return cuda_fail(cudaGetLastError());
+}
+
+size_t rollout_smem_bytes(int na, int spc, int unom_floats) {
+    if (na == 3) return rollout_smem<3>(spc, unom_floats);
+    if (na == 7) return rollout_smem<7>(spc, unom_floats);
+    return 0;
+}
+
+// Parse the scene blob into the device representation.
+int parse_model_blob(const void* blob, size_t len, DevModel* out, HostModelInfo* info) {
+    if (!blob || len < 16) return MPPI_ERR_INVALID_ARG;
+    uint32_t h[4];
+    std::memcpy(h, blob, 16);
+    if (h[0] != 0x4950504Du || h[1] != 1u) return MPPI_ERR_INVALID_ARG;
+    const size_t n = h[2];
+    if (n < 23 || len < 16 + 8 * n) return MPPI_ERR_INVALID_ARG;
+    std::vector<double> v(n);
+    std::memcpy(v.data(), static_cast<const unsigned char*>(blob) + 16, 8 * n);
+    const int na = (int)v[0], nb = (int)v[1], maxc = (int)v[2];
+    if (na < 1 || na > MAXL || nb < 0 || nb > MAXB || maxc < 1 || maxc > MAXC) return MPPI_ERR_INVALID_ARG;
+    const int nq = 2 * na + 7, nv = 2 * na + 6;
+    if (n != 23 + 2 * (12 + 39 * (size_t)na) + 6 * (size_t)nb + (size_t)(nq + nv)) return MPPI_ERR_INVALID_ARG;
+    DevModel M;
+    std::memset(&M, 0, sizeof M);
+    M.na = na;
+    M.nb = nb;
+    M.maxc = maxc;
+    M.dt = (float)v[3];
+    M.sweeps = (int)v[4];
+    M.mu = (float)v[5];
+    M.imp = (float)v[6];
+    M.erp = (float)v[7];
+    for (int k = 0; k < 3; ++k) M.g[k] = (float)v[8 + k];
+    M.floor_z = (float)v[11];
+    M.rb = (float)v[12];
+    M.mb = (float)v[13];
+    M.Ib = (float)v[14];
+    for (int k = 0; k < 3; ++k) M.goal[k] = (float)v[15 + k];
+    M.w_goal = (float)v[18];
+    M.w_u = (float)v[19];
+    M.w_pen = (float)v[20];
+    M.w_obst = (float)v[21];
+    M.w_grasp = (float)v[22];
+    if (!(M.dt > 0) || M.sweeps < 0 || M.sweeps > 1000 || !(M.imp > 0 && M.imp <= 1) || !(M.mb > 0) || !(M.Ib > 0))
+        return MPPI_ERR_INVALID_ARG;
+    size_t o = 23;
+    for (int a = 0; a < 2; ++a) {
+        for (int k = 0; k < 9; ++k) M.baseR[a][k] = (float)v[o++];
+        for (int k = 0; k < 3; ++k) M.basep[a][k] = (float)v[o++];
+        for (int i = 0; i < na; ++i) {
+            DevLink& L = M.link[a][i];
+            for (int k = 0; k < 9; ++k) L.FR[k] = (float)v[o++];
+            for (int k = 0; k < 3; ++k) L.Fp[k] = (float)v[o++];
+            L.mass = (float)v[o++];
+            for (int k = 0; k < 3; ++k) L.com[k] = (float)v[o++];
+            double I[9];
+            for (int k = 0; k < 9; ++k) I[k] = v[o++];
+            L.I[0] = (float)I[0];
+            L.I[1] = (float)I[4];
+            L.I[2] = (float)I[8];
+            L.I[3] = (float)(0.5 * (I[1] + I[3]));
+            L.I[4] = (float)(0.5 * (I[2] + I[6]));
+            L.I[5] = (float)(0.5 * (I[5] + I[7]));
+            for (int k = 0; k < 3; ++k) L.s0[k] = (float)v[o++];
+            for (int k = 0; k < 3; ++k) L.s1[k] = (float)v[o++];
+            L.rcap = (float)v[o++];
+            const double damping = v[o++], kv = v[o++];
+            L.D = (float)(damping + kv);
+            L.gear = (float)v[o++];
+            L.tau_max = (float)v[o++];
+            L.u_lo = (float)v[o++];
+            L.u_hi = (float)v[o++];
+            L.gravcomp = (float)v[o++];
+            if (!(L.mass > 0)) return MPPI_ERR_INVALID_ARG;
+        }
+    }
+    for (int b = 0; b < nb; ++b)
+        for (int k = 0; k < 6; ++k) M.box[b][k] = (float)v[o++];
+    if (info) {
+        info->na = na;
+        info->nb = nb;
+        info->x0.assign(nq + nv, 0.0f);
+        for (int k = 0; k < nq + nv; ++k) info->x0[k] = (float)v[o + k];
+    }
+    *out = M;
+    return MPPI_OK;
+}
+
+}  // namespace mppi
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+struct mppi_model {
+    DevModel host;
+    DevModel* dev = nullptr;
+    HostModelInfo info;
+    int device = 0;
+};
+
+struct mppi_ctx {
+    const mppi_model* m = nullptr;
+    int K = 0, H = 0, spc = 4;
+    float lambda = 1.0f;
+    uint64_t seed = 0;
+    float* d_sigma = nullptr;
+    float* d_ulo = nullptr;
+    float* d_uhi = nullptr;
+    float* d_costs = nullptr;
+    float* d_best = nullptr;
+    int* d_err = nullptr;
+    unsigned long long* d_iter = nullptr;
+    unsigned int* d_done = nullptr;
+    // captured solve
+    cudaGraphExec_t gexec = nullptr;
+    cudaGraph_t graph = nullptr;
+    const float* g_state = nullptr;
+    float* g_u = nullptr;
+    float* g_best = nullptr;
+    int g_iters = 0;
+    cudaStream_t g_stream = nullptr;
+    // profiling
+    int prof_cap = 0, prof_n = 0;
+    std::vector<cudaEvent_t> prof_ev;  // 3 per recorded iteration
+    unsigned long long* d_stats = nullptr;
+};
+
+extern "C" {
+
+const char* mppi_strerror(int code) {
+    switch (code) {
+        case MPPI_OK: return "ok";
+        case MPPI_ERR_INVALID_ARG: return "invalid argument";
+        case MPPI_ERR_OOM: return "out of memory";
+        case MPPI_ERR_CUDA: return "CUDA error";
+        case MPPI_ERR_NONFINITE: return "non-finite costs or state";
+        case MPPI_ERR_TIMEOUT: return "bounded device wait timed out";
+        case MPPI_ERR_ADMISSION: return "request does not fit the admission budget";
+        case MPPI_ERR_CHOLESKY: return "mass matrix lost positive definiteness";
+        case MPPI_ERR_UNSUPPORTED: return "model outside the compiled variants";
+        default: return "unknown error";
+    }
+}
+
+int mppi_model_load(const void* blob, size_t len, mppi_model** out) {
+    if (!out) return MPPI_ERR_INVALID_ARG;
+    *out = nullptr;
+    mppi_model* m = new (std::nothrow) mppi_model();
+    if (!m) return MPPI_ERR_OOM;
+    int rc = parse_model_blob(blob, len, &m->host, &m->info);
+    if (rc != MPPI_OK) {
+        delete m;
+        return rc;
+    }
+    cudaGetDevice(&m->device);
+    cudaError_t e = cudaMalloc(&m->dev, sizeof(DevModel));
+    if (e == cudaSuccess) e = cudaMemcpy(m->dev, &m->host, sizeof(DevModel), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        if (m->dev) cudaFree(m->dev);
+        delete m;
+        return cuda_fail(e);
+    }
+    *out = m;
+    return MPPI_OK;
+}
+
+void mppi_model_free(mppi_model* m) {
+    if (!m) return;
+    if (m->dev) cudaFree(m->dev);
+    delete m;
+}
+
+int mppi_model_dims(const mppi_model* m, int* nq, int* nv, int* nu, int* n_boxes) {
+    if (!m) return MPPI_ERR_INVALID_ARG;
+    const int na = m->info.na;
+    if (nq) *nq = 2 * na + 7;
+    if (nv) *nv = 2 * na + 6;
+    if (nu) *nu = 2 * na;
+    if (n_boxes) *n_boxes = m->info.nb;
+    return MPPI_OK;
+}
+
+int mppi_model_home(const mppi_model* m, float* x0) {
+    if (!m || !x0) return MPPI_ERR_INVALID_ARG;
+    std::memcpy(x0, m->info.x0.data(), m->info.x0.size() * sizeof(float));
+    return MPPI_OK;
+}
+
+int mppi_destroy(mppi_ctx* c) {
+    if (!c) return MPPI_OK;
+    for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
+    cudaFree(c->d_stats);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    cudaFree(c->d_sigma);
+    cudaFree(c->d_ulo);
+    cudaFree(c->d_uhi);
+    cudaFree(c->d_costs);
+    cudaFree(c->d_best);
+    cudaFree(c->d_err);
+    cudaFree(c->d_iter);
+    cudaFree(c->d_done);
+    delete c;
+    return MPPI_OK;
+}
+
+int mppi_create(const mppi_model* m, int K, int H, float lambda, const float* sigma, uint64_t seed, mppi_ctx** out) {
+    if (!m || !out || !sigma || K < 1 || K > (1 << 20) || H < 1 || H > 1024 || !(lambda > 0.0f))
+        return MPPI_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (m->info.na != 3 && m->info.na != 7) return MPPI_ERR_UNSUPPORTED;
+    mppi_ctx* c = new (std::nothrow) mppi_ctx();
+    if (!c) return MPPI_ERR_OOM;
+    c->m = m;
+    c->K = K;
+    c->H = H;
+    c->lambda = lambda;
+    c->seed = seed;
+    const int nu = 2 * m->info.na;
+    std::vector<float> lo(nu), hi(nu);
+    for (int j = 0; j < nu; ++j) {
+        lo[j] = m->host.link[j / m->info.na][j % m->info.na].u_lo;
+        hi[j] = m->host.link[j / m->info.na][j % m->info.na].u_hi;
+    }
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_sigma, nu * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_ulo, nu * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_uhi, nu * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_costs, (size_t)K * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_best, 2 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_iter, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_done, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_sigma, sigma, nu * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_ulo, lo.data(), nu * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_uhi, hi.data(), nu * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->d_iter, 0, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(c->d_done, 0, sizeof(unsigned int));
+    if (e != cudaSuccess) {
+        mppi_destroy(c);
+        return cuda_fail(e);
+    }
+    *out = c;
+    return MPPI_OK;
+}
+
+int mppi_profile(mppi_ctx* c, int n) {
+    if (!c || n < 0 || n > (1 << 20)) return MPPI_ERR_INVALID_ARG;
+    for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
+    c->prof_ev.clear();
+    c->prof_cap = 0;
+    c->prof_n = 0;
+    if (n == 0) return MPPI_OK;
+    cudaError_t e = cudaSuccess;
+    if (!c->d_stats) e = cudaMalloc(&c->d_stats, 4 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(c->d_stats, 0, 4 * sizeof(unsigned long long));
+    if (e != cudaSuccess) return cuda_fail(e);
+    c->prof_ev.resize(3 * (size_t)n);
+    for (auto& ev : c->prof_ev) {
+        e = cudaEventCreate(&ev);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    c->prof_cap = n;
+    return MPPI_OK;
+}
+
+int mppi_profile_read(mppi_ctx* c, int* n, float* rollout_ms, float* update_ms, double* contacts_per_step,
+                      double* box_tests_per_step) {
+    if (!c) return MPPI_ERR_INVALID_ARG;
+    float tr = 0.0f, tu = 0.0f;
+    for (int i = 0; i < c->prof_n; ++i) {
+        cudaError_t e = cudaEventSynchronize(c->prof_ev[3 * i + 2]);
+        float a = 0.0f, b = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&a, c->prof_ev[3 * i], c->prof_ev[3 * i + 1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&b, c->prof_ev[3 * i + 1], c->prof_ev[3 * i + 2]);
+        if (e != cudaSuccess) return cuda_fail(e);
+        tr += a;
+        tu += b;
+    }
+    unsigned long long st[4] = {0, 0, 0, 0};
+    if (c->d_stats) {
+        cudaError_t e = cudaMemcpy(st, c->d_stats, sizeof st, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    if (n) *n = c->prof_n;
+    if (rollout_ms) *rollout_ms = tr;
+    if (update_ms) *update_ms = tu;
+    if (contacts_per_step) *contacts_per_step = st[0] ? (double)st[1] / (double)st[0] : 0.0;
+    if (box_tests_per_step) *box_tests_per_step = st[0] ? (double)st[2] / (double)st[0] : 0.0;
+    return MPPI_OK;
+}
+
+int mppi_set_launch(mppi_ctx* c, int spc) {
+    if (!c || spc < 0 || spc > 16) return MPPI_ERR_INVALID_ARG;
+    c->spc = spc == 0 ? 4 : spc;
+    return MPPI_OK;
+}
+
+static RolloutArgs philox_args(mppi_ctx* c, const float* state, const float* u_nom) {
+    RolloutArgs a{};
+    a.model = c->m->dev;
+    a.n = c->K;
+    a.H = c->H;
+    a.states = state;
+    a.state_stride = 0;
+    a.u_nom = u_nom;
+    a.sigma = c->d_sigma;
+    a.seed = c->seed;
+    a.iter_ptr = c->d_iter;
+    a.costs = c->d_costs;
+    a.err = c->d_err;
+    a.stage_unom = c->H * 2 * c->m->info.na <= 2048;
+    return a;
+}
+
+static UpdateArgs update_args(mppi_ctx* c, const float* costs, const float* u_nom, float* u_out, int advance,
+                              float* best) {
+    UpdateArgs u{};
+    u.K = c->K;
+    u.costs = costs;
+    u.u_nom = u_nom;
+    u.u_out = u_out;
+    u.sigma = c->d_sigma;
+    u.u_lo = c->d_ulo;
+    u.u_hi = c->d_uhi;
+    u.lambda = c->lambda;
+    u.seed = c->seed;
+    u.iter_ptr = c->d_iter;
+    u.err = c->d_err;
+    u.best = best;
+    u.advance = advance;
+    u.done = c->d_done;
+    return u;
+}
+
+static int enqueue_step(mppi_ctx* c, const float* state, const float* u_nom, float* u_out, float* best,
+                        cudaStream_t s, bool capturing = false) {
+    RolloutArgs a = philox_args(c, state, u_nom);
+    const bool prof = !capturing && c->prof_n < c->prof_cap;
+    cudaEvent_t* ev = prof ? &c->prof_ev[3 * c->prof_n] : nullptr;
+    if (prof) {
+        a.stats = c->d_stats;
+        cudaEventRecord(ev[0], s);
+    }
+    int rc = launch_rollout(c->m->info.na, 1, a, c->spc, s);
+    if (rc != MPPI_OK) return rc;
+    if (prof) cudaEventRecord(ev[1], s);
+    UpdateArgs u = update_args(c, c->d_costs, u_nom, u_out, 1, best);
+    rc = launch_update(2 * c->m->info.na, u, c->H, s);
+    if (prof) {
+        cudaEventRecord(ev[2], s);
+        c->prof_n++;
+    }
+    return rc;
+}
+
+int mppi_step(mppi_ctx* c, const float* state, const float* u_nom, float* u_nom_out, void* stream) {
+    if (!c || !state || !u_nom || !u_nom_out) return MPPI_ERR_INVALID_ARG;
+    return enqueue_step(c, state, u_nom, u_nom_out, c->d_best, (cudaStream_t)stream);
+}
+
+int mppi_solve(mppi_ctx* c, const float* state, float* u, int iters, float* best_out, void* stream) {
+    if (!c || !state || !u || iters < 1) return MPPI_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    float* best = best_out ? best_out : c->d_best;
+    if (s == nullptr) {  // the legacy stream cannot be captured: run eagerly
+        for (int it = 0; it < iters; ++it) {
+            int rc = enqueue_step(c, state, u, u, best, s);
+            if (rc != MPPI_OK) return rc;
+        }
+        return MPPI_OK;
+    }
+    const bool hit = c->gexec && c->g_state == state && c->g_u == u && c->g_iters == iters && c->g_stream == s &&
+                     c->g_best == best;
+    if (!hit) {
+        if (c->gexec) cudaGraphExecDestroy(c->gexec);
+        if (c->graph) cudaGraphDestroy(c->graph);
+        c->gexec = nullptr;
+        c->graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(e);
+        int rc = MPPI_OK;
+        for (int it = 0; it < iters && rc == MPPI_OK; ++it) rc = enqueue_step(c, state, u, u, best, s, true);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(s, &g);
+        if (rc != MPPI_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return cuda_fail(e);
+        e = cudaGraphInstantiate(&c->gexec, g, 0);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(g);
+            return cuda_fail(e);
+        }
+        c->graph = g;
+        c->g_state = state;
+        c->g_u = u;
+        c->g_iters = iters;
+        c->g_stream = s;
+        c->g_best = best;
+    }
+    return cuda_fail(cudaGraphLaunch(c->gexec, s));
+}
+
+int mppi_update(mppi_ctx* c, const float* costs, const float* u_nom, float* u_out, void* stream) {
+    if (!c || !costs || !u_nom || !u_out) return MPPI_ERR_INVALID_ARG;
+    UpdateArgs u = update_args(c, costs, u_nom, u_out, 0, c->d_best);
+    return launch_update(2 * c->m->info.na, u, c->H, (cudaStream_t)stream);
+}
+
+int rollout_batch(mppi_ctx* c, int n, const float* states, const float* U, float* costs, float* states_out,
+                  void* stream) {
+    if (!c || n < 0 || n > c->K || (n > 0 && (!states || !U || !costs))) return MPPI_ERR_INVALID_ARG;
+    RolloutArgs a{};
+    a.model = c->m->dev;
+    a.n = n;
+    a.H = c->H;
+    a.states = states;
+    a.state_stride = 4 * c->m->info.na + 13;
+    a.U = U;
+    a.costs = costs;
+    a.states_out = states_out;
+    a.err = c->d_err;
+    return launch_rollout(c->m->info.na, 0, a, c->spc, (cudaStream_t)stream);
+}
+
+int sim_step(mppi_ctx* c, int n, float* states, const float* U1, void* stream) {
+    if (!c || n < 0 || n > c->K || (n > 0 && (!states || !U1))) return MPPI_ERR_INVALID_ARG;
+    RolloutArgs a{};
+    a.model = c->m->dev;
+    a.n = n;
+    a.H = 1;
+    a.states = states;
+    a.state_stride = 4 * c->m->info.na + 13;
+    a.U = U1;
+    a.costs = c->d_costs;
+    a.states_out = states;  // each warp reads its state before writing it back
+    a.err = c->d_err;
+    return launch_rollout(c->m->info.na, 0, a, c->spc, (cudaStream_t)stream);
+}
+
+int mppi_debug_noise(mppi_ctx* c, uint64_t iteration, float* eps, void* stream) {
+    if (!c || !eps) return MPPI_ERR_INVALID_ARG;
+    NoiseArgs a{};
+    a.K = c->K;
+    a.H = c->H;
+    a.sigma = c->d_sigma;
+    a.seed = c->seed;
+    a.iter = iteration;
+    a.eps = eps;
+    return launch_noise(2 * c->m->info.na, a, (cudaStream_t)stream);
+}
+
+int mppi_debug_philox(int n, const uint32_t* ctr, uint64_t key, uint32_t* out, void* stream) {
+    if (n < 0 || (n > 0 && (!ctr || !out))) return MPPI_ERR_INVALID_ARG;
+    if (n == 0) return MPPI_OK;
+    philox_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(
+        n, reinterpret_cast<const uint4*>(ctr), make_uint2((uint32_t)key, (uint32_t)(key >> 32)),
+        reinterpret_cast<uint4*>(out));
+    return cuda_fail(cudaGetLastError());
+}
+
+int mppi_get_iteration(mppi_ctx* c, uint64_t* it, void* stream) {
+    if (!c || !it) return MPPI_ERR_INVALID_ARG;
+    unsigned long long v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, c->d_iter, sizeof v, cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    *it = v;
+    return MPPI_OK;
+}
+
+int mppi_set_iteration(mppi_ctx* c, uint64_t it, void* stream) {
+    if (!c) return MPPI_ERR_INVALID_ARG;
+    unsigned long long v = it;
+    cudaError_t e = cudaMemcpyAsync(c->d_iter, &v, sizeof v, cudaMemcpyHostToDevice, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    return cuda_fail(e);
+}
+
+int mppi_sync(mppi_ctx* c, void* stream) {
+    if (!c) return MPPI_ERR_INVALID_ARG;
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    int err = 0;
+    e = cudaMemcpy(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (err & ERRB_TIMEOUT) return MPPI_ERR_TIMEOUT;
+    if (err & ERRB_CHOLESKY) return MPPI_ERR_CHOLESKY;
+    if (err & ERRB_NONFINITE) return MPPI_ERR_NONFINITE;
+    return MPPI_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,71 @@
+// Internal (non-ABI) declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+namespace mppi {
+
+struct DevModel;
+
+struct HostModelInfo {
+    int na = 0, nb = 0;
+    std::vector<float> x0;
+};
+
+// Arguments of the rollout kernel (one warp per sample).
+struct RolloutArgs {
+    const DevModel* model;
+    int n;                       // samples
+    int H;                       // horizon
+    const float* states;         // n x nx (stride state_stride; 0 = one shared state)
+    int state_stride;
+    const float* U;              // explicit controls n x H x nu (MODE 0)
+    const float* u_nom;          // H x nu (MODE 1)
+    const float* sigma;          // nu (MODE 1)
+    uint64_t seed;               // Philox key (MODE 1)
+    const unsigned long long* iter_ptr;  // iteration counter on the device, or null
+    unsigned long long iter_val;         // iteration when iter_ptr is null
+    float* costs;                // n
+    float* states_out;           // optional n x nx
+    int* err;                    // error word
+    int stage_unom;              // stage u_nom in shared memory
+    unsigned long long* stats;   // optional: [sample-steps, contacts, exact box tests]
+};
+
+// Arguments of the weighted-mean update (one CTA per horizon step).
+struct UpdateArgs {
+    int K;
+    const float* costs;
+    const float* u_nom;
+    float* u_out;
+    const float* sigma;
+    const float* u_lo;
+    const float* u_hi;
+    float lambda;
+    uint64_t seed;
+    unsigned long long* iter_ptr;
+    unsigned long long iter_val;
+    int* err;
+    float* best;        // optional: min cost, argmin
+    int advance;        // last CTA increments *iter_ptr
+    unsigned int* done; // CTA completion counter (reset by the last CTA)
+};
+
+struct NoiseArgs {
+    int K, H;
+    const float* sigma;
+    uint64_t seed;
+    uint64_t iter;
+    float* eps;
+};
+
+int parse_model_blob(const void* blob, size_t len, DevModel* out, HostModelInfo* info);
+int launch_rollout(int na, int mode, const RolloutArgs& a, int spc, cudaStream_t s);
+int launch_update(int nu, const UpdateArgs& a, int H, cudaStream_t s);
+int launch_noise(int nu, const NoiseArgs& a, cudaStream_t s);
+size_t rollout_smem_bytes(int na, int spc, int unom_floats);
+
+}  // namespace mppi

@@ -1,0 +1,68 @@
+"""Algorithmic FP32 operation count of one simulated sample-step.
+
+Counts what the method must compute per sample and per time step in this
+formulation (add, sub, mul = 1 FLOP, fused multiply-add = 2), with the
+recursive algorithms' O(n) prefix/suffix sums, the Cholesky factor of each
+arm's (M + dt D) block, and contact rows restricted to the degrees of
+freedom they touch.  Work the kernels do redundantly (several lanes drawing
+the same Philox block, zero blocks of contact rows, per-lane suffix sums)
+is not counted, so the figure cannot be inflated by waste.  Square roots,
+divisions, trigonometric, exponential and logarithmic functions run on the
+special-function units and are not FP32 FLOPs; Philox is integer work.
+
+The data-dependent terms (active contacts per step, capsule-box pairs that
+pass the bounding-sphere cull) are measured on the device during the timed
+run (mppi_profile_read).
+"""
+from __future__ import annotations
+
+
+def per_sample_step(scene, contacts: float, box_tests: float, breakdown: bool = False):
+    na = scene.n_a
+    nl, nv, nu, nb = 2 * na, 2 * na + 6, 2 * na, scene.n_boxes
+    sweeps = scene.sweeps
+    parts = {}
+    # a1 sampling: uniform mapping (2 x 2), -2 log(u), r * trig, sigma z + u
+    parts["sample"] = 8 * nu
+    # a2 kinematics per link: R Rz (6 x 3), p += Rj Fp (18), R Fp (9 x 5),
+    #    three points (COM, capsule ends) 3 x 18
+    parts["fk"] = nl * (18 + 18 + 45 + 54)
+    # a3 broad + narrow phase
+    sphere_capsule = 53
+    sphere_box = 25
+    cull = 28
+    golden = 37 * 20 + 34 * 3 + 40 + 25 + 12   # SDF evaluations, bookkeeping, refinement, witness
+    parts["collide"] = 4 + sphere_capsule * nl + sphere_box * nb + cull * nl * nb + golden * box_tests
+    # a4/a5 per link: world inertia (R I R^T 75, params 26), axis 6, composite 10,
+    #    F = I^c S 42, velocity 12, velocity-product acceleration 42, gravity 6,
+    #    I a and I v 84, force cross product 36, subtree force 6, S.F 11, drive 7
+    per_link = 75 + 26 + 6 + 10 + 42 + 12 + 42 + 6 + 84 + 36 + 6 + 11 + 7
+    mass_cols = 11 * na * (na + 1) // 2          # S_r . F_i for r <= i, per arm
+    parts["crba_rnea"] = nl * per_link + 2 * mass_cols + 12
+    # a6 Cholesky of each arm block, two triangular solves, free velocity
+    chol = sum(2 * j + (na - 1 - j) * (2 * j + 1) for j in range(na))
+    solve = 2 * na * (na - 1) + 2 * na
+    parts["cholesky"] = 2 * (chol + solve) + 6
+    # a7 contact rows: frame, Jacobian of the touched bodies (ball + one
+    #    link chain), half-solve with one arm factor, diagonal, reference
+    touched = na + 6
+    row = 12 + 18 + 19 * (na + 1) // 2 + na * (na - 1) + 2 * touched + 4
+    zf = 2 * na * (na + 1) + 6 if contacts > 0 else 0
+    back = 2 * na * (na - 1) if contacts > 0 else 0
+    parts["contact_rows"] = zf + 3 * row * contacts + back
+    # a8 PGS: per contact and sweep, normal (dot, update) and tangent pair
+    parts["pgs"] = sweeps * contacts * (12 * touched + 16)
+    # a9 integration (coordinates, quaternion)
+    parts["integrate"] = 2 * (2 * na + 3) + 50
+    # a10 stage cost
+    parts["cost"] = 8 + 2 * nu + 8 + (12 if scene.w_grasp else 0)
+    total = float(sum(parts.values()))
+    if breakdown:
+        return total, parts
+    return total
+
+
+def update_flops(K: int, H: int, nu: int) -> float:
+    """a11/a12 per iteration: weights (sub, mul) and the weighted sums, with
+    the samples regenerated (sampling counted as in per_sample_step)."""
+    return K * (2 + 1) * H + K * H * nu * (8 + 2)

@@ -1,0 +1,272 @@
+"""ctypes binding of libmppi (include/mppi.h).
+
+Argument marshalling only: every step of the optimiser and the simulator runs
+in the library's CUDA kernels.  PyTorch supplies device memory and streams;
+tensors are passed as raw device pointers.  There is no CPU fallback: if the
+library is missing or cannot load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import glob
+import os
+import subprocess
+from typing import Optional
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(_HERE, "csrc")
+BUILD = os.path.join(_HERE, "_build")
+LIB_PATH = os.path.join(BUILD, "libmppi.so")
+INCLUDE = os.path.join(os.path.dirname(_HERE), "include")
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+ERRORS = {0: "MPPI_OK", 1: "MPPI_ERR_INVALID_ARG", 2: "MPPI_ERR_OOM", 3: "MPPI_ERR_CUDA",
+          4: "MPPI_ERR_NONFINITE", 5: "MPPI_ERR_TIMEOUT", 6: "MPPI_ERR_ADMISSION",
+          7: "MPPI_ERR_CHOLESKY", 8: "MPPI_ERR_UNSUPPORTED"}
+
+
+class MPPIError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__(f"{what}: {ERRORS.get(code, code)}")
+
+
+def _sources():
+    return sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
+
+
+def _stale() -> bool:
+    if not os.path.exists(LIB_PATH):
+        return True
+    t = os.path.getmtime(LIB_PATH)
+    deps = _sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) \
+        + glob.glob(os.path.join(INCLUDE, "*.h"))
+    return any(os.path.getmtime(p) > t for p in deps)
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile every translation unit under csrc/ for sm_103a (in parallel)
+    and link libmppi.so in-tree."""
+    if not force and not _stale():
+        return LIB_PATH
+    os.makedirs(BUILD, exist_ok=True)
+    objs, procs = [], []
+    for src in _sources():
+        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+        cmd = ["nvcc", "-O3", "-std=c++17", "-Xcompiler", "-fPIC", *ARCH, "-lineinfo",
+               "-I", INCLUDE, "-c", src, "-o", obj]
+        if verbose:
+            cmd.insert(1, "-Xptxas=-v")
+        procs.append((subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT), src))
+        objs.append(obj)
+    failed = []
+    for p, src in procs:
+        out, _ = p.communicate()
+        if p.returncode != 0 or verbose:
+            print(out.decode(errors="replace"))
+        if p.returncode != 0:
+            failed.append(src)
+    if failed:
+        raise RuntimeError(f"nvcc failed for {failed}")
+    tmp = LIB_PATH + f".tmp{os.getpid()}"
+    subprocess.run(["nvcc", "-shared", *ARCH, "-o", tmp, *objs, "-lcudart", "-lpthread"], check=True)
+    os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+_lib = None
+EXPORTS = []
+
+
+def _decl(L, name, restype, argtypes):
+    f = getattr(L, name)
+    f.restype = restype
+    f.argtypes = argtypes
+    EXPORTS.append(name)
+    return f
+
+
+def lib():
+    """Load libmppi.so (built in-tree).  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libmppi.so not built ({LIB_PATH}); run __graft_entry__.build()")
+    L = C.CDLL(LIB_PATH)
+    i, vp, fp, sz = C.c_int, C.c_void_p, C.c_void_p, C.c_size_t
+    u64 = C.c_uint64
+    _decl(L, "mppi_strerror", C.c_char_p, [i])
+    _decl(L, "mppi_model_load", i, [vp, sz, C.POINTER(vp)])
+    _decl(L, "mppi_model_free", None, [vp])
+    _decl(L, "mppi_model_dims", i, [vp, C.POINTER(i), C.POINTER(i), C.POINTER(i), C.POINTER(i)])
+    _decl(L, "mppi_model_home", i, [vp, fp])
+    _decl(L, "mppi_create", i, [vp, i, i, C.c_float, fp, u64, C.POINTER(vp)])
+    _decl(L, "mppi_destroy", i, [vp])
+    _decl(L, "mppi_step", i, [vp, fp, fp, fp, vp])
+    _decl(L, "mppi_solve", i, [vp, fp, fp, i, fp, vp])
+    _decl(L, "mppi_update", i, [vp, fp, fp, fp, vp])
+    _decl(L, "rollout_batch", i, [vp, i, fp, fp, fp, fp, vp])
+    _decl(L, "sim_step", i, [vp, i, fp, fp, vp])
+    _decl(L, "mppi_debug_noise", i, [vp, u64, fp, vp])
+    _decl(L, "mppi_debug_philox", i, [i, fp, u64, fp, vp])
+    _decl(L, "mppi_get_iteration", i, [vp, C.POINTER(u64), vp])
+    _decl(L, "mppi_set_iteration", i, [vp, u64, vp])
+    _decl(L, "mppi_sync", i, [vp, vp])
+    _decl(L, "mppi_set_launch", i, [vp, i])
+    _decl(L, "mppi_profile", i, [vp, i])
+    _decl(L, "mppi_profile_read", i, [vp, C.POINTER(i), C.POINTER(C.c_float), C.POINTER(C.c_float),
+                                       C.POINTER(C.c_double), C.POINTER(C.c_double)])
+    _lib = L
+    return L
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise MPPIError(rc, what)
+
+
+def _ptr(t) -> Optional[int]:
+    """Device pointer of a CUDA float32 contiguous tensor (None -> NULL)."""
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch.Tensor")
+    if not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise ValueError("expected a contiguous float32 CUDA tensor")
+    return t.data_ptr()
+
+
+def _stream(stream) -> Optional[int]:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    if isinstance(stream, int):
+        return stream or None
+    return stream.cuda_stream or None
+
+
+def debug_philox(ctr, key: int, out, stream=None):
+    """Raw Philox words for the counters in ctr (CUDA int32/uint32 n x 4)."""
+    import torch
+    for t in (ctr, out):
+        if not t.is_cuda or t.dtype not in (torch.int32, torch.uint32) or not t.is_contiguous():
+            raise ValueError("expected contiguous 32-bit integer CUDA tensors")
+    _check(lib().mppi_debug_philox(ctr.shape[0], ctr.data_ptr(), C.c_uint64(key), out.data_ptr(),
+                                   _stream(stream)), "mppi_debug_philox")
+    return out
+
+
+class Model:
+    """A scene uploaded to the device (mppi_model_load)."""
+
+    def __init__(self, blob: bytes):
+        L = lib()
+        h = C.c_void_p()
+        buf = C.create_string_buffer(blob, len(blob))
+        _check(L.mppi_model_load(buf, len(blob), C.byref(h)), "mppi_model_load")
+        self._h = h
+        nq, nv, nu, nb = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        _check(L.mppi_model_dims(h, C.byref(nq), C.byref(nv), C.byref(nu), C.byref(nb)), "mppi_model_dims")
+        self.nq, self.nv, self.nu, self.n_boxes = nq.value, nv.value, nu.value, nb.value
+        self.nx = self.nq + self.nv
+
+    def home(self):
+        import numpy as np
+        x = np.zeros(self.nx, dtype=np.float32)
+        _check(lib().mppi_model_home(self._h, x.ctypes.data), "mppi_model_home")
+        return x
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mppi_model_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Controller:
+    """One MPPI controller (mppi_create).  All tensor arguments are CUDA
+    float32 tensors; `stream` defaults to torch's current stream."""
+
+    def __init__(self, model: Model, K: int, H: int, lam: float, sigma, seed: int):
+        import numpy as np
+        self.model = model
+        self.K, self.H = int(K), int(H)
+        sig = np.ascontiguousarray(np.asarray(sigma, dtype=np.float32).reshape(model.nu))
+        h = C.c_void_p()
+        _check(lib().mppi_create(model._h, self.K, self.H, float(lam), sig.ctypes.data, C.c_uint64(seed),
+                                 C.byref(h)), "mppi_create")
+        self._h = h
+
+    def step(self, state, u_nom, u_out=None, stream=None):
+        u_out = u_nom if u_out is None else u_out
+        _check(lib().mppi_step(self._h, _ptr(state), _ptr(u_nom), _ptr(u_out), _stream(stream)), "mppi_step")
+        return u_out
+
+    def solve(self, state, u_nom_inout, iters: int, best=None, stream=None):
+        _check(lib().mppi_solve(self._h, _ptr(state), _ptr(u_nom_inout), int(iters), _ptr(best), _stream(stream)),
+               "mppi_solve")
+        return u_nom_inout
+
+    def update(self, costs, u_nom, u_out, stream=None):
+        _check(lib().mppi_update(self._h, _ptr(costs), _ptr(u_nom), _ptr(u_out), _stream(stream)), "mppi_update")
+        return u_out
+
+    def rollout_batch(self, states, U, costs, states_out=None, stream=None):
+        n = states.shape[0]
+        _check(lib().rollout_batch(self._h, n, _ptr(states), _ptr(U), _ptr(costs), _ptr(states_out),
+                                   _stream(stream)), "rollout_batch")
+        return costs
+
+    def sim_step(self, states, U1, stream=None):
+        _check(lib().sim_step(self._h, states.shape[0], _ptr(states), _ptr(U1), _stream(stream)), "sim_step")
+        return states
+
+    def debug_noise(self, iteration: int, eps, stream=None):
+        _check(lib().mppi_debug_noise(self._h, C.c_uint64(iteration), _ptr(eps), _stream(stream)),
+               "mppi_debug_noise")
+        return eps
+
+    def iteration(self, stream=None) -> int:
+        v = C.c_uint64()
+        _check(lib().mppi_get_iteration(self._h, C.byref(v), _stream(stream)), "mppi_get_iteration")
+        return v.value
+
+    def set_iteration(self, it: int, stream=None):
+        _check(lib().mppi_set_iteration(self._h, C.c_uint64(it), _stream(stream)), "mppi_set_iteration")
+
+    def sync(self, stream=None) -> int:
+        """Synchronise and return the device error code (0 = ok)."""
+        return lib().mppi_sync(self._h, _stream(stream))
+
+    def profile(self, n: int):
+        """Record kernel times and contact counts for the next n iterations."""
+        _check(lib().mppi_profile(self._h, int(n)), "mppi_profile")
+
+    def profile_read(self):
+        n, tr, tu = C.c_int(), C.c_float(), C.c_float()
+        cps, bps = C.c_double(), C.c_double()
+        _check(lib().mppi_profile_read(self._h, C.byref(n), C.byref(tr), C.byref(tu), C.byref(cps),
+                                       C.byref(bps)), "mppi_profile_read")
+        return {"iterations": n.value, "rollout_ms": tr.value, "update_ms": tu.value,
+                "contacts_per_step": cps.value, "box_tests_per_step": bps.value}
+
+    def set_launch(self, samples_per_cta: int):
+        _check(lib().mppi_set_launch(self._h, int(samples_per_cta)), "mppi_set_launch")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mppi_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
