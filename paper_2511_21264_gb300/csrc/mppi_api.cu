@@ -111,7 +111,6 @@ __global__ void __launch_bounds__(512) rollout_kernel(RolloutArgs args) {
         if (!isfinite(cost)) atomicOr(args.err, ERRB_NONFINITE);
     }
     if (args.stats) {
-        n_exact = __reduce_add_sync(FULL, n_exact);
         if (lane == 0) {
             atomicAdd(&args.stats[0], (unsigned long long)args.H);
             atomicAdd(&args.stats[1], (unsigned long long)n_con);

@@ -6,14 +6,16 @@
 // step:
 //   - controls: lane j < nu draws its Gaussian from Philox4x32-10 (or reads
 //     the explicit control);
-//   - kinematics: lane 16a walks arm a's chain;
-//   - collision: all 32 lanes over the candidate pairs, compacted with a
-//     ballot in canonical pair order;
+//   - kinematics: one lane per link, prefix product of the link transforms;
+//   - collision: one lane per ball pair and per capsule-box cull, each
+//     surviving capsule-box pair minimised by the whole warp over a closed
+//     candidate set, contacts compacted with ballots in canonical order;
 //   - dynamics: lane 16a + i owns link i of arm a (spatial inertia, composite
 //     inertia, mass-matrix column, Newton-Euler bias force), lane 16a factors
 //     the arm's (M + dt D) block, lane 15 handles the ball;
 //   - contact rows: one lane per Jacobian row (half-solved by the Cholesky
-//     factor), projected Gauss-Seidel by lane 0 in the factor's coordinates;
+//     factor), the Delassus block across lanes, projected Gauss-Seidel by
+//     lane 0 in contact space;
 //   - integration: one lane per coordinate.
 // The formulation (world-frame spatial algebra, composite-rigid-body mass
 // matrix, recursive bias, half-solved contact rows) is independent of the
@@ -92,6 +94,7 @@ struct __align__(16) WarpWS {
     float f[d::NL][6];
     float Isp[d::NL][10];
     float L[2][NA][NA];
+    float Ldi[2][NA];  // reciprocal diagonal of the factors
     // contacts
     float cp[MAXC][3];
     float cn[MAXC][3];
@@ -99,10 +102,14 @@ struct __align__(16) WarpWS {
     int cA[MAXC];
     int cB[MAXC];
     float Y[MAXR][d::NV];
+    float G[MAXR * (MAXR + 1) / 2];  // Delassus block Y Y^T, packed upper triangle
+    float b[MAXR];                   // J v_f (unconstrained row velocities)
     float lam[MAXR];
     float Rr[MAXR];
-    float Ad[MAXR];
+    float iAd[MAXR];                 // 1 / (A_rr + R_rr)
     float vs[MAXR];
+    int tmask[MAXR];                 // blocks a row touches: 1 left arm, 2 right arm, 4 ball
+    short surv[2 * MAXL * MAXB];     // capsule-box pairs that pass the cull, in pair order
     int ncon;
     int nact;
     float pen_all;
@@ -188,46 +195,88 @@ __device__ __forceinline__ void spatial_inertia_apply(const float* I, const floa
 // ---------------------------------------------------------------------------
 template <int NA>
 __device__ __forceinline__ void forward_kinematics(const DevModel& M, WarpWS<NA>& w, int lane) {
-    if ((lane & 15) != 0) return;
-    const int a = lane >> 4;
+    // Lane 16a + i owns link i of arm a.  Each lane forms its local transform
+    // Rz(q_i) F_i; an inclusive prefix product over the 16-lane segment
+    // (Hillis-Steele, log2(n_a) shuffle rounds) gives the chain to link i;
+    // the base transform is applied last.  The joint axis and origin of link
+    // i are the previous link's frame (the base for i = 0).
+    const int a = lane >> 4, i = lane & 15;
+    const bool act = i < NA;
     float R[9], p[3];
+    if (act) {
+        const DevLink& L = M.link[a][i];
+        float sn, cs;
+        sincosf(w.q[a * NA + i], &sn, &cs);
 #pragma unroll
-    for (int k = 0; k < 9; ++k) R[k] = M.baseR[a][k];
+        for (int cc = 0; cc < 3; ++cc) {
+            R[cc] = cs * L.FR[cc] - sn * L.FR[3 + cc];
+            R[3 + cc] = sn * L.FR[cc] + cs * L.FR[3 + cc];
+            R[6 + cc] = L.FR[6 + cc];
+        }
+        p[0] = cs * L.Fp[0] - sn * L.Fp[1];
+        p[1] = sn * L.Fp[0] + cs * L.Fp[1];
+        p[2] = L.Fp[2];
+    } else {
 #pragma unroll
-    for (int k = 0; k < 3; ++k) p[k] = M.basep[a][k];
+        for (int k = 0; k < 9; ++k) R[k] = (k % 4 == 0) ? 1.0f : 0.0f;
+        p[0] = p[1] = p[2] = 0.0f;
+    }
 #pragma unroll
-    for (int i = 0; i < NA; ++i) {
+    for (int off = 1; off < NA; off <<= 1) {
+        float Rp[9], pp[3];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Rp[k] = __shfl_up_sync(FULL, R[k], off, 16);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) pp[k] = __shfl_up_sync(FULL, p[k], off, 16);
+        if (i >= off) {
+            float Rn[9], pn[3];
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+#pragma unroll
+                for (int cc = 0; cc < 3; ++cc)
+                    Rn[3 * r + cc] = Rp[3 * r] * R[cc] + Rp[3 * r + 1] * R[3 + cc] + Rp[3 * r + 2] * R[6 + cc];
+                pn[r] = Rp[3 * r] * p[0] + Rp[3 * r + 1] * p[1] + Rp[3 * r + 2] * p[2] + pp[r];
+            }
+#pragma unroll
+            for (int k = 0; k < 9; ++k) R[k] = Rn[k];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) p[k] = pn[k];
+        }
+    }
+    // world frame: base * chain
+    const float* B = M.baseR[a];
+    float Rw[9], pw[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) Rw[3 * r + cc] = B[3 * r] * R[cc] + B[3 * r + 1] * R[3 + cc] + B[3 * r + 2] * R[6 + cc];
+        pw[r] = B[3 * r] * p[0] + B[3 * r + 1] * p[1] + B[3 * r + 2] * p[2] + M.basep[a][r];
+    }
+    float zp[3], op[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        zp[r] = __shfl_up_sync(FULL, Rw[3 * r + 2], 1, 16);
+        op[r] = __shfl_up_sync(FULL, pw[r], 1, 16);
+    }
+    if (i == 0) {
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            zp[r] = B[3 * r + 2];
+            op[r] = M.basep[a][r];
+        }
+    }
+    if (act) {
         const DevLink& L = M.link[a][i];
         const int l = a * NA + i;
-        w.z[l][0] = R[2];
-        w.z[l][1] = R[5];
-        w.z[l][2] = R[8];
-        w.o[l][0] = p[0];
-        w.o[l][1] = p[1];
-        w.o[l][2] = p[2];
-        float s, c;
-        sincosf(w.q[a * NA + i], &s, &c);
-        float Rj[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) w.R[l][k] = Rw[k];
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
-            Rj[3 * r + 0] = c * R[3 * r + 0] + s * R[3 * r + 1];
-            Rj[3 * r + 1] = c * R[3 * r + 1] - s * R[3 * r + 0];
-            Rj[3 * r + 2] = R[3 * r + 2];
-        }
-#pragma unroll
-        for (int r = 0; r < 3; ++r) p[r] += Rj[3 * r] * L.Fp[0] + Rj[3 * r + 1] * L.Fp[1] + Rj[3 * r + 2] * L.Fp[2];
-#pragma unroll
-        for (int r = 0; r < 3; ++r)
-#pragma unroll
-            for (int cc = 0; cc < 3; ++cc)
-                R[3 * r + cc] = Rj[3 * r] * L.FR[cc] + Rj[3 * r + 1] * L.FR[3 + cc] + Rj[3 * r + 2] * L.FR[6 + cc];
-#pragma unroll
-        for (int k = 0; k < 9; ++k) w.R[l][k] = R[k];
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-            w.c[l][r] = R[3 * r] * L.com[0] + R[3 * r + 1] * L.com[1] + R[3 * r + 2] * L.com[2] + p[r];
-            w.a0[l][r] = R[3 * r] * L.s0[0] + R[3 * r + 1] * L.s0[1] + R[3 * r + 2] * L.s0[2] + p[r];
-            w.a1[l][r] = R[3 * r] * L.s1[0] + R[3 * r + 1] * L.s1[1] + R[3 * r + 2] * L.s1[2] + p[r];
+            w.z[l][r] = zp[r];
+            w.o[l][r] = op[r];
+            w.c[l][r] = Rw[3 * r] * L.com[0] + Rw[3 * r + 1] * L.com[1] + Rw[3 * r + 2] * L.com[2] + pw[r];
+            w.a0[l][r] = Rw[3 * r] * L.s0[0] + Rw[3 * r + 1] * L.s0[1] + Rw[3 * r + 2] * L.s0[2] + pw[r];
+            w.a1[l][r] = Rw[3 * r] * L.s1[0] + Rw[3 * r + 1] * L.s1[1] + Rw[3 * r + 2] * L.s1[2] + pw[r];
         }
     }
 }
@@ -295,102 +344,110 @@ __device__ __forceinline__ float box_sdf_only(const float* a, const float* d, fl
     return sqrtf(q2) + fminf(mx, 0.0f);
 }
 
-// Minimum of the box SDF along a capsule axis (convex in t): golden-section
-// search over [0,1] with the end points as candidates.
-__device__ __forceinline__ float capsule_box_t(const float* a, const float* d, const float* box) {
-    const float gr = 0.6180339887498949f;
-    float lo = 0.0f, hi = 1.0f;
-    float x1 = hi - gr * (hi - lo), x2 = lo + gr * (hi - lo);
-    float f1 = box_sdf_only(a, d, x1, box), f2 = box_sdf_only(a, d, x2, box);
-#pragma unroll 1
-    for (int it = 0; it < 34; ++it) {
-        if (f1 <= f2) {
-            hi = x2;
-            x2 = x1;
-            f2 = f1;
-            x1 = hi - gr * (hi - lo);
-            f1 = box_sdf_only(a, d, x1, box);
-        } else {
-            lo = x1;
-            x1 = x2;
-            f1 = f2;
-            x2 = lo + gr * (hi - lo);
-            f2 = box_sdf_only(a, d, x2, box);
-        }
-    }
-    float t = 0.5f * (lo + hi);
-    float ft = box_sdf_only(a, d, t, box);
-    const float f0 = box_sdf_only(a, d, 0.0f, box), fe = box_sdf_only(a, d, 1.0f, box);
-    if (f0 < ft) {
-        t = 0.0f;
-        ft = f0;
-    }
-    if (fe < ft) t = 1.0f;
-    // Near an edge or vertex minimum the function is flat to second order,
-    // so the search pins t only to ~sqrt(FP32 eps).  In such a region (two
-    // or three slabs exceeded, fixed signs) the squared distance is the
-    // quadratic sum_k (alpha_k + beta_k t)^2: take its exact minimiser if it
-    // stays in the same region.
-    {
+// Candidate minimisers of the box SDF along the segment a + t d, t in [0,1].
+// The SDF is convex along the segment and piecewise smooth; its minimum lies
+// at an end point, at a slab-plane or axis-centre crossing (kinks), at the
+// stationary point of the squared distance to an edge or vertex region (for
+// every set of >= 2 exceeded slabs and sign pattern), or inside the box where
+// two face distances cross.  43 candidates in all; each is clamped to [0,1].
+constexpr int CB_CANDIDATES = 43;
+__device__ __forceinline__ float capsule_box_candidate(int id, const float* a, const float* d, const float* box) {
+    float t = 0.0f;
+    if (id == 1) {
+        t = 1.0f;
+    } else if (id >= 2 && id < 8) {  // slab planes x_k = c_k +- h_k
+        const int k = (id - 2) >> 1;
+        const float sg = (id & 1) ? -1.0f : 1.0f;
+        t = (box[k] + sg * box[3 + k] - a[k]) / d[k];
+    } else if (id >= 8 && id < 11) {  // axis centres x_k = c_k
+        const int k = id - 8;
+        t = (box[k] - a[k]) / d[k];
+    } else if (id >= 11) {
         float al[3], be[3];
-        int nact = 0;
-        unsigned sig = 0;
+        int use = 7;
+        bool cross = false;
+        int q;
+        float sgn[3] = {1.0f, 1.0f, 1.0f};
+        if (id < 23) {  // two exceeded slabs (edge regions)
+            q = id - 11;
+            const int pair = q >> 2;
+            use = pair == 0 ? 3 : (pair == 1 ? 5 : 6);
+            int first = pair == 2 ? 1 : 0;
+            int second = pair == 0 ? 1 : 2;
+            sgn[first] = (q & 1) ? -1.0f : 1.0f;
+            sgn[second] = (q & 2) ? -1.0f : 1.0f;
+        } else if (id < 31) {  // three exceeded slabs (vertex regions)
+            q = id - 23;
+            sgn[0] = (q & 1) ? -1.0f : 1.0f;
+            sgn[1] = (q & 2) ? -1.0f : 1.0f;
+            sgn[2] = (q & 4) ? -1.0f : 1.0f;
+        } else {  // two face distances equal inside the box
+            q = id - 31;
+            const int pair = q >> 2;
+            use = pair == 0 ? 3 : (pair == 1 ? 5 : 6);
+            int first = pair == 2 ? 1 : 0;
+            int second = pair == 0 ? 1 : 2;
+            sgn[first] = (q & 1) ? -1.0f : 1.0f;
+            sgn[second] = (q & 2) ? -1.0f : 1.0f;
+            cross = true;
+        }
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const float xk = a[k] + t * d[k] - box[k];
-            const float s = xk >= 0.0f ? 1.0f : -1.0f;
-            const bool on = fabsf(xk) - box[3 + k] > 0.0f;
-            nact += on;
-            sig |= (on ? 1u : 0u) << (2 * k);
-            sig |= (s > 0.0f ? 1u : 0u) << (2 * k + 1);
-            al[k] = on ? s * (a[k] - box[k]) - box[3 + k] : 0.0f;
-            be[k] = on ? s * d[k] : 0.0f;
+            al[k] = sgn[k] * (a[k] - box[k]) - box[3 + k];
+            be[k] = sgn[k] * d[k];
         }
-        if (nact >= 2) {
-            const float den = be[0] * be[0] + be[1] * be[1] + be[2] * be[2];
-            const float num = al[0] * be[0] + al[1] * be[1] + al[2] * be[2];
-            if (den > 0.0f) {
-                const float tq = fminf(fmaxf(-num / den, 0.0f), 1.0f);
-                unsigned sq = 0;
+        if (!cross) {
+            float num = 0.0f, den = 0.0f;
 #pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    const float xk = a[k] + tq * d[k] - box[k];
-                    const bool on = fabsf(xk) - box[3 + k] > 0.0f;
-                    sq |= (on ? 1u : 0u) << (2 * k);
-                    sq |= (xk >= 0.0f ? 1u : 0u) << (2 * k + 1);
+            for (int k = 0; k < 3; ++k)
+                if (use & (1 << k)) {
+                    num += al[k] * be[k];
+                    den += be[k] * be[k];
                 }
-                // compare only the exceeded slabs and their sides
-                const unsigned m = ((sig & 0x15u) | ((sig & 0x15u) << 1));
-                if ((sq & m) == (sig & m) && (sq & 0x15u) == (sig & 0x15u)) t = tq;
-            }
+            t = -num / den;
+        } else {
+            int j = -1, k2 = -1;
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                if (use & (1 << k)) {
+                    if (j < 0) j = k;
+                    else k2 = k;
+                }
+            t = (al[k2] - al[j]) / (be[j] - be[k2]);
         }
     }
+    if (!(t >= 0.0f)) t = 0.0f;  // also maps NaN from degenerate directions
+    if (t > 1.0f) t = 1.0f;
     return t;
 }
 
-// All candidate pairs, 32 at a time across the warp, compacted in canonical
-// order (ball-floor, ball-links, ball-boxes, links x boxes).
+// Narrow phase in canonical pair order (ball-floor, ball-links, ball-boxes,
+// links x boxes).  Ball pairs: one lane per pair, exact, compacted with a
+// ballot.  Capsule-box pairs: a conservative bounding-sphere cull per lane,
+// then each surviving pair (in pair order) is minimised by the whole warp
+// over the candidate set above.  Returns the number of exact capsule-box
+// tests on lane 0 (0 on the other lanes).
 template <int NA>
 __device__ __forceinline__ int collide(const DevModel& M, WarpWS<NA>& w, int lane) {
     using d = Dims<NA>;
     const int nb = M.nb;
-    const int npairs = 1 + d::NL + nb + d::NL * nb;
+    const int nball = 1 + d::NL + nb;
+    const int nlb = d::NL * nb;
     const float* pb = &w.q[d::B];
     const float rb = M.rb;
-    int base = 0, exact = 0;
+    int base = 0, nsurv = 0;
     float pa = 0.0f, pbox = 0.0f;
-    for (int p0 = 0; p0 < npairs; p0 += 32) {
+    for (int p0 = 0; p0 < nball; p0 += 32) {
         const int p = p0 + lane;
         bool active = false, isbox = false;
         float dist = 1.0f, cp[3] = {0, 0, 0}, nn[3] = {0, 0, 1};
-        int A = -1, Bb = -1;
-        if (p < npairs) {
+        int Bb = -1;
+        if (p < nball) {
             if (p == 0) {  // ball - floor
                 dist = (pb[2] - M.floor_z) - rb;
                 cp[0] = pb[0];
                 cp[1] = pb[1];
                 cp[2] = 0.5f * ((pb[2] - rb) + M.floor_z);
-                A = d::B;
             } else if (p < 1 + d::NL) {  // ball - link capsule
                 const int l = p - 1;
                 const float* a0 = w.a0[l];
@@ -400,8 +457,8 @@ __device__ __forceinline__ int collide(const DevModel& M, WarpWS<NA>& w, int lan
                 const float den = dot3(dd, dd);
                 float t = den > 0.0f ? dot3(ac, dd) / den : 0.0f;
                 t = fminf(fmaxf(t, 0.0f), 1.0f);
-                float s[3] = {a0[0] + t * dd[0], a0[1] + t * dd[1], a0[2] + t * dd[2]};
-                float df[3] = {pb[0] - s[0], pb[1] - s[1], pb[2] - s[2]};
+                float sp[3] = {a0[0] + t * dd[0], a0[1] + t * dd[1], a0[2] + t * dd[2]};
+                float df[3] = {pb[0] - sp[0], pb[1] - sp[1], pb[2] - sp[2]};
                 const float len = sqrtf(dot3(df, df));
                 if (len > 0.0f) {
                     const float il = 1.0f / len;
@@ -412,45 +469,15 @@ __device__ __forceinline__ int collide(const DevModel& M, WarpWS<NA>& w, int lan
                 const float rc = M.link[l / NA][l % NA].rcap;
                 dist = len - rb - rc;
 #pragma unroll
-                for (int k = 0; k < 3; ++k) cp[k] = 0.5f * ((pb[k] - rb * nn[k]) + (s[k] + rc * nn[k]));
-                A = d::B;
+                for (int k = 0; k < 3; ++k) cp[k] = 0.5f * ((pb[k] - rb * nn[k]) + (sp[k] + rc * nn[k]));
                 Bb = l;
-            } else if (p < 1 + d::NL + nb) {  // ball - box
+            } else {  // ball - box
                 const float* box = M.box[p - 1 - d::NL];
                 float surf[3];
                 dist = box_sdf(pb, box, nn, surf) - rb;
 #pragma unroll
                 for (int k = 0; k < 3; ++k) cp[k] = 0.5f * ((pb[k] - rb * nn[k]) + surf[k]);
-                A = d::B;
                 isbox = true;
-            } else {  // link capsule - box
-                const int idx = p - 1 - d::NL - nb;
-                const int l = idx / nb, bi = idx - (idx / nb) * nb;
-                const float* box = M.box[bi];
-                const float* a0 = w.a0[l];
-                const float* a1 = w.a1[l];
-                const float rc = M.link[l / NA][l % NA].rcap;
-                float dd[3] = {a1[0] - a0[0], a1[1] - a0[1], a1[2] - a0[2]};
-                // bounding-sphere cull (conservative)
-                float mid[3] = {a0[0] + 0.5f * dd[0], a0[1] + 0.5f * dd[1], a0[2] + 0.5f * dd[2]};
-                const float rad = 0.5f * sqrtf(dot3(dd, dd)) + rc;
-                float lb2 = 0.0f;
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    const float e = fmaxf(fabsf(mid[k] - box[k]) - box[3 + k], 0.0f);
-                    lb2 += e * e;
-                }
-                if (lb2 < rad * rad) {
-                    ++exact;
-                    const float t = capsule_box_t(a0, dd, box);
-                    float x[3] = {a0[0] + t * dd[0], a0[1] + t * dd[1], a0[2] + t * dd[2]};
-                    float surf[3];
-                    dist = box_sdf(x, box, nn, surf) - rc;
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) cp[k] = 0.5f * ((x[k] - rc * nn[k]) + surf[k]);
-                    A = l;
-                    isbox = true;
-                }
             }
             active = dist < 0.0f;
         }
@@ -466,11 +493,86 @@ __device__ __forceinline__ int collide(const DevModel& M, WarpWS<NA>& w, int lan
                     w.cn[pos][k] = nn[k];
                 }
                 w.cdep[pos] = -dist;
-                w.cA[pos] = A;
+                w.cA[pos] = d::B;
                 w.cB[pos] = Bb;
             }
         }
         base += __popc(mask);
+    }
+    // capsule-box: bounding-sphere cull, survivors gathered in pair order
+    for (int p0 = 0; p0 < nlb; p0 += 32) {
+        const int idx = p0 + lane;
+        bool sv = false;
+        if (idx < nlb) {
+            const int l = idx / nb, bi = idx - l * nb;
+            const float* box = M.box[bi];
+            const float* a0 = w.a0[l];
+            const float* a1 = w.a1[l];
+            const float rc = M.link[l / NA][l % NA].rcap;
+            float dd[3] = {a1[0] - a0[0], a1[1] - a0[1], a1[2] - a0[2]};
+            float mid[3] = {a0[0] + 0.5f * dd[0], a0[1] + 0.5f * dd[1], a0[2] + 0.5f * dd[2]};
+            const float rad = 0.5f * sqrtf(dot3(dd, dd)) + rc;
+            float lb2 = 0.0f;
+            bool ov = true;  // axis-aligned boxes of the capsule and the box overlap
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const float e = fmaxf(fabsf(mid[k] - box[k]) - box[3 + k], 0.0f);
+                lb2 += e * e;
+                const float lo = fminf(a0[k], a1[k]) - rc, hi = fmaxf(a0[k], a1[k]) + rc;
+                ov = ov && (lo <= box[k] + box[3 + k]) && (hi >= box[k] - box[3 + k]);
+            }
+            sv = ov && lb2 < rad * rad;
+        }
+        const unsigned mask = __ballot_sync(FULL, sv);
+        if (sv) w.surv[nsurv + __popc(mask & ((1u << lane) - 1u))] = (short)idx;
+        nsurv += __popc(mask);
+    }
+    __syncwarp();
+    for (int si = 0; si < nsurv; ++si) {
+        const int idx = w.surv[si];
+        const int l = idx / nb, bi = idx - l * nb;
+        const float* box = M.box[bi];
+        const float* a0 = w.a0[l];
+        const float rc = M.link[l / NA][l % NA].rcap;
+        const float dd[3] = {w.a1[l][0] - a0[0], w.a1[l][1] - a0[1], w.a1[l][2] - a0[2]};
+        float bf = INFINITY, bt = 0.0f;
+        for (int cid = lane; cid < CB_CANDIDATES; cid += 32) {
+            const float t = capsule_box_candidate(cid, a0, dd, box);
+            const float f = box_sdf_only(a0, dd, t, box);
+            if (f < bf || (f == bf && t < bt)) {
+                bf = f;
+                bt = t;
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const float of = __shfl_xor_sync(FULL, bf, off);
+            const float ot = __shfl_xor_sync(FULL, bt, off);
+            if (of < bf || (of == bf && ot < bt)) {
+                bf = of;
+                bt = ot;
+            }
+        }
+        float x[3] = {a0[0] + bt * dd[0], a0[1] + bt * dd[1], a0[2] + bt * dd[2]};
+        float nn[3], surf[3];
+        const float dist = box_sdf(x, box, nn, surf) - rc;
+        if (dist < 0.0f) {
+            if (lane == 0) {
+                pa += -dist;
+                pbox += -dist;
+                if (base < M.maxc) {
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        w.cp[base][k] = 0.5f * ((x[k] - rc * nn[k]) + surf[k]);
+                        w.cn[base][k] = nn[k];
+                    }
+                    w.cdep[base] = -dist;
+                    w.cA[base] = l;
+                    w.cB[base] = -1;
+                }
+            }
+            ++base;
+        }
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -483,19 +585,55 @@ __device__ __forceinline__ int collide(const DevModel& M, WarpWS<NA>& w, int lan
         w.pen_all = pa;
         w.pen_box = pbox;
     }
-    return exact;
+    return lane == 0 ? nsurv : 0;
 }
 
 // ---------------------------------------------------------------------------
 // dynamics: free velocity vf = qd + dt (M + dt D)^-1 (tau_drive - c - D qd)
 // ---------------------------------------------------------------------------
+// Inclusive scans over the links of one arm (a 16-lane segment; lanes past
+// the last link hold zeros).  Suffix sums run towards the base, prefix sums
+// towards the tip.
+template <int N>
+__device__ __forceinline__ void seg_suffix_sum(float (&v)[N], int i, int nlinks) {
+#pragma unroll
+    for (int off = 1; off < 16; off <<= 1) {
+        if (off >= nlinks) break;
+#pragma unroll
+        for (int t = 0; t < N; ++t) {
+            const float o = __shfl_down_sync(FULL, v[t], off, 16);
+            if (i + off < 16) v[t] += o;
+        }
+    }
+}
+template <int N>
+__device__ __forceinline__ void seg_prefix_sum(float (&v)[N], int i, int nlinks) {
+#pragma unroll
+    for (int off = 1; off < 16; off <<= 1) {
+        if (off >= nlinks) break;
+#pragma unroll
+        for (int t = 0; t < N; ++t) {
+            const float o = __shfl_up_sync(FULL, v[t], off, 16);
+            if (i >= off) v[t] += o;
+        }
+    }
+}
+
 template <int NA>
 __device__ __forceinline__ void dynamics(const DevModel& M, WarpWS<NA>& w, int lane, int* err) {
     using d = Dims<NA>;
     const int a = lane >> 4, i = lane & 15;
     const bool act = i < NA;
-    const int l = a * NA + i;
-    // (1) spatial inertia of each link about the world origin; joint axis
+    const int l = a * NA + (act ? i : 0);
+    // (1) per link (lane i): spatial inertia about the world origin
+    //     (m, h = m c, J = R I R^T + m(|c|^2 E - c c^T)), joint motion axis
+    //     S = (z, o x z), velocity term S qd
+    float Is[10], S[6], sq[6];
+#pragma unroll
+    for (int t = 0; t < 10; ++t) Is[t] = 0.0f;
+#pragma unroll
+    for (int t = 0; t < 6; ++t) S[t] = sq[t] = 0.0f;
+    float qdi = 0.0f;
     if (act) {
         const DevLink& L = M.link[a][i];
         const float* R = w.R[l];
@@ -507,92 +645,72 @@ __device__ __forceinline__ void dynamics(const DevModel& M, WarpWS<NA>& w, int l
 #pragma unroll
             for (int cc = 0; cc < 3; ++cc)
                 T[3 * r + cc] = R[3 * r] * B9[cc] + R[3 * r + 1] * B9[3 + cc] + R[3 * r + 2] * B9[6 + cc];
-        const float Ixx = T[0] * R[0] + T[1] * R[1] + T[2] * R[2];
-        const float Iyy = T[3] * R[3] + T[4] * R[4] + T[5] * R[5];
-        const float Izz = T[6] * R[6] + T[7] * R[7] + T[8] * R[8];
-        const float Ixy = T[0] * R[3] + T[1] * R[4] + T[2] * R[5];
-        const float Ixz = T[0] * R[6] + T[1] * R[7] + T[2] * R[8];
-        const float Iyz = T[3] * R[6] + T[4] * R[7] + T[5] * R[8];
-        const float* c = w.c[l];
+        const float c0 = w.c[l][0], c1 = w.c[l][1], c2 = w.c[l][2];
         const float m = L.mass;
-        const float cc2 = dot3(c, c);
-        float* Is = w.Isp[l];
+        const float cc2 = c0 * c0 + c1 * c1 + c2 * c2;
         Is[0] = m;
-        Is[1] = m * c[0];
-        Is[2] = m * c[1];
-        Is[3] = m * c[2];
-        Is[4] = Ixx + m * (cc2 - c[0] * c[0]);
-        Is[5] = Iyy + m * (cc2 - c[1] * c[1]);
-        Is[6] = Izz + m * (cc2 - c[2] * c[2]);
-        Is[7] = Ixy - m * c[0] * c[1];
-        Is[8] = Ixz - m * c[0] * c[2];
-        Is[9] = Iyz - m * c[1] * c[2];
-        float* S = w.S[l];
+        Is[1] = m * c0;
+        Is[2] = m * c1;
+        Is[3] = m * c2;
+        Is[4] = T[0] * R[0] + T[1] * R[1] + T[2] * R[2] + m * (cc2 - c0 * c0);
+        Is[5] = T[3] * R[3] + T[4] * R[4] + T[5] * R[5] + m * (cc2 - c1 * c1);
+        Is[6] = T[6] * R[6] + T[7] * R[7] + T[8] * R[8] + m * (cc2 - c2 * c2);
+        Is[7] = T[0] * R[3] + T[1] * R[4] + T[2] * R[5] - m * c0 * c1;
+        Is[8] = T[0] * R[6] + T[1] * R[7] + T[2] * R[8] - m * c0 * c2;
+        Is[9] = T[3] * R[6] + T[4] * R[7] + T[5] * R[8] - m * c1 * c2;
         S[0] = w.z[l][0];
         S[1] = w.z[l][1];
         S[2] = w.z[l][2];
         cross3(w.o[l], w.z[l], S + 3);
+        qdi = w.qd[a * NA + i];
+#pragma unroll
+        for (int t = 0; t < 6; ++t) sq[t] = S[t] * qdi;
     }
-    __syncwarp();
-    // (2) composite inertia of the subtree (suffix sum) -> F_j = I^c_j S_j;
-    //     spatial velocity V_i = sum_{k<=i} S_k qd_k
-    if (act) {
-        float Ic[10];
+    // (2) composite inertia of the subtree (suffix) and F_i = I^c_i S_i;
+    //     spatial velocity V_i = sum_{k<=i} S_k qd_k (prefix)
+    float Ic[10];
 #pragma unroll
-        for (int t = 0; t < 10; ++t) Ic[t] = 0.0f;
-        for (int k = i; k < NA; ++k) {
-            const float* Is = w.Isp[a * NA + k];
+    for (int t = 0; t < 10; ++t) Ic[t] = Is[t];
+    seg_suffix_sum<10>(Ic, i, NA);
+    float F[6];
+    spatial_inertia_apply(Ic, S, F);
+    float V[6];
 #pragma unroll
-            for (int t = 0; t < 10; ++t) Ic[t] += Is[t];
-        }
-        spatial_inertia_apply(Ic, w.S[l], w.F[l]);
-        float V[6] = {0, 0, 0, 0, 0, 0};
-        for (int k = 0; k <= i; ++k) {
-            const float qdk = w.qd[a * NA + k];
-            const float* S = w.S[a * NA + k];
+    for (int t = 0; t < 6; ++t) V[t] = sq[t];
+    seg_prefix_sum<6>(V, i, NA);
+    // (3) velocity-product acceleration A_i = sum_{k<=i} V_{k-1} x (S_k qd_k)
+    float Vp[6];
 #pragma unroll
-            for (int t = 0; t < 6; ++t) V[t] += S[t] * qdk;
-        }
-#pragma unroll
-        for (int t = 0; t < 6; ++t) w.V[l][t] = V[t];
+    for (int t = 0; t < 6; ++t) {
+        Vp[t] = __shfl_up_sync(FULL, V[t], 1, 16);
+        if (i == 0) Vp[t] = 0.0f;
     }
-    __syncwarp();
-    // (3) mass-matrix column i: M[r][i] = S_r . F_i (r <= i);
-    //     bias force f_i = I_i (A_i + a_g) + V_i x* (I_i V_i) with the
-    //     velocity-product acceleration A_i = sum_{k<=i} V_{k-1} x (S_k qd_k)
-    if (act) {
-        const float* F = w.F[l];
-        for (int r = 0; r <= i; ++r) {
-            const float* S = w.S[a * NA + r];
-            const float mv = S[0] * F[0] + S[1] * F[1] + S[2] * F[2] + S[3] * F[3] + S[4] * F[4] + S[5] * F[5];
-            w.L[a][r][i] = mv;
-            w.L[a][i][r] = mv;
-        }
-        float Aa[6] = {0, 0, 0, 0, 0, 0};
-        for (int k = 1; k <= i; ++k) {
-            const float* Vp = w.V[a * NA + k - 1];
-            const float qdk = w.qd[a * NA + k];
-            const float* Sk = w.S[a * NA + k];
-            float s[6];
+    float Aa[6];
+    {
+        float t1[3], t2[3], t3[3];
+        cross3(Vp, sq, t1);
+        cross3(Vp, sq + 3, t2);
+        cross3(Vp + 3, sq, t3);
+        Aa[0] = t1[0];
+        Aa[1] = t1[1];
+        Aa[2] = t1[2];
+        Aa[3] = t2[0] + t3[0];
+        Aa[4] = t2[1] + t3[1];
+        Aa[5] = t2[2] + t3[2];
+    }
+    if (!act) {
 #pragma unroll
-            for (int t = 0; t < 6; ++t) s[t] = Sk[t] * qdk;
-            float t1[3], t2[3], t3[3];
-            cross3(Vp, s, t1);
-            cross3(Vp, s + 3, t2);
-            cross3(Vp + 3, s, t3);
-            Aa[0] += t1[0];
-            Aa[1] += t1[1];
-            Aa[2] += t1[2];
-            Aa[3] += t2[0] + t3[0];
-            Aa[4] += t2[1] + t3[1];
-            Aa[5] += t2[2] + t3[2];
-        }
-        const float gw = 1.0f - M.link[a][i].gravcomp;
+        for (int t = 0; t < 6; ++t) Aa[t] = 0.0f;
+    }
+    seg_prefix_sum<6>(Aa, i, NA);
+    // bias force of link i: I_i (A_i + a_g) + V_i x* (I_i V_i), gravity as a
+    // base acceleration -g on links without compensation
+    float f[6];
+    {
+        const float gw = act ? 1.0f - M.link[a][i].gravcomp : 0.0f;
         Aa[3] -= gw * M.g[0];
         Aa[4] -= gw * M.g[1];
         Aa[5] -= gw * M.g[2];
-        const float* Is = w.Isp[l];
-        const float* V = w.V[l];
         float IA[6], IV[6];
         spatial_inertia_apply(Is, Aa, IA);
         spatial_inertia_apply(Is, V, IV);
@@ -600,73 +718,106 @@ __device__ __forceinline__ void dynamics(const DevModel& M, WarpWS<NA>& w, int l
         cross3(V, IV, n1);
         cross3(V + 3, IV + 3, n2);
         cross3(V, IV + 3, f1);
-        float* f = w.f[l];
         f[0] = IA[0] + n1[0] + n2[0];
         f[1] = IA[1] + n1[1] + n2[1];
         f[2] = IA[2] + n1[2] + n2[2];
         f[3] = IA[3] + f1[0];
         f[4] = IA[4] + f1[1];
         f[5] = IA[5] + f1[2];
-    }
-    __syncwarp();
-    // (4) bias torque = S_i . (sum of subtree forces); drive; implicit damping
-    if (act) {
-        float Ff[6] = {0, 0, 0, 0, 0, 0};
-        for (int k = i; k < NA; ++k) {
-            const float* f = w.f[a * NA + k];
+        if (!act) {
 #pragma unroll
-            for (int t = 0; t < 6; ++t) Ff[t] += f[t];
+            for (int t = 0; t < 6; ++t) f[t] = 0.0f;
         }
-        const float* S = w.S[l];
-        const float tb = S[0] * Ff[0] + S[1] * Ff[1] + S[2] * Ff[2] + S[3] * Ff[3] + S[4] * Ff[4] + S[5] * Ff[5];
+    }
+    // (4) bias torque S_i . (subtree force); drive; implicit damping
+    seg_suffix_sum<6>(f, i, NA);
+    if (act) {
+        const float tb = S[0] * f[0] + S[1] * f[1] + S[2] * f[2] + S[3] * f[3] + S[4] * f[4] + S[5] * f[5];
         const DevLink& L = M.link[a][i];
         const int dof = a * NA + i;
         const float td = fminf(fmaxf(L.gear * w.u[dof], -L.tau_max), L.tau_max);
-        w.rhs[dof] = td - tb - L.D * w.qd[dof];
-        w.L[a][i][i] += M.dt * L.D;
+        w.rhs[dof] = td - tb - L.D * qdi;
+#pragma unroll
+        for (int t = 0; t < 6; ++t) {
+            w.S[l][t] = S[t];
+            w.F[l][t] = F[t];
+        }
     }
     __syncwarp();
-    // (5) Cholesky of each arm block and the free velocity; ball
+    // (5) mass-matrix entries M[r][c] = S_r . F_c (r <= c), spread over the
+    //     16 lanes of the arm's half-warp; dt D on the diagonal
+    constexpr int NENT = NA * (NA + 1) / 2;
+#pragma unroll
+    for (int e0 = 0; e0 < NENT; e0 += 16) {
+        const int e = e0 + i;
+        if (e < NENT) {
+            int c = 0, rem = e;
+#pragma unroll
+            for (int cc = 0; cc < NA; ++cc)
+                if (rem > c) {
+                    rem -= c + 1;
+                    ++c;
+                }
+            const int r = rem;
+            const float* Sr = w.S[a * NA + r];
+            const float* Fc = w.F[a * NA + c];
+            float mv = Sr[0] * Fc[0] + Sr[1] * Fc[1] + Sr[2] * Fc[2] + Sr[3] * Fc[3] + Sr[4] * Fc[4] + Sr[5] * Fc[5];
+            if (r == c) mv += M.dt * M.link[a][c].D;
+            w.L[a][c][r] = mv;
+        }
+    }
+    __syncwarp();
+    // (6) Cholesky of each arm block (in registers), the free velocity; ball
     if (i == 0) {
-        float (*Lm)[NA] = w.L[a];
+        float A[NA][NA];
+#pragma unroll
+        for (int r = 0; r < NA; ++r)
+#pragma unroll
+            for (int cc = 0; cc <= r; ++cc) A[r][cc] = w.L[a][r][cc];
         bool ok = true;
+        float di[NA];
 #pragma unroll
         for (int j = 0; j < NA; ++j) {
-            float s = Lm[j][j];
+            float sj = A[j][j];
 #pragma unroll
-            for (int k = 0; k < j; ++k) s -= Lm[j][k] * Lm[j][k];
-            // a NaN pivot comes from a non-finite state (reported as such
-            // through the cost); only a finite non-positive pivot is a loss
-            // of positive definiteness
-            ok = ok && !(s <= 0.0f);
-            const float dj = sqrtf(s);
-            const float inv = 1.0f / dj;
-            Lm[j][j] = dj;
+            for (int k = 0; k < j; ++k) sj -= A[j][k] * A[j][k];
+            // a NaN pivot comes from a non-finite state (reported through the
+            // cost); only a finite non-positive pivot is a loss of
+            // positive definiteness
+            ok = ok && !(sj <= 0.0f);
+            const float inv = rsqrtf(sj);
+            A[j][j] = sj * inv;
+            di[j] = inv;
 #pragma unroll
             for (int r = j + 1; r < NA; ++r) {
-                float t = Lm[r][j];
+                float t = A[r][j];
 #pragma unroll
-                for (int k = 0; k < j; ++k) t -= Lm[r][k] * Lm[j][k];
-                Lm[r][j] = t * inv;
+                for (int k = 0; k < j; ++k) t -= A[r][k] * A[j][k];
+                A[r][j] = t * inv;
             }
         }
         float y[NA];
 #pragma unroll
         for (int r = 0; r < NA; ++r) {
-            float s = w.rhs[a * NA + r];
+            float sr = w.rhs[a * NA + r];
 #pragma unroll
-            for (int k = 0; k < r; ++k) s -= Lm[r][k] * y[k];
-            y[r] = s / Lm[r][r];
+            for (int k = 0; k < r; ++k) sr -= A[r][k] * y[k];
+            y[r] = sr * di[r];
         }
 #pragma unroll
         for (int r = NA - 1; r >= 0; --r) {
-            float s = y[r];
+            float sr = y[r];
 #pragma unroll
-            for (int k = r + 1; k < NA; ++k) s -= Lm[k][r] * y[k];
-            y[r] = s / Lm[r][r];
+            for (int k = r + 1; k < NA; ++k) sr -= A[k][r] * y[k];
+            y[r] = sr * di[r];
         }
 #pragma unroll
-        for (int r = 0; r < NA; ++r) w.vf[a * NA + r] = w.qd[a * NA + r] + M.dt * y[r];
+        for (int r = 0; r < NA; ++r) {
+            w.vf[a * NA + r] = w.qd[a * NA + r] + M.dt * y[r];
+            w.Ldi[a][r] = di[r];
+#pragma unroll
+            for (int cc = 0; cc <= r; ++cc) w.L[a][r][cc] = A[r][cc];
+        }
         if (!ok) atomicOr(err, ERRB_CHOLESKY);
     }
     if (lane == 15) {
@@ -716,33 +867,17 @@ __device__ __forceinline__ void contact_frame_row(const float* n, int k, float* 
     cross3(n, t1, e);
 }
 
-template <int NA>
-__device__ __forceinline__ void add_body_row(const DevModel& M, const WarpWS<NA>& w, int body, float sgn,
-                                             const float* e, const float* p, float* y) {
-    using d = Dims<NA>;
-    if (body < 0) return;
-    if (body == d::B) {
-        const float* c = &w.q[d::B];
-        float dd[3] = {p[0] - c[0], p[1] - c[1], p[2] - c[2]};
-        float de[3];
-        cross3(dd, e, de);
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-            y[d::B + r] += sgn * e[r];
-            y[d::B + 3 + r] += sgn * de[r];
-        }
-        return;
-    }
-    const int a = body / NA, i = body - a * NA;
-    for (int k = 0; k <= i; ++k) {
-        const int l = a * NA + k;
-        float dd[3] = {p[0] - w.o[l][0], p[1] - w.o[l][1], p[2] - w.o[l][2]};
-        float col[3];
-        cross3(w.z[l], dd, col);
-        y[a * NA + k] += sgn * dot3(e, col);
-    }
+__device__ __forceinline__ int packed_index(int r, int s, int nr) {
+    // upper-triangle index of (min, max) in an nr x nr symmetric matrix
+    const int lo = r < s ? r : s, hi = r < s ? s : r;
+    return lo * nr - (lo * (lo - 1)) / 2 + (hi - lo);
 }
 
+// Soft contact by projected Gauss-Seidel in contact space.  With the
+// factor L L^T = M + dt D and rows Y_r = L^-1 J_r^T, the Delassus matrix is
+// G = Y Y^T and the unconstrained row velocities are b = Y z_f, z_f = L^T
+// v_f; after the sweeps v = L^-T (z_f + Y^T lambda).  This is the same
+// iteration as updating v row by row (J_r v = b_r + (G lambda)_r).
 template <int NA>
 __device__ __forceinline__ void contacts(const DevModel& M, WarpWS<NA>& w, int lane) {
     using d = Dims<NA>;
@@ -752,126 +887,210 @@ __device__ __forceinline__ void contacts(const DevModel& M, WarpWS<NA>& w, int l
         __syncwarp();
         return;
     }
-    const float smb = sqrtf(M.mb), sIb = sqrtf(M.Ib);
-    // z_f = L^T v_f
-    if ((lane & 15) == 0) {
-        const int a = lane >> 4;
+    const float ismb = rsqrtf(M.mb), isIb = rsqrtf(M.Ib);
+    // z_f = L^T v_f (one lane per arm coordinate; lane 15 the ball)
+    {
+        const int a = lane >> 4, i = lane & 15;
+        if (i < NA) {
+            float sz = 0.0f;
 #pragma unroll
-        for (int i = 0; i < NA; ++i) {
-            float s = 0.0f;
+            for (int k = 0; k < NA; ++k)
+                if (k >= i) sz += w.L[a][k][i] * w.vf[a * NA + k];
+            w.zz[a * NA + i] = sz;
+        }
+        if (lane == 15) {
+            const float smb = M.mb * ismb, sIb = M.Ib * isIb;
 #pragma unroll
-            for (int k = i; k < NA; ++k) s += w.L[a][k][i] * w.vf[a * NA + k];
-            w.zz[a * NA + i] = s;
+            for (int r = 0; r < 3; ++r) {
+                w.zz[d::B + r] = smb * w.vf[d::B + r];
+                w.zz[d::B + 3 + r] = sIb * w.vf[d::B + 3 + r];
+            }
         }
     }
-    if (lane == 15) {
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-            w.zz[d::B + r] = smb * w.vf[d::B + r];
-            w.zz[d::B + 3 + r] = sIb * w.vf[d::B + 3 + r];
-        }
-    }
+    // rows: Jacobian of the touched bodies (in registers), half-solved by
+    // the factor, one store per row
     const int nr = 3 * nc;
-    const float regc = (1.0f - M.imp) / M.imp;
     for (int r = lane; r < nr; r += 32) {
         const int c = r / 3, k = r - 3 * (r / 3);
         float e[3];
         contact_frame_row<NA>(w.cn[c], k, e);
+        const float* p = w.cp[c];
+        float ya[2][NA], yb[6];
+#pragma unroll
+        for (int q = 0; q < NA; ++q) ya[0][q] = ya[1][q] = 0.0f;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) yb[q] = 0.0f;
+        int msk = 0;
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            const int body = side == 0 ? w.cA[c] : w.cB[c];
+            const float sgn = side == 0 ? 1.0f : -1.0f;
+            if (body == d::B) {
+                const float* bc = &w.q[d::B];
+                float dd[3] = {p[0] - bc[0], p[1] - bc[1], p[2] - bc[2]};
+                float de[3];
+                cross3(dd, e, de);
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    yb[q] += sgn * e[q];
+                    yb[3 + q] += sgn * de[q];
+                }
+                msk |= 4;
+            } else if (body >= 0) {
+                const int ab = body >= NA ? 1 : 0;
+                const int ib = body - ab * NA;
+                float col[NA];
+#pragma unroll
+                for (int q = 0; q < NA; ++q) {
+                    col[q] = 0.0f;
+                    if (q <= ib) {
+                        const int lq = ab * NA + q;
+                        float dd[3] = {p[0] - w.o[lq][0], p[1] - w.o[lq][1], p[2] - w.o[lq][2]};
+                        float cz[3];
+                        cross3(w.z[lq], dd, cz);
+                        col[q] = sgn * dot3(e, cz);
+                    }
+                }
+                if (ab == 0) {
+#pragma unroll
+                    for (int q = 0; q < NA; ++q) ya[0][q] += col[q];
+                } else {
+#pragma unroll
+                    for (int q = 0; q < NA; ++q) ya[1][q] += col[q];
+                }
+                msk |= 1 << ab;
+            }
+        }
+#pragma unroll
+        for (int ab = 0; ab < 2; ++ab) {
+            if (msk & (1 << ab)) {
+#pragma unroll
+                for (int ii = 0; ii < NA; ++ii) {
+                    float sv = ya[ab][ii];
+#pragma unroll
+                    for (int kk = 0; kk < ii; ++kk) sv -= w.L[ab][ii][kk] * ya[ab][kk];
+                    ya[ab][ii] = sv * w.Ldi[ab][ii];
+                }
+            }
+        }
         float* y = w.Y[r];
 #pragma unroll
-        for (int t = 0; t < d::NV; ++t) y[t] = 0.0f;
-        add_body_row<NA>(M, w, w.cA[c], 1.0f, e, w.cp[c], y);
-        add_body_row<NA>(M, w, w.cB[c], -1.0f, e, w.cp[c], y);
-#pragma unroll
-        for (int a = 0; a < 2; ++a) {
-            float t[NA];
-#pragma unroll
-            for (int i = 0; i < NA; ++i) {
-                float s = y[a * NA + i];
-#pragma unroll
-                for (int kk = 0; kk < i; ++kk) s -= w.L[a][i][kk] * t[kk];
-                t[i] = s / w.L[a][i][i];
-            }
-#pragma unroll
-            for (int i = 0; i < NA; ++i) y[a * NA + i] = t[i];
+        for (int q = 0; q < NA; ++q) {
+            y[q] = ya[0][q];
+            y[NA + q] = ya[1][q];
         }
 #pragma unroll
-        for (int t = 0; t < 3; ++t) {
-            y[d::B + t] /= smb;
-            y[d::B + 3 + t] /= sIb;
+        for (int q = 0; q < 3; ++q) {
+            y[d::B + q] = yb[q] * ismb;
+            y[d::B + 3 + q] = yb[3 + q] * isIb;
         }
-        float A = 0.0f;
-#pragma unroll
-        for (int t = 0; t < d::NV; ++t) A += y[t] * y[t];
-        const float R = regc * A;
-        w.Rr[r] = R;
-        w.Ad[r] = A + R;
+        w.tmask[r] = msk;
         w.vs[r] = (k == 0) ? (M.erp / M.dt) * w.cdep[c] : 0.0f;
         w.lam[r] = 0.0f;
     }
     __syncwarp();
-    if (lane == 0) {
-        float z[d::NV];
+    // Delassus block G = Y Y^T (packed) and b = Y z_f, over the blocks rows share
+    const float regc = (1.0f - M.imp) / M.imp;
+    const int npk = nr * (nr + 1) / 2;
+    for (int t = lane; t < npk + nr; t += 32) {
+        if (t < npk) {
+            // decode (r, s), r <= s, from the packed index
+            int r = 0, rem = t;
+            while (rem >= nr - r) {
+                rem -= nr - r;
+                ++r;
+            }
+            const int sc = r + rem;
+            const int m = w.tmask[r] & w.tmask[sc];
+            const float* yr = w.Y[r];
+            const float* ys = w.Y[sc];
+            float g = 0.0f;
+            if (m & 1) {
 #pragma unroll
-        for (int t = 0; t < d::NV; ++t) z[t] = w.zz[t];
-        for (int s = 0; s < M.sweeps; ++s) {
+                for (int q = 0; q < NA; ++q) g += yr[q] * ys[q];
+            }
+            if (m & 2) {
+#pragma unroll
+                for (int q = NA; q < 2 * NA; ++q) g += yr[q] * ys[q];
+            }
+            if (m & 4) {
+#pragma unroll
+                for (int q = d::B; q < d::NV; ++q) g += yr[q] * ys[q];
+            }
+            w.G[t] = g;
+            if (sc == r) {
+                const float R = regc * g;
+                w.Rr[r] = R;
+                w.iAd[r] = 1.0f / (g + R);
+            }
+        } else {
+            const int r = t - npk;
+            const float* yr = w.Y[r];
+            float bb = 0.0f;
+#pragma unroll
+            for (int q = 0; q < d::NV; ++q) bb += yr[q] * w.zz[q];
+            w.b[r] = bb;
+        }
+    }
+    __syncwarp();
+    // projected Gauss-Seidel sweeps (normal row, then the tangent pair with
+    // the friction disk |lambda_t| <= mu lambda_n)
+    if (lane == 0) {
+        for (int sw = 0; sw < M.sweeps; ++sw) {
             for (int c = 0; c < nc; ++c) {
                 const int rn = 3 * c;
-                const float* yn = w.Y[rn];
-                float res = w.Rr[rn] * w.lam[rn] - w.vs[rn];
-#pragma unroll
-                for (int t = 0; t < d::NV; ++t) res += yn[t] * z[t];
-                const float ln = fmaxf(w.lam[rn] - res / w.Ad[rn], 0.0f);
-                const float dn = ln - w.lam[rn];
+                float res = w.b[rn] + w.Rr[rn] * w.lam[rn] - w.vs[rn];
+                for (int q = 0; q < nr; ++q) res += w.G[packed_index(rn, q, nr)] * w.lam[q];
+                const float ln = fmaxf(w.lam[rn] - res * w.iAd[rn], 0.0f);
                 w.lam[rn] = ln;
-#pragma unroll
-                for (int t = 0; t < d::NV; ++t) z[t] += yn[t] * dn;
-                const float* y1 = w.Y[rn + 1];
-                const float* y2 = w.Y[rn + 2];
-                float r1 = w.Rr[rn + 1] * w.lam[rn + 1], r2 = w.Rr[rn + 2] * w.lam[rn + 2];
-#pragma unroll
-                for (int t = 0; t < d::NV; ++t) {
-                    r1 += y1[t] * z[t];
-                    r2 += y2[t] * z[t];
+                float r1 = w.b[rn + 1] + w.Rr[rn + 1] * w.lam[rn + 1];
+                float r2 = w.b[rn + 2] + w.Rr[rn + 2] * w.lam[rn + 2];
+                for (int q = 0; q < nr; ++q) {
+                    const float lq = w.lam[q];
+                    r1 += w.G[packed_index(rn + 1, q, nr)] * lq;
+                    r2 += w.G[packed_index(rn + 2, q, nr)] * lq;
                 }
-                float l1 = w.lam[rn + 1] - r1 / w.Ad[rn + 1];
-                float l2 = w.lam[rn + 2] - r2 / w.Ad[rn + 2];
+                float l1 = w.lam[rn + 1] - r1 * w.iAd[rn + 1];
+                float l2 = w.lam[rn + 2] - r2 * w.iAd[rn + 2];
                 const float nrm = sqrtf(l1 * l1 + l2 * l2), lim = M.mu * ln;
                 if (nrm > lim) {
                     const float sc = nrm > 0.0f ? lim / nrm : 0.0f;
                     l1 *= sc;
                     l2 *= sc;
                 }
-                const float d1 = l1 - w.lam[rn + 1], d2 = l2 - w.lam[rn + 2];
                 w.lam[rn + 1] = l1;
                 w.lam[rn + 2] = l2;
-#pragma unroll
-                for (int t = 0; t < d::NV; ++t) z[t] += y1[t] * d1 + y2[t] * d2;
             }
         }
-#pragma unroll
-        for (int t = 0; t < d::NV; ++t) w.zz[t] = z[t];
     }
     __syncwarp();
-    // v = L^-T z
+    // z = z_f + Y^T lambda, then v = L^-T z
+    if (lane < d::NV) {
+        float zv = w.zz[lane];
+        for (int r = 0; r < nr; ++r) zv += w.Y[r][lane] * w.lam[r];
+        w.zz[lane] = zv;
+    }
+    __syncwarp();
     if ((lane & 15) == 0) {
         const int a = lane >> 4;
-        float t[NA];
+        float zl[NA], t[NA];
 #pragma unroll
-        for (int i = NA - 1; i >= 0; --i) {
-            float s = w.zz[a * NA + i];
+        for (int ii = 0; ii < NA; ++ii) zl[ii] = w.zz[a * NA + ii];
 #pragma unroll
-            for (int k = i + 1; k < NA; ++k) s -= w.L[a][k][i] * t[k];
-            t[i] = s / w.L[a][i][i];
+        for (int ii = NA - 1; ii >= 0; --ii) {
+            float sv = zl[ii];
+#pragma unroll
+            for (int k = ii + 1; k < NA; ++k) sv -= w.L[a][k][ii] * t[k];
+            t[ii] = sv * w.Ldi[a][ii];
         }
 #pragma unroll
-        for (int i = 0; i < NA; ++i) w.v[a * NA + i] = t[i];
+        for (int ii = 0; ii < NA; ++ii) w.v[a * NA + ii] = t[ii];
     }
     if (lane == 15) {
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
-            w.v[d::B + r] = w.zz[d::B + r] / smb;
-            w.v[d::B + 3 + r] = w.zz[d::B + 3 + r] / sIb;
+            w.v[d::B + r] = w.zz[d::B + r] * ismb;
+            w.v[d::B + 3 + r] = w.zz[d::B + 3 + r] * isIb;
         }
     }
     __syncwarp();
