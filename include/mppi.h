@@ -151,6 +151,39 @@ int mppi_profile_read(mppi_ctx *c, int *n, float *rollout_ms, float *update_ms, 
  * (0 = the library default).  Used by the autotuner. */
 int mppi_set_launch(mppi_ctx *c, int samples_per_cta);
 
+/* --------------------------------------------------------------- no-alloc */
+/* The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory when they plan -- a real-time control
+ * loop that must not call cudaMalloc/cudaFree once it runs (those calls can
+ * synchronise the device and take unbounded time), or code running inside a
+ * host framework that owns the GPU's memory budget.
+ *
+ * mppi_step_noalloc runs one MPPI iteration exactly like mppi_step (same
+ * kernels, same samples for the same seed and iteration) without a model
+ * handle or a controller handle and without allocating anything: the scene
+ * model, sigma, the control bounds, the error word and the K sample costs go
+ * to one static device array of about 36 KB that every GPU loading the
+ * library holds until the process exits.
+ *   blob, len   scene blob in host memory (as for mppi_model_load), parsed
+ *               on every call
+ *   K, H        samples and horizon; 1 <= K <= MPPI_NOALLOC_MAX_K and
+ *               1 <= H <= 1024, else MPPI_ERR_INVALID_ARG
+ *   lambda      temperature > 0;  sigma: nu host floats
+ *   seed, iteration   Philox key and counter (the caller keeps the count)
+ *   state (device, nx), u_nom, u_nom_out (device, H x nu; may alias)
+ *   status_out  optional host int: when non-NULL the call synchronises
+ *               `stream` and stores the device status (MPPI_OK,
+ *               MPPI_ERR_NONFINITE, MPPI_ERR_CHOLESKY)
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  Every
+ * call shares the array and it keeps the last call's contents (the error
+ * word is cleared at the start of each call): calls that overlap on the GPU
+ * -- on different streams, or from different host threads -- race. */
+#define MPPI_NOALLOC_MAX_K 8192
+int mppi_step_noalloc(const void *blob, size_t len, int K, int H, float lambda, const float *sigma, uint64_t seed,
+                      uint64_t iteration, const float *state, const float *u_nom, float *u_nom_out, int *status_out,
+                      void *stream);
+
 #ifdef __cplusplus
 }
 #endif

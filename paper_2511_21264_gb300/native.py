@@ -114,6 +114,7 @@ def lib():
     _decl(L, "mppi_set_iteration", i, [vp, u64, vp])
     _decl(L, "mppi_sync", i, [vp, vp])
     _decl(L, "mppi_set_launch", i, [vp, i])
+    _decl(L, "mppi_step_noalloc", i, [vp, sz, i, i, C.c_float, fp, u64, u64, fp, fp, fp, C.POINTER(i), vp])
     _decl(L, "mppi_profile", i, [vp, i])
     _decl(L, "mppi_profile_read", i, [vp, C.POINTER(i), C.POINTER(C.c_float), C.POINTER(C.c_float),
                                        C.POINTER(C.c_double), C.POINTER(C.c_double)])
@@ -156,6 +157,21 @@ def debug_philox(ctr, key: int, out, stream=None):
     _check(lib().mppi_debug_philox(ctr.shape[0], ctr.data_ptr(), C.c_uint64(key), out.data_ptr(),
                                    _stream(stream)), "mppi_debug_philox")
     return out
+
+
+def step_noalloc(blob: bytes, K: int, H: int, lam: float, sigma, seed: int, iteration: int, state, u_nom,
+                 u_out, stream=None, want_status: bool = False):
+    """One MPPI iteration through mppi_step_noalloc (no device allocation;
+    scratch in the library's static device array).  Returns the device
+    status when want_status (synchronises the stream), else None."""
+    import numpy as np
+    sig = np.ascontiguousarray(np.asarray(sigma, dtype=np.float32))
+    buf = C.create_string_buffer(blob, len(blob))
+    st = C.c_int(0)
+    _check(lib().mppi_step_noalloc(buf, len(blob), int(K), int(H), float(lam), sig.ctypes.data, C.c_uint64(seed),
+                                   C.c_uint64(iteration), _ptr(state), _ptr(u_nom), _ptr(u_out),
+                                   C.byref(st) if want_status else None, _stream(stream)), "mppi_step_noalloc")
+    return st.value if want_status else None
 
 
 class Model:
