@@ -73,13 +73,25 @@ __global__ void __launch_bounds__(512) rollout_kernel(RolloutArgs args) {
     const float* gb = M.goal;
     unsigned n_exact = 0, n_con = 0;
     for (int h = 0; h < args.H; ++h) {
-        if (lane < d::NU) {
-            if (MODE == 1) {
-                const float un = unom_n ? unom_s[h * d::NU + lane] : args.u_nom[h * d::NU + lane];
-                w.u[lane] = sample_control(key, iter, k, h, lane, un, sig, lo, hi);
-            } else {
-                w.u[lane] = args.U[((size_t)k * args.H + h) * d::NU + lane];
+        if (MODE == 1) {
+            // every 8 steps the 32 lanes draw one Philox block each: 8 steps x
+            // 16 controls of standard normals (the same values sample_control
+            // draws one at a time)
+            if ((h & 7) == 0) {
+                const int jb = lane & 3, hs = h + (lane >> 2);
+                if (4 * jb < d::NU && hs < args.H) {
+                    const uint4 wv = philox4x32_10(make_uint4((uint32_t)jb, (uint32_t)hs, (uint32_t)k, iter), key);
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) w.zn[lane >> 2][4 * jb + t] = block_normal(wv, t);
+                }
+                __syncwarp();
             }
+            if (lane < d::NU) {
+                const float un = unom_n ? unom_s[h * d::NU + lane] : args.u_nom[h * d::NU + lane];
+                w.u[lane] = fminf(fmaxf(__fmaf_rn(sig, w.zn[h & 7][lane], un), lo), hi);
+            }
+        } else if (lane < d::NU) {
+            w.u[lane] = args.U[((size_t)k * args.H + h) * d::NU + lane];
         }
         forward_kinematics<NA>(M, w, lane);
         __syncwarp();
@@ -106,6 +118,9 @@ __global__ void __launch_bounds__(512) rollout_kernel(RolloutArgs args) {
         __syncwarp();
         if (lane == 0) cost += M.w_grasp * grasp_term<NA>(w);
     }
+    // a non-finite state poisons the sample's cost (weight 0 in the update)
+    const bool bad = (lane < d::NQ && !isfinite(w.q[lane])) || (lane < d::NV && !isfinite(w.qd[lane]));
+    if (__any_sync(FULL, bad)) cost = __int_as_float(0x7fc00000);
     if (lane == 0) {
         args.costs[k] = cost;
         if (!isfinite(cost)) atomicOr(args.err, ERRB_NONFINITE);

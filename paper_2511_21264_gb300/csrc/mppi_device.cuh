@@ -80,6 +80,7 @@ struct __align__(16) WarpWS {
     float zz[d::NV];
     float rhs[d::NV];
     float u[d::NU];
+    float zn[8][16];  // standard normals of the next 8 steps (Philox path)
     // kinematics, per link
     float R[d::NL][9];
     float z[d::NL][3];
@@ -90,9 +91,6 @@ struct __align__(16) WarpWS {
     // dynamics
     float S[d::NL][6];
     float F[d::NL][6];
-    float V[d::NL][6];
-    float f[d::NL][6];
-    float Isp[d::NL][10];
     float L[2][NA][NA];
     float Ldi[2][NA];  // reciprocal diagonal of the factors
     // contacts
@@ -103,11 +101,8 @@ struct __align__(16) WarpWS {
     int cB[MAXC];
     float Y[MAXR][d::NV];
     float G[MAXR * (MAXR + 1) / 2];  // Delassus block Y Y^T, packed upper triangle
-    float b[MAXR];                   // J v_f (unconstrained row velocities)
+    float4 rc4[MAXR];                // per row: b = J v_f, R, 1/(A+R), reference velocity
     float lam[MAXR];
-    float Rr[MAXR];
-    float iAd[MAXR];                 // 1 / (A_rr + R_rr)
-    float vs[MAXR];
     int tmask[MAXR];                 // blocks a row touches: 1 left arm, 2 right arm, 4 ball
     short surv[2 * MAXL * MAXB];     // capsule-box pairs that pass the cull, in pair order
     int ncon;
@@ -432,7 +427,6 @@ __device__ __forceinline__ int collide(const DevModel& M, WarpWS<NA>& w, int lan
     using d = Dims<NA>;
     const int nb = M.nb;
     const int nball = 1 + d::NL + nb;
-    const int nlb = d::NL * nb;
     const float* pb = &w.q[d::B];
     const float rb = M.rb;
     int base = 0, nsurv = 0;
@@ -499,33 +493,51 @@ __device__ __forceinline__ int collide(const DevModel& M, WarpWS<NA>& w, int lan
         }
         base += __popc(mask);
     }
-    // capsule-box: bounding-sphere cull, survivors gathered in pair order
-    for (int p0 = 0; p0 < nlb; p0 += 32) {
-        const int idx = p0 + lane;
-        bool sv = false;
-        if (idx < nlb) {
-            const int l = idx / nb, bi = idx - l * nb;
-            const float* box = M.box[bi];
-            const float* a0 = w.a0[l];
-            const float* a1 = w.a1[l];
-            const float rc = M.link[l / NA][l % NA].rcap;
-            float dd[3] = {a1[0] - a0[0], a1[1] - a0[1], a1[2] - a0[2]};
-            float mid[3] = {a0[0] + 0.5f * dd[0], a0[1] + 0.5f * dd[1], a0[2] + 0.5f * dd[2]};
-            const float rad = 0.5f * sqrtf(dot3(dd, dd)) + rc;
-            float lb2 = 0.0f;
-            bool ov = true;  // axis-aligned boxes of the capsule and the box overlap
+    // capsule-box: one lane per link tests its capsule against every box
+    // (bounding sphere and axis-aligned overlap, both conservative); the
+    // survivors are placed link-major, box-minor by a warp prefix sum
+    if (nb > 0) {
+        unsigned smask = 0u;
+        if (lane < d::NL) {
+            const float* a0 = w.a0[lane];
+            const float* a1 = w.a1[lane];
+            const float rc = M.link[lane / NA][lane % NA].rcap;
+            float mid[3], lo[3], hi[3];
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                const float e = fmaxf(fabsf(mid[k] - box[k]) - box[3 + k], 0.0f);
-                lb2 += e * e;
-                const float lo = fminf(a0[k], a1[k]) - rc, hi = fmaxf(a0[k], a1[k]) + rc;
-                ov = ov && (lo <= box[k] + box[3 + k]) && (hi >= box[k] - box[3 + k]);
+                mid[k] = 0.5f * (a0[k] + a1[k]);
+                lo[k] = fminf(a0[k], a1[k]) - rc;
+                hi[k] = fmaxf(a0[k], a1[k]) + rc;
             }
-            sv = ov && lb2 < rad * rad;
+            const float dx = a1[0] - a0[0], dy = a1[1] - a0[1], dz = a1[2] - a0[2];
+            const float rad = 0.5f * sqrtf(dx * dx + dy * dy + dz * dz) + rc;
+            for (int bi = 0; bi < nb; ++bi) {
+                const float* box = M.box[bi];
+                float lb2 = 0.0f;
+                bool ov = true;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const float e = fmaxf(fabsf(mid[k] - box[k]) - box[3 + k], 0.0f);
+                    lb2 += e * e;
+                    ov = ov && (lo[k] <= box[k] + box[3 + k]) && (hi[k] >= box[k] - box[3 + k]);
+                }
+                if (ov && lb2 < rad * rad) smask |= 1u << bi;
+            }
         }
-        const unsigned mask = __ballot_sync(FULL, sv);
-        if (sv) w.surv[nsurv + __popc(mask & ((1u << lane) - 1u))] = (short)idx;
-        nsurv += __popc(mask);
+        const int cnt = __popc(smask);
+        int pre = cnt;  // inclusive prefix over lanes
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int o = __shfl_up_sync(FULL, pre, off);
+            if (lane >= off) pre += o;
+        }
+        int pos = pre - cnt;
+        while (smask) {
+            const int bi = __ffs(smask) - 1;
+            smask &= smask - 1u;
+            w.surv[pos++] = (short)(lane * nb + bi);
+        }
+        nsurv = __shfl_sync(FULL, pre, 31);
     }
     __syncwarp();
     for (int si = 0; si < nsurv; ++si) {
@@ -985,12 +997,14 @@ __device__ __forceinline__ void contacts(const DevModel& M, WarpWS<NA>& w, int l
             y[d::B + 3 + q] = yb[3 + q] * isIb;
         }
         w.tmask[r] = msk;
-        w.vs[r] = (k == 0) ? (M.erp / M.dt) * w.cdep[c] : 0.0f;
+        w.rc4[r].w = (k == 0) ? (M.erp / M.dt) * w.cdep[c] : 0.0f;
         w.lam[r] = 0.0f;
     }
     __syncwarp();
-    // Delassus block G = Y Y^T (packed) and b = Y z_f, over the blocks rows share
+    // Delassus block G = Y Y^T and b = Y z_f, over the blocks rows share.  G
+    // is stored as a full nr x nr square when nr <= 32, else packed.
     const float regc = (1.0f - M.imp) / M.imp;
+    const bool square = nr <= 32;
     const int npk = nr * (nr + 1) / 2;
     for (int t = lane; t < npk + nr; t += 32) {
         if (t < npk) {
@@ -1017,51 +1031,112 @@ __device__ __forceinline__ void contacts(const DevModel& M, WarpWS<NA>& w, int l
 #pragma unroll
                 for (int q = d::B; q < d::NV; ++q) g += yr[q] * ys[q];
             }
-            w.G[t] = g;
+            if (square) {
+                w.G[r * nr + sc] = g;
+                w.G[sc * nr + r] = g;
+            } else {
+                w.G[t] = g;
+            }
             if (sc == r) {
                 const float R = regc * g;
-                w.Rr[r] = R;
-                w.iAd[r] = 1.0f / (g + R);
+                w.rc4[r].y = R;
+                w.rc4[r].z = 1.0f / (g + R);
             }
         } else {
             const int r = t - npk;
+            const int m = w.tmask[r];
             const float* yr = w.Y[r];
             float bb = 0.0f;
+            if (m & 1) {
 #pragma unroll
-            for (int q = 0; q < d::NV; ++q) bb += yr[q] * w.zz[q];
-            w.b[r] = bb;
+                for (int q = 0; q < NA; ++q) bb += yr[q] * w.zz[q];
+            }
+            if (m & 2) {
+#pragma unroll
+                for (int q = NA; q < 2 * NA; ++q) bb += yr[q] * w.zz[q];
+            }
+            if (m & 4) {
+#pragma unroll
+                for (int q = d::B; q < d::NV; ++q) bb += yr[q] * w.zz[q];
+            }
+            w.rc4[r].x = bb;
         }
     }
     __syncwarp();
     // projected Gauss-Seidel sweeps (normal row, then the tangent pair with
-    // the friction disk |lambda_t| <= mu lambda_n)
-    if (lane == 0) {
+    // the friction disk |lambda_t| <= mu lambda_n).  Lane q holds lambda_q
+    // (and lambda_{q+32}); the three residuals of a contact are one
+    // butterfly reduction of G_rq lambda_q over the lanes, and the tangent
+    // residuals take the normal update through G's normal column.
+    {
+        float lamA = 0.0f, lamB = 0.0f;
+        int width = 1;
+        while (width < nr && width < 32) width <<= 1;
         for (int sw = 0; sw < M.sweeps; ++sw) {
             for (int c = 0; c < nc; ++c) {
                 const int rn = 3 * c;
-                float res = w.b[rn] + w.Rr[rn] * w.lam[rn] - w.vs[rn];
-                for (int q = 0; q < nr; ++q) res += w.G[packed_index(rn, q, nr)] * w.lam[q];
-                const float ln = fmaxf(w.lam[rn] - res * w.iAd[rn], 0.0f);
-                w.lam[rn] = ln;
-                float r1 = w.b[rn + 1] + w.Rr[rn + 1] * w.lam[rn + 1];
-                float r2 = w.b[rn + 2] + w.Rr[rn + 2] * w.lam[rn + 2];
-                for (int q = 0; q < nr; ++q) {
-                    const float lq = w.lam[q];
-                    r1 += w.G[packed_index(rn + 1, q, nr)] * lq;
-                    r2 += w.G[packed_index(rn + 2, q, nr)] * lq;
+                float p0 = 0.0f, p1 = 0.0f, p2 = 0.0f;
+                if (square) {
+                    if (lane < nr) {
+                        p0 = w.G[rn * nr + lane] * lamA;
+                        p1 = w.G[(rn + 1) * nr + lane] * lamA;
+                        p2 = w.G[(rn + 2) * nr + lane] * lamA;
+                    }
+                } else {
+                    if (lane < nr) {
+                        p0 = w.G[packed_index(rn, lane, nr)] * lamA;
+                        p1 = w.G[packed_index(rn + 1, lane, nr)] * lamA;
+                        p2 = w.G[packed_index(rn + 2, lane, nr)] * lamA;
+                    }
+                    if (lane + 32 < nr) {
+                        p0 += w.G[packed_index(rn, lane + 32, nr)] * lamB;
+                        p1 += w.G[packed_index(rn + 1, lane + 32, nr)] * lamB;
+                        p2 += w.G[packed_index(rn + 2, lane + 32, nr)] * lamB;
+                    }
                 }
-                float l1 = w.lam[rn + 1] - r1 * w.iAd[rn + 1];
-                float l2 = w.lam[rn + 2] - r2 * w.iAd[rn + 2];
-                const float nrm = sqrtf(l1 * l1 + l2 * l2), lim = M.mu * ln;
-                if (nrm > lim) {
-                    const float sc = nrm > 0.0f ? lim / nrm : 0.0f;
+                const float4 cN = w.rc4[rn], c1 = w.rc4[rn + 1], c2 = w.rc4[rn + 2];
+                const float g1n = square ? w.G[(rn + 1) * nr + rn] : w.G[packed_index(rn + 1, rn, nr)];
+                const float g2n = square ? w.G[(rn + 2) * nr + rn] : w.G[packed_index(rn + 2, rn, nr)];
+                // lanes >= 32 of the rows sit in lamB of the same lanes, so a
+                // reduction over `width` lanes covers every row
+                for (int off = 1; off < width; off <<= 1) {
+                    p0 += __shfl_xor_sync(FULL, p0, off);
+                    p1 += __shfl_xor_sync(FULL, p1, off);
+                    p2 += __shfl_xor_sync(FULL, p2, off);
+                }
+                const bool hiN = rn >= 32, hi1 = rn + 1 >= 32, hi2 = rn + 2 >= 32;
+                const float ln0 = __shfl_sync(FULL, hiN ? lamB : lamA, rn & 31);
+                const float l10 = __shfl_sync(FULL, hi1 ? lamB : lamA, (rn + 1) & 31);
+                const float l20 = __shfl_sync(FULL, hi2 ? lamB : lamA, (rn + 2) & 31);
+                const float res = cN.x + p0 + cN.y * ln0 - cN.w;
+                const float ln = fmaxf(ln0 - res * cN.z, 0.0f);
+                const float dn = ln - ln0;
+                const float r1 = c1.x + p1 + g1n * dn + c1.y * l10;
+                const float r2 = c2.x + p2 + g2n * dn + c2.y * l20;
+                float l1 = l10 - r1 * c1.z;
+                float l2 = l20 - r2 * c2.z;
+                const float n2 = l1 * l1 + l2 * l2, lim = M.mu * ln;
+                if (n2 > lim * lim) {
+                    const float sc = lim * rsqrtf(n2);
                     l1 *= sc;
                     l2 *= sc;
                 }
-                w.lam[rn + 1] = l1;
-                w.lam[rn + 2] = l2;
+                if (lane == (rn & 31)) {
+                    if (hiN) lamB = ln;
+                    else lamA = ln;
+                }
+                if (lane == ((rn + 1) & 31)) {
+                    if (hi1) lamB = l1;
+                    else lamA = l1;
+                }
+                if (lane == ((rn + 2) & 31)) {
+                    if (hi2) lamB = l2;
+                    else lamA = l2;
+                }
             }
         }
+        if (lane < nr) w.lam[lane] = lamA;
+        if (lane + 32 < nr) w.lam[lane + 32] = lamB;
     }
     __syncwarp();
     // z = z_f + Y^T lambda, then v = L^-T z
