@@ -151,6 +151,62 @@ int mppi_profile_read(mppi_ctx *c, int *n, float *rollout_ms, float *update_ms, 
  * (0 = the library default).  Used by the autotuner. */
 int mppi_set_launch(mppi_ctx *c, int samples_per_cta);
 
+/* ---------------------------------------------------------------- batch */
+/* Many independent controllers advanced together (the paper runs one
+ * optimiser; batching them is this library's serving pattern).  Every
+ * instance has its own model, K, H, lambda, sigma and Philox key; all must
+ * share the arm size n_a.  One iteration of every instance is one
+ * persistent rollout launch -- CTAs take (instance, tile of samples) work
+ * items from a device counter, longest instances first -- and one update
+ * launch with a CTA per (instance, horizon step).  Each instance's result
+ * is bitwise the one mppi_step gives it alone: a sample's rollout is one
+ * warp's work and the update reduces in a fixed order. */
+typedef struct mppi_batch mppi_batch;
+typedef struct {
+    const mppi_model *model; /* kept alive by the caller for the batch's lifetime */
+    int K, H;
+    float lambda;
+    const float *sigma; /* host, nu floats (copied) */
+    uint64_t seed;
+} mppi_batch_desc;
+
+int mppi_batch_create(const mppi_batch_desc *desc, int n, mppi_batch **out);
+int mppi_batch_destroy(mppi_batch *b);
+/* One iteration of every instance: states (host array of n device pointers
+ * to nx floats), u (host array of n device pointers to H_i x nu floats,
+ * updated in place).  Advances each instance's iteration counter. */
+int mppi_batch_step(mppi_batch *b, const float *const *states, float *const *u, void *stream);
+/* The same iteration replayed from a CUDA graph (descriptor copy from a
+ * pinned table, rollout, update) captured on the first call for `stream`
+ * (not the legacy stream).  Passing different pointers than the previous
+ * call synchronises `stream` before the table is rewritten. */
+int mppi_batch_step_graph(mppi_batch *b, const float *const *states, float *const *u, void *stream);
+/* Synchronise; per-instance device status into errors (host, n; optional);
+ * returns the first non-OK status. */
+int mppi_batch_sync(mppi_batch *b, int *errors, void *stream);
+/* Iteration counter of instance i (i = -1 in set: all instances). */
+int mppi_batch_iteration(mppi_batch *b, int i, uint64_t *iteration, void *stream);
+int mppi_batch_set_iteration(mppi_batch *b, int i, uint64_t iteration, void *stream);
+/* Device pointer to instance i's K sample costs of the last iteration. */
+const float *mppi_batch_costs(const mppi_batch *b, int i);
+/* Launch shape: samples (warps) per CTA 1..16; order 0 = as given,
+ * 1 = longest instances first. */
+int mppi_batch_set_launch(mppi_batch *b, int samples_per_cta, int order);
+int mppi_batch_get_launch(const mppi_batch *b, int *samples_per_cta, int *order);
+/* Autotuner: times `reps` iterations of every shape (samples per CTA in
+ * {1,2,4,8} x both orders) on the given buffers (u is modified: pass
+ * scratch copies), keeps the fastest, restores the iteration counters and
+ * appends the choice to the tuning table under a key of (nv, box-count
+ * bucket, instances, total K, longest H); mppi_batch_create applies a
+ * stored choice for its key.  best_ms (optional): time of one iteration. */
+int mppi_batch_autotune(mppi_batch *b, const float *const *states, float *const *u, int reps, void *stream,
+                        float *best_ms);
+/* Tuning table: text file of "key spc order ms" lines at $MPPI_TUNE_FILE
+ * (default ~/.cache/mppi_tune.txt); the last entry of a key wins.  Host
+ * only; no GPU needed. */
+int mppi_tune_store(const char *key, int samples_per_cta, int order, float ms);
+int mppi_tune_lookup(const char *key, int *samples_per_cta, int *order);
+
 /* --------------------------------------------------------------- no-alloc */
 /* The paper has no counterpart to this entry point; it exists for callers
  * that cannot allocate device memory when they plan -- a real-time control

@@ -23,6 +23,7 @@
 #include "../../include/mppi.h"
 #include "mppi_device.cuh"
 #include "mppi_internal.h"
+#include "mppi_kernels.cuh"
 
 using namespace mppi;
 
@@ -40,211 +41,40 @@ __global__ void __launch_bounds__(512) rollout_kernel(RolloutArgs args) {
     const int unom_n = (MODE == 1 && args.stage_unom) ? args.H * d::NU : 0;
     const size_t ws_off = sizeof(DevModel) + ((size_t)unom_n * sizeof(float) + 15) / 16 * 16;
     WarpWS<NA>* wsb = reinterpret_cast<WarpWS<NA>*>(smem + ws_off);
-
-    {  // stage the model (and u_nom) in shared memory
-        const float4* src = reinterpret_cast<const float4*>(args.model);
-        float4* dst = reinterpret_cast<float4*>(smem);
-        for (int t = threadIdx.x; t < (int)(sizeof(DevModel) / 16); t += blockDim.x) dst[t] = src[t];
-        for (int t = threadIdx.x; t < unom_n; t += blockDim.x) unom_s[t] = args.u_nom[t];
-    }
+    stage_model(smem, args.model, unom_s, args.u_nom, unom_n);
     __syncthreads();
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int k = blockIdx.x * (blockDim.x >> 5) + warp;
     if (k >= args.n) return;
-    WarpWS<NA>& w = wsb[warp];
-    const float* x = args.states + (size_t)k * args.state_stride;
-    if (lane < d::NQ) w.q[lane] = x[lane];
-    if (lane < d::NV) w.qd[lane] = x[d::NQ + lane];
-    uint32_t iter = 0;
-    uint2 key = make_uint2(0, 0);
-    float sig = 0.0f, lo = 0.0f, hi = 0.0f;
+    SampleIO io{};
+    io.x = args.states + (size_t)k * args.state_stride;
+    io.k = k;
+    io.H = args.H;
+    io.err = args.err;
+    io.stats = args.stats;
+    io.x_out = args.states_out ? args.states_out + (size_t)k * d::NX : nullptr;
     if (MODE == 1) {
-        iter = (uint32_t)(args.iter_ptr ? *args.iter_ptr : args.iter_val);
-        key = make_uint2((uint32_t)args.seed, (uint32_t)(args.seed >> 32));
+        io.unom = unom_n ? unom_s : args.u_nom;
+        io.iter = (uint32_t)(args.iter_ptr ? *args.iter_ptr : args.iter_val);
+        io.key = make_uint2((uint32_t)args.seed, (uint32_t)(args.seed >> 32));
         if (lane < d::NU) {
-            sig = args.sigma[lane];
-            lo = M.link[lane / NA][lane % NA].u_lo;
-            hi = M.link[lane / NA][lane % NA].u_hi;
+            io.sig = args.sigma[lane];
+            io.lo = M.link[lane / NA][lane % NA].u_lo;
+            io.hi = M.link[lane / NA][lane % NA].u_hi;
         }
+    } else {
+        io.U = args.U + (size_t)k * args.H * d::NU;
     }
-    __syncwarp();
-    float cost = 0.0f;
-    const float* gb = M.goal;
-    unsigned n_exact = 0, n_con = 0;
-    for (int h = 0; h < args.H; ++h) {
-        if (MODE == 1) {
-            // every 8 steps the 32 lanes draw one Philox block each: 8 steps x
-            // 16 controls of standard normals (the same values sample_control
-            // draws one at a time)
-            if ((h & 7) == 0) {
-                const int jb = lane & 3, hs = h + (lane >> 2);
-                if (4 * jb < d::NU && hs < args.H) {
-                    const uint4 wv = philox4x32_10(make_uint4((uint32_t)jb, (uint32_t)hs, (uint32_t)k, iter), key);
-#pragma unroll
-                    for (int t = 0; t < 4; ++t) w.zn[lane >> 2][4 * jb + t] = block_normal(wv, t);
-                }
-                __syncwarp();
-            }
-            if (lane < d::NU) {
-                const float un = unom_n ? unom_s[h * d::NU + lane] : args.u_nom[h * d::NU + lane];
-                w.u[lane] = fminf(fmaxf(__fmaf_rn(sig, w.zn[h & 7][lane], un), lo), hi);
-            }
-        } else if (lane < d::NU) {
-            w.u[lane] = args.U[((size_t)k * args.H + h) * d::NU + lane];
-        }
-        forward_kinematics<NA>(M, w, lane);
-        __syncwarp();
-        if (h > 0 && lane == 0 && M.w_grasp != 0.0f) cost += M.w_grasp * grasp_term<NA>(w);
-        n_exact += collide<NA>(M, w, lane);
-        __syncwarp();
-        n_con += w.ncon;
-        dynamics<NA>(M, w, lane, args.err);
-        contacts<NA>(M, w, lane);
-        integrate<NA>(M, w, lane);
-        if (lane == 0) {
-            const float* pb = &w.q[d::B];
-            const float e0 = pb[0] - gb[0], e1 = pb[1] - gb[1], e2 = pb[2] - gb[2];
-            float uu = 0.0f;
-#pragma unroll
-            for (int j = 0; j < d::NU; ++j) uu += w.u[j] * w.u[j];
-            cost += M.w_goal * (e0 * e0 + e1 * e1 + e2 * e2) + M.w_u * uu + M.w_pen * w.pen_all +
-                    M.w_obst * w.pen_box;
-        }
-        __syncwarp();
-    }
-    if (M.w_grasp != 0.0f) {
-        forward_kinematics<NA>(M, w, lane);
-        __syncwarp();
-        if (lane == 0) cost += M.w_grasp * grasp_term<NA>(w);
-    }
-    // a non-finite state poisons the sample's cost (weight 0 in the update)
-    const bool bad = (lane < d::NQ && !isfinite(w.q[lane])) || (lane < d::NV && !isfinite(w.qd[lane]));
-    if (__any_sync(FULL, bad)) cost = __int_as_float(0x7fc00000);
-    if (lane == 0) {
-        args.costs[k] = cost;
-        if (!isfinite(cost)) atomicOr(args.err, ERRB_NONFINITE);
-    }
-    if (args.stats) {
-        if (lane == 0) {
-            atomicAdd(&args.stats[0], (unsigned long long)args.H);
-            atomicAdd(&args.stats[1], (unsigned long long)n_con);
-            atomicAdd(&args.stats[2], (unsigned long long)n_exact);
-        }
-    }
-    if (args.states_out) {
-        float* xo = args.states_out + (size_t)k * d::NX;
-        if (lane < d::NQ) xo[lane] = w.q[lane];
-        if (lane < d::NV) xo[d::NQ + lane] = w.qd[lane];
-    }
+    const float cost = rollout_sample<NA, MODE>(M, wsb[warp], lane, io);
+    if (lane == 0) args.costs[k] = cost;
 }
 
 template <int NU>
 __global__ void __launch_bounds__(256) update_kernel(UpdateArgs a) {
-    constexpr int T = 256;
-    __shared__ float red[NU + 1][T];
-    __shared__ float rmin[T];
-    __shared__ int ridx[T];
-    __shared__ int is_last;
-    const int h = blockIdx.x, tid = threadIdx.x;
-    const uint32_t iter = (uint32_t)(a.iter_ptr ? *a.iter_ptr : a.iter_val);
-    const uint2 key = make_uint2((uint32_t)a.seed, (uint32_t)(a.seed >> 32));
-    // (1) lowest finite cost (first index among equals)
-    float cm = INFINITY;
-    int ci = 0x7fffffff;
-    for (int k = tid; k < a.K; k += T) {
-        const float c = a.costs[k];
-        if (isfinite(c) && (c < cm)) {
-            cm = c;
-            ci = k;
-        }
-    }
-    rmin[tid] = cm;
-    ridx[tid] = ci;
-    __syncthreads();
-    for (int s = T / 2; s > 0; s >>= 1) {
-        if (tid < s) {
-            const float o = rmin[tid + s];
-            const int oi = ridx[tid + s];
-            if (o < rmin[tid] || (o == rmin[tid] && oi < ridx[tid])) {
-                rmin[tid] = o;
-                ridx[tid] = oi;
-            }
-        }
-        __syncthreads();
-    }
-    const float cmin = rmin[0];
-    const int cidx = ridx[0];
-    __syncthreads();
-    const bool any = isfinite(cmin);
-    // (2) weighted sums with regenerated samples
-    float acc[NU];
-#pragma unroll
-    for (int j = 0; j < NU; ++j) acc[j] = 0.0f;
-    float Z = 0.0f;
-    float un[NU], sg[NU], lo[NU], hi[NU];
-#pragma unroll
-    for (int j = 0; j < NU; ++j) {
-        un[j] = a.u_nom[h * NU + j];
-        sg[j] = a.sigma[j];
-        lo[j] = a.u_lo[j];
-        hi[j] = a.u_hi[j];
-    }
-    if (any) {
-        const float inv_lam = 1.0f / a.lambda;
-        for (int k = tid; k < a.K; k += T) {
-            const float c = a.costs[k];
-            const float wk = isfinite(c) ? expf(-(c - cmin) * inv_lam) : 0.0f;
-            Z += wk;
-#pragma unroll
-            for (int jb = 0; jb < (NU + 3) / 4; ++jb) {
-                const uint4 wv = philox4x32_10(make_uint4((uint32_t)jb, (uint32_t)h, (uint32_t)k, iter), key);
-#pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    const int j = 4 * jb + t;
-                    if (j < NU) {
-                        const float z = block_normal(wv, t);
-                        const float u = fminf(fmaxf(__fmaf_rn(sg[j], z, un[j]), lo[j]), hi[j]);
-                        acc[j] += wk * u;
-                    }
-                }
-            }
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < NU; ++j) red[j][tid] = acc[j];
-    red[NU][tid] = Z;
-    __syncthreads();
-    for (int s = T / 2; s > 0; s >>= 1) {
-        if (tid < s) {
-#pragma unroll
-            for (int j = 0; j <= NU; ++j) red[j][tid] += red[j][tid + s];
-        }
-        __syncthreads();
-    }
-    if (tid < NU) a.u_out[h * NU + tid] = any ? red[tid][0] / red[NU][0] : un[tid];
-    if (h == 0 && tid == 0) {
-        if (!any) atomicOr(a.err, ERRB_NONFINITE);
-        if (a.best) {
-            a.best[0] = cmin;
-            a.best[1] = (float)cidx;
-        }
-    }
-    // last CTA to finish advances the iteration counter (no waiting)
-    if (a.advance) {
-        __syncthreads();
-        if (tid == 0) {
-            __threadfence();
-            const unsigned t = atomicAdd(a.done, 1u);
-            is_last = (t == gridDim.x - 1);
-        }
-        __syncthreads();
-        if (is_last && tid == 0) {
-            *a.done = 0u;
-            *a.iter_ptr += 1ull;
-            __threadfence();
-        }
-    }
+    __shared__ UpdateSmem<NU> sm;
+    update_step<NU>(a, blockIdx.x, sm);
+    update_finish<NU>(a, gridDim.x, sm);
 }
 
 template <int NU>
@@ -450,6 +280,15 @@ struct mppi_ctx {
     std::vector<cudaEvent_t> prof_ev;  // 3 per recorded iteration
     unsigned long long* d_stats = nullptr;
 };
+
+namespace mppi {
+const DevModel* model_device(const mppi_model* m) { return m ? m->dev : nullptr; }
+void model_bounds(const mppi_model* m, int j, float* lo, float* hi) {
+    const int na = m->info.na;
+    *lo = m->host.link[j / na][j % na].u_lo;
+    *hi = m->host.link[j / na][j % na].u_hi;
+}
+}  // namespace mppi
 
 extern "C" {
 

@@ -1,0 +1,626 @@
+// Batched MPPI: many independent controllers (uneven K, H and obstacle
+// counts, same arm model size) advanced by one persistent rollout launch and
+// one update launch per iteration, optionally replayed from a CUDA graph,
+// with an autotuner for the launch shape (see include/mppi.h).
+#include <cuda_runtime.h>
+#include <sys/stat.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/mppi.h"
+#include "mppi_device.cuh"
+#include "mppi_internal.h"
+#include "mppi_kernels.cuh"
+
+using namespace mppi;
+
+namespace mppi {
+
+struct BatchInst {
+    const DevModel* model;
+    const float* state;
+    float* u;  // nominal controls, updated in place
+    float* costs;
+    const float* sigma;
+    const float* u_lo;
+    const float* u_hi;
+    unsigned long long* iter;
+    unsigned int* done;
+    int* err;
+    float* best;
+    unsigned long long seed;
+    int K, H;
+    float lambda;
+    int stage_unom;
+};
+
+struct BatchTile {
+    int inst, k0;
+};
+
+struct BatchCtl {
+    unsigned int next;    // next tile to take
+    unsigned int exited;  // CTAs that finished
+};
+
+// Persistent rollout: each CTA takes (instance, tile of samples-per-CTA
+// samples) work items from a counter until none are left.  The model and
+// u_nom of the tile's instance are staged when the instance changes.  The
+// last CTA out resets the counters for the next launch (no CTA waits).
+template <int NA>
+__global__ void __launch_bounds__(512) batch_rollout_kernel(const BatchInst* insts, const BatchTile* tiles,
+                                                             int ntiles, BatchCtl* ctl, int max_unom) {
+    using d = Dims<NA>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_tile;
+    DevModel& M = *reinterpret_cast<DevModel*>(smem);
+    float* unom_s = reinterpret_cast<float*>(smem + sizeof(DevModel));
+    WarpWS<NA>* wsb =
+        reinterpret_cast<WarpWS<NA>*>(smem + sizeof(DevModel) + ((size_t)max_unom * sizeof(float) + 15) / 16 * 16);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int staged = -1;
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = (int)atomicAdd(&ctl->next, 1u);
+        __syncthreads();
+        const int t = s_tile;
+        if (t >= ntiles) break;
+        const BatchTile tl = tiles[t];
+        const BatchInst& I = insts[tl.inst];
+        const int unom_n = I.stage_unom ? I.H * d::NU : 0;
+        if (tl.inst != staged) {
+            stage_model(smem, I.model, unom_s, I.u, unom_n);
+            staged = tl.inst;
+        }
+        __syncthreads();
+        const int k = tl.k0 + warp;
+        if (k < I.K) {
+            SampleIO io{};
+            io.x = I.state;
+            io.k = k;
+            io.H = I.H;
+            io.err = I.err;
+            io.unom = unom_n ? unom_s : I.u;
+            io.iter = (uint32_t)(*I.iter);
+            io.key = make_uint2((uint32_t)I.seed, (uint32_t)(I.seed >> 32));
+            if (lane < d::NU) {
+                io.sig = I.sigma[lane];
+                io.lo = I.u_lo[lane];
+                io.hi = I.u_hi[lane];
+            }
+            const float cost = rollout_sample<NA, 1>(M, wsb[warp], lane, io);
+            if (lane == 0) I.costs[k] = cost;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned e = atomicAdd(&ctl->exited, 1u);
+        if (e == gridDim.x - 1) {
+            ctl->next = 0u;
+            ctl->exited = 0u;
+            __threadfence();
+        }
+    }
+}
+
+// One CTA per (instance, horizon step); each instance's last CTA advances
+// that instance's iteration counter.
+template <int NU>
+__global__ void __launch_bounds__(256) batch_update_kernel(const BatchInst* insts, const int2* rows) {
+    __shared__ UpdateSmem<NU> sm;
+    const int2 r = rows[blockIdx.x];
+    const BatchInst& I = insts[r.x];
+    UpdateArgs a{};
+    a.K = I.K;
+    a.costs = I.costs;
+    a.u_nom = I.u;
+    a.u_out = I.u;
+    a.sigma = I.sigma;
+    a.u_lo = I.u_lo;
+    a.u_hi = I.u_hi;
+    a.lambda = I.lambda;
+    a.seed = I.seed;
+    a.iter_ptr = I.iter;
+    a.err = I.err;
+    a.best = I.best;
+    a.advance = 1;
+    a.done = I.done;
+    update_step<NU>(a, r.y, sm);
+    update_finish<NU>(a, I.H, sm);
+}
+
+}  // namespace mppi
+
+// ---------------------------------------------------------------------------
+// autotuner table: "key spc order ms" lines in a text file
+// ---------------------------------------------------------------------------
+namespace {
+
+std::mutex g_tune_mu;
+
+std::string tune_path() {
+    const char* p = std::getenv("MPPI_TUNE_FILE");
+    if (p && *p) return p;
+    const char* home = std::getenv("HOME");
+    return std::string(home && *home ? home : "/tmp") + "/.cache/mppi_tune.txt";
+}
+
+}  // namespace
+
+extern "C" int mppi_tune_lookup(const char* key, int* spc, int* order) {
+    if (!key || !spc || !order) return MPPI_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    FILE* f = std::fopen(tune_path().c_str(), "r");
+    if (!f) return MPPI_ERR_INVALID_ARG;
+    char k[256];
+    int s = 0, o = 0;
+    float ms = 0.0f;
+    int found = MPPI_ERR_INVALID_ARG;
+    while (std::fscanf(f, "%255s %d %d %f", k, &s, &o, &ms) == 4) {
+        if (std::strcmp(k, key) == 0) {  // the last entry for a key wins
+            *spc = s;
+            *order = o;
+            found = MPPI_OK;
+        }
+    }
+    std::fclose(f);
+    return found;
+}
+
+extern "C" int mppi_tune_store(const char* key, int spc, int order, float ms) {
+    if (!key || !*key || std::strlen(key) > 255 || std::strchr(key, ' ') || spc < 1 || spc > 16 || order < 0 ||
+        order > 1)
+        return MPPI_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    const std::string path = tune_path();
+    const size_t slash = path.find_last_of('/');
+    if (slash != std::string::npos) {
+        const std::string dir = path.substr(0, slash);  // create it without a shell
+        for (size_t i = 1; i <= dir.size(); ++i)
+            if (i == dir.size() || dir[i] == '/') {
+                std::string part = dir.substr(0, i);
+                FILE* probe = std::fopen((part + "/.").c_str(), "r");
+                if (probe) std::fclose(probe);
+                else mkdir(part.c_str(), 0755);
+            }
+    }
+    FILE* f = std::fopen(path.c_str(), "a");
+    if (!f) return MPPI_ERR_INVALID_ARG;
+    std::fprintf(f, "%s %d %d %.6f\n", key, spc, order, ms);
+    std::fclose(f);
+    return MPPI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batch handle
+// ---------------------------------------------------------------------------
+struct mppi_batch {
+    int n = 0, na = 0, nu = 0, max_h = 0, spc = 4, order = 1;
+    std::vector<mppi_batch_desc> desc;
+    std::vector<BatchInst> host;  // device pointers per instance (pinned copy below)
+    BatchInst* h_pinned = nullptr;
+    BatchInst* d_insts = nullptr;
+    BatchTile* d_tiles = nullptr;
+    int ntiles = 0;
+    int2* d_rows = nullptr;
+    int nrows = 0;
+    BatchCtl* d_ctl = nullptr;
+    float* d_pool = nullptr;  // costs, sigma, bounds, best (per instance)
+    unsigned long long* d_iter = nullptr;
+    unsigned int* d_done = nullptr;
+    int* d_err = nullptr;
+    int grid = 0;
+    size_t smem = 0;
+    std::string key;
+    cudaGraphExec_t gexec = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaStream_t gstream = nullptr;
+};
+
+namespace {
+
+int cuda_rc(cudaError_t e) {
+    if (e == cudaSuccess) return MPPI_OK;
+    if (e == cudaErrorMemoryAllocation) return MPPI_ERR_OOM;
+    return MPPI_ERR_CUDA;
+}
+
+template <int NA>
+size_t batch_smem(int spc, int max_unom) {
+    return sizeof(DevModel) + ((size_t)max_unom * sizeof(float) + 15) / 16 * 16 + (size_t)spc * sizeof(WarpWS<NA>);
+}
+
+template <int NA>
+int batch_shape(mppi_batch* b) {
+    const int max_unom = b->max_h * Dims<NA>::NU <= 2048 ? b->max_h * Dims<NA>::NU : 0;
+    b->smem = batch_smem<NA>(b->spc, max_unom);
+    auto fn = batch_rollout_kernel<NA>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
+    if (e != cudaSuccess) return cuda_rc(e);
+    int per_sm = 0, dev = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, b->spc * 32, b->smem);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_rc(e);
+    b->grid = std::max(1, per_sm) * sms;
+    return MPPI_OK;
+}
+
+// Tile table for the current shape: instance order is either as given or
+// longest-first (estimated work H x (1 + boxes/4) x K, largest first), and
+// tiles of one instance stay contiguous.
+int build_tiles(mppi_batch* b) {
+    std::vector<int> ord(b->n);
+    std::iota(ord.begin(), ord.end(), 0);
+    if (b->order == 1) {
+        std::vector<double> work(b->n);
+        for (int i = 0; i < b->n; ++i) {
+            int nb = 0;
+            mppi_model_dims(b->desc[i].model, nullptr, nullptr, nullptr, &nb);
+            work[i] = (double)b->desc[i].H * (1.0 + nb / 4.0) * b->desc[i].K;
+        }
+        std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return work[x] > work[y]; });
+    }
+    std::vector<BatchTile> tiles;
+    for (int i : ord)
+        for (int k0 = 0; k0 < b->desc[i].K; k0 += b->spc) tiles.push_back({i, k0});
+    if (b->d_tiles) cudaFree(b->d_tiles);
+    b->d_tiles = nullptr;
+    b->ntiles = (int)tiles.size();
+    cudaError_t e = cudaMalloc(&b->d_tiles, tiles.size() * sizeof(BatchTile));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_tiles, tiles.data(), tiles.size() * sizeof(BatchTile), cudaMemcpyHostToDevice);
+    return cuda_rc(e);
+}
+
+int reshape(mppi_batch* b) {
+    int rc = b->na == 3 ? batch_shape<3>(b) : batch_shape<7>(b);
+    if (rc != MPPI_OK) return rc;
+    rc = build_tiles(b);
+    if (rc != MPPI_OK) return rc;
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->gexec = nullptr;
+    b->graph = nullptr;
+    return MPPI_OK;
+}
+
+int enqueue_batch(mppi_batch* b, cudaStream_t s) {
+    const int max_unom = b->max_h * 2 * b->na <= 2048 ? b->max_h * 2 * b->na : 0;
+    if (b->na == 3)
+        batch_rollout_kernel<3><<<b->grid, b->spc * 32, b->smem, s>>>(b->d_insts, b->d_tiles, b->ntiles, b->d_ctl,
+                                                                       max_unom);
+    else
+        batch_rollout_kernel<7><<<b->grid, b->spc * 32, b->smem, s>>>(b->d_insts, b->d_tiles, b->ntiles, b->d_ctl,
+                                                                       max_unom);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_rc(e);
+    if (b->nu == 6) batch_update_kernel<6><<<b->nrows, 256, 0, s>>>(b->d_insts, b->d_rows);
+    else batch_update_kernel<14><<<b->nrows, 256, 0, s>>>(b->d_insts, b->d_rows);
+    return cuda_rc(cudaGetLastError());
+}
+
+// Write the caller's state and control pointers into the host descriptor
+// table; returns whether any changed.
+bool stage_pointers(mppi_batch* b, const float* const* states, float* const* u) {
+    bool changed = false;
+    for (int i = 0; i < b->n; ++i) {
+        if (b->host[i].state != states[i] || b->host[i].u != u[i]) changed = true;
+        b->host[i].state = states[i];
+        b->host[i].u = u[i];
+    }
+    return changed;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mppi_batch_destroy(mppi_batch* b) {
+    if (!b) return MPPI_OK;
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    cudaFreeHost(b->h_pinned);
+    cudaFree(b->d_insts);
+    cudaFree(b->d_tiles);
+    cudaFree(b->d_rows);
+    cudaFree(b->d_ctl);
+    cudaFree(b->d_pool);
+    cudaFree(b->d_iter);
+    cudaFree(b->d_done);
+    cudaFree(b->d_err);
+    delete b;
+    return MPPI_OK;
+}
+
+int mppi_batch_create(const mppi_batch_desc* desc, int n, mppi_batch** out) {
+    if (!desc || !out || n < 1 || n > 65536) return MPPI_ERR_INVALID_ARG;
+    *out = nullptr;
+    int nq0 = 0;
+    mppi_model_dims(desc[0].model, &nq0, nullptr, nullptr, nullptr);
+    const int na = (nq0 - 7) / 2;
+    if (na != 3 && na != 7) return MPPI_ERR_UNSUPPORTED;
+    for (int i = 0; i < n; ++i) {
+        int nq = 0;
+        if (!desc[i].model || !desc[i].sigma || desc[i].K < 1 || desc[i].K > (1 << 20) || desc[i].H < 1 ||
+            desc[i].H > 1024 || !(desc[i].lambda > 0.0f))
+            return MPPI_ERR_INVALID_ARG;
+        mppi_model_dims(desc[i].model, &nq, nullptr, nullptr, nullptr);
+        if (nq != nq0) return MPPI_ERR_INVALID_ARG;
+    }
+    mppi_batch* b = new (std::nothrow) mppi_batch();
+    if (!b) return MPPI_ERR_OOM;
+    b->n = n;
+    b->na = na;
+    b->nu = 2 * na;
+    b->desc.assign(desc, desc + n);
+    for (int i = 0; i < n; ++i) b->max_h = std::max(b->max_h, desc[i].H);
+    // per instance: costs K, sigma/lo/hi 3 x 16, best 2 (floats)
+    std::vector<size_t> off(n);
+    size_t total = 0;
+    for (int i = 0; i < n; ++i) {
+        off[i] = total;
+        total += ((size_t)desc[i].K + 48 + 2 + 63) / 64 * 64;
+    }
+    cudaError_t e = cudaMalloc(&b->d_pool, total * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_iter, n * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_done, n * sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_err, n * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_insts, n * sizeof(BatchInst));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_ctl, sizeof(BatchCtl));
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_pinned, n * sizeof(BatchInst));
+    if (e == cudaSuccess) e = cudaMemset(b->d_iter, 0, n * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(b->d_done, 0, n * sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemset(b->d_err, 0, n * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(b->d_ctl, 0, sizeof(BatchCtl));
+    if (e != cudaSuccess) {
+        mppi_batch_destroy(b);
+        return cuda_rc(e);
+    }
+    std::vector<float> params(48);
+    b->host.resize(n);
+    std::vector<int2> rows;
+    for (int i = 0; i < n; ++i) {
+        const mppi_batch_desc& dsc = desc[i];
+        float* base = b->d_pool + off[i];
+        BatchInst& I = b->host[i];
+        std::memset(&I, 0, sizeof I);
+        I.model = model_device(dsc.model);
+        I.costs = base;
+        I.sigma = base + dsc.K;
+        I.u_lo = base + dsc.K + 16;
+        I.u_hi = base + dsc.K + 32;
+        I.best = base + dsc.K + 48;
+        I.iter = b->d_iter + i;
+        I.done = b->d_done + i;
+        I.err = b->d_err + i;
+        I.seed = dsc.seed;
+        I.K = dsc.K;
+        I.H = dsc.H;
+        I.lambda = dsc.lambda;
+        I.stage_unom = dsc.H * b->nu <= 2048;
+        std::fill(params.begin(), params.end(), 0.0f);
+        for (int j = 0; j < b->nu; ++j) {
+            params[j] = dsc.sigma[j];
+            model_bounds(dsc.model, j, &params[16 + j], &params[32 + j]);
+        }
+        e = cudaMemcpy(base + dsc.K, params.data(), 48 * sizeof(float), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            mppi_batch_destroy(b);
+            return cuda_rc(e);
+        }
+        for (int h = 0; h < dsc.H; ++h) rows.push_back(make_int2(i, h));
+    }
+    b->nrows = (int)rows.size();
+    e = cudaMalloc(&b->d_rows, rows.size() * sizeof(int2));
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_rows, rows.data(), rows.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        mppi_batch_destroy(b);
+        return cuda_rc(e);
+    }
+    // autotuner key: arm size, box-count bucket, total samples, longest horizon
+    int boxes = 0;
+    long long ksum = 0;
+    for (int i = 0; i < n; ++i) {
+        int nb = 0;
+        mppi_model_dims(desc[i].model, nullptr, nullptr, nullptr, &nb);
+        boxes = std::max(boxes, nb);
+        ksum += desc[i].K;
+    }
+    char key[128];
+    std::snprintf(key, sizeof key, "nv%d_nb%d_n%d_K%lld_H%d", 2 * na + 6, boxes <= 0 ? 0 : (boxes <= 8 ? 8 : 16), n,
+                  ksum, b->max_h);
+    b->key = key;
+    int spc = 0, order = 0;
+    if (mppi_tune_lookup(key, &spc, &order) == MPPI_OK) {
+        b->spc = spc;
+        b->order = order;
+    }
+    int rc = reshape(b);
+    if (rc != MPPI_OK) {
+        mppi_batch_destroy(b);
+        return rc;
+    }
+    *out = b;
+    return MPPI_OK;
+}
+
+int mppi_batch_set_launch(mppi_batch* b, int spc, int order) {
+    if (!b || spc < 1 || spc > 16 || order < 0 || order > 1) return MPPI_ERR_INVALID_ARG;
+    b->spc = spc;
+    b->order = order;
+    return reshape(b);
+}
+
+int mppi_batch_get_launch(const mppi_batch* b, int* spc, int* order) {
+    if (!b) return MPPI_ERR_INVALID_ARG;
+    if (spc) *spc = b->spc;
+    if (order) *order = b->order;
+    return MPPI_OK;
+}
+
+int mppi_batch_step(mppi_batch* b, const float* const* states, float* const* u, void* stream) {
+    if (!b || !states || !u) return MPPI_ERR_INVALID_ARG;
+    for (int i = 0; i < b->n; ++i)
+        if (!states[i] || !u[i]) return MPPI_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    stage_pointers(b, states, u);
+    cudaError_t e = cudaMemcpyAsync(b->d_insts, b->host.data(), b->n * sizeof(BatchInst), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_rc(e);
+    return enqueue_batch(b, s);
+}
+
+int mppi_batch_step_graph(mppi_batch* b, const float* const* states, float* const* u, void* stream) {
+    if (!b || !states || !u || !stream) return MPPI_ERR_INVALID_ARG;
+    for (int i = 0; i < b->n; ++i)
+        if (!states[i] || !u[i]) return MPPI_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    stage_pointers(b, states, u);
+    // the graph's copy node reads the pinned table when it executes: rewrite
+    // it only when its content changes, after any launch in flight is done
+    const bool changed = std::memcmp(b->h_pinned, b->host.data(), b->n * sizeof(BatchInst)) != 0;
+    if (changed) {
+        if (b->gexec) {
+            cudaError_t e = cudaStreamSynchronize(b->gstream);
+            if (e != cudaSuccess) return cuda_rc(e);
+        }
+        std::memcpy(b->h_pinned, b->host.data(), b->n * sizeof(BatchInst));
+    }
+    if (!b->gexec || b->gstream != s) {
+        if (b->gexec) cudaGraphExecDestroy(b->gexec);
+        if (b->graph) cudaGraphDestroy(b->graph);
+        b->gexec = nullptr;
+        b->graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_rc(e);
+        e = cudaMemcpyAsync(b->d_insts, b->h_pinned, b->n * sizeof(BatchInst), cudaMemcpyHostToDevice, s);
+        int rc = e == cudaSuccess ? enqueue_batch(b, s) : cuda_rc(e);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(s, &g);
+        if (rc != MPPI_OK || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return rc != MPPI_OK ? rc : cuda_rc(e);
+        }
+        e = cudaGraphInstantiate(&b->gexec, g, 0);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(g);
+            return cuda_rc(e);
+        }
+        b->graph = g;
+        b->gstream = s;
+    }
+    return cuda_rc(cudaGraphLaunch(b->gexec, s));
+}
+
+int mppi_batch_sync(mppi_batch* b, int* errors, void* stream) {
+    if (!b) return MPPI_ERR_INVALID_ARG;
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_rc(e);
+    std::vector<int> err(b->n);
+    e = cudaMemcpy(err.data(), b->d_err, b->n * sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(b->d_err, 0, b->n * sizeof(int));
+    if (e != cudaSuccess) return cuda_rc(e);
+    int worst = MPPI_OK;
+    for (int i = 0; i < b->n; ++i) {
+        const int c = (err[i] & ERRB_TIMEOUT) ? MPPI_ERR_TIMEOUT
+                      : (err[i] & ERRB_CHOLESKY) ? MPPI_ERR_CHOLESKY
+                      : (err[i] & ERRB_NONFINITE) ? MPPI_ERR_NONFINITE
+                                                  : MPPI_OK;
+        if (errors) errors[i] = c;
+        if (c != MPPI_OK && worst == MPPI_OK) worst = c;
+    }
+    return worst;
+}
+
+int mppi_batch_iteration(mppi_batch* b, int i, uint64_t* it, void* stream) {
+    if (!b || i < 0 || i >= b->n || !it) return MPPI_ERR_INVALID_ARG;
+    unsigned long long v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, b->d_iter + i, sizeof v, cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_rc(e);
+    *it = v;
+    return MPPI_OK;
+}
+
+int mppi_batch_set_iteration(mppi_batch* b, int i, uint64_t it, void* stream) {
+    if (!b || i < -1 || i >= b->n) return MPPI_ERR_INVALID_ARG;
+    std::vector<unsigned long long> v(b->n, (unsigned long long)it);
+    cudaError_t e;
+    if (i < 0)
+        e = cudaMemcpyAsync(b->d_iter, v.data(), b->n * sizeof(unsigned long long), cudaMemcpyHostToDevice,
+                            (cudaStream_t)stream);
+    else
+        e = cudaMemcpyAsync(b->d_iter + i, v.data(), sizeof(unsigned long long), cudaMemcpyHostToDevice,
+                            (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    return cuda_rc(e);
+}
+
+const float* mppi_batch_costs(const mppi_batch* b, int i) {
+    if (!b || i < 0 || i >= b->n) return nullptr;
+    return b->host[i].costs;
+}
+
+int mppi_batch_autotune(mppi_batch* b, const float* const* states, float* const* u, int reps, void* stream,
+                        float* best_ms) {
+    if (!b || !states || !u || reps < 1 || !stream) return MPPI_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<unsigned long long> iters(b->n);
+    cudaError_t e = cudaMemcpyAsync(iters.data(), b->d_iter, b->n * sizeof(unsigned long long),
+                                    cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_rc(e);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int bs = b->spc, bo = b->order;
+    const int spcs[4] = {1, 2, 4, 8};
+    int rc = MPPI_OK;
+    for (int si = 0; si < 4 && rc == MPPI_OK; ++si)
+        for (int o = 0; o < 2 && rc == MPPI_OK; ++o) {
+            b->spc = spcs[si];
+            b->order = o;
+            rc = reshape(b);
+            if (rc != MPPI_OK) break;
+            rc = mppi_batch_step(b, states, u, stream);  // warm-up
+            if (rc != MPPI_OK) break;
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < reps && rc == MPPI_OK; ++r) rc = mppi_batch_step(b, states, u, stream);
+            cudaEventRecord(e1, s);
+            e = cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) rc = cuda_rc(e);
+            ms /= reps;
+            if (ms < best) {
+                best = ms;
+                bs = spcs[si];
+                bo = o;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->spc = bs;
+    b->order = bo;
+    if (rc == MPPI_OK) rc = reshape(b);
+    // the tuning iterations do not count: restore the counters
+    if (rc == MPPI_OK) {
+        e = cudaMemcpyAsync(b->d_iter, iters.data(), b->n * sizeof(unsigned long long), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = cuda_rc(e);
+    }
+    if (rc == MPPI_OK) mppi_tune_store(b->key.c_str(), bs, bo, best);
+    if (best_ms) *best_ms = best;
+    return rc;
+}
+
+}  // extern "C"

@@ -62,6 +62,13 @@ struct NoiseArgs {
     float* eps;
 };
 
+// accessors of the opaque model handle for the other translation units
+}  // namespace mppi
+struct mppi_model;
+namespace mppi {
+const DevModel* model_device(const mppi_model* m);
+void model_bounds(const mppi_model* m, int j, float* lo, float* hi);
+
 int parse_model_blob(const void* blob, size_t len, DevModel* out, HostModelInfo* info);
 int launch_rollout(int na, int mode, const RolloutArgs& a, int spc, cudaStream_t s);
 int launch_update(int nu, const UpdateArgs& a, int H, cudaStream_t s);

@@ -115,6 +115,19 @@ def lib():
     _decl(L, "mppi_sync", i, [vp, vp])
     _decl(L, "mppi_set_launch", i, [vp, i])
     _decl(L, "mppi_step_noalloc", i, [vp, sz, i, i, C.c_float, fp, u64, u64, fp, fp, fp, C.POINTER(i), vp])
+    _decl(L, "mppi_batch_create", i, [vp, i, C.POINTER(vp)])
+    _decl(L, "mppi_batch_destroy", i, [vp])
+    _decl(L, "mppi_batch_step", i, [vp, vp, vp, vp])
+    _decl(L, "mppi_batch_step_graph", i, [vp, vp, vp, vp])
+    _decl(L, "mppi_batch_sync", i, [vp, C.POINTER(i), vp])
+    _decl(L, "mppi_batch_iteration", i, [vp, i, C.POINTER(u64), vp])
+    _decl(L, "mppi_batch_set_iteration", i, [vp, i, u64, vp])
+    _decl(L, "mppi_batch_costs", C.c_void_p, [vp, i])
+    _decl(L, "mppi_batch_set_launch", i, [vp, i, i])
+    _decl(L, "mppi_batch_get_launch", i, [vp, C.POINTER(i), C.POINTER(i)])
+    _decl(L, "mppi_batch_autotune", i, [vp, vp, vp, i, vp, C.POINTER(C.c_float)])
+    _decl(L, "mppi_tune_store", i, [C.c_char_p, i, i, C.c_float])
+    _decl(L, "mppi_tune_lookup", i, [C.c_char_p, C.POINTER(i), C.POINTER(i)])
     _decl(L, "mppi_profile", i, [vp, i])
     _decl(L, "mppi_profile_read", i, [vp, C.POINTER(i), C.POINTER(C.c_float), C.POINTER(C.c_float),
                                        C.POINTER(C.c_double), C.POINTER(C.c_double)])
@@ -172,6 +185,80 @@ def step_noalloc(blob: bytes, K: int, H: int, lam: float, sigma, seed: int, iter
                                    C.c_uint64(iteration), _ptr(state), _ptr(u_nom), _ptr(u_out),
                                    C.byref(st) if want_status else None, _stream(stream)), "mppi_step_noalloc")
     return st.value if want_status else None
+
+
+class BatchDesc(C.Structure):
+    _fields_ = [("model", C.c_void_p), ("K", C.c_int), ("H", C.c_int), ("lam", C.c_float),
+                ("sigma", C.c_void_p), ("seed", C.c_uint64)]
+
+
+class Batch:
+    """Many controllers advanced together (mppi_batch_*).  `instances` is a
+    list of (Model, K, H, lam, sigma, seed)."""
+
+    def __init__(self, instances):
+        import numpy as np
+        self._keep = []
+        descs = (BatchDesc * len(instances))()
+        for i, (model, K, H, lam, sigma, seed) in enumerate(instances):
+            sig = np.ascontiguousarray(np.asarray(sigma, dtype=np.float32).reshape(model.nu))
+            self._keep.append((model, sig))
+            descs[i] = BatchDesc(model._h.value, int(K), int(H), float(lam), sig.ctypes.data, int(seed))
+        h = C.c_void_p()
+        _check(lib().mppi_batch_create(descs, len(instances), C.byref(h)), "mppi_batch_create")
+        self._h = h
+        self.n = len(instances)
+
+    @staticmethod
+    def _ptrs(ts):
+        arr = (C.c_void_p * len(ts))(*[_ptr(t) for t in ts])
+        return arr
+
+    def step(self, states, us, stream=None, graph=False):
+        fn = lib().mppi_batch_step_graph if graph else lib().mppi_batch_step
+        _check(fn(self._h, self._ptrs(states), self._ptrs(us), _stream(stream)), "mppi_batch_step")
+
+    def sync(self, stream=None):
+        errs = (C.c_int * self.n)()
+        rc = lib().mppi_batch_sync(self._h, errs, _stream(stream))
+        return rc, list(errs)
+
+    def iteration(self, i, stream=None) -> int:
+        v = C.c_uint64()
+        _check(lib().mppi_batch_iteration(self._h, i, C.byref(v), _stream(stream)), "mppi_batch_iteration")
+        return v.value
+
+    def set_iteration(self, i, it, stream=None):
+        _check(lib().mppi_batch_set_iteration(self._h, i, C.c_uint64(it), _stream(stream)),
+               "mppi_batch_set_iteration")
+
+    def costs_ptr(self, i) -> int:
+        return lib().mppi_batch_costs(self._h, i)
+
+    def set_launch(self, samples_per_cta, order):
+        _check(lib().mppi_batch_set_launch(self._h, samples_per_cta, order), "mppi_batch_set_launch")
+
+    def get_launch(self):
+        s, o = C.c_int(), C.c_int()
+        _check(lib().mppi_batch_get_launch(self._h, C.byref(s), C.byref(o)), "mppi_batch_get_launch")
+        return s.value, o.value
+
+    def autotune(self, states, us, reps=3, stream=None):
+        ms = C.c_float()
+        _check(lib().mppi_batch_autotune(self._h, self._ptrs(states), self._ptrs(us), reps, _stream(stream),
+                                         C.byref(ms)), "mppi_batch_autotune")
+        return ms.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mppi_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Model:
