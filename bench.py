@@ -36,8 +36,14 @@ UNIT = "sample-steps/s"
 WORKLOAD = "7-DoF bimanual ball lift, K=1024 samples, H=32 steps, dt=0.01 s, 4 PGS sweeps, FP32"
 
 
-def _config_json(sc, n_gpus):
-    return {"workload": WORKLOAD, "scene": sc.name, "K": sc.K, "H": sc.H, "nv": sc.nv, "n_boxes": sc.n_boxes,
+WORKLOADS = {
+    "lift": WORKLOAD,
+    "transfer": "7-DoF ball transfer past 8 boxes, K=4096 samples, H=64 steps, dt=0.01 s, 4 PGS sweeps, FP32",
+}
+
+
+def _config_json(sc, n_gpus, workload="lift"):
+    return {"workload": WORKLOADS[workload], "scene": sc.name, "K": sc.K, "H": sc.H, "nv": sc.nv, "n_boxes": sc.n_boxes,
             "lambda": sc.lam, "sigma": sc.sigma, "per_rank": "one independent controller (own Philox key)",
             "parallelism": f"replicas x{n_gpus}",
             "l2": "flushed between timed steps (256 MiB write); working set < 1 MiB"}
@@ -188,7 +194,7 @@ def run_ours(args):
     torch.cuda.set_device(dev)
     native.build() if rank == 0 and world == 1 else None
     native.lib()
-    sc = scenes.config(2)
+    sc = scenes.config(3 if args.workload == "transfer" else 2)
     K, H = sc.K, sc.H
     model = native.Model(sc.to_blob())
     ctl = native.Controller(model, K, H, sc.lam, sc.sigma_vec(), scenes.controller_key(sc.seed, rank))
@@ -258,7 +264,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": _config_json(sc, world),
+        "config": _config_json(sc, world, args.workload),
         "iters_per_s": args.steps * world / (total_ms * 1e-3),
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(4 * (x.numel() + u.numel())),
                 "d2h_bytes_per_step": int(4 * u.numel())},
@@ -273,6 +279,8 @@ def run_ours(args):
                      "box_tests_per_step": kt["box_tests_per_step"]},
         "clocks": clocks,
     }
+    if args.workload != "lift":
+        line["metric"] = METRIC.replace("MPPI iteration", "MPPI iteration, " + args.workload)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sc, seconds=args.cpu_seconds)
     print(json.dumps(line), flush=True)
@@ -282,12 +290,198 @@ def run_ours(args):
     return 0
 
 
+def run_batched(args):
+    """64 independent controllers per iteration: the persistent batched
+    launch (autotuned shape, graph replay) against 64 sequential plain
+    launches of the same controllers."""
+    import torch
+    from paper_2511_21264_gb300 import native
+    rank, world, local = _dist_setup(args.gpus)
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    native.build() if rank == 0 and world == 1 else None
+    native.lib()
+    pool = scenes.batched_pool(64, seed=0)
+    models = [native.Model(sc.to_blob()) for sc in pool]
+    inst = [(m, sc.K, sc.H, sc.lam, sc.sigma_vec(), scenes.controller_key(sc.seed, rank))
+            for m, sc in zip(models, pool)]
+    units = sum(sc.K * sc.H for sc in pool)
+    b = native.Batch(inst)
+    stream = torch.cuda.Stream(device=dev)
+    xs = [torch.tensor(m.home(), device=dev) for m in models]
+    us = [torch.zeros((sc.H, sc.nu), device=dev) for sc in pool]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def timed(fn, steps):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
+            flush.fill_(i & 0xFF)
+            ev[i][0].record(stream)
+            fn()
+            ev[i][1].record(stream)
+        stream.synchronize()
+        return [a.elapsed_time(c) for a, c in ev]
+
+    with torch.cuda.stream(stream):
+        tune_ms = b.autotune(xs, [u.clone() for u in us], reps=2, stream=stream)
+        spc, order = b.get_launch()
+        for _ in range(args.warmup):
+            b.step(xs, us, stream=stream, graph=True)
+        stream.synchronize()
+        _barrier(world)
+        with ClockSampler(local) as clk:
+            time.sleep(0.3)
+            t_batch = timed(lambda: b.step(xs, us, stream=stream, graph=True), args.steps)
+        rc, errs = b.sync(stream=stream)
+        if rc != 0:
+            raise RuntimeError(f"device error {rc} in the batched steps")
+        # sequential plain launches of the same controllers
+        ctls = [native.Controller(m, K, H, lam, sig, key) for (m, K, H, lam, sig, key) in inst]
+        useq = [torch.zeros_like(u) for u in us]
+
+        def seq():
+            for c, x, u in zip(ctls, xs, useq):
+                c.step(x, u, u, stream=stream)
+        for _ in range(args.warmup):
+            seq()
+        stream.synchronize()
+        seq_steps = max(3, args.steps // 4)
+        t_seq = timed(seq, seq_steps)
+        # end to end: pinned H2D of every state and u_nom, the batched
+        # iteration, D2H of every u_nom'
+        xh = [torch.tensor(m.home()).pin_memory() for m in models]
+        uh = [torch.zeros((sc.H, sc.nu)).pin_memory() for sc in pool]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(args.steps):
+            for a, c in zip(xs, xh):
+                a.copy_(c, non_blocking=True)
+            for a, c in zip(us, uh):
+                a.copy_(c, non_blocking=True)
+            b.step(xs, us, stream=stream, graph=True)
+            for a, c in zip(uh, us):
+                a.copy_(c, non_blocking=True)
+            stream.synchronize()
+        e1.record(stream)
+        stream.synchronize()
+        e2e_ms = _max_over_ranks(e0.elapsed_time(e1), world)
+    total = _max_over_ranks(sum(t_batch), world)
+    value = units * args.steps * world / (total * 1e-3)
+    seq_value = units * seq_steps / (sum(t_seq) * 1e-3)
+    if rank != 0:
+        return 0
+    props = torch.cuda.get_device_properties(dev)
+    clocks = clk.summary()
+    sm_mhz = clocks["sm_mhz"] or 1477.0
+    peak = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12
+    fl = sum(flops.per_sample_step(sc, 1.0, 0.0) * sc.K * sc.H for sc in pool)
+    ms = total / args.steps
+    hb = sum(4 * (sc.nq + sc.nv + sc.H * sc.nu) for sc in pool)
+    line = {
+        "metric": METRIC.replace("MPPI iteration", "MPPI iteration of 64 batched controllers"),
+        "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "64 independent 7-DoF controllers, K in {256..4096}, H in {16..64}, "
+                               "0..16 boxes (seeded), one persistent launch + update, graph replay",
+                   "instances": 64, "sample_steps_per_iteration": units, "autotuned_samples_per_cta": spc,
+                   "autotuned_order": "longest first" if order == 1 else "as given",
+                   "autotune_ms": tune_ms, "parallelism": f"replicas x{world}",
+                   "l2": "flushed between timed steps (256 MiB write)"},
+        "iters_per_s": 64 * args.steps * world / (total * 1e-3),
+        "sequential_plain": {"value": seq_value, "unit": UNIT, "ms_per_step": sum(t_seq) / seq_steps,
+                             "launches_per_step": 128},
+        "speedup_vs_sequential": value / world / seq_value,
+        "e2e": {"value": units * args.steps * world / (e2e_ms * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": hb, "d2h_bytes_per_step": sum(4 * sc.H * sc.nu for sc in pool)},
+        "gpu_launches": 2 * args.steps,
+        "roofline": {"bound": "alu", "kernel": "batch_rollout_kernel<7> + batch_update_kernel<14>",
+                     "achieved": fl / (ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                     "frac": fl / (ms * 1e-3) / 1e12 / peak, "traffic": None,
+                     "flops_basis": "lower bound (1 contact, no capsule-box test per step) over the whole "
+                                    "iteration time"},
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve(args):
+    """Continuous-batching replan server: Poisson arrivals at each rate over
+    a pool of 256 scenes (7-DoF arms, 0-16 boxes, K in {512..4096}, H in
+    {16..64}), M = 10 MPPI iterations per request, warm-started resident
+    state per scene.  The batched server (64 slots, 256 MiB budget) against a
+    server that runs one request at a time on the same arrival trace."""
+    import torch
+    from paper_2511_21264_gb300 import native
+    rank, world, local = _dist_setup(args.gpus)
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    native.build() if rank == 0 and world == 1 else None
+    native.lib()
+    pool = scenes.served_pool(256, seed=0)
+    models = [native.Model(sc.to_blob()) for sc in pool]
+    rates = [float(r) for r in args.serve_rates.split(",")]
+    M = 10
+
+    def serve(max_active, rate, seconds):
+        srv = native.Server(256 << 20, max_active, M)
+        for m, sc in zip(models, pool):
+            srv.add_scene(m, sc.K, sc.H, sc.lam, sc.sigma_vec(), scenes.controller_key(sc.seed, rank))
+        srv.start()
+        t0 = time.perf_counter()
+        srv.run_load(rate, seconds, seed=int(rate), drain_ms=600000)
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        rc = srv.stop()
+        if rc != 0:
+            raise RuntimeError(f"server error {rc}")
+        srv.close()
+        st["wall_s"] = wall
+        return st
+
+    out = {}
+    with ClockSampler(local) as clk:
+        for r in rates:
+            b = serve(64, r, args.serve_seconds)
+            entry = {"batched": {k: b[k] for k in ("p50_ms", "p99_ms", "mean_ms", "sample_steps_per_s", "completed",
+                                                   "mean_active", "admission_waits", "wall_s")}}
+            if r <= 200:
+                p = serve(1, r, min(args.serve_seconds, 5.0))
+                entry["one_at_a_time"] = {k: p[k] for k in ("p50_ms", "p99_ms", "mean_ms", "sample_steps_per_s",
+                                                            "completed", "wall_s")}
+            out[f"{r:g}_req_per_s"] = entry
+    if rank != 0:
+        return 0
+    top = out[f"{max(rates):g}_req_per_s"]["batched"]
+    line = {
+        "metric": "replan server: simulated sample-steps/s and p50/p99 replan latency (ms) under Poisson load",
+        "value": top["sample_steps_per_s"], "unit": UNIT, "n_gpus": world, "steps": None, "warmup": 0,
+        "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "256 scenes (7-DoF arms, 0-16 boxes, K 512..4096, H 16..64), M=10 iterations per "
+                               "request, Poisson arrivals", "rates_req_per_s": rates,
+                   "arrival_window_s": args.serve_seconds, "max_active": 64, "budget_bytes": 256 << 20},
+        "latency": out,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", choices=("lift", "transfer", "batched", "serve"), default="lift",
+                    help="lift: 7-DoF ball lift K=1024 H=32 (default); transfer: 8-box transfer K=4096 "
+                         "H=64; batched: 64 instances (K 256..4096, H 16..64, 0..16 boxes) in one "
+                         "persistent launch vs 64 sequential plain launches; serve: Poisson replan "
+                         "requests over 256 scenes, batched server vs one-at-a-time server")
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help="arrival window per rate (serve)")
+    ap.add_argument("--serve-rates", type=str, default="50,200,1000")
     ap.add_argument("--spc", type=int, default=0, help="samples per CTA (0 = library default)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -298,6 +492,10 @@ def main(argv=None):
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_ours(args)
 
 

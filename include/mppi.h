@@ -207,6 +207,58 @@ int mppi_batch_autotune(mppi_batch *b, const float *const *states, float *const 
 int mppi_tune_store(const char *key, int samples_per_cta, int order, float ms);
 int mppi_tune_lookup(const char *key, int *samples_per_cta, int *order);
 
+/* --------------------------------------------------------------- server */
+/* Replanning with continuous batching.  Registered scenes keep their
+ * simulator state, warm-started nominal sequence and Philox counter on the
+ * device (receding horizon with warm start, paper §III-A).  A request asks
+ * for one replan of one scene: `iters_per_request` MPPI iterations (Alg. 1
+ * with M = iters_per_request).  A scheduler thread works at iteration
+ * boundaries: it admits waiting requests while there are free slots
+ * (max_active), the scene has no request in flight and the request's
+ * workspace (K sample costs) fits the device-memory budget; runs one
+ * batched iteration of every active request; and retires those that
+ * reached M iterations -- the plan is copied out, the scene's state
+ * advances one simulator step under u_nom[0] and u_nom shifts by one step
+ * (last step kept).  Latency = retirement time - submission time.
+ * max_active = 1 serves one request at a time (no batching). */
+typedef struct mppi_server mppi_server;
+typedef struct {
+    size_t mem_budget_bytes; /* device arena for active requests' workspaces */
+    int max_active;          /* 1..4096 */
+    int iters_per_request;   /* M >= 1 */
+    int samples_per_cta;     /* launch shape, 0 = default */
+} mppi_server_config;
+typedef struct {
+    long long completed, iterations, waiting, active, admission_waits;
+    double p50_ms, p99_ms, mean_ms, mean_active, sample_steps_per_s;
+} srv_stats_t;
+
+int srv_create(const mppi_server_config *cfg, mppi_server **out);
+int srv_destroy(mppi_server *s);
+/* Register a scene before srv_start: model (kept alive by the caller), K,
+ * H, lambda, sigma (host, nu), Philox key, initial state (host nx; NULL =
+ * the model's home state).  MPPI_ERR_ADMISSION if one request of it can
+ * never fit the budget. */
+int srv_add_scene(mppi_server *s, const mppi_model *m, int K, int H, float lambda, const float *sigma, uint64_t seed,
+                  const float *x0, int *scene_id);
+int srv_start(mppi_server *s);
+/* Stop the scheduler thread (requests in flight are abandoned); returns the
+ * first device or CUDA error the scheduler met. */
+int srv_stop(mppi_server *s);
+int srv_submit(mppi_server *s, int scene_id, uint64_t *ticket);
+/* Withdraw a request that has not been admitted yet. */
+int srv_cancel(mppi_server *s, uint64_t ticket);
+/* done = 1 when the request is finished: u_out (host, up to u_len floats of
+ * the H x nu plan), latency_ms; the ticket is then released.  Waits up to
+ * wait_ms for completion.  Returns the request's status. */
+int srv_poll(mppi_server *s, uint64_t ticket, float *u_out, int u_len, double *latency_ms, int *done, int wait_ms);
+/* Resident state of a scene (host nx); fails while a request of it is active. */
+int srv_get_state(mppi_server *s, int scene_id, float *x_host);
+int srv_stats(mppi_server *s, srv_stats_t *out);
+/* Poisson load: arrivals at rate_hz for duration_s over the registered
+ * scenes (uniform), then wait up to drain_ms for all of them. */
+int srv_run_load(mppi_server *s, double rate_hz, double duration_s, uint64_t seed, int drain_ms);
+
 /* --------------------------------------------------------------- no-alloc */
 /* The paper has no counterpart to this entry point; it exists for callers
  * that cannot allocate device memory when they plan -- a real-time control

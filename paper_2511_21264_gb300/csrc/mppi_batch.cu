@@ -24,40 +24,25 @@ using namespace mppi;
 
 namespace mppi {
 
-struct BatchInst {
-    const DevModel* model;
-    const float* state;
-    float* u;  // nominal controls, updated in place
-    float* costs;
-    const float* sigma;
-    const float* u_lo;
-    const float* u_hi;
-    unsigned long long* iter;
-    unsigned int* done;
-    int* err;
-    float* best;
-    unsigned long long seed;
-    int K, H;
-    float lambda;
-    int stage_unom;
-};
-
-struct BatchTile {
-    int inst, k0;
-};
-
-struct BatchCtl {
-    unsigned int next;    // next tile to take
-    unsigned int exited;  // CTAs that finished
-};
-
 // Persistent rollout: each CTA takes (instance, tile of samples-per-CTA
 // samples) work items from a counter until none are left.  The model and
 // u_nom of the tile's instance are staged when the instance changes.  The
 // last CTA out resets the counters for the next launch (no CTA waits).
+// instance owning work item t: the last instance whose first item is <= t
+__device__ __forceinline__ int owner(const BatchInst* insts, int n, int t, bool rows) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        const int first = rows ? insts[mid].row0 : insts[mid].tile0;
+        if (first <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 template <int NA>
-__global__ void __launch_bounds__(512) batch_rollout_kernel(const BatchInst* insts, const BatchTile* tiles,
-                                                             int ntiles, BatchCtl* ctl, int max_unom) {
+__global__ void __launch_bounds__(512) batch_rollout_kernel(const BatchInst* insts, int n, int ntiles, BatchCtl* ctl,
+                                                             int max_unom) {
     using d = Dims<NA>;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_tile;
@@ -72,15 +57,15 @@ __global__ void __launch_bounds__(512) batch_rollout_kernel(const BatchInst* ins
         __syncthreads();
         const int t = s_tile;
         if (t >= ntiles) break;
-        const BatchTile tl = tiles[t];
-        const BatchInst& I = insts[tl.inst];
+        const int inst = owner(insts, n, t, false);
+        const BatchInst& I = insts[inst];
         const int unom_n = I.stage_unom ? I.H * d::NU : 0;
-        if (tl.inst != staged) {
+        if (inst != staged) {
             stage_model(smem, I.model, unom_s, I.u, unom_n);
-            staged = tl.inst;
+            staged = inst;
         }
         __syncthreads();
-        const int k = tl.k0 + warp;
+        const int k = (t - I.tile0) * (int)(blockDim.x >> 5) + warp;
         if (k < I.K) {
             SampleIO io{};
             io.x = I.state;
@@ -114,10 +99,11 @@ __global__ void __launch_bounds__(512) batch_rollout_kernel(const BatchInst* ins
 // One CTA per (instance, horizon step); each instance's last CTA advances
 // that instance's iteration counter.
 template <int NU>
-__global__ void __launch_bounds__(256) batch_update_kernel(const BatchInst* insts, const int2* rows) {
+__global__ void __launch_bounds__(256) batch_update_kernel(const BatchInst* insts, int n) {
     __shared__ UpdateSmem<NU> sm;
-    const int2 r = rows[blockIdx.x];
-    const BatchInst& I = insts[r.x];
+    const int inst = owner(insts, n, blockIdx.x, true);
+    const BatchInst& I = insts[inst];
+    const int h = blockIdx.x - I.row0;
     UpdateArgs a{};
     a.K = I.K;
     a.costs = I.costs;
@@ -133,8 +119,61 @@ __global__ void __launch_bounds__(256) batch_update_kernel(const BatchInst* inst
     a.best = I.best;
     a.advance = 1;
     a.done = I.done;
-    update_step<NU>(a, r.y, sm);
+    update_step<NU>(a, h, sm);
     update_finish<NU>(a, I.H, sm);
+}
+
+// Shift a nominal sequence one step: u[h] <- u[h+1], the last step kept.
+__global__ void shift_kernel(float* u, int H, int nu) {
+    for (int j = threadIdx.x; j < nu; j += blockDim.x) {
+        for (int h = 0; h + 1 < H; ++h) u[h * nu + j] = u[(h + 1) * nu + j];
+    }
+}
+
+template <int NA>
+int batch_shape_t(int spc, int max_h, BatchLaunch* L) {
+    const int max_unom = max_h * Dims<NA>::NU <= 2048 ? max_h * Dims<NA>::NU : 0;
+    L->max_unom = max_unom;
+    L->smem = sizeof(DevModel) + ((size_t)max_unom * sizeof(float) + 15) / 16 * 16 + (size_t)spc * sizeof(WarpWS<NA>);
+    auto fn = batch_rollout_kernel<NA>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L->smem);
+    if (e != cudaSuccess) return MPPI_ERR_CUDA;
+    int per_sm = 0, dev = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, spc * 32, L->smem);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return MPPI_ERR_CUDA;
+    L->grid = (per_sm > 0 ? per_sm : 1) * sms;
+    L->spc = spc;
+    L->na = NA;
+    return MPPI_OK;
+}
+
+int batch_shape(int na, int spc, int max_h, BatchLaunch* L) {
+    if (na == 3) return batch_shape_t<3>(spc, max_h, L);
+    if (na == 7) return batch_shape_t<7>(spc, max_h, L);
+    return MPPI_ERR_UNSUPPORTED;
+}
+
+// One batched iteration: persistent rollout over all tiles, then the update
+// CTAs.  insts (device) are in execution order with tile0/row0 prefixes.
+int launch_batch_iteration(const BatchInst* insts, int n, int ntiles, int nrows, BatchCtl* ctl, const BatchLaunch& L,
+                           cudaStream_t s) {
+    if (n <= 0) return MPPI_OK;
+    if (L.na == 3)
+        batch_rollout_kernel<3><<<L.grid, L.spc * 32, L.smem, s>>>(insts, n, ntiles, ctl, L.max_unom);
+    else
+        batch_rollout_kernel<7><<<L.grid, L.spc * 32, L.smem, s>>>(insts, n, ntiles, ctl, L.max_unom);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return MPPI_ERR_CUDA;
+    if (L.na == 3) batch_update_kernel<6><<<nrows, 256, 0, s>>>(insts, n);
+    else batch_update_kernel<14><<<nrows, 256, 0, s>>>(insts, n);
+    return cudaGetLastError() == cudaSuccess ? MPPI_OK : MPPI_ERR_CUDA;
+}
+
+int launch_shift(float* u, int H, int nu, cudaStream_t s) {
+    shift_kernel<<<1, 32, 0, s>>>(u, H, nu);
+    return cudaGetLastError() == cudaSuccess ? MPPI_OK : MPPI_ERR_CUDA;
 }
 
 }  // namespace mppi
@@ -205,20 +244,19 @@ extern "C" int mppi_tune_store(const char* key, int spc, int order, float ms) {
 struct mppi_batch {
     int n = 0, na = 0, nu = 0, max_h = 0, spc = 4, order = 1;
     std::vector<mppi_batch_desc> desc;
-    std::vector<BatchInst> host;  // device pointers per instance (pinned copy below)
+    std::vector<BatchInst> inst;  // per user instance
+    std::vector<int> perm;        // execution order -> user instance
+    std::vector<BatchInst> host;  // descriptor table in execution order
     BatchInst* h_pinned = nullptr;
     BatchInst* d_insts = nullptr;
-    BatchTile* d_tiles = nullptr;
     int ntiles = 0;
-    int2* d_rows = nullptr;
     int nrows = 0;
+    BatchLaunch L;
     BatchCtl* d_ctl = nullptr;
     float* d_pool = nullptr;  // costs, sigma, bounds, best (per instance)
     unsigned long long* d_iter = nullptr;
     unsigned int* d_done = nullptr;
     int* d_err = nullptr;
-    int grid = 0;
-    size_t smem = 0;
     std::string key;
     cudaGraphExec_t gexec = nullptr;
     cudaGraph_t graph = nullptr;
@@ -233,33 +271,11 @@ int cuda_rc(cudaError_t e) {
     return MPPI_ERR_CUDA;
 }
 
-template <int NA>
-size_t batch_smem(int spc, int max_unom) {
-    return sizeof(DevModel) + ((size_t)max_unom * sizeof(float) + 15) / 16 * 16 + (size_t)spc * sizeof(WarpWS<NA>);
-}
-
-template <int NA>
-int batch_shape(mppi_batch* b) {
-    const int max_unom = b->max_h * Dims<NA>::NU <= 2048 ? b->max_h * Dims<NA>::NU : 0;
-    b->smem = batch_smem<NA>(b->spc, max_unom);
-    auto fn = batch_rollout_kernel<NA>;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
-    if (e != cudaSuccess) return cuda_rc(e);
-    int per_sm = 0, dev = 0, sms = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, b->spc * 32, b->smem);
-    if (e == cudaSuccess) e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return cuda_rc(e);
-    b->grid = std::max(1, per_sm) * sms;
-    return MPPI_OK;
-}
-
-// Tile table for the current shape: instance order is either as given or
-// longest-first (estimated work H x (1 + boxes/4) x K, largest first), and
-// tiles of one instance stay contiguous.
-int build_tiles(mppi_batch* b) {
-    std::vector<int> ord(b->n);
-    std::iota(ord.begin(), ord.end(), 0);
+// Execution order (as given, or longest first: estimated work
+// H x (1 + boxes/4) x K, largest first) and the tile/row prefixes.
+void build_order(mppi_batch* b) {
+    b->perm.resize(b->n);
+    std::iota(b->perm.begin(), b->perm.end(), 0);
     if (b->order == 1) {
         std::vector<double> work(b->n);
         for (int i = 0; i < b->n; ++i) {
@@ -267,25 +283,26 @@ int build_tiles(mppi_batch* b) {
             mppi_model_dims(b->desc[i].model, nullptr, nullptr, nullptr, &nb);
             work[i] = (double)b->desc[i].H * (1.0 + nb / 4.0) * b->desc[i].K;
         }
-        std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return work[x] > work[y]; });
+        std::stable_sort(b->perm.begin(), b->perm.end(), [&](int x, int y) { return work[x] > work[y]; });
     }
-    std::vector<BatchTile> tiles;
-    for (int i : ord)
-        for (int k0 = 0; k0 < b->desc[i].K; k0 += b->spc) tiles.push_back({i, k0});
-    if (b->d_tiles) cudaFree(b->d_tiles);
-    b->d_tiles = nullptr;
-    b->ntiles = (int)tiles.size();
-    cudaError_t e = cudaMalloc(&b->d_tiles, tiles.size() * sizeof(BatchTile));
-    if (e == cudaSuccess)
-        e = cudaMemcpy(b->d_tiles, tiles.data(), tiles.size() * sizeof(BatchTile), cudaMemcpyHostToDevice);
-    return cuda_rc(e);
+    b->host.resize(b->n);
+    int t = 0, r = 0;
+    for (int e = 0; e < b->n; ++e) {
+        BatchInst I = b->inst[b->perm[e]];
+        I.tile0 = t;
+        I.row0 = r;
+        t += (I.K + b->spc - 1) / b->spc;
+        r += I.H;
+        b->host[e] = I;
+    }
+    b->ntiles = t;
+    b->nrows = r;
 }
 
 int reshape(mppi_batch* b) {
-    int rc = b->na == 3 ? batch_shape<3>(b) : batch_shape<7>(b);
+    int rc = batch_shape(b->na, b->spc, b->max_h, &b->L);
     if (rc != MPPI_OK) return rc;
-    rc = build_tiles(b);
-    if (rc != MPPI_OK) return rc;
+    build_order(b);
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     if (b->graph) cudaGraphDestroy(b->graph);
     b->gexec = nullptr;
@@ -294,30 +311,19 @@ int reshape(mppi_batch* b) {
 }
 
 int enqueue_batch(mppi_batch* b, cudaStream_t s) {
-    const int max_unom = b->max_h * 2 * b->na <= 2048 ? b->max_h * 2 * b->na : 0;
-    if (b->na == 3)
-        batch_rollout_kernel<3><<<b->grid, b->spc * 32, b->smem, s>>>(b->d_insts, b->d_tiles, b->ntiles, b->d_ctl,
-                                                                       max_unom);
-    else
-        batch_rollout_kernel<7><<<b->grid, b->spc * 32, b->smem, s>>>(b->d_insts, b->d_tiles, b->ntiles, b->d_ctl,
-                                                                       max_unom);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_rc(e);
-    if (b->nu == 6) batch_update_kernel<6><<<b->nrows, 256, 0, s>>>(b->d_insts, b->d_rows);
-    else batch_update_kernel<14><<<b->nrows, 256, 0, s>>>(b->d_insts, b->d_rows);
-    return cuda_rc(cudaGetLastError());
+    return launch_batch_iteration(b->d_insts, b->n, b->ntiles, b->nrows, b->d_ctl, b->L, s);
 }
 
-// Write the caller's state and control pointers into the host descriptor
-// table; returns whether any changed.
-bool stage_pointers(mppi_batch* b, const float* const* states, float* const* u) {
-    bool changed = false;
-    for (int i = 0; i < b->n; ++i) {
-        if (b->host[i].state != states[i] || b->host[i].u != u[i]) changed = true;
-        b->host[i].state = states[i];
-        b->host[i].u = u[i];
+// Write the caller's state and control pointers into the execution-order
+// descriptor table.
+void stage_pointers(mppi_batch* b, const float* const* states, float* const* u) {
+    for (int e = 0; e < b->n; ++e) {
+        const int i = b->perm[e];
+        b->inst[i].state = states[i];
+        b->inst[i].u = u[i];
+        b->host[e].state = states[i];
+        b->host[e].u = u[i];
     }
-    return changed;
 }
 
 }  // namespace
@@ -330,8 +336,6 @@ int mppi_batch_destroy(mppi_batch* b) {
     if (b->graph) cudaGraphDestroy(b->graph);
     cudaFreeHost(b->h_pinned);
     cudaFree(b->d_insts);
-    cudaFree(b->d_tiles);
-    cudaFree(b->d_rows);
     cudaFree(b->d_ctl);
     cudaFree(b->d_pool);
     cudaFree(b->d_iter);
@@ -386,12 +390,11 @@ int mppi_batch_create(const mppi_batch_desc* desc, int n, mppi_batch** out) {
         return cuda_rc(e);
     }
     std::vector<float> params(48);
-    b->host.resize(n);
-    std::vector<int2> rows;
+    b->inst.resize(n);
     for (int i = 0; i < n; ++i) {
         const mppi_batch_desc& dsc = desc[i];
         float* base = b->d_pool + off[i];
-        BatchInst& I = b->host[i];
+        BatchInst& I = b->inst[i];
         std::memset(&I, 0, sizeof I);
         I.model = model_device(dsc.model);
         I.costs = base;
@@ -417,14 +420,6 @@ int mppi_batch_create(const mppi_batch_desc* desc, int n, mppi_batch** out) {
             mppi_batch_destroy(b);
             return cuda_rc(e);
         }
-        for (int h = 0; h < dsc.H; ++h) rows.push_back(make_int2(i, h));
-    }
-    b->nrows = (int)rows.size();
-    e = cudaMalloc(&b->d_rows, rows.size() * sizeof(int2));
-    if (e == cudaSuccess) e = cudaMemcpy(b->d_rows, rows.data(), rows.size() * sizeof(int2), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) {
-        mppi_batch_destroy(b);
-        return cuda_rc(e);
     }
     // autotuner key: arm size, box-count bucket, total samples, longest horizon
     int boxes = 0;
@@ -566,7 +561,7 @@ int mppi_batch_set_iteration(mppi_batch* b, int i, uint64_t it, void* stream) {
 
 const float* mppi_batch_costs(const mppi_batch* b, int i) {
     if (!b || i < 0 || i >= b->n) return nullptr;
-    return b->host[i].costs;
+    return b->inst[i].costs;
 }
 
 int mppi_batch_autotune(mppi_batch* b, const float* const* states, float* const* u, int reps, void* stream,

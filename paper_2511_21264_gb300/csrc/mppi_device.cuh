@@ -24,6 +24,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "mppi_internal.h"
+
 namespace mppi {
 
 constexpr int MAXL = 7;    // joints per arm
@@ -32,10 +34,6 @@ constexpr int MAXC = 16;   // contacts kept per step
 constexpr int MAXR = 3 * MAXC;
 constexpr unsigned FULL = 0xffffffffu;
 
-// error word bits (device)
-constexpr int ERRB_NONFINITE = 1;
-constexpr int ERRB_CHOLESKY = 2;
-constexpr int ERRB_TIMEOUT = 4;
 
 struct __align__(16) DevLink {
     float FR[9];

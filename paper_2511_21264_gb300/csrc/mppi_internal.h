@@ -8,6 +8,11 @@
 
 namespace mppi {
 
+// bits of a controller's device error word
+constexpr int ERRB_NONFINITE = 1;
+constexpr int ERRB_CHOLESKY = 2;
+constexpr int ERRB_TIMEOUT = 4;
+
 struct DevModel;
 
 struct HostModelInfo {
@@ -68,6 +73,42 @@ struct mppi_model;
 namespace mppi {
 const DevModel* model_device(const mppi_model* m);
 void model_bounds(const mppi_model* m, int j, float* lo, float* hi);
+
+// descriptor of one controller in a batched iteration (device table)
+struct BatchInst {
+    const DevModel* model;
+    const float* state;
+    float* u;  // nominal controls, updated in place
+    float* costs;
+    const float* sigma;
+    const float* u_lo;
+    const float* u_hi;
+    unsigned long long* iter;
+    unsigned int* done;
+    int* err;
+    float* best;
+    unsigned long long seed;
+    int K, H;
+    float lambda;
+    int stage_unom;
+    int tile0;  // first work item (tile of samples) of this instance
+    int row0;   // first update CTA of this instance
+};
+
+struct BatchCtl {
+    unsigned int next;    // next tile to take
+    unsigned int exited;  // CTAs that finished
+};
+
+// launch shape of the persistent batched rollout
+struct BatchLaunch {
+    int na = 7, spc = 4, grid = 0, max_unom = 0;
+    size_t smem = 0;
+};
+int batch_shape(int na, int spc, int max_h, BatchLaunch* L);
+int launch_batch_iteration(const BatchInst* insts, int n, int ntiles, int nrows, BatchCtl* ctl, const BatchLaunch& L,
+                           cudaStream_t s);
+int launch_shift(float* u, int H, int nu, cudaStream_t s);
 
 int parse_model_blob(const void* blob, size_t len, DevModel* out, HostModelInfo* info);
 int launch_rollout(int na, int mode, const RolloutArgs& a, int spc, cudaStream_t s);

@@ -128,6 +128,17 @@ def lib():
     _decl(L, "mppi_batch_autotune", i, [vp, vp, vp, i, vp, C.POINTER(C.c_float)])
     _decl(L, "mppi_tune_store", i, [C.c_char_p, i, i, C.c_float])
     _decl(L, "mppi_tune_lookup", i, [C.c_char_p, C.POINTER(i), C.POINTER(i)])
+    _decl(L, "srv_create", i, [C.POINTER(ServerConfig), C.POINTER(vp)])
+    _decl(L, "srv_destroy", i, [vp])
+    _decl(L, "srv_add_scene", i, [vp, vp, i, i, C.c_float, fp, u64, fp, C.POINTER(i)])
+    _decl(L, "srv_start", i, [vp])
+    _decl(L, "srv_stop", i, [vp])
+    _decl(L, "srv_submit", i, [vp, i, C.POINTER(u64)])
+    _decl(L, "srv_cancel", i, [vp, u64])
+    _decl(L, "srv_poll", i, [vp, u64, fp, i, C.POINTER(C.c_double), C.POINTER(i), i])
+    _decl(L, "srv_get_state", i, [vp, i, fp])
+    _decl(L, "srv_stats", i, [vp, C.POINTER(SrvStats)])
+    _decl(L, "srv_run_load", i, [vp, C.c_double, C.c_double, u64, i])
     _decl(L, "mppi_profile", i, [vp, i])
     _decl(L, "mppi_profile_read", i, [vp, C.POINTER(i), C.POINTER(C.c_float), C.POINTER(C.c_float),
                                        C.POINTER(C.c_double), C.POINTER(C.c_double)])
@@ -185,6 +196,89 @@ def step_noalloc(blob: bytes, K: int, H: int, lam: float, sigma, seed: int, iter
                                    C.c_uint64(iteration), _ptr(state), _ptr(u_nom), _ptr(u_out),
                                    C.byref(st) if want_status else None, _stream(stream)), "mppi_step_noalloc")
     return st.value if want_status else None
+
+
+class ServerConfig(C.Structure):
+    _fields_ = [("mem_budget_bytes", C.c_size_t), ("max_active", C.c_int), ("iters_per_request", C.c_int),
+                ("samples_per_cta", C.c_int)]
+
+
+class SrvStats(C.Structure):
+    _fields_ = [(n, C.c_longlong) for n in ("completed", "iterations", "waiting", "active", "admission_waits")] + \
+               [(n, C.c_double) for n in ("p50_ms", "p99_ms", "mean_ms", "mean_active", "sample_steps_per_s")]
+
+
+class Server:
+    """Replan server with continuous batching (srv_*)."""
+
+    def __init__(self, mem_budget_bytes: int, max_active: int, iters_per_request: int, samples_per_cta: int = 0):
+        cfg = ServerConfig(int(mem_budget_bytes), int(max_active), int(iters_per_request), int(samples_per_cta))
+        h = C.c_void_p()
+        _check(lib().srv_create(C.byref(cfg), C.byref(h)), "srv_create")
+        self._h = h
+        self._keep = []
+        self.dims = {}
+
+    def add_scene(self, model, K, H, lam, sigma, seed, x0=None) -> int:
+        import numpy as np
+        sig = np.ascontiguousarray(np.asarray(sigma, dtype=np.float32))
+        x = None if x0 is None else np.ascontiguousarray(np.asarray(x0, dtype=np.float32))
+        self._keep.append((model, sig, x))
+        sid = C.c_int()
+        _check(lib().srv_add_scene(self._h, model._h, int(K), int(H), float(lam), sig.ctypes.data, C.c_uint64(seed),
+                                   None if x is None else x.ctypes.data, C.byref(sid)), "srv_add_scene")
+        self.dims[sid.value] = (int(H), model.nu, model.nx)
+        return sid.value
+
+    def start(self):
+        _check(lib().srv_start(self._h), "srv_start")
+
+    def stop(self) -> int:
+        return lib().srv_stop(self._h)
+
+    def submit(self, scene: int) -> int:
+        t = C.c_uint64()
+        _check(lib().srv_submit(self._h, int(scene), C.byref(t)), "srv_submit")
+        return t.value
+
+    def cancel(self, ticket: int) -> int:
+        return lib().srv_cancel(self._h, C.c_uint64(ticket))
+
+    def poll(self, ticket: int, scene: int, wait_ms: int = 0):
+        """(status, done, plan H x nu, latency_ms)."""
+        import numpy as np
+        H, nu, _ = self.dims[scene]
+        u = np.zeros((H, nu), dtype=np.float32)
+        lat, done = C.c_double(), C.c_int()
+        st = lib().srv_poll(self._h, C.c_uint64(ticket), u.ctypes.data, H * nu, C.byref(lat), C.byref(done),
+                            int(wait_ms))
+        return st, bool(done.value), u, lat.value
+
+    def state(self, scene: int):
+        import numpy as np
+        x = np.zeros(self.dims[scene][2], dtype=np.float32)
+        _check(lib().srv_get_state(self._h, int(scene), x.ctypes.data), "srv_get_state")
+        return x
+
+    def stats(self) -> dict:
+        st = SrvStats()
+        _check(lib().srv_stats(self._h, C.byref(st)), "srv_stats")
+        return {n: getattr(st, n) for n, _ in SrvStats._fields_}
+
+    def run_load(self, rate_hz: float, duration_s: float, seed: int = 0, drain_ms: int = 120000):
+        _check(lib().srv_run_load(self._h, float(rate_hz), float(duration_s), C.c_uint64(seed), int(drain_ms)),
+               "srv_run_load")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().srv_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class BatchDesc(C.Structure):
