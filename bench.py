@@ -151,9 +151,16 @@ def cpu_baseline(sc, seconds=15.0, nthreads=None):
         done += Kp * sc.H
         it += 1
     el = time.perf_counter() - t0
+    # the same oracle on one thread, on a smaller sample
+    K1 = max(4, Kp // max(1, nthreads))
+    t1 = time.perf_counter()
+    om.mppi_iteration(x, u, K1, sc.lam, sig, 1, it, nthreads=1)
+    one = K1 * sc.H / (time.perf_counter() - t1)
     return {"value": done / el, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+            "value_1_thread": one,
             "sample": f"{it} MPPI iterations of K'={Kp} samples (of K={sc.K}), H={sc.H}, same scene; "
-                      f"{el:.1f} s of FP64 work on {nthreads} threads"}
+                      f"{el:.1f} s of FP64 work on {nthreads} threads; 1-thread figure from one iteration "
+                      f"of K'={K1}"}
 
 
 def run_reference(args):

@@ -522,11 +522,13 @@ static int enqueue_step(mppi_ctx* c, const float* state, const float* u_nom, flo
 
 int mppi_step(mppi_ctx* c, const float* state, const float* u_nom, float* u_nom_out, void* stream) {
     if (!c || !state || !u_nom || !u_nom_out) return MPPI_ERR_INVALID_ARG;
+    NvtxRange r("mppi_step");
     return enqueue_step(c, state, u_nom, u_nom_out, c->d_best, (cudaStream_t)stream);
 }
 
 int mppi_solve(mppi_ctx* c, const float* state, float* u, int iters, float* best_out, void* stream) {
     if (!c || !state || !u || iters < 1) return MPPI_ERR_INVALID_ARG;
+    NvtxRange r("mppi_solve");
     cudaStream_t s = (cudaStream_t)stream;
     float* best = best_out ? best_out : c->d_best;
     if (s == nullptr) {  // the legacy stream cannot be captured: run eagerly
@@ -578,6 +580,7 @@ int mppi_update(mppi_ctx* c, const float* costs, const float* u_nom, float* u_ou
 int rollout_batch(mppi_ctx* c, int n, const float* states, const float* U, float* costs, float* states_out,
                   void* stream) {
     if (!c || n < 0 || n > c->K || (n > 0 && (!states || !U || !costs))) return MPPI_ERR_INVALID_ARG;
+    NvtxRange r("rollout_batch");
     RolloutArgs a{};
     a.model = c->m->dev;
     a.n = n;

@@ -467,6 +467,7 @@ int mppi_batch_step(mppi_batch* b, const float* const* states, float* const* u, 
     for (int i = 0; i < b->n; ++i)
         if (!states[i] || !u[i]) return MPPI_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
+    NvtxRange r("mppi_batch_step");
     stage_pointers(b, states, u);
     cudaError_t e = cudaMemcpyAsync(b->d_insts, b->host.data(), b->n * sizeof(BatchInst), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_rc(e);
@@ -478,6 +479,7 @@ int mppi_batch_step_graph(mppi_batch* b, const float* const* states, float* cons
     for (int i = 0; i < b->n; ++i)
         if (!states[i] || !u[i]) return MPPI_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
+    NvtxRange r("mppi_batch_step_graph");
     stage_pointers(b, states, u);
     // the graph's copy node reads the pinned table when it executes: rewrite
     // it only when its content changes, after any launch in flight is done

@@ -1,12 +1,22 @@
 // Internal (non-ABI) declarations shared by the library's translation units.
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstddef>
 #include <cstdint>
 #include <vector>
 
 namespace mppi {
+
+// NVTX range for the lifetime of a scope (shows up in nsys / ncu timelines;
+// costs nothing when no tool is attached)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // bits of a controller's device error word
 constexpr int ERRB_NONFINITE = 1;

@@ -171,6 +171,7 @@ bool scheduler_step(mppi_server* S) {
         for (uint64_t tk : S->active) act.push_back(&S->reqs.at(tk));
     }
     if (act.empty()) return false;
+    NvtxRange range("srv_iteration");
     // descriptor table: longest (K H) first, tile and row prefixes
     std::stable_sort(act.begin(), act.end(), [&](const Request* a, const Request* b) {
         const Scene& x = S->scenes[a->scene];

@@ -353,3 +353,26 @@ def test_statistical_parity_planar_100_seeds(native):
     if 0 < p < 1:
         zstat = (pg - po) / np.sqrt(2 * p * (1 - p) / 100)
         assert abs(zstat) < 2.58
+
+
+# ------------------------------------------------------- checkpoint / resume
+def test_checkpoint_resume_reproduces_iterations_bitwise(native):
+    """Snapshot (state, u_nom, Philox key, iteration counter); restoring it
+    reproduces the next iterations bitwise (warm start, Sec. III-A)."""
+    sc, gm, om, ctl, key = _setup(2, K=128, H=8)
+    x = _t(_f32(sc.x0))
+    u = torch.zeros((8, sc.nu), device=DEV)
+    for _ in range(2):
+        ctl.step(x, u, u)
+    snap_u, snap_it = u.clone(), ctl.iteration()
+    for _ in range(3):
+        ctl.step(x, u, u)
+    first = u.clone()
+    ctl2 = __import__("paper_2511_21264_gb300.native", fromlist=["x"]).Controller(gm, 128, 8, sc.lam,
+                                                                                   sc.sigma_vec(), key)
+    ctl2.set_iteration(snap_it)
+    u2 = snap_u.clone()
+    for _ in range(3):
+        ctl2.step(x, u2, u2)
+    assert ctl.sync() == 0 and ctl2.sync() == 0
+    assert torch.equal(first, u2)
