@@ -189,7 +189,7 @@ int mppi_batch_iteration(mppi_batch *b, int i, uint64_t *iteration, void *stream
 int mppi_batch_set_iteration(mppi_batch *b, int i, uint64_t iteration, void *stream);
 /* Device pointer to instance i's K sample costs of the last iteration. */
 const float *mppi_batch_costs(const mppi_batch *b, int i);
-/* Launch shape: samples (warps) per CTA 1..16; order 0 = as given,
+/* Launch shape: samples (warps) per CTA 1..8; order 0 = as given,
  * 1 = longest instances first. */
 int mppi_batch_set_launch(mppi_batch *b, int samples_per_cta, int order);
 int mppi_batch_get_launch(const mppi_batch *b, int *samples_per_cta, int *order);

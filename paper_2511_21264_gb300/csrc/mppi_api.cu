@@ -173,7 +173,8 @@ int parse_model_blob(const void* blob, size_t len, DevModel* out, HostModelInfo*
     std::vector<double> v(n);
     std::memcpy(v.data(), static_cast<const unsigned char*>(blob) + 16, 8 * n);
     const int na = (int)v[0], nb = (int)v[1], maxc = (int)v[2];
-    if (na < 1 || na > MAXL || nb < 0 || nb > MAXB || maxc < 1 || maxc > MAXC) return MPPI_ERR_INVALID_ARG;
+    if (na < 1 || na > MAXL || nb < 0 || nb > MAXB || maxc < 1 || maxc > 16) return MPPI_ERR_INVALID_ARG;
+    if (maxc > MAXC) return MPPI_ERR_UNSUPPORTED;  // more contacts than the device solver keeps
     const int nq = 2 * na + 7, nv = 2 * na + 6;
     if (n != 23 + 2 * (12 + 39 * (size_t)na) + 6 * (size_t)nb + (size_t)(nq + nv)) return MPPI_ERR_INVALID_ARG;
     DevModel M;

@@ -41,7 +41,7 @@ __device__ __forceinline__ int owner(const BatchInst* insts, int n, int t, bool 
 }
 
 template <int NA>
-__global__ void __launch_bounds__(512) batch_rollout_kernel(const BatchInst* insts, int n, int ntiles, BatchCtl* ctl,
+__global__ void __launch_bounds__(256, 3) batch_rollout_kernel(const BatchInst* insts, int n, int ntiles, BatchCtl* ctl,
                                                              int max_unom) {
     using d = Dims<NA>;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -449,7 +449,7 @@ int mppi_batch_create(const mppi_batch_desc* desc, int n, mppi_batch** out) {
 }
 
 int mppi_batch_set_launch(mppi_batch* b, int spc, int order) {
-    if (!b || spc < 1 || spc > 16 || order < 0 || order > 1) return MPPI_ERR_INVALID_ARG;
+    if (!b || spc < 1 || spc > 8 || order < 0 || order > 1) return MPPI_ERR_INVALID_ARG;
     b->spc = spc;
     b->order = order;
     return reshape(b);

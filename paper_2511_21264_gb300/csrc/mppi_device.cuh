@@ -30,7 +30,7 @@ namespace mppi {
 
 constexpr int MAXL = 7;    // joints per arm
 constexpr int MAXB = 16;   // boxes
-constexpr int MAXC = 16;   // contacts kept per step
+constexpr int MAXC = 8;    // contacts kept per step (models with a larger cap are rejected)
 constexpr int MAXR = 3 * MAXC;
 constexpr unsigned FULL = 0xffffffffu;
 
@@ -67,7 +67,10 @@ struct Dims {
     static constexpr int NX = NQ + NV, B = 2 * NA;
 };
 
-// Per-warp (per-sample) workspace in shared memory.
+// Per-warp (per-sample) workspace in shared memory.  Scratch that lives in
+// one phase only shares storage: the capsule-box survivor list (collision),
+// the joint axes and subtree forces (dynamics) and the contact rows,
+// Delassus block and impulses (contacts).
 template <int NA>
 struct __align__(16) WarpWS {
     using d = Dims<NA>;
@@ -79,34 +82,40 @@ struct __align__(16) WarpWS {
     float rhs[d::NV];
     float u[d::NU];
     float zn[8][16];  // standard normals of the next 8 steps (Philox path)
-    // kinematics, per link
-    float R[d::NL][9];
+    // kinematics, per link (read across lanes)
     float z[d::NL][3];
     float o[d::NL][3];
-    float c[d::NL][3];
     float a0[d::NL][3];
     float a1[d::NL][3];
-    // dynamics
-    float S[d::NL][6];
-    float F[d::NL][6];
+    // factors of (M + dt D), per arm
     float L[2][NA][NA];
     float Ldi[2][NA];  // reciprocal diagonal of the factors
-    // contacts
+    // contacts of this step, canonical order
     float cp[MAXC][3];
     float cn[MAXC][3];
     float cdep[MAXC];
     int cA[MAXC];
     int cB[MAXC];
-    float Y[MAXR][d::NV];
-    float G[MAXR * (MAXR + 1) / 2];  // Delassus block Y Y^T, packed upper triangle
-    float4 rc4[MAXR];                // per row: b = J v_f, R, 1/(A+R), reference velocity
-    float lam[MAXR];
-    int tmask[MAXR];                 // blocks a row touches: 1 left arm, 2 right arm, 4 ball
-    short surv[2 * MAXL * MAXB];     // capsule-box pairs that pass the cull, in pair order
     int ncon;
     int nact;
     float pen_all;
     float pen_box;
+    union Phase {
+        struct {
+            short surv[2 * MAXL * MAXB];  // capsule-box pairs that pass the cull
+        } col;
+        struct {
+            float S[d::NL][6];
+            float F[d::NL][6];
+        } dyn;
+        struct {
+            float Y[MAXR][d::NV];
+            float G[MAXR * MAXR];  // Delassus block Y Y^T, nr x nr
+            float4 rc4[MAXR];      // per row: b = J v_f, R, 1/(A+R), reference velocity
+            float lam[MAXR];
+            int tmask[MAXR];       // blocks a row touches: 1 left arm, 2 right arm, 4 ball
+        } con;
+    } ph;
 };
 
 // ---------------------------------------------------------------------------
@@ -187,7 +196,8 @@ __device__ __forceinline__ void spatial_inertia_apply(const float* I, const floa
 // kinematics: lane 16a walks arm a
 // ---------------------------------------------------------------------------
 template <int NA>
-__device__ __forceinline__ void forward_kinematics(const DevModel& M, WarpWS<NA>& w, int lane) {
+__device__ __forceinline__ void forward_kinematics(const DevModel& M, WarpWS<NA>& w, int lane, float (&Rl)[9],
+                                                   float (&cl)[3]) {
     // Lane 16a + i owns link i of arm a.  Each lane forms its local transform
     // Rz(q_i) F_i; an inclusive prefix product over the 16-lane segment
     // (Hillis-Steele, log2(n_a) shuffle rounds) gives the chain to link i;
@@ -262,12 +272,12 @@ __device__ __forceinline__ void forward_kinematics(const DevModel& M, WarpWS<NA>
         const DevLink& L = M.link[a][i];
         const int l = a * NA + i;
 #pragma unroll
-        for (int k = 0; k < 9; ++k) w.R[l][k] = Rw[k];
+        for (int k = 0; k < 9; ++k) Rl[k] = Rw[k];
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
             w.z[l][r] = zp[r];
             w.o[l][r] = op[r];
-            w.c[l][r] = Rw[3 * r] * L.com[0] + Rw[3 * r + 1] * L.com[1] + Rw[3 * r + 2] * L.com[2] + pw[r];
+            cl[r] = Rw[3 * r] * L.com[0] + Rw[3 * r + 1] * L.com[1] + Rw[3 * r + 2] * L.com[2] + pw[r];
             w.a0[l][r] = Rw[3 * r] * L.s0[0] + Rw[3 * r + 1] * L.s0[1] + Rw[3 * r + 2] * L.s0[2] + pw[r];
             w.a1[l][r] = Rw[3 * r] * L.s1[0] + Rw[3 * r + 1] * L.s1[1] + Rw[3 * r + 2] * L.s1[2] + pw[r];
         }
@@ -533,13 +543,13 @@ __device__ __forceinline__ int collide(const DevModel& M, WarpWS<NA>& w, int lan
         while (smask) {
             const int bi = __ffs(smask) - 1;
             smask &= smask - 1u;
-            w.surv[pos++] = (short)(lane * nb + bi);
+            w.ph.col.surv[pos++] = (short)(lane * nb + bi);
         }
         nsurv = __shfl_sync(FULL, pre, 31);
     }
     __syncwarp();
     for (int si = 0; si < nsurv; ++si) {
-        const int idx = w.surv[si];
+        const int idx = w.ph.col.surv[si];
         const int l = idx / nb, bi = idx - l * nb;
         const float* box = M.box[bi];
         const float* a0 = w.a0[l];
@@ -630,7 +640,8 @@ __device__ __forceinline__ void seg_prefix_sum(float (&v)[N], int i, int nlinks)
 }
 
 template <int NA>
-__device__ __forceinline__ void dynamics(const DevModel& M, WarpWS<NA>& w, int lane, int* err) {
+__device__ __forceinline__ void dynamics(const DevModel& M, WarpWS<NA>& w, int lane, int* err, const float (&R)[9],
+                                         const float (&cl)[3]) {
     using d = Dims<NA>;
     const int a = lane >> 4, i = lane & 15;
     const bool act = i < NA;
@@ -646,7 +657,6 @@ __device__ __forceinline__ void dynamics(const DevModel& M, WarpWS<NA>& w, int l
     float qdi = 0.0f;
     if (act) {
         const DevLink& L = M.link[a][i];
-        const float* R = w.R[l];
         const float* Ib = L.I;
         const float B9[9] = {Ib[0], Ib[3], Ib[4], Ib[3], Ib[1], Ib[5], Ib[4], Ib[5], Ib[2]};
         float T[9];
@@ -655,7 +665,7 @@ __device__ __forceinline__ void dynamics(const DevModel& M, WarpWS<NA>& w, int l
 #pragma unroll
             for (int cc = 0; cc < 3; ++cc)
                 T[3 * r + cc] = R[3 * r] * B9[cc] + R[3 * r + 1] * B9[3 + cc] + R[3 * r + 2] * B9[6 + cc];
-        const float c0 = w.c[l][0], c1 = w.c[l][1], c2 = w.c[l][2];
+        const float c0 = cl[0], c1 = cl[1], c2 = cl[2];
         const float m = L.mass;
         const float cc2 = c0 * c0 + c1 * c1 + c2 * c2;
         Is[0] = m;
@@ -749,8 +759,8 @@ __device__ __forceinline__ void dynamics(const DevModel& M, WarpWS<NA>& w, int l
         w.rhs[dof] = td - tb - L.D * qdi;
 #pragma unroll
         for (int t = 0; t < 6; ++t) {
-            w.S[l][t] = S[t];
-            w.F[l][t] = F[t];
+            w.ph.dyn.S[l][t] = S[t];
+            w.ph.dyn.F[l][t] = F[t];
         }
     }
     __syncwarp();
@@ -769,8 +779,8 @@ __device__ __forceinline__ void dynamics(const DevModel& M, WarpWS<NA>& w, int l
                     ++c;
                 }
             const int r = rem;
-            const float* Sr = w.S[a * NA + r];
-            const float* Fc = w.F[a * NA + c];
+            const float* Sr = w.ph.dyn.S[a * NA + r];
+            const float* Fc = w.ph.dyn.F[a * NA + c];
             float mv = Sr[0] * Fc[0] + Sr[1] * Fc[1] + Sr[2] * Fc[2] + Sr[3] * Fc[3] + Sr[4] * Fc[4] + Sr[5] * Fc[5];
             if (r == c) mv += M.dt * M.link[a][c].D;
             w.L[a][c][r] = mv;
@@ -877,11 +887,6 @@ __device__ __forceinline__ void contact_frame_row(const float* n, int k, float* 
     cross3(n, t1, e);
 }
 
-__device__ __forceinline__ int packed_index(int r, int s, int nr) {
-    // upper-triangle index of (min, max) in an nr x nr symmetric matrix
-    const int lo = r < s ? r : s, hi = r < s ? s : r;
-    return lo * nr - (lo * (lo - 1)) / 2 + (hi - lo);
-}
 
 // Soft contact by projected Gauss-Seidel in contact space.  With the
 // factor L L^T = M + dt D and rows Y_r = L^-1 J_r^T, the Delassus matrix is
@@ -983,7 +988,7 @@ __device__ __forceinline__ void contacts(const DevModel& M, WarpWS<NA>& w, int l
                 }
             }
         }
-        float* y = w.Y[r];
+        float* y = w.ph.con.Y[r];
 #pragma unroll
         for (int q = 0; q < NA; ++q) {
             y[q] = ya[0][q];
@@ -994,28 +999,27 @@ __device__ __forceinline__ void contacts(const DevModel& M, WarpWS<NA>& w, int l
             y[d::B + q] = yb[q] * ismb;
             y[d::B + 3 + q] = yb[3 + q] * isIb;
         }
-        w.tmask[r] = msk;
-        w.rc4[r].w = (k == 0) ? (M.erp / M.dt) * w.cdep[c] : 0.0f;
-        w.lam[r] = 0.0f;
+        w.ph.con.tmask[r] = msk;
+        w.ph.con.rc4[r].w = (k == 0) ? (M.erp / M.dt) * w.cdep[c] : 0.0f;
+        w.ph.con.lam[r] = 0.0f;
     }
     __syncwarp();
-    // Delassus block G = Y Y^T and b = Y z_f, over the blocks rows share.  G
-    // is stored as a full nr x nr square when nr <= 32, else packed.
+    // Delassus block G = Y Y^T (nr x nr) and b = Y z_f, over the blocks rows
+    // share
     const float regc = (1.0f - M.imp) / M.imp;
-    const bool square = nr <= 32;
     const int npk = nr * (nr + 1) / 2;
     for (int t = lane; t < npk + nr; t += 32) {
         if (t < npk) {
-            // decode (r, s), r <= s, from the packed index
+            // decode (r, s), r <= s, from the upper-triangle index
             int r = 0, rem = t;
             while (rem >= nr - r) {
                 rem -= nr - r;
                 ++r;
             }
             const int sc = r + rem;
-            const int m = w.tmask[r] & w.tmask[sc];
-            const float* yr = w.Y[r];
-            const float* ys = w.Y[sc];
+            const int m = w.ph.con.tmask[r] & w.ph.con.tmask[sc];
+            const float* yr = w.ph.con.Y[r];
+            const float* ys = w.ph.con.Y[sc];
             float g = 0.0f;
             if (m & 1) {
 #pragma unroll
@@ -1029,21 +1033,17 @@ __device__ __forceinline__ void contacts(const DevModel& M, WarpWS<NA>& w, int l
 #pragma unroll
                 for (int q = d::B; q < d::NV; ++q) g += yr[q] * ys[q];
             }
-            if (square) {
-                w.G[r * nr + sc] = g;
-                w.G[sc * nr + r] = g;
-            } else {
-                w.G[t] = g;
-            }
+            w.ph.con.G[r * nr + sc] = g;
+            w.ph.con.G[sc * nr + r] = g;
             if (sc == r) {
                 const float R = regc * g;
-                w.rc4[r].y = R;
-                w.rc4[r].z = 1.0f / (g + R);
+                w.ph.con.rc4[r].y = R;
+                w.ph.con.rc4[r].z = 1.0f / (g + R);
             }
         } else {
             const int r = t - npk;
-            const int m = w.tmask[r];
-            const float* yr = w.Y[r];
+            const int m = w.ph.con.tmask[r];
+            const float* yr = w.ph.con.Y[r];
             float bb = 0.0f;
             if (m & 1) {
 #pragma unroll
@@ -1057,7 +1057,7 @@ __device__ __forceinline__ void contacts(const DevModel& M, WarpWS<NA>& w, int l
 #pragma unroll
                 for (int q = d::B; q < d::NV; ++q) bb += yr[q] * w.zz[q];
             }
-            w.rc4[r].x = bb;
+            w.ph.con.rc4[r].x = bb;
         }
     }
     __syncwarp();
@@ -1067,45 +1067,29 @@ __device__ __forceinline__ void contacts(const DevModel& M, WarpWS<NA>& w, int l
     // butterfly reduction of G_rq lambda_q over the lanes, and the tangent
     // residuals take the normal update through G's normal column.
     {
-        float lamA = 0.0f, lamB = 0.0f;
+        float lamA = 0.0f;  // lambda of row `lane` (nr <= 24 rows)
         int width = 1;
         while (width < nr && width < 32) width <<= 1;
         for (int sw = 0; sw < M.sweeps; ++sw) {
             for (int c = 0; c < nc; ++c) {
                 const int rn = 3 * c;
                 float p0 = 0.0f, p1 = 0.0f, p2 = 0.0f;
-                if (square) {
-                    if (lane < nr) {
-                        p0 = w.G[rn * nr + lane] * lamA;
-                        p1 = w.G[(rn + 1) * nr + lane] * lamA;
-                        p2 = w.G[(rn + 2) * nr + lane] * lamA;
-                    }
-                } else {
-                    if (lane < nr) {
-                        p0 = w.G[packed_index(rn, lane, nr)] * lamA;
-                        p1 = w.G[packed_index(rn + 1, lane, nr)] * lamA;
-                        p2 = w.G[packed_index(rn + 2, lane, nr)] * lamA;
-                    }
-                    if (lane + 32 < nr) {
-                        p0 += w.G[packed_index(rn, lane + 32, nr)] * lamB;
-                        p1 += w.G[packed_index(rn + 1, lane + 32, nr)] * lamB;
-                        p2 += w.G[packed_index(rn + 2, lane + 32, nr)] * lamB;
-                    }
+                if (lane < nr) {
+                    p0 = w.ph.con.G[rn * nr + lane] * lamA;
+                    p1 = w.ph.con.G[(rn + 1) * nr + lane] * lamA;
+                    p2 = w.ph.con.G[(rn + 2) * nr + lane] * lamA;
                 }
-                const float4 cN = w.rc4[rn], c1 = w.rc4[rn + 1], c2 = w.rc4[rn + 2];
-                const float g1n = square ? w.G[(rn + 1) * nr + rn] : w.G[packed_index(rn + 1, rn, nr)];
-                const float g2n = square ? w.G[(rn + 2) * nr + rn] : w.G[packed_index(rn + 2, rn, nr)];
-                // lanes >= 32 of the rows sit in lamB of the same lanes, so a
-                // reduction over `width` lanes covers every row
+                const float4 cN = w.ph.con.rc4[rn], c1 = w.ph.con.rc4[rn + 1], c2 = w.ph.con.rc4[rn + 2];
+                const float g1n = w.ph.con.G[(rn + 1) * nr + rn];
+                const float g2n = w.ph.con.G[(rn + 2) * nr + rn];
                 for (int off = 1; off < width; off <<= 1) {
                     p0 += __shfl_xor_sync(FULL, p0, off);
                     p1 += __shfl_xor_sync(FULL, p1, off);
                     p2 += __shfl_xor_sync(FULL, p2, off);
                 }
-                const bool hiN = rn >= 32, hi1 = rn + 1 >= 32, hi2 = rn + 2 >= 32;
-                const float ln0 = __shfl_sync(FULL, hiN ? lamB : lamA, rn & 31);
-                const float l10 = __shfl_sync(FULL, hi1 ? lamB : lamA, (rn + 1) & 31);
-                const float l20 = __shfl_sync(FULL, hi2 ? lamB : lamA, (rn + 2) & 31);
+                const float ln0 = __shfl_sync(FULL, lamA, rn);
+                const float l10 = __shfl_sync(FULL, lamA, rn + 1);
+                const float l20 = __shfl_sync(FULL, lamA, rn + 2);
                 const float res = cN.x + p0 + cN.y * ln0 - cN.w;
                 const float ln = fmaxf(ln0 - res * cN.z, 0.0f);
                 const float dn = ln - ln0;
@@ -1119,28 +1103,18 @@ __device__ __forceinline__ void contacts(const DevModel& M, WarpWS<NA>& w, int l
                     l1 *= sc;
                     l2 *= sc;
                 }
-                if (lane == (rn & 31)) {
-                    if (hiN) lamB = ln;
-                    else lamA = ln;
-                }
-                if (lane == ((rn + 1) & 31)) {
-                    if (hi1) lamB = l1;
-                    else lamA = l1;
-                }
-                if (lane == ((rn + 2) & 31)) {
-                    if (hi2) lamB = l2;
-                    else lamA = l2;
-                }
+                if (lane == rn) lamA = ln;
+                if (lane == rn + 1) lamA = l1;
+                if (lane == rn + 2) lamA = l2;
             }
         }
-        if (lane < nr) w.lam[lane] = lamA;
-        if (lane + 32 < nr) w.lam[lane + 32] = lamB;
+        if (lane < nr) w.ph.con.lam[lane] = lamA;
     }
     __syncwarp();
     // z = z_f + Y^T lambda, then v = L^-T z
     if (lane < d::NV) {
         float zv = w.zz[lane];
-        for (int r = 0; r < nr; ++r) zv += w.Y[r][lane] * w.lam[r];
+        for (int r = 0; r < nr; ++r) zv += w.ph.con.Y[r][lane] * w.ph.con.lam[r];
         w.zz[lane] = zv;
     }
     __syncwarp();

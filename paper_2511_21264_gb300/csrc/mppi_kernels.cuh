@@ -60,13 +60,14 @@ __device__ __forceinline__ float rollout_sample(const DevModel& M, WarpWS<NA>& w
         } else if (lane < d::NU) {
             w.u[lane] = io.U[(size_t)h * d::NU + lane];
         }
-        forward_kinematics<NA>(M, w, lane);
+        float Rl[9], cl[3];  // this lane's link rotation and COM, kept for the dynamics
+        forward_kinematics<NA>(M, w, lane, Rl, cl);
         __syncwarp();
         if (h > 0 && lane == 0 && M.w_grasp != 0.0f) cost += M.w_grasp * grasp_term<NA>(w);
         n_exact += collide<NA>(M, w, lane);
         __syncwarp();
         n_con += w.ncon;
-        dynamics<NA>(M, w, lane, io.err);
+        dynamics<NA>(M, w, lane, io.err, Rl, cl);
         contacts<NA>(M, w, lane);
         integrate<NA>(M, w, lane);
         if (lane == 0) {
@@ -81,7 +82,8 @@ __device__ __forceinline__ float rollout_sample(const DevModel& M, WarpWS<NA>& w
         __syncwarp();
     }
     if (M.w_grasp != 0.0f) {
-        forward_kinematics<NA>(M, w, lane);
+        float Rl[9], cl[3];
+        forward_kinematics<NA>(M, w, lane, Rl, cl);
         __syncwarp();
         if (lane == 0) cost += M.w_grasp * grasp_term<NA>(w);
     }

@@ -78,7 +78,8 @@ int parse_blob_noalloc(const void* blob, size_t len, DevModel* M) {
     const size_t n = h[2];
     if (n < 23 || len < 16 + 8 * n) return MPPI_ERR_INVALID_ARG;
     const int na = (int)blob_value(b, 0), nb = (int)blob_value(b, 1), maxc = (int)blob_value(b, 2);
-    if (na < 1 || na > MAXL || nb < 0 || nb > MAXB || maxc < 1 || maxc > MAXC) return MPPI_ERR_INVALID_ARG;
+    if (na < 1 || na > MAXL || nb < 0 || nb > MAXB || maxc < 1 || maxc > 16) return MPPI_ERR_INVALID_ARG;
+    if (maxc > MAXC) return MPPI_ERR_UNSUPPORTED;  // more contacts than the device solver keeps
     const int nq = 2 * na + 7, nv = 2 * na + 6;
     if (n != 23 + 2 * (12 + 39 * (size_t)na) + 6 * (size_t)nb + (size_t)(nq + nv)) return MPPI_ERR_INVALID_ARG;
     std::memset(M, 0, sizeof *M);

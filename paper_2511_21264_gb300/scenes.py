@@ -18,7 +18,7 @@ Blob layout (all little-endian)::
     u32 magic 0x4950504D ("MPPI"), u32 version (1), u32 n (float64 count), u32 0
     f64[n] payload:
       [0] n_a   joints per arm (1..7)        [1] n_boxes (0..16)
-      [2] max_contacts (1..16)                [3] dt
+      [2] max_contacts (1..16; the GPU path takes up to 8)  [3] dt
       [4] PGS sweeps                          [5] friction mu
       [6] impedance d in (0,1]                [7] ERP
       [8..10] gravity                         [11] floor height
@@ -57,7 +57,7 @@ LINK_VALUES = 39
 BOX_VALUES = 6
 MAX_LINKS = 7
 MAX_BOXES = 16
-MAX_CONTACTS = 16
+MAX_CONTACTS = 8
 BIG = 1.0e30
 
 
