@@ -888,6 +888,58 @@ __device__ __forceinline__ void contact_frame_row(const float* n, int k, float* 
 }
 
 
+// Projected Gauss-Seidel for one or two contacts with the Delassus block in
+// registers: every lane runs the same sweeps (no shuffles, no shared-memory
+// round trips), then lane r stores lambda_r.  The same iteration as the
+// lane-parallel path below, summed in a different order.
+template <int NA, int NC>
+__device__ __forceinline__ void pgs_small(const DevModel& M, WarpWS<NA>& w, int lane) {
+    constexpr int NR = 3 * NC;
+    float G[NR][NR], bb[NR], R[NR], iA[NR], vs[NR], lam[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+#pragma unroll
+        for (int q = 0; q < NR; ++q) G[r][q] = w.ph.con.G[r * NR + q];
+        const float4 c4 = w.ph.con.rc4[r];
+        bb[r] = c4.x;
+        R[r] = c4.y;
+        iA[r] = c4.z;
+        vs[r] = c4.w;
+        lam[r] = 0.0f;
+    }
+    for (int sw = 0; sw < M.sweeps; ++sw) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const int rn = 3 * c;
+            float res = bb[rn] + R[rn] * lam[rn] - vs[rn];
+#pragma unroll
+            for (int q = 0; q < NR; ++q) res += G[rn][q] * lam[q];
+            const float ln = fmaxf(lam[rn] - res * iA[rn], 0.0f);
+            lam[rn] = ln;
+            float r1 = bb[rn + 1] + R[rn + 1] * lam[rn + 1];
+            float r2 = bb[rn + 2] + R[rn + 2] * lam[rn + 2];
+#pragma unroll
+            for (int q = 0; q < NR; ++q) {
+                r1 += G[rn + 1][q] * lam[q];
+                r2 += G[rn + 2][q] * lam[q];
+            }
+            float l1 = lam[rn + 1] - r1 * iA[rn + 1];
+            float l2 = lam[rn + 2] - r2 * iA[rn + 2];
+            const float n2 = l1 * l1 + l2 * l2, lim = M.mu * ln;
+            if (n2 > lim * lim) {
+                const float sc = lim * rsqrtf(n2);
+                l1 *= sc;
+                l2 *= sc;
+            }
+            lam[rn + 1] = l1;
+            lam[rn + 2] = l2;
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+        if (lane == r) w.ph.con.lam[r] = lam[r];
+}
+
 // Soft contact by projected Gauss-Seidel in contact space.  With the
 // factor L L^T = M + dt D and rows Y_r = L^-1 J_r^T, the Delassus matrix is
 // G = Y Y^T and the unconstrained row velocities are b = Y z_f, z_f = L^T
@@ -1062,11 +1114,16 @@ __device__ __forceinline__ void contacts(const DevModel& M, WarpWS<NA>& w, int l
     }
     __syncwarp();
     // projected Gauss-Seidel sweeps (normal row, then the tangent pair with
-    // the friction disk |lambda_t| <= mu lambda_n).  Lane q holds lambda_q
-    // (and lambda_{q+32}); the three residuals of a contact are one
-    // butterfly reduction of G_rq lambda_q over the lanes, and the tangent
-    // residuals take the normal update through G's normal column.
-    {
+    // the friction disk |lambda_t| <= mu lambda_n).  One or two contacts:
+    // registers.  More: lane q holds lambda_q; the three residuals of a
+    // contact are one butterfly reduction of G_rq lambda_q over the lanes,
+    // and the tangent residuals take the normal update through G's normal
+    // column.
+    if (nc == 1) {
+        pgs_small<NA, 1>(M, w, lane);
+    } else if (nc == 2) {
+        pgs_small<NA, 2>(M, w, lane);
+    } else {
         float lamA = 0.0f;  // lambda of row `lane` (nr <= 24 rows)
         int width = 1;
         while (width < nr && width < 32) width <<= 1;
