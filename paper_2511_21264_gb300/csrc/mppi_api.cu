@@ -54,6 +54,8 @@ __global__ void __launch_bounds__(512) rollout_kernel(RolloutArgs args) {
     io.err = args.err;
     io.stats = args.stats;
     io.x_out = args.states_out ? args.states_out + (size_t)k * d::NX : nullptr;
+    io.U_store = MODE == 1 ? args.U_store : nullptr;
+    io.Kn = args.n;
     if (MODE == 1) {
         io.unom = unom_n ? unom_s : args.u_nom;
         io.iter = (uint32_t)(args.iter_ptr ? *args.iter_ptr : args.iter_val);
@@ -280,6 +282,7 @@ struct mppi_ctx {
     int prof_cap = 0, prof_n = 0;
     std::vector<cudaEvent_t> prof_ev;  // 3 per recorded iteration
     unsigned long long* d_stats = nullptr;
+    float* d_U = nullptr;  // sampled controls of the last rollout (H x K x nu), when it fits
 };
 
 namespace mppi {
@@ -356,6 +359,7 @@ int mppi_destroy(mppi_ctx* c) {
     if (!c) return MPPI_OK;
     for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
     cudaFree(c->d_stats);
+    cudaFree(c->d_U);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->graph) cudaGraphDestroy(c->graph);
     cudaFree(c->d_sigma);
@@ -403,6 +407,10 @@ int mppi_create(const mppi_model* m, int K, int H, float lambda, const float* si
     if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(c->d_iter, 0, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(c->d_done, 0, sizeof(unsigned int));
+    // the update reads the rollout's samples instead of regenerating them
+    // when the buffer is modest
+    const size_t ubytes = (size_t)K * H * nu * sizeof(float);
+    if (e == cudaSuccess && ubytes <= ((size_t)256 << 20)) e = cudaMalloc(&c->d_U, ubytes);
     if (e != cudaSuccess) {
         mppi_destroy(c);
         return cuda_fail(e);
@@ -477,6 +485,7 @@ static RolloutArgs philox_args(mppi_ctx* c, const float* state, const float* u_n
     a.costs = c->d_costs;
     a.err = c->d_err;
     a.stage_unom = c->H * 2 * c->m->info.na <= 2048;
+    a.U_store = c->d_U;
     return a;
 }
 
@@ -513,6 +522,7 @@ static int enqueue_step(mppi_ctx* c, const float* state, const float* u_nom, flo
     if (rc != MPPI_OK) return rc;
     if (prof) cudaEventRecord(ev[1], s);
     UpdateArgs u = update_args(c, c->d_costs, u_nom, u_out, 1, best);
+    u.U_stored = c->d_U;
     rc = launch_update(2 * c->m->info.na, u, c->H, s);
     if (prof) {
         cudaEventRecord(ev[2], s);

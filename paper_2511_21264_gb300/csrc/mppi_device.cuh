@@ -955,17 +955,27 @@ __device__ __forceinline__ void contacts(const DevModel& M, WarpWS<NA>& w, int l
         return;
     }
     const float ismb = rsqrtf(M.mb), isIb = rsqrtf(M.Ib);
+    // blocks any contact touches (warp-uniform): 1 left arm, 2 right arm,
+    // 4 ball.  Untouched blocks keep v = v_f and skip the z-space work.
+    int tb = 0;
+    if (lane < nc) {
+        const int A = w.cA[lane], Bb = w.cB[lane];
+        if (A == d::B || Bb == d::B) tb |= 4;
+        if (A >= 0 && A < d::B) tb |= 1 << (A / NA);
+        if (Bb >= 0 && Bb < d::B) tb |= 1 << (Bb / NA);
+    }
+    tb = (int)__reduce_or_sync(FULL, (unsigned)tb);
     // z_f = L^T v_f (one lane per arm coordinate; lane 15 the ball)
     {
         const int a = lane >> 4, i = lane & 15;
-        if (i < NA) {
+        if (i < NA && ((tb >> a) & 1)) {
             float sz = 0.0f;
 #pragma unroll
             for (int k = 0; k < NA; ++k)
                 if (k >= i) sz += w.L[a][k][i] * w.vf[a * NA + k];
             w.zz[a * NA + i] = sz;
         }
-        if (lane == 15) {
+        if (lane == 15 && (tb & 4)) {
             const float smb = M.mb * ismb, sIb = M.Ib * isIb;
 #pragma unroll
             for (int r = 0; r < 3; ++r) {
@@ -1168,14 +1178,19 @@ __device__ __forceinline__ void contacts(const DevModel& M, WarpWS<NA>& w, int l
         if (lane < nr) w.ph.con.lam[lane] = lamA;
     }
     __syncwarp();
-    // z = z_f + Y^T lambda, then v = L^-T z
+    // z = z_f + Y^T lambda, then v = L^-T z on the touched blocks
     if (lane < d::NV) {
-        float zv = w.zz[lane];
-        for (int r = 0; r < nr; ++r) zv += w.ph.con.Y[r][lane] * w.ph.con.lam[r];
-        w.zz[lane] = zv;
+        const int blk = lane < NA ? 1 : (lane < 2 * NA ? 2 : 4);
+        if (tb & blk) {
+            float zv = w.zz[lane];
+            for (int r = 0; r < nr; ++r) zv += w.ph.con.Y[r][lane] * w.ph.con.lam[r];
+            w.zz[lane] = zv;
+        } else {
+            w.v[lane] = w.vf[lane];
+        }
     }
     __syncwarp();
-    if ((lane & 15) == 0) {
+    if ((lane & 15) == 0 && ((tb >> (lane >> 4)) & 1)) {
         const int a = lane >> 4;
         float zl[NA], t[NA];
 #pragma unroll
@@ -1190,7 +1205,7 @@ __device__ __forceinline__ void contacts(const DevModel& M, WarpWS<NA>& w, int l
 #pragma unroll
         for (int ii = 0; ii < NA; ++ii) w.v[a * NA + ii] = t[ii];
     }
-    if (lane == 15) {
+    if (lane == 15 && (tb & 4)) {
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
             w.v[d::B + r] = w.zz[d::B + r] * ismb;

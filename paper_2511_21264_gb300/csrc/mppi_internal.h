@@ -48,6 +48,7 @@ struct RolloutArgs {
     int* err;                    // error word
     int stage_unom;              // stage u_nom in shared memory
     unsigned long long* stats;   // optional: [sample-steps, contacts, exact box tests]
+    float* U_store;              // optional: sampled controls, H x n x nu (h-major), MODE 1
 };
 
 // Arguments of the weighted-mean update (one CTA per horizon step).
@@ -67,6 +68,7 @@ struct UpdateArgs {
     float* best;        // optional: min cost, argmin
     int advance;        // last CTA increments *iter_ptr
     unsigned int* done; // CTA completion counter (reset by the last CTA)
+    const float* U_stored;  // optional: the rollout's sampled controls (H x K x nu), else regenerated
 };
 
 struct NoiseArgs {

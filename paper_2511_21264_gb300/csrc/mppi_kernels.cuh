@@ -16,6 +16,8 @@ struct SampleIO {
     uint32_t iter;             // Philox iteration word, MODE 1
     int k, H;                  // sample index, horizon
     float* x_out;              // optional final state (nx)
+    float* U_store;            // optional: sampled controls out, H x Kn x nu (h-major)
+    int Kn;                    // sample count of U_store
     int* err;                  // error word
     unsigned long long* stats; // optional [sample-steps, contacts, exact box tests]
 };
@@ -55,8 +57,10 @@ __device__ __forceinline__ float rollout_sample(const DevModel& M, WarpWS<NA>& w
                 }
                 __syncwarp();
             }
-            if (lane < d::NU)
+            if (lane < d::NU) {
                 w.u[lane] = fminf(fmaxf(__fmaf_rn(io.sig, w.zn[h & 7][lane], io.unom[h * d::NU + lane]), io.lo), io.hi);
+                if (io.U_store) io.U_store[((size_t)h * io.Kn + k) * d::NU + lane] = w.u[lane];
+            }
         } else if (lane < d::NU) {
             w.u[lane] = io.U[(size_t)h * d::NU + lane];
         }
@@ -168,16 +172,23 @@ __device__ __forceinline__ void update_step(const UpdateArgs& a, int h, UpdateSm
             const float c = a.costs[k];
             const float wk = isfinite(c) ? expf(-(c - cmin) * inv_lam) : 0.0f;
             Z += wk;
+            if (a.U_stored) {
+                // the rollout's own samples (bit-identical to regenerating them)
+                const float* uk = a.U_stored + ((size_t)h * a.K + k) * NU;
 #pragma unroll
-            for (int jb = 0; jb < (NU + 3) / 4; ++jb) {
-                const uint4 wv = philox4x32_10(make_uint4((uint32_t)jb, (uint32_t)h, (uint32_t)k, iter), key);
+                for (int j = 0; j < NU; ++j) acc[j] += wk * uk[j];
+            } else {
 #pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    const int j = 4 * jb + t;
-                    if (j < NU) {
-                        const float z = block_normal(wv, t);
-                        const float u = fminf(fmaxf(__fmaf_rn(sg[j], z, un[j]), lo[j]), hi[j]);
-                        acc[j] += wk * u;
+                for (int jb = 0; jb < (NU + 3) / 4; ++jb) {
+                    const uint4 wv = philox4x32_10(make_uint4((uint32_t)jb, (uint32_t)h, (uint32_t)k, iter), key);
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const int j = 4 * jb + t;
+                        if (j < NU) {
+                            const float z = block_normal(wv, t);
+                            const float u = fminf(fmaxf(__fmaf_rn(sg[j], z, un[j]), lo[j]), hi[j]);
+                            acc[j] += wk * u;
+                        }
                     }
                 }
             }
