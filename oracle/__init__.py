@@ -84,6 +84,11 @@ def lib():
         L.or_mppi_update.restype = i
         L.or_mppi_iteration.argtypes = [vp, dp, dp, i, i, d, dp, C.c_uint64, C.c_uint64, dp, dp, dp, i]
         L.or_mppi_iteration.restype = i
+        ip = C.POINTER(C.c_int)
+        L.or_elite_update.argtypes = [i, i, i, dp, dp, i, d, d, i, d, dp, dp, dp, dp, ip]
+        L.or_elite_update.restype = i
+        L.or_sample_cov.argtypes = [vp, C.c_uint64, C.c_uint64, i, i, dp, dp, dp]
+        L.or_sample_cov.restype = i
         _lib = L
     return _lib
 
@@ -181,6 +186,17 @@ class Model:
                               _dp(costs), nthreads)
         return costs
 
+    def sample_cov(self, seed, iteration, K, nu_in, Sigma):
+        """Samples U (K x H x nu) from per-step covariance blocks."""
+        nu_in = _f64(nu_in)
+        H = nu_in.shape[0]
+        U = np.zeros((K, H, self.nu))
+        rc = lib().or_sample_cov(self.ptr, C.c_uint64(seed), C.c_uint64(iteration), K, H, _dp(nu_in),
+                                 _dp(_f64(Sigma)), _dp(U))
+        if rc != 0:
+            raise FloatingPointError("oracle: covariance block not positive definite")
+        return U
+
     def mppi_iteration(self, x, u_nom, K, lam, sigma, seed, iteration, nthreads=1,
                        want_samples=False):
         u_nom = _f64(u_nom)
@@ -244,6 +260,21 @@ def noise(seed, iteration, K, H, nu, sigma):
     eps = np.zeros((K, H, nu))
     lib().or_noise(C.c_uint64(seed), C.c_uint64(iteration), K, H, nu, _dp(_f64(sigma)), _dp(eps))
     return eps
+
+
+def elite_update(costs, U, n_elite, beta, eta, nu_in, Sigma_in, update_cov=True, cov_floor=0.0):
+    """Eq. 8 in full: elite set, learning rate, per-step covariance blocks.
+    Returns (nu', Sigma', elite indices in cost order, status)."""
+    costs = _f64(costs)
+    U = _f64(U)
+    K, H, nu = U.shape
+    nu_out = np.zeros((H, nu))
+    S_out = np.zeros((H, nu, nu))
+    elite = np.zeros(max(1, min(n_elite, K)), dtype=np.int32)
+    st = lib().or_elite_update(K, H, nu, _dp(costs), _dp(U), int(n_elite), float(beta), float(eta), int(update_cov),
+                               float(cov_floor), _dp(_f64(nu_in)), _dp(_f64(Sigma_in)), _dp(nu_out), _dp(S_out),
+                               elite.ctypes.data_as(C.POINTER(C.c_int)))
+    return nu_out, S_out, elite, st
 
 
 def mppi_update(costs, U, lam, u_nom):

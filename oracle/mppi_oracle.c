@@ -1036,3 +1036,112 @@ int or_mppi_iteration(const or_model *m, const double *x, const double *u_nom, i
     if (!U_out) free(U);
     return st;
 }
+
+/* --------------------------------------------------------------------- */
+/* Eq. 8 in full: elite set, learning rate, covariance                    */
+/* --------------------------------------------------------------------- */
+/* Per horizon step h the sampling covariance is a full nu x nu block
+ * Sigma_h (a reading: the paper does not fix the covariance structure);
+ * samples are U_k[h] = clamp(nu_h + L_h z_k[h]) with L_h the Cholesky factor
+ * of Sigma_h and z the standard normals of or_noise.
+ *
+ * One update (Eq. 8a-8d):
+ *   EliteSet = the n_e samples of lowest cost (ties -> lower index);
+ *   s_j = exp(-(c_j - c_min)/beta) over the elite set (the shift cancels);
+ *   nu'      = (1 - eta) nu + eta sum_j s_j U_j / sum_j s_j;
+ *   dSigma_h = sum_j s_j (U_j[h] - nu'_h)(U_j[h] - nu'_h)^T / sum_j s_j;
+ *   Sigma'_h = (1 - eta) Sigma_h + eta dSigma_h + floor I.
+ * Returns 0, or 1 when no cost is finite (everything unchanged). */
+typedef struct { double c; int k; } or_key;
+static int or_key_cmp(const void *a, const void *b) {
+    const or_key *x = (const or_key *)a, *y = (const or_key *)b;
+    if (x->c < y->c) return -1;
+    if (x->c > y->c) return 1;
+    return (x->k > y->k) - (x->k < y->k);
+}
+
+int or_elite_update(int K, int H, int nu, const double *costs, const double *U, int n_elite, double beta, double eta,
+                    int update_cov, double cov_floor, const double *nu_in, const double *Sigma_in, double *nu_out,
+                    double *Sigma_out, int *elite_out) {
+    or_key *keys = (or_key *)malloc(sizeof(or_key) * K);
+    int nf = 0;
+    for (int k = 0; k < K; k++) {
+        keys[k].c = isfinite(costs[k]) ? costs[k] : INFINITY;
+        keys[k].k = k;
+        nf += isfinite(costs[k]) ? 1 : 0;
+    }
+    if (nf == 0) {
+        memcpy(nu_out, nu_in, sizeof(double) * H * nu);
+        if (Sigma_out) memcpy(Sigma_out, Sigma_in, sizeof(double) * H * nu * nu);
+        free(keys);
+        return 1;
+    }
+    qsort(keys, K, sizeof(or_key), or_key_cmp);
+    int ne = n_elite < nf ? n_elite : nf;
+    if (ne < 1) ne = 1;
+    double cmin = keys[0].c, Z = 0.0;
+    double *s = (double *)malloc(sizeof(double) * ne);
+    for (int e = 0; e < ne; e++) {
+        s[e] = exp(-(keys[e].c - cmin) / beta);
+        Z += s[e];
+        if (elite_out) elite_out[e] = keys[e].k;
+    }
+    for (int i = 0; i < H * nu; i++) {
+        double acc = 0.0;
+        for (int e = 0; e < ne; e++) acc += s[e] * U[(size_t)keys[e].k * H * nu + i];
+        nu_out[i] = (1.0 - eta) * nu_in[i] + eta * acc / Z;
+    }
+    if (Sigma_out) {
+        for (int h = 0; h < H; h++)
+            for (int a = 0; a < nu; a++)
+                for (int b = 0; b < nu; b++) {
+                    double acc = 0.0;
+                    if (update_cov) {
+                        for (int e = 0; e < ne; e++) {
+                            const double *u = U + (size_t)keys[e].k * H * nu + (size_t)h * nu;
+                            acc += s[e] * (u[a] - nu_out[h * nu + a]) * (u[b] - nu_out[h * nu + b]);
+                        }
+                        acc /= Z;
+                    }
+                    size_t idx = ((size_t)h * nu + a) * nu + b;
+                    double v = update_cov ? (1.0 - eta) * Sigma_in[idx] + eta * acc : Sigma_in[idx];
+                    if (update_cov && a == b) v += cov_floor;
+                    Sigma_out[idx] = v;
+                }
+    }
+    free(s);
+    free(keys);
+    return 0;
+}
+
+/* Samples from per-step covariance blocks: U_k[h] = clamp(nu_h + L_h z)
+ * with L_h = chol(Sigma_h) (dense Cholesky) and z the unit normals of
+ * (seed, iteration).  Returns -1 if a block is not positive definite. */
+int or_sample_cov(const or_model *m, uint64_t seed, uint64_t iteration, int K, int H, const double *nu_in,
+                  const double *Sigma, double *U) {
+    int nu = m->nu;
+    double *z = (double *)malloc(sizeof(double) * (size_t)K * H * nu);
+    double *ones = (double *)malloc(sizeof(double) * nu);
+    for (int j = 0; j < nu; j++) ones[j] = 1.0;
+    or_noise(seed, iteration, K, H, nu, ones, z);
+    double L[OR_MAXNV * OR_MAXNV];
+    int rc = 0;
+    for (int h = 0; h < H && rc == 0; h++) {
+        memcpy(L, Sigma + (size_t)h * nu * nu, sizeof(double) * nu * nu);
+        if (cholesky(L, nu) != 0) { rc = -1; break; }
+        for (int k = 0; k < K; k++) {
+            const double *zk = z + ((size_t)k * H + h) * nu;
+            for (int j = 0; j < nu; j++) {
+                double acc = nu_in[h * nu + j];
+                for (int i = 0; i <= j; i++) acc += L[j * nu + i] * zk[i];
+                const or_link *Lk = &m->L[j / m->na][j % m->na];
+                if (acc < Lk->u_lo) acc = Lk->u_lo;
+                if (acc > Lk->u_hi) acc = Lk->u_hi;
+                U[((size_t)k * H + h) * nu + j] = acc;
+            }
+        }
+    }
+    free(z);
+    free(ones);
+    return rc;
+}
