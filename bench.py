@@ -207,6 +207,8 @@ def run_ours(args):
     ctl = native.Controller(model, K, H, sc.lam, sc.sigma_vec(), scenes.controller_key(sc.seed, rank))
     if args.spc:
         ctl.set_launch(args.spc)
+    if args.elite or args.eta != 1.0 or args.cov:
+        ctl.set_update(args.elite or K, args.eta, args.cov, 1e-6)
     stream = torch.cuda.Stream(device=dev)
     x = torch.tensor(model.home(), device=dev)
     u = torch.zeros((H, sc.nu), device=dev)
@@ -288,6 +290,9 @@ def run_ours(args):
     }
     if args.workload != "lift":
         line["metric"] = METRIC.replace("MPPI iteration", "MPPI iteration, " + args.workload)
+    if args.elite or args.eta != 1.0 or args.cov:
+        line["config"]["update"] = {"n_elite": args.elite or K, "eta": args.eta, "covariance": bool(args.cov)}
+        line["metric"] = line["metric"].replace("weights + update", "elite set + Eq. 8 update")
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sc, seconds=args.cpu_seconds)
     print(json.dumps(line), flush=True)
@@ -487,6 +492,9 @@ def main(argv=None):
                          "H=64; batched: 64 instances (K 256..4096, H 16..64, 0..16 boxes) in one "
                          "persistent launch vs 64 sequential plain launches; serve: Poisson replan "
                          "requests over 256 scenes, batched server vs one-at-a-time server")
+    ap.add_argument("--elite", type=int, default=0, help="elite set size (0 = all samples: the plain update)")
+    ap.add_argument("--eta", type=float, default=1.0, help="learning rate of Eq. 8 (elite mode)")
+    ap.add_argument("--cov", action="store_true", help="update the per-step covariance blocks (Eq. 8b/8c)")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="arrival window per rate (serve)")
     ap.add_argument("--serve-rates", type=str, default="50,200,1000")
     ap.add_argument("--spc", type=int, default=0, help="samples per CTA (0 = library default)")

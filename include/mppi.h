@@ -147,6 +147,28 @@ int mppi_profile(mppi_ctx *c, int n);
 int mppi_profile_read(mppi_ctx *c, int *n, float *rollout_ms, float *update_ms, double *contacts_per_step,
                       double *box_tests_per_step);
 
+/* The paper's full update (Eq. 8a-8d): the elite set is the n_elite
+ * samples of lowest cost (ties -> lower index; non-finite costs never
+ * elite), s_j = exp(-(c_j - c_min)/lambda) over the elite set,
+ *   nu'      = (1 - eta) nu + eta sum_j s_j U_j / sum_j s_j,
+ * and with update_cov = 1
+ *   Sigma'_h = (1 - eta) Sigma_h + eta sum_j s_j (U_j[h] - nu'_h)(...)^T /
+ *              sum_j s_j + cov_floor I
+ * for one nu x nu block per horizon step h (a reading: the paper does not
+ * fix the covariance structure); later iterations then sample
+ * U = clamp(nu + L_h z) with L_h the block's Cholesky factor.  Defaults:
+ * n_elite = K, eta = 1, update_cov = 0 (the plain update).  n_elite < K
+ * needs K <= 8192; update_cov needs the controller's sample buffer
+ * (K H nu floats <= 256 MB). */
+int mppi_set_update(mppi_ctx *c, int n_elite, float eta, int update_cov, float cov_floor);
+/* Covariance blocks Sigma_h (device, H x nu x nu).  set: each block must be
+ * positive definite (factored on the host); sampling then uses them. */
+int mppi_get_covariance(mppi_ctx *c, float *Sigma, void *stream);
+int mppi_set_covariance(mppi_ctx *c, const float *Sigma, void *stream);
+/* Controls of the lowest-cost sample of the last elite update (device,
+ * H x nu): the optimiser's output besides nu and Sigma (Alg. 1). */
+int mppi_best_controls(mppi_ctx *c, float *U_best, void *stream);
+
 /* Launch shape: samples (warps) per CTA for the rollout kernels, 1..16
  * (0 = the library default).  Used by the autotuner. */
 int mppi_set_launch(mppi_ctx *c, int samples_per_cta);

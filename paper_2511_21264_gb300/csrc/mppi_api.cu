@@ -56,6 +56,7 @@ __global__ void __launch_bounds__(512) rollout_kernel(RolloutArgs args) {
     io.x_out = args.states_out ? args.states_out + (size_t)k * d::NX : nullptr;
     io.U_store = MODE == 1 ? args.U_store : nullptr;
     io.Kn = args.n;
+    io.Lfac = MODE == 1 ? args.Lfac : nullptr;
     if (MODE == 1) {
         io.unom = unom_n ? unom_s : args.u_nom;
         io.iter = (uint32_t)(args.iter_ptr ? *args.iter_ptr : args.iter_val);
@@ -89,6 +90,67 @@ __global__ void noise_kernel(NoiseArgs a) {
         const int k = (int)(i / ((size_t)NU * a.H));
         const uint4 wv = philox4x32_10(make_uint4((uint32_t)(j >> 2), (uint32_t)h, (uint32_t)k, (uint32_t)a.iter), key);
         a.eps[i] = __fmul_rn(a.sigma[j], block_normal(wv, j & 3));
+    }
+}
+
+// Elite threshold: bitonic sort of (cost, index) keys in shared memory (one
+// CTA, P = power of two >= K); sel = [key of the n_e-th elite, lowest key,
+// finite count].
+__global__ void __launch_bounds__(1024) elite_select_kernel(const float* costs, int K, int P, int n_elite,
+                                                            unsigned long long* sel) {
+    extern __shared__ unsigned long long keys[];
+    __shared__ int nfin;
+    if (threadIdx.x == 0) nfin = 0;
+    __syncthreads();
+    int mine = 0;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const float c = i < K ? costs[i] : 0.0f;
+        keys[i] = i < K ? cost_key(c, i) : ~0ull;
+        mine += (i < K && isfinite(c)) ? 1 : 0;
+    }
+    atomicAdd(&nfin, mine);
+    __syncthreads();
+    for (int size = 2; size <= P; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                const int j = i ^ stride;
+                if (j > i) {
+                    const bool asc = (i & size) == 0;
+                    const unsigned long long x = keys[i], y = keys[j];
+                    if ((x > y) == asc) {
+                        keys[i] = y;
+                        keys[j] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    if (threadIdx.x == 0) {
+        const int nf = nfin;
+        const int ne = nf == 0 ? 0 : (n_elite < nf ? n_elite : nf);
+        sel[0] = ne > 0 ? keys[ne - 1] : 0ull;
+        sel[1] = keys[0];
+        sel[2] = (unsigned long long)nf;
+    }
+}
+
+template <int NU>
+__global__ void __launch_bounds__(256) elite_update_kernel(EliteArgs a) {
+    __shared__ EliteSmem<NU> sm;
+    elite_update_step<NU>(a, blockIdx.x, sm);
+    if (a.advance) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            const unsigned t = atomicAdd(a.done, 1u);
+            sm.is_last = (t == gridDim.x - 1);
+        }
+        __syncthreads();
+        if (sm.is_last && threadIdx.x == 0) {
+            *a.done = 0u;
+            *const_cast<unsigned long long*>(a.iter_ptr) += 1ull;
+            __threadfence();
+        }
     }
 }
 
@@ -283,6 +345,14 @@ struct mppi_ctx {
     std::vector<cudaEvent_t> prof_ev;  // 3 per recorded iteration
     unsigned long long* d_stats = nullptr;
     float* d_U = nullptr;  // sampled controls of the last rollout (H x K x nu), when it fits
+    // full Eq. 8 (elite set, learning rate, covariance blocks)
+    int n_elite = 0;
+    float eta = 1.0f, cov_floor = 0.0f;
+    int update_cov = 0, cov_sampling = 0;
+    float* d_Sigma = nullptr;  // H x nu x nu
+    float* d_L = nullptr;      // H x nu x nu factors used for sampling
+    unsigned long long* d_sel = nullptr;
+    float* d_bestU = nullptr;  // H x nu
 };
 
 namespace mppi {
@@ -360,6 +430,10 @@ int mppi_destroy(mppi_ctx* c) {
     for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
     cudaFree(c->d_stats);
     cudaFree(c->d_U);
+    cudaFree(c->d_Sigma);
+    cudaFree(c->d_L);
+    cudaFree(c->d_sel);
+    cudaFree(c->d_bestU);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->graph) cudaGraphDestroy(c->graph);
     cudaFree(c->d_sigma);
@@ -386,6 +460,7 @@ int mppi_create(const mppi_model* m, int K, int H, float lambda, const float* si
     c->H = H;
     c->lambda = lambda;
     c->seed = seed;
+    c->n_elite = K;
     const int nu = 2 * m->info.na;
     std::vector<float> lo(nu), hi(nu);
     for (int j = 0; j < nu; ++j) {
@@ -465,6 +540,110 @@ int mppi_profile_read(mppi_ctx* c, int* n, float* rollout_ms, float* update_ms, 
     return MPPI_OK;
 }
 
+int mppi_set_update(mppi_ctx* c, int n_elite, float eta, int update_cov, float cov_floor) {
+    if (!c || n_elite < 1 || n_elite > c->K || !(eta > 0.0f && eta <= 1.0f) || update_cov < 0 || update_cov > 1 ||
+        !(cov_floor >= 0.0f))
+        return MPPI_ERR_INVALID_ARG;
+    if (n_elite < c->K && c->K > 8192) return MPPI_ERR_UNSUPPORTED;  // the elite sort holds 8192 keys
+    const int nu = 2 * c->m->info.na;
+    if (update_cov && !c->d_U) return MPPI_ERR_UNSUPPORTED;  // needs the stored samples
+    cudaError_t e = cudaSuccess;
+    const size_t blk = (size_t)c->H * nu * nu;
+    if (!c->d_Sigma) {
+        e = cudaMalloc(&c->d_Sigma, blk * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc(&c->d_L, blk * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc(&c->d_sel, 3 * sizeof(unsigned long long));
+        if (e == cudaSuccess) e = cudaMalloc(&c->d_bestU, (size_t)c->H * nu * sizeof(float));
+        if (e != cudaSuccess) return cuda_fail(e);
+        // Sigma_0 = diag(sigma^2), its factor diag(sigma)
+        std::vector<float> sig(nu), S(blk, 0.0f), Lh(blk, 0.0f);
+        e = cudaMemcpy(sig.data(), c->d_sigma, nu * sizeof(float), cudaMemcpyDeviceToHost);
+        for (int h = 0; h < c->H; ++h)
+            for (int j = 0; j < nu; ++j) {
+                S[((size_t)h * nu + j) * nu + j] = sig[j] * sig[j];
+                Lh[((size_t)h * nu + j) * nu + j] = sig[j];
+            }
+        if (e == cudaSuccess) e = cudaMemcpy(c->d_Sigma, S.data(), blk * sizeof(float), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(c->d_L, Lh.data(), blk * sizeof(float), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    c->n_elite = n_elite;
+    c->eta = eta;
+    c->update_cov = update_cov;
+    c->cov_floor = cov_floor;
+    if (update_cov) c->cov_sampling = 1;
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->gexec = nullptr;
+    c->graph = nullptr;
+    return MPPI_OK;
+}
+
+int mppi_get_covariance(mppi_ctx* c, float* Sigma, void* stream) {
+    if (!c || !Sigma) return MPPI_ERR_INVALID_ARG;
+    const int nu = 2 * c->m->info.na;
+    const size_t blk = (size_t)c->H * nu * nu;
+    if (!c->d_Sigma) {  // fixed diagonal Sigma = diag(sigma^2)
+        std::vector<float> sig(nu), S(blk, 0.0f);
+        cudaError_t e = cudaMemcpy(sig.data(), c->d_sigma, nu * sizeof(float), cudaMemcpyDeviceToHost);
+        for (int h = 0; h < c->H; ++h)
+            for (int j = 0; j < nu; ++j) S[((size_t)h * nu + j) * nu + j] = sig[j] * sig[j];
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(Sigma, S.data(), blk * sizeof(float), cudaMemcpyHostToDevice, (cudaStream_t)stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+        return cuda_fail(e);
+    }
+    return cuda_fail(cudaMemcpyAsync(Sigma, c->d_Sigma, blk * sizeof(float), cudaMemcpyDeviceToDevice,
+                                     (cudaStream_t)stream));
+}
+
+int mppi_set_covariance(mppi_ctx* c, const float* Sigma, void* stream) {
+    if (!c || !Sigma) return MPPI_ERR_INVALID_ARG;
+    if (!c->d_Sigma) {
+        int rc = mppi_set_update(c, c->n_elite, c->eta, c->update_cov, c->cov_floor);
+        if (rc != MPPI_OK) return rc;
+    }
+    const int nu = 2 * c->m->info.na;
+    const size_t blk = (size_t)c->H * nu * nu;
+    std::vector<float> S(blk), Lh(blk, 0.0f);
+    cudaError_t e = cudaMemcpyAsync(S.data(), Sigma, blk * sizeof(float), cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    for (int h = 0; h < c->H; ++h) {  // factor on the host (FP64), once
+        const float* A = &S[(size_t)h * nu * nu];
+        std::vector<double> L(nu * nu, 0.0);
+        for (int j = 0; j < nu; ++j) {
+            double d = A[j * nu + j];
+            for (int k = 0; k < j; ++k) d -= L[j * nu + k] * L[j * nu + k];
+            if (!(d > 0.0)) return MPPI_ERR_INVALID_ARG;  // not positive definite
+            d = std::sqrt(d);
+            L[j * nu + j] = d;
+            for (int r = j + 1; r < nu; ++r) {
+                double t = A[r * nu + j];
+                for (int k = 0; k < j; ++k) t -= L[r * nu + k] * L[j * nu + k];
+                L[r * nu + j] = t / d;
+            }
+        }
+        for (int q = 0; q < nu * nu; ++q) Lh[(size_t)h * nu * nu + q] = (float)L[q];
+    }
+    e = cudaMemcpy(c->d_Sigma, S.data(), blk * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_L, Lh.data(), blk * sizeof(float), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e);
+    c->cov_sampling = 1;
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->gexec = nullptr;
+    c->graph = nullptr;
+    return MPPI_OK;
+}
+
+int mppi_best_controls(mppi_ctx* c, float* U_best, void* stream) {
+    if (!c || !U_best || !c->d_bestU) return MPPI_ERR_INVALID_ARG;
+    const int nu = 2 * c->m->info.na;
+    return cuda_fail(cudaMemcpyAsync(U_best, c->d_bestU, (size_t)c->H * nu * sizeof(float), cudaMemcpyDeviceToDevice,
+                                     (cudaStream_t)stream));
+}
+
 int mppi_set_launch(mppi_ctx* c, int spc) {
     if (!c || spc < 0 || spc > 16) return MPPI_ERR_INVALID_ARG;
     c->spc = spc == 0 ? 4 : spc;
@@ -486,7 +665,54 @@ static RolloutArgs philox_args(mppi_ctx* c, const float* state, const float* u_n
     a.err = c->d_err;
     a.stage_unom = c->H * 2 * c->m->info.na <= 2048;
     a.U_store = c->d_U;
+    a.Lfac = c->cov_sampling ? c->d_L : nullptr;
     return a;
+}
+
+static bool elite_mode(const mppi_ctx* c) {
+    return c->n_elite != c->K || c->eta != 1.0f || c->update_cov || c->cov_sampling;
+}
+
+static int launch_elite(mppi_ctx* c, const float* costs, const float* u_nom, float* u_out, int advance,
+                        const float* U_stored, cudaStream_t s) {
+    const int nu = 2 * c->m->info.na;
+    int P = 1;
+    while (P < c->K) P <<= 1;
+    const size_t sm = (size_t)P * sizeof(unsigned long long);
+    if (sm > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(elite_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    elite_select_kernel<<<1, 1024, sm, s>>>(costs, c->K, P, c->n_elite, c->d_sel);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e);
+    EliteArgs a{};
+    a.K = c->K;
+    a.n_elite = c->n_elite;
+    a.update_cov = c->update_cov;
+    a.beta = c->lambda;
+    a.eta = c->eta;
+    a.cov_floor = c->cov_floor;
+    a.costs = costs;
+    a.u_nom = u_nom;
+    a.u_out = u_out;
+    a.sigma = c->d_sigma;
+    a.Lfac = c->cov_sampling ? c->d_L : nullptr;
+    a.u_lo = c->d_ulo;
+    a.u_hi = c->d_uhi;
+    a.Sigma = c->d_Sigma;
+    a.Lout = c->d_L;
+    a.seed = c->seed;
+    a.iter_ptr = c->d_iter;
+    a.U_stored = U_stored;
+    a.sel = c->d_sel;
+    a.best_U = c->d_bestU;
+    a.err = c->d_err;
+    a.advance = advance;
+    a.done = c->d_done;
+    if (nu == 6) elite_update_kernel<6><<<c->H, 256, 0, s>>>(a);
+    else elite_update_kernel<14><<<c->H, 256, 0, s>>>(a);
+    return cuda_fail(cudaGetLastError());
 }
 
 static UpdateArgs update_args(mppi_ctx* c, const float* costs, const float* u_nom, float* u_out, int advance,
@@ -521,9 +747,13 @@ static int enqueue_step(mppi_ctx* c, const float* state, const float* u_nom, flo
     int rc = launch_rollout(c->m->info.na, 1, a, c->spc, s);
     if (rc != MPPI_OK) return rc;
     if (prof) cudaEventRecord(ev[1], s);
-    UpdateArgs u = update_args(c, c->d_costs, u_nom, u_out, 1, best);
-    u.U_stored = c->d_U;
-    rc = launch_update(2 * c->m->info.na, u, c->H, s);
+    if (elite_mode(c)) {
+        rc = launch_elite(c, c->d_costs, u_nom, u_out, 1, c->d_U, s);
+    } else {
+        UpdateArgs u = update_args(c, c->d_costs, u_nom, u_out, 1, best);
+        u.U_stored = c->d_U;
+        rc = launch_update(2 * c->m->info.na, u, c->H, s);
+    }
     if (prof) {
         cudaEventRecord(ev[2], s);
         c->prof_n++;
@@ -584,6 +814,7 @@ int mppi_solve(mppi_ctx* c, const float* state, float* u, int iters, float* best
 
 int mppi_update(mppi_ctx* c, const float* costs, const float* u_nom, float* u_out, void* stream) {
     if (!c || !costs || !u_nom || !u_out) return MPPI_ERR_INVALID_ARG;
+    if (elite_mode(c)) return launch_elite(c, costs, u_nom, u_out, 0, nullptr, (cudaStream_t)stream);
     UpdateArgs u = update_args(c, costs, u_nom, u_out, 0, c->d_best);
     return launch_update(2 * c->m->info.na, u, c->H, (cudaStream_t)stream);
 }

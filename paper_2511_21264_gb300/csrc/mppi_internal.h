@@ -49,6 +49,7 @@ struct RolloutArgs {
     int stage_unom;              // stage u_nom in shared memory
     unsigned long long* stats;   // optional: [sample-steps, contacts, exact box tests]
     float* U_store;              // optional: sampled controls, H x n x nu (h-major), MODE 1
+    const float* Lfac;           // optional: covariance factors H x nu x nu (MODE 1), else diagonal sigma
 };
 
 // Arguments of the weighted-mean update (one CTA per horizon step).

@@ -18,6 +18,7 @@ struct SampleIO {
     float* x_out;              // optional final state (nx)
     float* U_store;            // optional: sampled controls out, H x Kn x nu (h-major)
     int Kn;                    // sample count of U_store
+    const float* Lfac;         // optional: H x nu x nu factors of the sampling covariance blocks
     int* err;                  // error word
     unsigned long long* stats; // optional [sample-steps, contacts, exact box tests]
 };
@@ -58,7 +59,14 @@ __device__ __forceinline__ float rollout_sample(const DevModel& M, WarpWS<NA>& w
                 __syncwarp();
             }
             if (lane < d::NU) {
-                w.u[lane] = fminf(fmaxf(__fmaf_rn(io.sig, w.zn[h & 7][lane], io.unom[h * d::NU + lane]), io.lo), io.hi);
+                float acc = io.unom[h * d::NU + lane];
+                if (io.Lfac) {  // u = nu + L_h z, FMAs in the order sample_row uses
+                    const float* Lr = io.Lfac + ((size_t)h * d::NU + lane) * d::NU;
+                    for (int i = 0; i <= lane; ++i) acc = __fmaf_rn(Lr[i], w.zn[h & 7][i], acc);
+                } else {
+                    acc = __fmaf_rn(io.sig, w.zn[h & 7][lane], acc);
+                }
+                w.u[lane] = fminf(fmaxf(acc, io.lo), io.hi);
                 if (io.U_store) io.U_store[((size_t)h * io.Kn + k) * d::NU + lane] = w.u[lane];
             }
         } else if (lane < d::NU) {
@@ -232,6 +240,236 @@ __device__ __forceinline__ void update_finish(const UpdateArgs& a, int ncta, Upd
         *a.iter_ptr += 1ull;
         __threadfence();
     }
+}
+
+}  // namespace mppi
+
+namespace mppi {
+
+// ---------------------------------------------------------------------------
+// Eq. 8 in full: elite set, learning rate, per-step covariance blocks
+// ---------------------------------------------------------------------------
+// Sample row h of sample k: u_j = clamp(nu_j + sum_{i<=j} L_h[j][i] z_i)
+// (FMAs in the order i = 0..j, as the rollout computes it), or with a
+// diagonal sigma u_j = clamp(nu_j + sigma_j z_j).
+template <int NU>
+__device__ __forceinline__ void sample_row(uint2 key, uint32_t iter, int k, int h, const float* unom_h,
+                                           const float* sigma, const float* L_h, const float* lo, const float* hi,
+                                           float (&u)[NU]) {
+    float z[NU];
+#pragma unroll
+    for (int jb = 0; jb < (NU + 3) / 4; ++jb) {
+        const uint4 wv = philox4x32_10(make_uint4((uint32_t)jb, (uint32_t)h, (uint32_t)k, iter), key);
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+            if (4 * jb + t < NU) z[4 * jb + t] = block_normal(wv, t);
+    }
+#pragma unroll
+    for (int j = 0; j < NU; ++j) {
+        float acc = unom_h[j];
+        if (L_h) {
+#pragma unroll
+            for (int i = 0; i <= j; ++i) acc = __fmaf_rn(L_h[j * NU + i], z[i], acc);
+        } else {
+            acc = __fmaf_rn(sigma[j], z[j], acc);
+        }
+        u[j] = fminf(fmaxf(acc, lo[j]), hi[j]);
+    }
+}
+
+// Orderable 64-bit key of (cost, index): lower cost first, then lower index;
+// non-finite costs sort last.
+__device__ __forceinline__ unsigned long long cost_key(float c, int k) {
+    unsigned u = isfinite(c) ? __float_as_uint(c) : 0xFFFFFFFFu;
+    if (isfinite(c)) u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+    return ((unsigned long long)u << 32) | (unsigned)k;
+}
+
+struct EliteArgs {
+    int K, n_elite, update_cov;
+    float beta, eta, cov_floor;
+    const float* costs;
+    const float* u_nom;
+    float* u_out;
+    const float* sigma;
+    const float* Lfac;  // H x NU x NU factors of the sampling blocks, or null (diagonal sigma)
+    const float* u_lo;
+    const float* u_hi;
+    float* Sigma;       // H x NU x NU, updated in place when update_cov
+    float* Lout;        // H x NU x NU, new factors when update_cov
+    uint64_t seed;
+    const unsigned long long* iter_ptr;
+    unsigned long long iter_val;
+    const float* U_stored;  // H x K x NU, or null (regenerate)
+    const unsigned long long* sel;  // [threshold key, best key, finite count]
+    float* best_U;      // optional H x NU: controls of the lowest-cost sample
+    int* err;
+    int advance;
+    unsigned int* done;
+};
+
+template <int NU>
+struct EliteSmem {
+    float red[NU + 1][256];
+    float d[64][NU + 1];      // a chunk of weighted deviations
+    float cov[NU][NU];
+    float mean[NU];
+    int is_last;
+};
+
+template <int NU>
+__device__ __forceinline__ void elite_row(const EliteArgs& a, int h, int k, uint2 key, uint32_t iter,
+                                          const float* unom_h, float (&u)[NU]) {
+    if (a.U_stored) {
+        const float* uk = a.U_stored + ((size_t)h * a.K + k) * NU;
+#pragma unroll
+        for (int j = 0; j < NU; ++j) u[j] = uk[j];
+    } else {
+        sample_row<NU>(key, iter, k, h, unom_h, a.sigma, a.Lfac ? a.Lfac + (size_t)h * NU * NU : nullptr, a.u_lo,
+                       a.u_hi, u);
+    }
+}
+
+// One CTA per horizon step h (256 threads).
+template <int NU>
+__device__ __forceinline__ void elite_update_step(const EliteArgs& a, int h, EliteSmem<NU>& sm) {
+    constexpr int T = 256;
+    const int tid = threadIdx.x;
+    const uint32_t iter = (uint32_t)(a.iter_ptr ? *a.iter_ptr : a.iter_val);
+    const uint2 key = make_uint2((uint32_t)a.seed, (uint32_t)(a.seed >> 32));
+    const unsigned long long thr = a.sel[0], bestk = a.sel[1];
+    const bool any = a.sel[2] > 0;
+    const float cmin = any ? a.costs[(int)(bestk & 0xFFFFFFFFull)] : 0.0f;
+    float unom_h[NU];
+#pragma unroll
+    for (int j = 0; j < NU; ++j) unom_h[j] = a.u_nom[h * NU + j];
+    const float inv_beta = 1.0f / a.beta;
+    // (1) weighted elite mean
+    float acc[NU];
+#pragma unroll
+    for (int j = 0; j < NU; ++j) acc[j] = 0.0f;
+    float Z = 0.0f;
+    if (any) {
+        for (int k = tid; k < a.K; k += T) {
+            const float c = a.costs[k];
+            if (!isfinite(c) || cost_key(c, k) > thr) continue;
+            const float wk = expf(-(c - cmin) * inv_beta);
+            float u[NU];
+            elite_row<NU>(a, h, k, key, iter, unom_h, u);
+            Z += wk;
+#pragma unroll
+            for (int j = 0; j < NU; ++j) acc[j] += wk * u[j];
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < NU; ++j) sm.red[j][tid] = acc[j];
+    sm.red[NU][tid] = Z;
+    __syncthreads();
+    for (int st = T / 2; st > 0; st >>= 1) {
+        if (tid < st) {
+#pragma unroll
+            for (int j = 0; j <= NU; ++j) sm.red[j][tid] += sm.red[j][tid + st];
+        }
+        __syncthreads();
+    }
+    const float Zs = sm.red[NU][0];
+    if (tid < NU) {
+        const float m = any ? sm.red[tid][0] / Zs : unom_h[tid];
+        sm.mean[tid] = any ? (1.0f - a.eta) * unom_h[tid] + a.eta * m : unom_h[tid];
+    }
+    // the lowest-cost sample's row, read before this CTA rewrites the block's
+    // factor (regeneration samples through the current factor)
+    if (a.best_U && any && tid == 0) {
+        float u[NU];
+        elite_row<NU>(a, h, (int)(bestk & 0xFFFFFFFFull), key, iter, unom_h, u);
+#pragma unroll
+        for (int j = 0; j < NU; ++j) a.best_U[h * NU + j] = u[j];
+    }
+    __syncthreads();
+    // (2) weighted covariance about the new mean, one block per step
+    if (a.update_cov && any) {
+        constexpr int NE = NU * (NU + 1) / 2;
+        float cv = 0.0f;
+        int ci = 0, cj = 0;
+        if (tid < NE) {  // entry (ci, cj), cj <= ci
+            int rem = tid;
+            while (rem > ci) {
+                rem -= ci + 1;
+                ++ci;
+            }
+            cj = rem;
+        }
+        for (int k0 = 0; k0 < a.K; k0 += 64) {
+            if (tid < 64) {
+                const int k = k0 + tid;
+                float wk = 0.0f;
+                float u[NU];
+#pragma unroll
+                for (int j = 0; j < NU; ++j) u[j] = sm.mean[j];
+                if (k < a.K) {
+                    const float c = a.costs[k];
+                    if (isfinite(c) && cost_key(c, k) <= thr) {
+                        wk = expf(-(c - cmin) * inv_beta);
+                        elite_row<NU>(a, h, k, key, iter, unom_h, u);
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < NU; ++j) sm.d[tid][j] = u[j] - sm.mean[j];
+                sm.d[tid][NU] = wk;
+            }
+            __syncthreads();
+            if (tid < NE) {
+#pragma unroll 4
+                for (int t = 0; t < 64; ++t) cv += sm.d[t][NU] * sm.d[t][ci] * sm.d[t][cj];
+            }
+            __syncthreads();
+        }
+        if (tid < NE) {
+            float* S = a.Sigma + (size_t)h * NU * NU;
+            float v = (1.0f - a.eta) * S[ci * NU + cj] + a.eta * (cv / Zs);
+            if (ci == cj) v += a.cov_floor;
+            sm.cov[ci][cj] = v;
+            sm.cov[cj][ci] = v;
+        }
+        __syncthreads();
+        if (tid < NU * NU) a.Sigma[(size_t)h * NU * NU + tid] = sm.cov[tid / NU][tid % NU];
+        if (tid == 0) {  // factor the new block for the next iteration's sampling
+            float Lm[NU][NU];
+            bool ok = true;
+#pragma unroll
+            for (int r = 0; r < NU; ++r)
+#pragma unroll
+                for (int q = 0; q < NU; ++q) Lm[r][q] = q <= r ? sm.cov[r][q] : 0.0f;
+#pragma unroll
+            for (int j = 0; j < NU; ++j) {
+                float s = Lm[j][j];
+#pragma unroll
+                for (int q = 0; q < j; ++q) s -= Lm[j][q] * Lm[j][q];
+                ok = ok && s > 0.0f;
+                const float dj = sqrtf(fmaxf(s, 1e-30f)), inv = 1.0f / dj;
+                Lm[j][j] = dj;
+#pragma unroll
+                for (int r = j + 1; r < NU; ++r) {
+                    float t = Lm[r][j];
+#pragma unroll
+                    for (int q = 0; q < j; ++q) t -= Lm[r][q] * Lm[j][q];
+                    Lm[r][j] = t * inv;
+                }
+            }
+            if (ok) {
+                float* Lo = a.Lout + (size_t)h * NU * NU;
+#pragma unroll
+                for (int r = 0; r < NU; ++r)
+#pragma unroll
+                    for (int q = 0; q < NU; ++q) Lo[r * NU + q] = Lm[r][q];
+            } else {
+                atomicOr(a.err, ERRB_CHOLESKY);
+            }
+        }
+    }
+    // (3) outputs (u_out may alias u_nom: this CTA read its row above)
+    if (tid < NU) a.u_out[h * NU + tid] = sm.mean[tid];
+    if (h == 0 && tid == 0 && !any) atomicOr(a.err, ERRB_NONFINITE);
 }
 
 }  // namespace mppi

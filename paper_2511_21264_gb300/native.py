@@ -114,6 +114,10 @@ def lib():
     _decl(L, "mppi_set_iteration", i, [vp, u64, vp])
     _decl(L, "mppi_sync", i, [vp, vp])
     _decl(L, "mppi_set_launch", i, [vp, i])
+    _decl(L, "mppi_set_update", i, [vp, i, C.c_float, i, C.c_float])
+    _decl(L, "mppi_get_covariance", i, [vp, fp, vp])
+    _decl(L, "mppi_set_covariance", i, [vp, fp, vp])
+    _decl(L, "mppi_best_controls", i, [vp, fp, vp])
     _decl(L, "mppi_step_noalloc", i, [vp, sz, i, i, C.c_float, fp, u64, u64, fp, fp, fp, C.POINTER(i), vp])
     _decl(L, "mppi_batch_create", i, [vp, i, C.POINTER(vp)])
     _decl(L, "mppi_batch_destroy", i, [vp])
@@ -453,6 +457,22 @@ class Controller:
                                        C.byref(bps)), "mppi_profile_read")
         return {"iterations": n.value, "rollout_ms": tr.value, "update_ms": tu.value,
                 "contacts_per_step": cps.value, "box_tests_per_step": bps.value}
+
+    def set_update(self, n_elite: int, eta: float = 1.0, update_cov: bool = False, cov_floor: float = 0.0):
+        """The paper's full Eq. 8: elite set size, learning rate, covariance update."""
+        _check(lib().mppi_set_update(self._h, int(n_elite), float(eta), int(bool(update_cov)), float(cov_floor)),
+               "mppi_set_update")
+
+    def covariance(self, out, stream=None):
+        _check(lib().mppi_get_covariance(self._h, _ptr(out), _stream(stream)), "mppi_get_covariance")
+        return out
+
+    def set_covariance(self, Sigma, stream=None):
+        _check(lib().mppi_set_covariance(self._h, _ptr(Sigma), _stream(stream)), "mppi_set_covariance")
+
+    def best_controls(self, out, stream=None):
+        _check(lib().mppi_best_controls(self._h, _ptr(out), _stream(stream)), "mppi_best_controls")
+        return out
 
     def set_launch(self, samples_per_cta: int):
         _check(lib().mppi_set_launch(self._h, int(samples_per_cta)), "mppi_set_launch")
