@@ -89,6 +89,8 @@ def lib():
         L.or_elite_update.restype = i
         L.or_sample_cov.argtypes = [vp, C.c_uint64, C.c_uint64, i, i, dp, dp, dp]
         L.or_sample_cov.restype = i
+        L.or_qp_project.argtypes = [i, d, d, dp, i, dp, d, d, dp, dp, dp]
+        L.or_qp_project.restype = d
         _lib = L
     return _lib
 
@@ -275,6 +277,24 @@ def elite_update(costs, U, n_elite, beta, eta, nu_in, Sigma_in, update_cov=True,
                                float(cov_floor), _dp(_f64(nu_in)), _dp(_f64(Sigma_in)), _dp(nu_out), _dp(S_out),
                                elite.ctypes.data_as(C.POINTER(C.c_int)))
     return nu_out, S_out, elite, st
+
+
+QP_SCALES = (0.1, 1.0, 2.0, 4.0)
+
+
+def qp_project(vt, bounds, q, qd, dt, rho=1.0, iters=100, scales=QP_SCALES):
+    """QP smoothing projection of one joint's velocity sequence (Eq. 5):
+    `iters` ADMM iterations on the row groups (position, velocity,
+    acceleration, jerk) scaled by `scales`.  bounds: (lo, hi) for position,
+    velocity, acceleration, jerk (8 values; +-inf leaves a group free).
+    Returns (v, scaled duals in row order P, V, A, J, largest violation)."""
+    vt = _f64(vt)
+    H = vt.shape[0]
+    v = np.zeros(H)
+    y = np.zeros(4 * H - 1)
+    r = lib().or_qp_project(H, float(dt), float(rho), _dp(_f64(scales)), int(iters), _dp(_f64(bounds)), float(q),
+                            float(qd), _dp(vt), _dp(v), _dp(y))
+    return v, y, r
 
 
 def mppi_update(costs, U, lam, u_nom):

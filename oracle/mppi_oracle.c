@@ -1145,3 +1145,109 @@ int or_sample_cov(const or_model *m, uint64_t seed, uint64_t iteration, int K, i
     free(ones);
     return rc;
 }
+
+/* --------------------------------------------------------------------- */
+/* QP smoothing projection (Eq. 5)                                        */
+/* --------------------------------------------------------------------- */
+/* One joint's H commanded velocities v are projected onto the bounds of
+ * Eq. 5b, r = 0..3 (the set of r is stated in Sec. III): minimise
+ * 1/2 |v - vt|^2 subject to
+ *   r=0  theta_{t+1} = q + dt sum_{i<=t} v_i              in [b0, b1], t = 0..H-1
+ *   r=1  v_t                                             in [b2, b3], t = 0..H-1
+ *   r=2  (v_t - v_{t-1}) / dt,             v_{-1} = qd   in [b4, b5], t = 0..H-1
+ *   r=3  (v_t - 2 v_{t-1} + v_{t-2}) / dt^2, v_{-1} = qd in [b6, b7], t = 1..H-1
+ * (qd, the joint's present velocity, fixes the first differences; the jerk at
+ * t = 0 would need the velocity before it and is not bounded).
+ *
+ * The paper does not name its solver.  Read here as a fixed number of ADMM
+ * iterations on the equilibrated rows
+ *   D v = [s0 sum_{i<=t} v_i ; s1 v_t ; s2 (v_t - v_{t-1}) ; s3 (v_t - 2 v_{t-1} + v_{t-2})]
+ * (position / dt, velocity, acceleration * dt, jerk * dt^2, times the group
+ * scales s0..s3; the terms in qd move into the bounds lo, hi; a group whose
+ * bounds are both infinite bounds nothing and takes no rows), in scaled
+ * form with penalty rho, from v = vt and y = 0.  Each iteration:
+ *   s = D v + y,  w = clip(s, lo, hi),  y = s - w,
+ *   v = (I + rho D^T D)^{-1} (vt + rho D^T (w - y)).
+ * A feasible vt is a fixed point.  The matrix is formed densely and factored
+ * by Cholesky.  Returns the largest bound violation of the returned v in the
+ * scaled rows; y_out (optional, 4H - 1 values in row order P, V, A, J) holds
+ * the scaled duals (rho y are the multipliers at convergence). */
+static void qp_rows(int H, double dt, const double *sc_in, const double *b, double q, double qd, double *D,
+                    double *lo, double *hi) {
+    int m = 4 * H - 1;
+    double sc[4];
+    for (int g = 0; g < 4; g++) sc[g] = (isinf(b[2 * g]) && b[2 * g] < 0 && isinf(b[2 * g + 1]) && b[2 * g + 1] > 0)
+                                            ? 0.0 : sc_in[g];
+    memset(D, 0, sizeof(double) * (size_t)m * H);
+    for (int t = 0; t < H; t++) {
+        for (int i = 0; i <= t; i++) D[(size_t)t * H + i] = sc[0];
+        lo[t] = sc[0] * (b[0] - q) / dt;
+        hi[t] = sc[0] * (b[1] - q) / dt;
+        D[(size_t)(H + t) * H + t] = sc[1];
+        lo[H + t] = sc[1] * b[2];
+        hi[H + t] = sc[1] * b[3];
+        D[(size_t)(2 * H + t) * H + t] = sc[2];
+        if (t > 0) D[(size_t)(2 * H + t) * H + t - 1] = -sc[2];
+        lo[2 * H + t] = sc[2] * (b[4] * dt + (t == 0 ? qd : 0.0));
+        hi[2 * H + t] = sc[2] * (b[5] * dt + (t == 0 ? qd : 0.0));
+    }
+    for (int t = 1; t < H; t++) {
+        int r = 3 * H + t - 1;
+        D[(size_t)r * H + t] = sc[3];
+        D[(size_t)r * H + t - 1] = -2.0 * sc[3];
+        if (t >= 2) D[(size_t)r * H + t - 2] = sc[3];
+        lo[r] = sc[3] * (b[6] * dt * dt - (t == 1 ? qd : 0.0));
+        hi[r] = sc[3] * (b[7] * dt * dt - (t == 1 ? qd : 0.0));
+    }
+    for (int g = 0; g < 4; g++) /* rows of a free group stay zero, unbounded */
+        if (sc[g] == 0.0)
+            for (int r = g * H; r < (g == 3 ? 4 * H - 1 : (g + 1) * H); r++) {
+                lo[r] = -INFINITY;
+                hi[r] = INFINITY;
+            }
+}
+
+double or_qp_project(int H, double dt, double rho, const double *sc, int iters, const double *b, double q, double qd,
+                     const double *vt, double *v_out, double *y_out) {
+    int m = 4 * H - 1;
+    double *D = (double *)malloc(sizeof(double) * (size_t)m * H);
+    double *lo = (double *)malloc(sizeof(double) * m), *hi = (double *)malloc(sizeof(double) * m);
+    qp_rows(H, dt, sc, b, q, qd, D, lo, hi);
+    double *A = (double *)calloc((size_t)H * H, sizeof(double));
+    for (int i = 0; i < H; i++)
+        for (int j = 0; j < H; j++) {
+            double s = 0.0;
+            for (int r = 0; r < m; r++) s += D[(size_t)r * H + i] * D[(size_t)r * H + j];
+            A[i * H + j] = (i == j ? 1.0 : 0.0) + rho * s;
+        }
+    cholesky(A, H);
+    double *y = (double *)calloc(m, sizeof(double)), *g = (double *)malloc(sizeof(double) * m);
+    double *rhs = (double *)malloc(sizeof(double) * H);
+    memcpy(v_out, vt, sizeof(double) * H);
+    for (int it = 0; it < iters; it++) {
+        for (int r = 0; r < m; r++) {
+            double s = y[r];
+            for (int i = 0; i < H; i++) s += D[(size_t)r * H + i] * v_out[i];
+            double w = s < lo[r] ? lo[r] : (s > hi[r] ? hi[r] : s);
+            y[r] = s - w;
+            g[r] = w - y[r];
+        }
+        for (int i = 0; i < H; i++) {
+            double s = 0.0;
+            for (int r = 0; r < m; r++) s += D[(size_t)r * H + i] * g[r];
+            rhs[i] = vt[i] + rho * s;
+        }
+        chol_solve(A, H, rhs);
+        memcpy(v_out, rhs, sizeof(double) * H);
+    }
+    double viol = 0.0;
+    for (int r = 0; r < m; r++) {
+        double s = 0.0;
+        for (int i = 0; i < H; i++) s += D[(size_t)r * H + i] * v_out[i];
+        double e = s < lo[r] ? lo[r] - s : (s > hi[r] ? s - hi[r] : 0.0);
+        if (e > viol) viol = e;
+    }
+    if (y_out) memcpy(y_out, y, sizeof(double) * m);
+    free(D); free(lo); free(hi); free(A); free(y); free(g); free(rhs);
+    return viol;
+}
