@@ -209,6 +209,8 @@ def run_ours(args):
         ctl.set_launch(args.spc)
     if args.elite or args.eta != 1.0 or args.cov:
         ctl.set_update(args.elite or K, args.eta, args.cov, 1e-6)
+    if args.qp:
+        ctl.set_projection(scenes.projection_bounds(sc), iters=args.qp)
     stream = torch.cuda.Stream(device=dev)
     x = torch.tensor(model.home(), device=dev)
     u = torch.zeros((H, sc.nu), device=dev)
@@ -234,6 +236,7 @@ def run_ours(args):
             raise RuntimeError(f"device error {rc} during the timed steps")
         total_ms = _max_over_ranks(sum(step_ms), world)
         kt = ctl.profile_read()
+        qp_ms = ctl.profile_projection() / max(1, kt["iterations"])
         ctl.profile(0)
 
         # end to end through the public API with host buffers: pinned H2D
@@ -269,6 +272,7 @@ def run_ours(args):
     fl = flops.per_sample_step(sc, kt["contacts_per_step"], kt["box_tests_per_step"])
     roll_ms = kt["rollout_ms"] / max(1, kt["iterations"])
     achieved = fl * K * H / (roll_ms * 1e-3) / 1e12
+    elite = bool(args.elite or args.eta != 1.0 or args.cov)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -277,7 +281,7 @@ def run_ours(args):
         "iters_per_s": args.steps * world / (total_ms * 1e-3),
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(4 * (x.numel() + u.numel())),
                 "d2h_bytes_per_step": int(4 * u.numel())},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": (2 + (1 if elite else 0) + (1 if args.qp else 0)) * args.steps,
         "roofline": {"bound": "alu", "kernel": "rollout_kernel<7,1>", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak, "traffic": args.traffic,
                      "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (median SM clock "
@@ -290,9 +294,18 @@ def run_ours(args):
     }
     if args.workload != "lift":
         line["metric"] = METRIC.replace("MPPI iteration", "MPPI iteration, " + args.workload)
-    if args.elite or args.eta != 1.0 or args.cov:
+    if elite:
         line["config"]["update"] = {"n_elite": args.elite or K, "eta": args.eta, "covariance": bool(args.cov)}
         line["metric"] = line["metric"].replace("weights + update", "elite set + Eq. 8 update")
+    if args.qp:
+        qfl = flops.qp_flops(sc.H, args.qp)
+        line["config"]["projection"] = {"iters": args.qp, "rho": 1.0,
+                                        "bounds": "home +-1 rad, +-pi rad/s, +-10 rad/s^2, +-300 rad/s^3"}
+        line["metric"] = line["metric"].replace("sample + rollout", "sample + QP projection + rollout")
+        qa = qfl * K * sc.nu / (qp_ms * 1e-3) / 1e12
+        line["qp_projection"] = {"kernel": "qp_project_kernel", "ms": qp_ms, "bound": "alu",
+                                 "flops_per_sequence": qfl, "achieved": qa, "peak": peak, "unit": "TFLOP/s",
+                                 "frac": qa / peak}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sc, seconds=args.cpu_seconds)
     print(json.dumps(line), flush=True)
@@ -495,6 +508,7 @@ def main(argv=None):
     ap.add_argument("--elite", type=int, default=0, help="elite set size (0 = all samples: the plain update)")
     ap.add_argument("--eta", type=float, default=1.0, help="learning rate of Eq. 8 (elite mode)")
     ap.add_argument("--cov", action="store_true", help="update the per-step covariance blocks (Eq. 8b/8c)")
+    ap.add_argument("--qp", type=int, default=0, help="QP smoothing projection (Eq. 5) iterations (0 = off)")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="arrival window per rate (serve)")
     ap.add_argument("--serve-rates", type=str, default="50,200,1000")
     ap.add_argument("--spc", type=int, default=0, help="samples per CTA (0 = library default)")

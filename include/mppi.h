@@ -146,6 +146,9 @@ int mppi_sync(mppi_ctx *c, void *stream);
 int mppi_profile(mppi_ctx *c, int n);
 int mppi_profile_read(mppi_ctx *c, int *n, float *rollout_ms, float *update_ms, double *contacts_per_step,
                       double *box_tests_per_step);
+/* Total time (ms) of the QP projection launches over the recorded
+ * iterations (0 when the projection is off); synchronises the events. */
+int mppi_profile_projection(mppi_ctx *c, float *qp_ms);
 
 /* The paper's full update (Eq. 8a-8d): the elite set is the n_elite
  * samples of lowest cost (ties -> lower index; non-finite costs never
@@ -168,6 +171,52 @@ int mppi_set_covariance(mppi_ctx *c, const float *Sigma, void *stream);
 /* Controls of the lowest-cost sample of the last elite update (device,
  * H x nu): the optimiser's output besides nu and Sigma (Alg. 1). */
 int mppi_best_controls(mppi_ctx *c, float *U_best, void *stream);
+
+/* ------------------------------------------------ QP smoothing projection */
+/* Eq. 5a-5b (Alg. 1, the step between sampling and rollout): a joint's H
+ * commanded velocities vt are replaced by
+ *   v = argmin 1/2 |v - vt|^2  subject to, for r = 0..3 (Sec. III),
+ *   position      b0 <= q + dt sum_{i<=t} v_i              <= b1, t = 0..H-1
+ *   velocity      b2 <= v_t                                <= b3, t = 0..H-1
+ *   acceleration  b4 <= (v_t - v_{t-1}) / dt               <= b5, t = 0..H-1
+ *   jerk          b6 <= (v_t - 2 v_{t-1} + v_{t-2}) / dt^2 <= b7, t = 1..H-1
+ * with q, qd the joint's present position and velocity (v_{-1} = qd).  A
+ * group whose two bounds are -inf and +inf is left out.  The paper names no
+ * solver: this library runs `iters` iterations of ADMM (scaled form, penalty
+ * rho, row groups scaled by `scales` = position/dt, velocity, acceleration*dt
+ * and jerk*dt^2 weights) from v = vt, so a feasible vt is returned
+ * unchanged (up to FP32 rounding), and returns the last iterate: after 30
+ * iterations white-noise samples that broke the jerk bound 40-fold keep
+ * every derivative within about 5% of its bound, after 100 within 0.3%.  An
+ * infeasible problem (a present state the bounds cannot hold) returns a
+ * compromise.  Every sequence runs the same iteration count. */
+#define MPPI_QP_MAX_H 256
+#define MPPI_QP_SCALE_POSITION 0.1f
+#define MPPI_QP_SCALE_VELOCITY 1.0f
+#define MPPI_QP_SCALE_ACCELERATION 2.0f
+#define MPPI_QP_SCALE_JERK 4.0f
+/* Projection of n independent sequences sharing one set of bounds.
+ *   bounds   HOST, 8 floats (lo, hi) x (position, velocity, acceleration,
+ *            jerk); lo <= hi, no NaN
+ *   scales   HOST, 4 floats > 0, or NULL for the MPPI_QP_SCALE_* defaults
+ *   q0, qd0  device, n floats: each sequence's present position, velocity
+ *   v_in     device, n x H; v_out device, n x H (may alias v_in)
+ * 1 <= H <= MPPI_QP_MAX_H, iters >= 0, rho > 0, dt > 0.  Allocates a small
+ * stream-ordered scratch block (cudaMallocAsync) per call. */
+int mppi_qp_project(int n, int H, float dt, const float *bounds, int iters, float rho, const float *scales,
+                    const float *q0, const float *qd0, const float *v_in, float *v_out, void *stream);
+/* Turn the projection on inside the controller's iteration (iters > 0) or
+ * off (iters = 0).  bounds: HOST, nu x 8 floats, one row per joint as
+ * above; q, qd come from the state passed to each step.  While on, the
+ * samples are drawn unclamped (nu + sigma z, or nu + L_h z), projected, and
+ * the projected sequences are what the rollout simulates and the update
+ * averages (Eq. 8 uses the projected samples).  Needs the controller's
+ * sample buffer (K H nu floats <= 256 MB) and H <= MPPI_QP_MAX_H. */
+int mppi_set_projection(mppi_ctx *c, const float *bounds, int iters, float rho, const float *scales);
+/* The samples of the last iteration as the rollout used them (device,
+ * H x K x nu, h-major): projected when the projection is on, else the
+ * clamped samples.  Needs the sample buffer. */
+int mppi_get_samples(mppi_ctx *c, float *U, void *stream);
 
 /* Launch shape: samples (warps) per CTA for the rollout kernels, 1..16
  * (0 = the library default).  Used by the autotuner. */

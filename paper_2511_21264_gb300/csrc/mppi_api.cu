@@ -67,7 +67,13 @@ __global__ void __launch_bounds__(512) rollout_kernel(RolloutArgs args) {
             io.hi = M.link[lane / NA][lane % NA].u_hi;
         }
     } else {
-        io.U = args.U + (size_t)k * args.H * d::NU;
+        if (args.U_hmajor) {
+            io.U = args.U + (size_t)k * d::NU;
+            io.u_stride = (long long)args.n * d::NU;
+        } else {
+            io.U = args.U + (size_t)k * args.H * d::NU;
+            io.u_stride = d::NU;
+        }
     }
     const float cost = rollout_sample<NA, MODE>(M, wsb[warp], lane, io);
     if (lane == 0) args.costs[k] = cost;
@@ -97,7 +103,7 @@ __global__ void noise_kernel(NoiseArgs a) {
 // CTA, P = power of two >= K); sel = [key of the n_e-th elite, lowest key,
 // finite count].
 __global__ void __launch_bounds__(1024) elite_select_kernel(const float* costs, int K, int P, int n_elite,
-                                                            unsigned long long* sel) {
+                                                            unsigned long long* sel, int* eidx) {
     extern __shared__ unsigned long long keys[];
     __shared__ int nfin;
     if (threadIdx.x == 0) nfin = 0;
@@ -125,9 +131,10 @@ __global__ void __launch_bounds__(1024) elite_select_kernel(const float* costs, 
             }
             __syncthreads();
         }
+    const int nf = nfin;
+    const int ne = nf == 0 ? 0 : (n_elite < nf ? n_elite : nf);
+    for (int e = threadIdx.x; e < ne; e += blockDim.x) eidx[e] = (int)(keys[e] & 0xFFFFFFFFull);
     if (threadIdx.x == 0) {
-        const int nf = nfin;
-        const int ne = nf == 0 ? 0 : (n_elite < nf ? n_elite : nf);
         sel[0] = ne > 0 ? keys[ne - 1] : 0ull;
         sel[1] = keys[0];
         sel[2] = (unsigned long long)nf;
@@ -342,7 +349,7 @@ struct mppi_ctx {
     cudaStream_t g_stream = nullptr;
     // profiling
     int prof_cap = 0, prof_n = 0;
-    std::vector<cudaEvent_t> prof_ev;  // 3 per recorded iteration
+    std::vector<cudaEvent_t> prof_ev;  // 4 per recorded iteration: start, projected, rolled out, updated
     unsigned long long* d_stats = nullptr;
     float* d_U = nullptr;  // sampled controls of the last rollout (H x K x nu), when it fits
     // full Eq. 8 (elite set, learning rate, covariance blocks)
@@ -352,7 +359,12 @@ struct mppi_ctx {
     float* d_Sigma = nullptr;  // H x nu x nu
     float* d_L = nullptr;      // H x nu x nu factors used for sampling
     unsigned long long* d_sel = nullptr;
+    int* d_eidx = nullptr;     // elite indices (K)
     float* d_bestU = nullptr;  // H x nu
+    // QP smoothing projection (Eq. 5)
+    int qp_iters = 0;
+    float qp_dt = 0.0f;
+    void* d_qp = nullptr;  // nu QPClass records, then nu x 2H band rows
 };
 
 namespace mppi {
@@ -433,6 +445,8 @@ int mppi_destroy(mppi_ctx* c) {
     cudaFree(c->d_Sigma);
     cudaFree(c->d_L);
     cudaFree(c->d_sel);
+    cudaFree(c->d_eidx);
+    cudaFree(c->d_qp);
     cudaFree(c->d_bestU);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->graph) cudaGraphDestroy(c->graph);
@@ -505,7 +519,7 @@ int mppi_profile(mppi_ctx* c, int n) {
     if (!c->d_stats) e = cudaMalloc(&c->d_stats, 4 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(c->d_stats, 0, 4 * sizeof(unsigned long long));
     if (e != cudaSuccess) return cuda_fail(e);
-    c->prof_ev.resize(3 * (size_t)n);
+    c->prof_ev.resize(4 * (size_t)n);
     for (auto& ev : c->prof_ev) {
         e = cudaEventCreate(&ev);
         if (e != cudaSuccess) return cuda_fail(e);
@@ -519,10 +533,10 @@ int mppi_profile_read(mppi_ctx* c, int* n, float* rollout_ms, float* update_ms, 
     if (!c) return MPPI_ERR_INVALID_ARG;
     float tr = 0.0f, tu = 0.0f;
     for (int i = 0; i < c->prof_n; ++i) {
-        cudaError_t e = cudaEventSynchronize(c->prof_ev[3 * i + 2]);
+        cudaError_t e = cudaEventSynchronize(c->prof_ev[4 * i + 3]);
         float a = 0.0f, b = 0.0f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&a, c->prof_ev[3 * i], c->prof_ev[3 * i + 1]);
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&b, c->prof_ev[3 * i + 1], c->prof_ev[3 * i + 2]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&a, c->prof_ev[4 * i + 1], c->prof_ev[4 * i + 2]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&b, c->prof_ev[4 * i + 2], c->prof_ev[4 * i + 3]);
         if (e != cudaSuccess) return cuda_fail(e);
         tr += a;
         tu += b;
@@ -540,6 +554,20 @@ int mppi_profile_read(mppi_ctx* c, int* n, float* rollout_ms, float* update_ms, 
     return MPPI_OK;
 }
 
+int mppi_profile_projection(mppi_ctx* c, float* qp_ms) {
+    if (!c || !qp_ms) return MPPI_ERR_INVALID_ARG;
+    float tq = 0.0f;
+    for (int i = 0; i < c->prof_n; ++i) {
+        cudaError_t e = cudaEventSynchronize(c->prof_ev[4 * i + 3]);
+        float a = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&a, c->prof_ev[4 * i], c->prof_ev[4 * i + 1]);
+        if (e != cudaSuccess) return cuda_fail(e);
+        tq += a;
+    }
+    *qp_ms = tq;
+    return MPPI_OK;
+}
+
 int mppi_set_update(mppi_ctx* c, int n_elite, float eta, int update_cov, float cov_floor) {
     if (!c || n_elite < 1 || n_elite > c->K || !(eta > 0.0f && eta <= 1.0f) || update_cov < 0 || update_cov > 1 ||
         !(cov_floor >= 0.0f))
@@ -553,6 +581,7 @@ int mppi_set_update(mppi_ctx* c, int n_elite, float eta, int update_cov, float c
         e = cudaMalloc(&c->d_Sigma, blk * sizeof(float));
         if (e == cudaSuccess) e = cudaMalloc(&c->d_L, blk * sizeof(float));
         if (e == cudaSuccess) e = cudaMalloc(&c->d_sel, 3 * sizeof(unsigned long long));
+        if (e == cudaSuccess) e = cudaMalloc(&c->d_eidx, (size_t)c->K * sizeof(int));
         if (e == cudaSuccess) e = cudaMalloc(&c->d_bestU, (size_t)c->H * nu * sizeof(float));
         if (e != cudaSuccess) return cuda_fail(e);
         // Sigma_0 = diag(sigma^2), its factor diag(sigma)
@@ -669,6 +698,89 @@ static RolloutArgs philox_args(mppi_ctx* c, const float* state, const float* u_n
     return a;
 }
 
+static void drop_graph(mppi_ctx* c) {
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->gexec = nullptr;
+    c->graph = nullptr;
+}
+
+// Projection launch: sequence i = j * K + k (a warp's sequences share a
+// joint, hence a band factor); output U[h][k][j] (h-major sample buffer).
+static int launch_projection(mppi_ctx* c, const float* state, const float* u_nom, cudaStream_t s) {
+    const int na = c->m->info.na, nu = 2 * na, nq = 2 * na + 7;
+    QPArgs q{};
+    q.n = c->K * nu;
+    q.H = c->H;
+    q.iters = c->qp_iters;
+    q.per_cls = c->K;
+    q.dt = c->qp_dt;
+    q.cls = static_cast<const QPClass*>(c->d_qp);
+    q.band = reinterpret_cast<const float4*>(static_cast<unsigned char*>(c->d_qp) + (size_t)nu * sizeof(QPClass));
+    q.q0 = state;
+    q.qd0 = state + nq;
+    q.q_per_seq = 0;
+    q.vin = nullptr;
+    q.nu = nu;
+    q.u_nom = u_nom;
+    q.sigma = c->d_sigma;
+    q.Lfac = c->cov_sampling ? c->d_L : nullptr;
+    q.seed = c->seed;
+    q.iter_ptr = c->d_iter;
+    q.out = c->d_U;
+    q.o_a = nu;                        // member k
+    q.o_b = 1;                         // class j
+    q.o_h = (long long)c->K * nu;      // step h
+    return launch_qp(q, s);
+}
+
+int mppi_set_projection(mppi_ctx* c, const float* bounds, int iters, float rho, const float* scales) {
+    static const float kDefault[4] = {MPPI_QP_SCALE_POSITION, MPPI_QP_SCALE_VELOCITY, MPPI_QP_SCALE_ACCELERATION,
+                                      MPPI_QP_SCALE_JERK};
+    if (!c || iters < 0) return MPPI_ERR_INVALID_ARG;
+    if (iters == 0) {
+        if (c->qp_iters) drop_graph(c);
+        c->qp_iters = 0;
+        return MPPI_OK;
+    }
+    if (!bounds) return MPPI_ERR_INVALID_ARG;
+    const float* sc = scales ? scales : kDefault;
+    const int nu = 2 * c->m->info.na;
+    for (int j = 0; j < nu; ++j) {
+        const int rc = qp_validate(bounds + 8 * j, sc, rho);
+        if (rc != MPPI_OK) return rc;
+    }
+    if (c->H > MPPI_QP_MAX_H || !c->d_U) return MPPI_ERR_UNSUPPORTED;
+    const float dt = c->m->host.dt;
+    const size_t bytes = (size_t)nu * sizeof(QPClass) + (size_t)nu * 2 * c->H * sizeof(float4);
+    std::vector<unsigned char> host(bytes);
+    QPClass* cls = reinterpret_cast<QPClass*>(host.data());
+    float4* band = reinterpret_cast<float4*>(host.data() + (size_t)nu * sizeof(QPClass));
+    for (int j = 0; j < nu; ++j) {
+        qp_make_class(bounds + 8 * j, sc, rho, &cls[j]);
+        const double scd[4] = {cls[j].s[0], cls[j].s[1], cls[j].s[2], cls[j].s[3]};
+        const int rc = qp_band_factor(c->H, rho, scd, band + (size_t)j * 2 * c->H);
+        if (rc != MPPI_OK) return rc;
+    }
+    if (!c->d_qp) {
+        cudaError_t e = cudaMalloc(&c->d_qp, bytes);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    cudaError_t e = cudaMemcpy(c->d_qp, host.data(), bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e);
+    c->qp_iters = iters;
+    c->qp_dt = dt;
+    drop_graph(c);  // a captured solve holds the old launches
+    return MPPI_OK;
+}
+
+int mppi_get_samples(mppi_ctx* c, float* U, void* stream) {
+    if (!c || !U) return MPPI_ERR_INVALID_ARG;
+    if (!c->d_U) return MPPI_ERR_UNSUPPORTED;
+    const size_t n = (size_t)c->H * c->K * 2 * c->m->info.na;
+    return cuda_fail(cudaMemcpyAsync(U, c->d_U, n * sizeof(float), cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+}
+
 static bool elite_mode(const mppi_ctx* c) {
     return c->n_elite != c->K || c->eta != 1.0f || c->update_cov || c->cov_sampling;
 }
@@ -683,7 +795,7 @@ static int launch_elite(mppi_ctx* c, const float* costs, const float* u_nom, flo
         cudaError_t e = cudaFuncSetAttribute(elite_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return cuda_fail(e);
     }
-    elite_select_kernel<<<1, 1024, sm, s>>>(costs, c->K, P, c->n_elite, c->d_sel);
+    elite_select_kernel<<<1, 1024, sm, s>>>(costs, c->K, P, c->n_elite, c->d_sel, c->d_eidx);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e);
     EliteArgs a{};
@@ -706,6 +818,7 @@ static int launch_elite(mppi_ctx* c, const float* costs, const float* u_nom, flo
     a.iter_ptr = c->d_iter;
     a.U_stored = U_stored;
     a.sel = c->d_sel;
+    a.eidx = c->d_eidx;
     a.best_U = c->d_bestU;
     a.err = c->d_err;
     a.advance = advance;
@@ -739,14 +852,26 @@ static int enqueue_step(mppi_ctx* c, const float* state, const float* u_nom, flo
                         cudaStream_t s, bool capturing = false) {
     RolloutArgs a = philox_args(c, state, u_nom);
     const bool prof = !capturing && c->prof_n < c->prof_cap;
-    cudaEvent_t* ev = prof ? &c->prof_ev[3 * c->prof_n] : nullptr;
+    cudaEvent_t* ev = prof ? &c->prof_ev[4 * c->prof_n] : nullptr;
     if (prof) {
         a.stats = c->d_stats;
         cudaEventRecord(ev[0], s);
     }
-    int rc = launch_rollout(c->m->info.na, 1, a, c->spc, s);
-    if (rc != MPPI_OK) return rc;
+    int rc = MPPI_OK;
+    int mode = 1;
+    if (c->qp_iters > 0) {  // sample, project (Eq. 5), then roll the projected sequences out
+        rc = launch_projection(c, state, u_nom, s);
+        if (rc != MPPI_OK) return rc;
+        a.U = c->d_U;
+        a.U_hmajor = 1;
+        a.U_store = nullptr;
+        a.Lfac = nullptr;
+        mode = 0;
+    }
     if (prof) cudaEventRecord(ev[1], s);
+    rc = launch_rollout(c->m->info.na, mode, a, c->spc, s);
+    if (rc != MPPI_OK) return rc;
+    if (prof) cudaEventRecord(ev[2], s);
     if (elite_mode(c)) {
         rc = launch_elite(c, c->d_costs, u_nom, u_out, 1, c->d_U, s);
     } else {
@@ -755,7 +880,7 @@ static int enqueue_step(mppi_ctx* c, const float* state, const float* u_nom, flo
         rc = launch_update(2 * c->m->info.na, u, c->H, s);
     }
     if (prof) {
-        cudaEventRecord(ev[2], s);
+        cudaEventRecord(ev[3], s);
         c->prof_n++;
     }
     return rc;

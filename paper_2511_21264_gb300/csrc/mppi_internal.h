@@ -49,6 +49,7 @@ struct RolloutArgs {
     int stage_unom;              // stage u_nom in shared memory
     unsigned long long* stats;   // optional: [sample-steps, contacts, exact box tests]
     float* U_store;              // optional: sampled controls, H x n x nu (h-major), MODE 1
+    int U_hmajor;                // MODE 0: U is H x n x nu (h-major) instead of n x H x nu
     const float* Lfac;           // optional: covariance factors H x nu x nu (MODE 1), else diagonal sigma
 };
 
@@ -122,6 +123,43 @@ int batch_shape(int na, int spc, int max_h, BatchLaunch* L);
 int launch_batch_iteration(const BatchInst* insts, int n, int ntiles, int nrows, BatchCtl* ctl, const BatchLaunch& L,
                            cudaStream_t s);
 int launch_shift(float* u, int H, int nu, cudaStream_t s);
+
+// QP smoothing projection (Eq. 5): one class of sequences (a joint)
+struct QPClass {
+    float lo[4], hi[4];  // bounds on position, velocity, acceleration, jerk
+    float s[4];          // row-group scales; 0 marks a free group (both bounds infinite)
+    float rho;           // ADMM penalty
+    float pad[3];
+};
+
+// Arguments of the projection kernel (one thread per sequence).  Sequence i
+// belongs to class i / per_cls as member i % per_cls; element h of its input
+// and output sits at (member * a + class * b + h * h_stride).
+struct QPArgs {
+    int n, H, iters, per_cls;
+    float dt;
+    const QPClass* cls;  // classes
+    const float4* band;  // per class 2H: forward then backward band factor rows
+    const float* q0;     // present position, per sequence (q_per_seq) or per class
+    const float* qd0;    // present velocity, same indexing
+    int q_per_seq;
+    const float* vin;    // explicit input, or null to sample (member = sample k, class = joint j)
+    long long i_a, i_b, i_h;
+    // sampling: v = u_nom[h, j] + sigma_j z_j, or + (L_h z)_j with Lfac (no clamp)
+    int nu;
+    const float* u_nom;
+    const float* sigma;
+    const float* Lfac;
+    uint64_t seed;
+    const unsigned long long* iter_ptr;
+    unsigned long long iter_val;
+    float* out;
+    long long o_a, o_b, o_h;
+};
+int qp_band_factor(int H, double rho, const double sc[4], float4* band);
+void qp_make_class(const float b[8], const float sc[4], float rho, QPClass* c);
+int qp_validate(const float b[8], const float sc[4], float rho);
+int launch_qp(const QPArgs& a, cudaStream_t s);
 
 int parse_model_blob(const void* blob, size_t len, DevModel* out, HostModelInfo* info);
 int launch_rollout(int na, int mode, const RolloutArgs& a, int spc, cudaStream_t s);

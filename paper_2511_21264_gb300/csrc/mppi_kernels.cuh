@@ -9,7 +9,8 @@ namespace mppi {
 // Inputs of one sample's rollout (one warp).
 struct SampleIO {
     const float* x;            // start state (nx)
-    const float* U;            // explicit controls of this sample (H x nu), MODE 0
+    const float* U;            // explicit controls of this sample, row h at U + h * u_stride, MODE 0
+    long long u_stride;
     const float* unom;         // nominal controls (H x nu, shared or global), MODE 1
     float sig, lo, hi;         // this lane's sigma and control bounds (lane < nu), MODE 1
     uint2 key;                 // Philox key, MODE 1
@@ -70,7 +71,7 @@ __device__ __forceinline__ float rollout_sample(const DevModel& M, WarpWS<NA>& w
                 if (io.U_store) io.U_store[((size_t)h * io.Kn + k) * d::NU + lane] = w.u[lane];
             }
         } else if (lane < d::NU) {
-            w.u[lane] = io.U[(size_t)h * d::NU + lane];
+            w.u[lane] = io.U[h * io.u_stride + lane];
         }
         float Rl[9], cl[3];  // this lane's link rotation and COM, kept for the dynamics
         forward_kinematics<NA>(M, w, lane, Rl, cl);
@@ -302,6 +303,7 @@ struct EliteArgs {
     unsigned long long iter_val;
     const float* U_stored;  // H x K x NU, or null (regenerate)
     const unsigned long long* sel;  // [threshold key, best key, finite count]
+    const int* eidx;    // elite sample indices, lowest cost first
     float* best_U;      // optional H x NU: controls of the lowest-cost sample
     int* err;
     int advance;
@@ -337,29 +339,28 @@ __device__ __forceinline__ void elite_update_step(const EliteArgs& a, int h, Eli
     const int tid = threadIdx.x;
     const uint32_t iter = (uint32_t)(a.iter_ptr ? *a.iter_ptr : a.iter_val);
     const uint2 key = make_uint2((uint32_t)a.seed, (uint32_t)(a.seed >> 32));
-    const unsigned long long thr = a.sel[0], bestk = a.sel[1];
+    const unsigned long long bestk = a.sel[1];
     const bool any = a.sel[2] > 0;
     const float cmin = any ? a.costs[(int)(bestk & 0xFFFFFFFFull)] : 0.0f;
     float unom_h[NU];
 #pragma unroll
     for (int j = 0; j < NU; ++j) unom_h[j] = a.u_nom[h * NU + j];
     const float inv_beta = 1.0f / a.beta;
-    // (1) weighted elite mean
+    // (1) weighted elite mean over the elite list
+    const int nfin = (int)a.sel[2];
+    const int ne = nfin < a.n_elite ? nfin : a.n_elite;
     float acc[NU];
 #pragma unroll
     for (int j = 0; j < NU; ++j) acc[j] = 0.0f;
     float Z = 0.0f;
-    if (any) {
-        for (int k = tid; k < a.K; k += T) {
-            const float c = a.costs[k];
-            if (!isfinite(c) || cost_key(c, k) > thr) continue;
-            const float wk = expf(-(c - cmin) * inv_beta);
-            float u[NU];
-            elite_row<NU>(a, h, k, key, iter, unom_h, u);
-            Z += wk;
+    for (int e = tid; e < ne; e += T) {
+        const int k = a.eidx[e];
+        const float wk = expf(-(a.costs[k] - cmin) * inv_beta);
+        float u[NU];
+        elite_row<NU>(a, h, k, key, iter, unom_h, u);
+        Z += wk;
 #pragma unroll
-            for (int j = 0; j < NU; ++j) acc[j] += wk * u[j];
-        }
+        for (int j = 0; j < NU; ++j) acc[j] += wk * u[j];
     }
 #pragma unroll
     for (int j = 0; j < NU; ++j) sm.red[j][tid] = acc[j];
@@ -399,19 +400,17 @@ __device__ __forceinline__ void elite_update_step(const EliteArgs& a, int h, Eli
             }
             cj = rem;
         }
-        for (int k0 = 0; k0 < a.K; k0 += 64) {
+        for (int e0 = 0; e0 < ne; e0 += 64) {
             if (tid < 64) {
-                const int k = k0 + tid;
+                const int e = e0 + tid;
                 float wk = 0.0f;
                 float u[NU];
 #pragma unroll
                 for (int j = 0; j < NU; ++j) u[j] = sm.mean[j];
-                if (k < a.K) {
-                    const float c = a.costs[k];
-                    if (isfinite(c) && cost_key(c, k) <= thr) {
-                        wk = expf(-(c - cmin) * inv_beta);
-                        elite_row<NU>(a, h, k, key, iter, unom_h, u);
-                    }
+                if (e < ne) {
+                    const int k = a.eidx[e];
+                    wk = expf(-(a.costs[k] - cmin) * inv_beta);
+                    elite_row<NU>(a, h, k, key, iter, unom_h, u);
                 }
 #pragma unroll
                 for (int j = 0; j < NU; ++j) sm.d[tid][j] = u[j] - sm.mean[j];
@@ -419,8 +418,9 @@ __device__ __forceinline__ void elite_update_step(const EliteArgs& a, int h, Eli
             }
             __syncthreads();
             if (tid < NE) {
+                const int nt = ne - e0 < 64 ? ne - e0 : 64;
 #pragma unroll 4
-                for (int t = 0; t < 64; ++t) cv += sm.d[t][NU] * sm.d[t][ci] * sm.d[t][cj];
+                for (int t = 0; t < nt; ++t) cv += sm.d[t][NU] * sm.d[t][ci] * sm.d[t][cj];
             }
             __syncthreads();
         }
@@ -433,36 +433,28 @@ __device__ __forceinline__ void elite_update_step(const EliteArgs& a, int h, Eli
         }
         __syncthreads();
         if (tid < NU * NU) a.Sigma[(size_t)h * NU * NU + tid] = sm.cov[tid / NU][tid % NU];
-        if (tid == 0) {  // factor the new block for the next iteration's sampling
-            float Lm[NU][NU];
+        __syncthreads();
+        if (tid < 32) {  // factor the new block in place (one warp, right-looking) for the next sampling
             bool ok = true;
-#pragma unroll
-            for (int r = 0; r < NU; ++r)
-#pragma unroll
-                for (int q = 0; q < NU; ++q) Lm[r][q] = q <= r ? sm.cov[r][q] : 0.0f;
-#pragma unroll
             for (int j = 0; j < NU; ++j) {
-                float s = Lm[j][j];
-#pragma unroll
-                for (int q = 0; q < j; ++q) s -= Lm[j][q] * Lm[j][q];
+                const float s = sm.cov[j][j];
                 ok = ok && s > 0.0f;
                 const float dj = sqrtf(fmaxf(s, 1e-30f)), inv = 1.0f / dj;
-                Lm[j][j] = dj;
-#pragma unroll
-                for (int r = j + 1; r < NU; ++r) {
-                    float t = Lm[r][j];
-#pragma unroll
-                    for (int q = 0; q < j; ++q) t -= Lm[r][q] * Lm[j][q];
-                    Lm[r][j] = t * inv;
+                __syncwarp();
+                for (int r = j + 1 + tid; r < NU; r += 32) sm.cov[r][j] *= inv;
+                if (tid == 0) sm.cov[j][j] = dj;
+                __syncwarp();
+                const int n = NU - j - 1;
+                for (int t = tid; t < n * n; t += 32) {
+                    const int r = j + 1 + t / n, q = j + 1 + t % n;
+                    if (q <= r) sm.cov[r][q] -= sm.cov[r][j] * sm.cov[q][j];
                 }
+                __syncwarp();
             }
             if (ok) {
                 float* Lo = a.Lout + (size_t)h * NU * NU;
-#pragma unroll
-                for (int r = 0; r < NU; ++r)
-#pragma unroll
-                    for (int q = 0; q < NU; ++q) Lo[r * NU + q] = Lm[r][q];
-            } else {
+                for (int t = tid; t < NU * NU; t += 32) Lo[t] = (t % NU) <= (t / NU) ? sm.cov[t / NU][t % NU] : 0.0f;
+            } else if (tid == 0) {
                 atomicOr(a.err, ERRB_CHOLESKY);
             }
         }

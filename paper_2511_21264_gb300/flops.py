@@ -66,3 +66,14 @@ def update_flops(K: int, H: int, nu: int) -> float:
     """a11/a12 per iteration: weights (sub, mul) and the weighted sums, with
     the samples regenerated (sampling counted as in per_sample_step)."""
     return K * (2 + 1) * H + K * H * nu * (8 + 2)
+
+
+def qp_flops(H: int, iters: int) -> float:
+    """Algorithmic FP32 operations of the QP smoothing projection (Eq. 5) of
+    one sequence: `iters` ADMM iterations in the banded form.  Per horizon
+    step and iteration: the four row values (11), clip, dual and scaled
+    residual of each row (4 x 5 = 20), the right-hand side scatter (14) and
+    one row each of the forward and backward band substitutions (7 + 7);
+    FMA = 2, min/max = 1 each.  The start point (prefix sums, B^T vt) adds
+    3 per step; sampling is not counted."""
+    return float(iters) * 59.0 * H + 3.0 * H

@@ -146,6 +146,10 @@ def lib():
     _decl(L, "mppi_profile", i, [vp, i])
     _decl(L, "mppi_profile_read", i, [vp, C.POINTER(i), C.POINTER(C.c_float), C.POINTER(C.c_float),
                                        C.POINTER(C.c_double), C.POINTER(C.c_double)])
+    _decl(L, "mppi_profile_projection", i, [vp, C.POINTER(C.c_float)])
+    _decl(L, "mppi_qp_project", i, [i, i, C.c_float, fp, i, C.c_float, fp, fp, fp, fp, fp, vp])
+    _decl(L, "mppi_set_projection", i, [vp, fp, i, C.c_float, fp])
+    _decl(L, "mppi_get_samples", i, [vp, fp, vp])
     _lib = L
     return L
 
@@ -200,6 +204,32 @@ def step_noalloc(blob: bytes, K: int, H: int, lam: float, sigma, seed: int, iter
                                    C.c_uint64(iteration), _ptr(state), _ptr(u_nom), _ptr(u_out),
                                    C.byref(st) if want_status else None, _stream(stream)), "mppi_step_noalloc")
     return st.value if want_status else None
+
+
+QP_SCALES = (0.1, 1.0, 2.0, 4.0)  # the library's MPPI_QP_SCALE_* defaults
+
+
+def _host_f32(a, n=None):
+    import numpy as np
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    if n is not None and a.size != n:
+        raise ValueError(f"expected {n} values, got {a.size}")
+    return a
+
+
+def qp_project(v_in, bounds, q0, qd0, dt: float, iters: int = 30, rho: float = 1.0, scales=None, v_out=None,
+               stream=None):
+    """QP smoothing projection (Eq. 5) of n sequences (CUDA n x H) sharing
+    one set of bounds (8 host values: lo, hi for position, velocity,
+    acceleration, jerk); q0, qd0: CUDA n present positions and velocities."""
+    n, H = v_in.shape
+    v_out = v_in if v_out is None else v_out
+    b = _host_f32(bounds, 8)
+    sc = None if scales is None else _host_f32(scales, 4)
+    _check(lib().mppi_qp_project(int(n), int(H), float(dt), b.ctypes.data, int(iters), float(rho),
+                                 None if sc is None else sc.ctypes.data, _ptr(q0), _ptr(qd0), _ptr(v_in),
+                                 _ptr(v_out), _stream(stream)), "mppi_qp_project")
+    return v_out
 
 
 class ServerConfig(C.Structure):
@@ -476,6 +506,28 @@ class Controller:
 
     def set_launch(self, samples_per_cta: int):
         _check(lib().mppi_set_launch(self._h, int(samples_per_cta)), "mppi_set_launch")
+
+    def set_projection(self, bounds, iters: int = 30, rho: float = 1.0, scales=None):
+        """QP smoothing projection (Eq. 5) of every sample: bounds is nu x 8
+        (per joint: lo, hi for position, velocity, acceleration, jerk); iters=0
+        turns it off."""
+        if int(iters) == 0:
+            _check(lib().mppi_set_projection(self._h, None, 0, 1.0, None), "mppi_set_projection")
+            return
+        b = _host_f32(bounds, 8 * self.model.nu)
+        sc = None if scales is None else _host_f32(scales, 4)
+        _check(lib().mppi_set_projection(self._h, b.ctypes.data, int(iters), float(rho),
+                                         None if sc is None else sc.ctypes.data), "mppi_set_projection")
+
+    def samples(self, out, stream=None):
+        """The last iteration's samples as rolled out (H x K x nu)."""
+        _check(lib().mppi_get_samples(self._h, _ptr(out), _stream(stream)), "mppi_get_samples")
+        return out
+
+    def profile_projection(self) -> float:
+        ms = C.c_float()
+        _check(lib().mppi_profile_projection(self._h, C.byref(ms)), "mppi_profile_projection")
+        return ms.value
 
     def close(self):
         if getattr(self, "_h", None):

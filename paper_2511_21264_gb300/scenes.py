@@ -462,3 +462,19 @@ def random_states(scene: Scene, n: int, seed: int, q_spread=0.3, v_spread=0.3,
     quat /= np.linalg.norm(quat, axis=1, keepdims=True)
     X[:, na2 + 3:na2 + 7] = quat
     return X
+
+
+def projection_bounds(scene: Scene, pos_margin: float = 1.0, vel: float = math.pi, acc: float = 10.0,
+                      jerk: float = 300.0) -> np.ndarray:
+    """Bounds of the QP smoothing projection (Eq. 5), nu x 8 per joint:
+    position within pos_margin of the home pose, velocity within +-vel and
+    the control bounds, acceleration +-acc, jerk +-jerk.  The paper gives no
+    values; these are UR5e-like rates (3.1 rad/s, 10 rad/s^2) and a jerk
+    bound that makes the projection active on white-noise samples."""
+    b = np.zeros((scene.nu, 8))
+    q_home = scene.x0[: scene.nu]
+    for j in range(scene.nu):
+        ln = scene.links[j // scene.n_a][j % scene.n_a]
+        b[j] = [q_home[j] - pos_margin, q_home[j] + pos_margin, max(ln.u_lo, -vel), min(ln.u_hi, vel),
+                -acc, acc, -jerk, jerk]
+    return b
