@@ -364,7 +364,8 @@ struct mppi_ctx {
     // QP smoothing projection (Eq. 5)
     int qp_iters = 0;
     float qp_dt = 0.0f;
-    void* d_qp = nullptr;  // nu QPClass records, then nu x 2H band rows
+    void* d_qp = nullptr;  // nu QPClass records, then per joint the inverse (H <= 32) or 2H band rows
+    size_t qp_bytes = 0;
 };
 
 namespace mppi {
@@ -716,7 +717,9 @@ static int launch_projection(mppi_ctx* c, const float* state, const float* u_nom
     q.per_cls = c->K;
     q.dt = c->qp_dt;
     q.cls = static_cast<const QPClass*>(c->d_qp);
-    q.band = reinterpret_cast<const float4*>(static_cast<unsigned char*>(c->d_qp) + (size_t)nu * sizeof(QPClass));
+    const unsigned char* fac = static_cast<unsigned char*>(c->d_qp) + (size_t)nu * sizeof(QPClass);
+    if (c->H <= QP_WARP_MAX_H) q.minv = reinterpret_cast<const float*>(fac);
+    else q.band = reinterpret_cast<const float4*>(fac);
     q.q0 = state;
     q.qd0 = state + nq;
     q.q_per_seq = 0;
@@ -752,19 +755,28 @@ int mppi_set_projection(mppi_ctx* c, const float* bounds, int iters, float rho, 
     }
     if (c->H > MPPI_QP_MAX_H || !c->d_U) return MPPI_ERR_UNSUPPORTED;
     const float dt = c->m->host.dt;
-    const size_t bytes = (size_t)nu * sizeof(QPClass) + (size_t)nu * 2 * c->H * sizeof(float4);
+    // per joint: the dense inverse (H <= 32, warp kernel) or band factor rows
+    const bool warp = c->H <= QP_WARP_MAX_H;
+    const size_t per = warp ? 32 * 32 * sizeof(float) : 2 * (size_t)c->H * sizeof(float4);
+    const size_t bytes = (size_t)nu * sizeof(QPClass) + (size_t)nu * per;
     std::vector<unsigned char> host(bytes);
     QPClass* cls = reinterpret_cast<QPClass*>(host.data());
-    float4* band = reinterpret_cast<float4*>(host.data() + (size_t)nu * sizeof(QPClass));
+    unsigned char* fac = host.data() + (size_t)nu * sizeof(QPClass);
     for (int j = 0; j < nu; ++j) {
         qp_make_class(bounds + 8 * j, sc, rho, &cls[j]);
         const double scd[4] = {cls[j].s[0], cls[j].s[1], cls[j].s[2], cls[j].s[3]};
-        const int rc = qp_band_factor(c->H, rho, scd, band + (size_t)j * 2 * c->H);
+        const int rc = warp ? qp_dense_inverse(c->H, rho, scd, reinterpret_cast<float*>(fac + j * per))
+                            : qp_band_factor(c->H, rho, scd, reinterpret_cast<float4*>(fac + j * per));
         if (rc != MPPI_OK) return rc;
+    }
+    if (c->d_qp && c->qp_bytes != bytes) {
+        cudaFree(c->d_qp);
+        c->d_qp = nullptr;
     }
     if (!c->d_qp) {
         cudaError_t e = cudaMalloc(&c->d_qp, bytes);
         if (e != cudaSuccess) return cuda_fail(e);
+        c->qp_bytes = bytes;
     }
     cudaError_t e = cudaMemcpy(c->d_qp, host.data(), bytes, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e);

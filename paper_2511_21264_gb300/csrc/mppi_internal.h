@@ -155,8 +155,11 @@ struct QPArgs {
     unsigned long long iter_val;
     float* out;
     long long o_a, o_b, o_h;
+    const float* minv;   // H <= 32: per class the 32 x 32 inverse (I + rho D^T D)^-1 in velocity coordinates
 };
+constexpr int QP_WARP_MAX_H = 32;
 int qp_band_factor(int H, double rho, const double sc[4], float4* band);
+int qp_dense_inverse(int H, double rho, const double sc[4], float* minv);
 void qp_make_class(const float b[8], const float sc[4], float rho, QPClass* c);
 int qp_validate(const float b[8], const float sc[4], float rho);
 int launch_qp(const QPArgs& a, cudaStream_t s);

@@ -2,8 +2,18 @@
 // moved to the nearest sequence (in the 2-norm) whose position, velocity,
 // acceleration and jerk (r = 0..3, Sec. III) stay within their bounds.
 //
-// Solver: a fixed number of ADMM iterations (the paper names none), one
-// thread per sequence.  The iteration is run in the coordinates
+// Solver: a fixed number of ADMM iterations (the paper names none).  Two
+// kernels run the same iteration:
+//
+// H <= 32: one warp per sequence, lane t = horizon step, in the velocity
+// coordinates themselves.  The rows come from warp scans and neighbour
+// shuffles (position = prefix sum, acceleration and jerk = differences),
+// their transposes from a suffix scan and two shuffles, and the linear
+// solve is a product with the precomputed inverse of I + rho D^T D (shared
+// by every sequence of a class), whose row t each lane keeps in registers.
+// Many warps per SM hide the shuffle and FMA latencies.
+//
+// Longer horizons: one thread per sequence.  The iteration is run in the coordinates
 //   x_i = sum_{t<i} v_t   (i = 1..H, the position offset over dt),
 // where every constraint row touches at most four consecutive x_i and the
 // ADMM linear system  N x = B^T vt + rho D^T (w - y),  N = B^T B + rho D^T D
@@ -86,6 +96,67 @@ int qp_band_factor(int H, double rho, const double sc[4], float4* band) {
         const double dinv = 1.0 / L(i, i);
         band[i] = make_float4((float)dinv, (float)L(i, i - 1), (float)L(i, i - 2), (float)L(i, i - 3));
         band[H + i] = make_float4((float)dinv, (float)L(i + 1, i), (float)L(i + 2, i), (float)L(i + 3, i));
+    }
+    return MPPI_OK;
+}
+
+// Inverse of I + rho D^T D in velocity coordinates (H <= 32), rows padded to
+// 32 columns, rows >= H zero.  D's rows: position (prefix sums), velocity,
+// acceleration (first differences), jerk (second differences, t >= 1), each
+// group times its scale.
+int qp_dense_inverse(int H, double rho, const double sc[4], float* minv) {
+    if (H < 1 || H > QP_WARP_MAX_H) return MPPI_ERR_INVALID_ARG;
+    std::vector<double> A((size_t)H * H, 0.0), row(H);
+    auto add_row = [&](double w) {
+        for (int a = 0; a < H; ++a)
+            if (row[a] != 0.0)
+                for (int b = 0; b < H; ++b) A[(size_t)a * H + b] += w * row[a] * row[b];
+    };
+    for (int t = 0; t < H; ++t) {
+        std::fill(row.begin(), row.end(), 0.0);
+        for (int i = 0; i <= t; ++i) row[i] = 1.0;
+        add_row(rho * sc[0] * sc[0]);
+        std::fill(row.begin(), row.end(), 0.0);
+        row[t] = 1.0;
+        add_row(rho * sc[1] * sc[1]);
+        if (t >= 1) row[t - 1] = -1.0;
+        add_row(rho * sc[2] * sc[2]);
+        if (t >= 1) {
+            std::fill(row.begin(), row.end(), 0.0);
+            row[t] = 1.0;
+            row[t - 1] = -2.0;
+            if (t >= 2) row[t - 2] = 1.0;
+            add_row(rho * sc[3] * sc[3]);
+        }
+    }
+    for (int i = 0; i < H; ++i) A[(size_t)i * H + i] += 1.0;
+    // Cholesky, then the inverse column by column
+    for (int j = 0; j < H; ++j) {
+        double s = A[(size_t)j * H + j];
+        for (int k = 0; k < j; ++k) s -= A[(size_t)j * H + k] * A[(size_t)j * H + k];
+        if (!(s > 0.0)) return MPPI_ERR_CHOLESKY;
+        const double d = std::sqrt(s);
+        A[(size_t)j * H + j] = d;
+        for (int i = j + 1; i < H; ++i) {
+            double t = A[(size_t)i * H + j];
+            for (int k = 0; k < j; ++k) t -= A[(size_t)i * H + k] * A[(size_t)j * H + k];
+            A[(size_t)i * H + j] = t / d;
+        }
+    }
+    std::fill(minv, minv + 32 * 32, 0.0f);
+    std::vector<double> x(H);
+    for (int c = 0; c < H; ++c) {
+        for (int i = 0; i < H; ++i) {  // L y = e_c
+            double t = i == c ? 1.0 : 0.0;
+            for (int k = 0; k < i; ++k) t -= A[(size_t)i * H + k] * x[k];
+            x[i] = t / A[(size_t)i * H + i];
+        }
+        for (int i = H - 1; i >= 0; --i) {  // L^T x = y
+            double t = x[i];
+            for (int k = i + 1; k < H; ++k) t -= A[(size_t)k * H + i] * x[k];
+            x[i] = t / A[(size_t)i * H + i];
+        }
+        for (int i = 0; i < H; ++i) minv[i * 32 + c] = (float)x[i];
     }
     return MPPI_OK;
 }
@@ -214,6 +285,135 @@ __device__ void qp_admm(const QPClass& c, const float4* __restrict__ band, int H
     }
 }
 
+// Raw sample h of member k (sample) in class j (joint): the value the
+// rollout's sampler draws, unclamped.
+__device__ __forceinline__ float qp_sample(const QPArgs& a, uint2 key, uint32_t iter, int k, int j, int h) {
+    float v = a.u_nom[h * a.nu + j];
+    if (a.Lfac) {
+        const float* Lr = a.Lfac + ((size_t)h * a.nu + j) * a.nu;
+        for (int jb = 0; 4 * jb <= j; ++jb) {
+            const uint4 w = philox4x32_10(make_uint4((uint32_t)jb, (uint32_t)h, (uint32_t)k, iter), key);
+            for (int t = 0; t < 4 && 4 * jb + t <= j; ++t) v = __fmaf_rn(Lr[4 * jb + t], block_normal(w, t), v);
+        }
+    } else {
+        const uint4 w = philox4x32_10(make_uint4((uint32_t)(j >> 2), (uint32_t)h, (uint32_t)k, iter), key);
+        v = __fmaf_rn(a.sigma[j], block_normal(w, j & 3), v);
+    }
+    return v;
+}
+
+// ADMM iterations of one sequence held by one warp (lane = step t < H);
+// Mi = this lane's row of the inverse, bc = 32 floats of this warp's shared
+// memory.  Returns v_t (0 on lanes >= H).
+__device__ __forceinline__ float qp_warp_admm(const QPClass& c, const float (&Mi)[32], int H, int iters, float dt,
+                                              float q, float qd, float vt, int lane, float* bc) {
+    const bool act = lane < H;
+    const float s0 = c.s[0], s1 = c.s[1], s2 = c.s[2], s3 = c.s[3];
+    const float rs0 = c.rho * s0, rs1 = c.rho * s1, rs2 = c.rho * s2, rs3 = c.rho * s3;
+    const float idt = 1.0f / dt, dt2 = dt * dt;
+    float Plo, Phi, Vlo, Vhi, Alo, Ahi, Jlo, Jhi;
+    qp_bound(s0, (c.lo[0] - q) * idt, (c.hi[0] - q) * idt, Plo, Phi);
+    qp_bound(s1, c.lo[1], c.hi[1], Vlo, Vhi);
+    // v_{-1} = qd moves into the bounds of the first acceleration and jerk rows
+    qp_bound(s2, c.lo[2] * dt + (lane == 0 ? qd : 0.0f), c.hi[2] * dt + (lane == 0 ? qd : 0.0f), Alo, Ahi);
+    qp_bound(s3, c.lo[3] * dt2 - (lane == 1 ? qd : 0.0f), c.hi[3] * dt2 - (lane == 1 ? qd : 0.0f), Jlo, Jhi);
+    float v = act ? vt : 0.0f;
+    const float vt0 = v;
+    float yP = 0.0f, yV = 0.0f, yA = 0.0f, yJ = 0.0f;
+    const float4* bc4 = reinterpret_cast<const float4*>(bc);
+    for (int it = 0; it < iters; ++it) {
+        // rows at step t: prefix sum, v, first and second differences
+        float pre = v;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const float n = __shfl_up_sync(FULL, pre, d);
+            if (lane >= d) pre += n;
+        }
+        float vm1 = __shfl_up_sync(FULL, v, 1), vm2 = __shfl_up_sync(FULL, v, 2);
+        if (lane < 1) vm1 = 0.0f;
+        if (lane < 2) vm2 = 0.0f;
+        const float d1 = v - vm1, d2 = d1 - (vm1 - vm2);
+        float eP = qp_row(s0 * pre, yP, Plo, Phi, rs0);
+        float eV = qp_row(s1 * v, yV, Vlo, Vhi, rs1);
+        float eA = qp_row(s2 * d1, yA, Alo, Ahi, rs2);
+        float eJ = lane >= 1 ? qp_row(s3 * d2, yJ, Jlo, Jhi, rs3) : 0.0f;
+        if (!act) eP = eV = eA = eJ = 0.0f;
+        // right-hand side vt + D^T e: suffix sum (position), e (velocity),
+        // e_t - e_{t+1} (acceleration), e_t - 2 e_{t+1} + e_{t+2} (jerk)
+        float suf = eP;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const float n = __shfl_down_sync(FULL, suf, d);
+            if (lane + d < 32) suf += n;
+        }
+        float c1 = __shfl_down_sync(FULL, -eA - 2.0f * eJ, 1), c2 = __shfl_down_sync(FULL, eJ, 2);
+        if (lane + 1 >= 32) c1 = 0.0f;
+        if (lane + 2 >= 32) c2 = 0.0f;
+        const float rhs = vt0 + suf + eV + eA + eJ + c1 + c2;
+        // v = (I + rho D^T D)^-1 rhs
+        bc[lane] = rhs;
+        __syncwarp();
+        float acc0 = 0.0f, acc1 = 0.0f, acc2 = 0.0f, acc3 = 0.0f;
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            const float4 r = bc4[s];
+            acc0 = __fmaf_rn(Mi[4 * s + 0], r.x, acc0);
+            acc1 = __fmaf_rn(Mi[4 * s + 1], r.y, acc1);
+            acc2 = __fmaf_rn(Mi[4 * s + 2], r.z, acc2);
+            acc3 = __fmaf_rn(Mi[4 * s + 3], r.w, acc3);
+        }
+        __syncwarp();
+        v = act ? (acc0 + acc1) + (acc2 + acc3) : 0.0f;
+    }
+    return v;
+}
+
+__device__ __forceinline__ void qp_load_row(const float* minv_cls, int lane, float (&Mi)[32]) {
+    const float4* r = reinterpret_cast<const float4*>(minv_cls + (size_t)lane * 32);
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+        const float4 m = __ldg(&r[s]);
+        Mi[4 * s + 0] = m.x;
+        Mi[4 * s + 1] = m.y;
+        Mi[4 * s + 2] = m.z;
+        Mi[4 * s + 3] = m.w;
+    }
+}
+
+// Controller form: CTA = sample k, warp = joint j (nu warps); the CTA's
+// projected sequences are staged in shared memory and written to the h-major
+// sample buffer as contiguous rows of nu values.
+__global__ void __launch_bounds__(14 * 32, 2) qp_warp_sample_kernel(QPArgs a) {
+    extern __shared__ __align__(16) float wsm[];
+    const int lane = threadIdx.x & 31, j = threadIdx.x >> 5, k = blockIdx.x, nu = a.nu;
+    float* bc = wsm + 32 * j;
+    float* stage = wsm + 32 * nu;  // H x nu
+    const uint2 key = make_uint2((uint32_t)a.seed, (uint32_t)(a.seed >> 32));
+    const uint32_t iter = (uint32_t)(a.iter_ptr ? *a.iter_ptr : a.iter_val);
+    const QPClass c = a.cls[j];
+    float Mi[32];
+    qp_load_row(a.minv + (size_t)j * 32 * 32, lane, Mi);
+    const float vt = lane < a.H ? qp_sample(a, key, iter, k, j, lane) : 0.0f;
+    const float v = qp_warp_admm(c, Mi, a.H, a.iters, a.dt, a.q0[j], a.qd0[j], vt, lane, bc);
+    if (lane < a.H) stage[lane * nu + j] = v;
+    __syncthreads();
+    for (int i = threadIdx.x; i < a.H * nu; i += blockDim.x)
+        a.out[((size_t)(i / nu) * a.per_cls + k) * nu + (i % nu)] = stage[i];
+}
+
+// Standalone form: 8 warps per CTA, one sequence (class 0) each.
+__global__ void __launch_bounds__(256) qp_warp_kernel(QPArgs a) {
+    __shared__ __align__(16) float bcs[8][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int i = blockIdx.x * 8 + w;
+    if (i >= a.n) return;
+    float Mi[32];
+    qp_load_row(a.minv, lane, Mi);
+    const float vt = lane < a.H ? a.vin[(size_t)i * a.H + lane] : 0.0f;
+    const float v = qp_warp_admm(a.cls[0], Mi, a.H, a.iters, a.dt, a.q0[i], a.qd0[i], vt, lane, bcs[w]);
+    if (lane < a.H) a.out[(size_t)i * a.H + lane] = v;
+}
+
 // Sequence i: class i / per_cls, member i % per_cls.
 __global__ void __launch_bounds__(QP_THREADS) qp_project_kernel(QPArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -238,20 +438,8 @@ __global__ void __launch_bounds__(QP_THREADS) qp_project_kernel(QPArgs a) {
         float vt;
         if (a.vin) {
             vt = a.vin[base_in + (long long)h * a.i_h];
-        } else {  // sample (k = mem, joint j = cls): the values the rollout's sampler draws, unclamped
-            const int j = cls, k = mem;
-            float v = a.u_nom[h * a.nu + j];
-            if (a.Lfac) {
-                const float* Lr = a.Lfac + ((size_t)h * a.nu + j) * a.nu;
-                for (int jb = 0; 4 * jb <= j; ++jb) {
-                    const uint4 w = philox4x32_10(make_uint4((uint32_t)jb, (uint32_t)h, (uint32_t)k, iter), key);
-                    for (int t = 0; t < 4 && 4 * jb + t <= j; ++t) v = __fmaf_rn(Lr[4 * jb + t], block_normal(w, t), v);
-                }
-            } else {
-                const uint4 w = philox4x32_10(make_uint4((uint32_t)(j >> 2), (uint32_t)h, (uint32_t)k, iter), key);
-                v = __fmaf_rn(a.sigma[j], block_normal(w, j & 3), v);
-            }
-            vt = v;
+        } else {  // sample k = member, joint j = class
+            vt = qp_sample(a, key, iter, mem, cls, h);
         }
         acc += vt;
         if (h > 0) xb[(size_t)(h - 1) * T].y = prev - vt;
@@ -277,6 +465,16 @@ size_t qp_smem_bytes(int H) { return (size_t)H * qp_threads(H) * (sizeof(float4)
 
 int launch_qp(const QPArgs& a, cudaStream_t s) {
     if (a.n <= 0) return MPPI_OK;
+    if (a.minv && a.H <= QP_WARP_MAX_H) {
+        if (a.vin) {  // standalone, one class
+            qp_warp_kernel<<<(a.n + 7) / 8, 256, 0, s>>>(a);
+        } else {      // controller: CTA = sample, warp = joint
+            if (a.nu > 14 || a.n != a.per_cls * a.nu) return MPPI_ERR_UNSUPPORTED;
+            const size_t sm = (size_t)(32 * a.nu + a.H * a.nu) * sizeof(float);
+            qp_warp_sample_kernel<<<a.per_cls, 32 * a.nu, sm, s>>>(a);
+        }
+        return cudaGetLastError() == cudaSuccess ? MPPI_OK : MPPI_ERR_CUDA;
+    }
     const size_t sm = qp_smem_bytes(a.H);
     if (sm > 227 * 1024) return MPPI_ERR_UNSUPPORTED;
     const int T = qp_threads(a.H);
@@ -307,12 +505,15 @@ extern "C" int mppi_qp_project(int n, int H, float dt, const float* bounds, int 
     if (n == 0) return MPPI_OK;
     QPClass c;
     qp_make_class(bounds, sc, rho, &c);
-    std::vector<float4> band(2 * (size_t)H);
+    const bool warp = H <= QP_WARP_MAX_H;
+    // band factor rows (thread kernel) or the dense inverse (warp kernel), as float4s
+    std::vector<float4> band(warp ? 32 * 32 / 4 : 2 * (size_t)H);
     const double scd[4] = {c.s[0], c.s[1], c.s[2], c.s[3]};
-    rc = qp_band_factor(H, rho, scd, band.data());
+    rc = warp ? qp_dense_inverse(H, rho, scd, reinterpret_cast<float*>(band.data()))
+              : qp_band_factor(H, rho, scd, band.data());
     if (rc != MPPI_OK) return rc;
     cudaStream_t s = (cudaStream_t)stream;
-    // the class record and band live in one stream-ordered scratch block
+    // the class record and the factor live in one stream-ordered scratch block
     const size_t bytes = sizeof(QPClass) + band.size() * sizeof(float4);
     void* d = nullptr;
     cudaError_t e = cudaMallocAsync(&d, bytes, s);
@@ -329,6 +530,7 @@ extern "C" int mppi_qp_project(int n, int H, float dt, const float* bounds, int 
     a.per_cls = n;
     a.cls = static_cast<const QPClass*>(d);
     a.band = reinterpret_cast<const float4*>(static_cast<unsigned char*>(d) + sizeof(QPClass));
+    if (warp) a.minv = reinterpret_cast<const float*>(a.band);
     a.q0 = q0;
     a.qd0 = qd0;
     a.q_per_seq = 1;

@@ -2,11 +2,13 @@
 by element, through the C ABI: the standalone entry (mppi_qp_project) and
 the projection inside a controller's iteration (mppi_set_projection).
 
-Tolerance: |v_gpu - v_oracle| <= 2e-4 + 1e-4 |v| per element.  The kernel
-runs the same ADMM iterations in other coordinates (scaled positions with a
-band Cholesky factor) and in FP32; an FP32 emulation of it stays within
-2e-5 of the oracle on these workloads, so the bound leaves a margin of 10
-for the summation order of the device code.  A full MPPI step with the
+Tolerance: |v_gpu - v_oracle| <= 2e-4 + 1e-4 |v| per element.  Both
+kernels run the oracle's ADMM iterations in FP32: for H <= 32 one warp per
+sequence in the same velocity coordinates with the precomputed inverse
+(an FP32 emulation stays within 2e-6 of the oracle), for longer horizons
+one thread per sequence in scaled-position coordinates with a band
+Cholesky factor (emulation within 2e-5); the bound leaves a margin of 10
+for the device code's summation order.  A full MPPI step with the
 projection matches the oracle's composition (sample, project, roll out,
 update) within the existing full-step bound of 1e-3."""
 import numpy as np
