@@ -91,6 +91,17 @@ def lib():
         L.or_sample_cov.restype = i
         L.or_qp_project.argtypes = [i, d, d, dp, i, dp, d, d, dp, dp, dp]
         L.or_qp_project.restype = d
+        L.or_capsule_capsule.argtypes = [dp, dp, d, dp, dp, d, dp]
+        L.or_rot_to_quat.argtypes = [dp, dp]
+        L.or_ee_state.argtypes = [vp, dp, dp]
+        L.or_pair_distances.argtypes = [vp, dp, i, dp]
+        L.or_pair_distances.restype = i
+        L.or_task_cost_features.argtypes = [dp, i, i, i, dp, dp, dp, dp]
+        L.or_task_cost_features.restype = d
+        L.or_task_cost.argtypes = [vp, dp, dp, i, dp]
+        L.or_task_cost.restype = d
+        L.or_rollout_task.argtypes = [vp, dp, dp, dp, i, dp, dp]
+        L.or_rollout_task.restype = d
         _lib = L
     return _lib
 
@@ -188,6 +199,34 @@ class Model:
                               _dp(costs), nthreads)
         return costs
 
+    # -- ball-task cost suite (Sec. IV-B) ---------------------------------
+    def ee_state(self, x):
+        """End effectors at state x: dict p (2x3), v (2x3), quat (2x4)."""
+        ee = np.zeros(20)
+        lib().or_ee_state(self.ptr, _dp(_f64(x)), _dp(ee))
+        return {"p": ee[0:6].reshape(2, 3), "v": ee[6:12].reshape(2, 3), "quat": ee[12:20].reshape(2, 4)}
+
+    def pair_distances(self, x, phase: int):
+        d = np.zeros(MAX_PAIRS)
+        n = lib().or_pair_distances(self.ptr, _dp(_f64(x)), int(phase), _dp(d))
+        return d[:n].copy()
+
+    def task_cost(self, task, traj):
+        """(total, terms[8]) of a trajectory of H+1 states."""
+        traj = _f64(traj)
+        terms = np.zeros(8)
+        c = lib().or_task_cost(self.ptr, _dp(_f64(task)), _dp(traj), traj.shape[0] - 1, _dp(terms))
+        return c, terms
+
+    def rollout_task(self, x, U, task):
+        """(total, terms[8], trajectory) of the rollout of U (H x nu)."""
+        U = _f64(U)
+        H = U.shape[0]
+        traj = np.zeros((H + 1, self.nq + self.nv))
+        terms = np.zeros(8)
+        c = lib().or_rollout_task(self.ptr, _dp(_f64(task)), _dp(_f64(x)), _dp(U), H, _dp(traj), _dp(terms))
+        return c, terms, traj
+
     def sample_cov(self, seed, iteration, K, nu_in, Sigma):
         """Samples U (K x H x nu) from per-step covariance blocks."""
         nu_in = _f64(nu_in)
@@ -277,6 +316,34 @@ def elite_update(costs, U, n_elite, beta, eta, nu_in, Sigma_in, update_cov=True,
                                float(cov_floor), _dp(_f64(nu_in)), _dp(_f64(Sigma_in)), _dp(nu_out), _dp(S_out),
                                elite.ctypes.data_as(C.POINTER(C.c_int)))
     return nu_out, S_out, elite, st
+
+
+TASK_N = 26        # task parameters before theta_home
+MAX_PAIRS = 2 * 7 * 16 + 2 * 7 + 7 * 7
+TASK_TERMS = ("C_c", "C_theta", "C_yz", "C_v", "C_r", "C_l", "C_eef_obj", "C_obj_targ")
+
+
+def capsule_capsule(a0, a1, ra, b0, b1, rb) -> float:
+    d = np.zeros(1)
+    lib().or_capsule_capsule(_dp(_f64(a0)), _dp(_f64(a1)), float(ra), _dp(_f64(b0)), _dp(_f64(b1)), float(rb),
+                             _dp(d))
+    return float(d[0])
+
+
+def rot_to_quat(R):
+    q = np.zeros(4)
+    lib().or_rot_to_quat(_dp(_f64(R).reshape(9).copy()), _dp(q))
+    return q
+
+
+def task_cost_features(task, D, TH, EE):
+    """Task cost from features of x_0..x_H: D (H+1, B), TH (H+1, nu),
+    EE (H+1, 20).  Returns (total, terms[8])."""
+    D, TH, EE = _f64(D), _f64(TH), _f64(EE)
+    terms = np.zeros(8)
+    c = lib().or_task_cost_features(_dp(_f64(task)), TH.shape[1], D.shape[1], D.shape[0] - 1, _dp(D), _dp(TH),
+                                    _dp(EE), _dp(terms))
+    return c, terms
 
 
 QP_SCALES = (0.1, 1.0, 2.0, 4.0)

@@ -1251,3 +1251,220 @@ double or_qp_project(int H, double dt, double rho, const double *sc, int iters, 
     free(D); free(lo); free(hi); free(A); free(y); free(g); free(rhs);
     return viol;
 }
+
+/* --------------------------------------------------------------------- */
+/* Ball-task cost suite (Sec. IV-B)                                       */
+/* --------------------------------------------------------------------- */
+/* Task parameters: a flat array of OR_TASK_N + nu values
+ *   [0] phase (0 pick, 1 move)  [1] w_c  [2] gamma  [3] w_theta  [4] w_yz
+ *   [5] w_v  [6] w_r  [7] w_l  [8] l_ball  [9] w_eef_obj  [10] w_obj_targ
+ *   [11] eps  [12..14] ball position before the pick  [15..17] target
+ *   [18..21] q1*  [22..25] q2* (unit quaternions, w first)
+ *   [26..26+nu) theta_home. */
+#define OR_TASK_N 26
+#define OR_MAXPAIRS (2 * OR_MAXL * OR_MAXB + 2 * OR_MAXL + OR_MAXL * OR_MAXL)
+
+/* Distance between two capsules: the minimum over s, t in [0, 1] of
+ * |a0 + s (a1 - a0) - b0 - t (b1 - b0)|, minus both radii.  The squared
+ * distance is a convex quadratic on the unit square, so its minimum is the
+ * interior stationary point when that lies inside, else the best of the
+ * four edge minima (each a clamped 1-D quadratic). */
+static double seg_point_t(const double *p0, const double *d, double dd, const double *x) {
+    if (dd <= 0.0) return 0.0;
+    double t = ((x[0] - p0[0]) * d[0] + (x[1] - p0[1]) * d[1] + (x[2] - p0[2]) * d[2]) / dd;
+    return t < 0.0 ? 0.0 : (t > 1.0 ? 1.0 : t);
+}
+static double seg_seg_d2(const double *a0, const double *u, const double *b0, const double *v, double s, double t) {
+    double e[3];
+    for (int k = 0; k < 3; k++) e[k] = a0[k] + s * u[k] - b0[k] - t * v[k];
+    return v3_dot(e, e);
+}
+void or_capsule_capsule(const double *a0, const double *a1, double ra, const double *b0, const double *b1, double rb,
+                        double *dist) {
+    double u[3], v[3], w[3];
+    v3_sub(a1, a0, u);
+    v3_sub(b1, b0, v);
+    v3_sub(a0, b0, w);
+    double A = v3_dot(u, u), B = v3_dot(u, v), C = v3_dot(v, v), D = v3_dot(u, w), E = v3_dot(v, w);
+    double best = INFINITY;
+    double den = A * C - B * B;
+    if (den > 1e-14 * (A * C + 1e-300)) { /* interior stationary point */
+        double s = (B * E - C * D) / den, t = (A * E - B * D) / den;
+        if (s >= 0.0 && s <= 1.0 && t >= 0.0 && t <= 1.0) best = seg_seg_d2(a0, u, b0, v, s, t);
+    }
+    double pts[3];
+    /* edges s = 0, s = 1 (closest t to a point), t = 0, t = 1 (closest s) */
+    for (int e = 0; e < 2; e++) {
+        for (int k = 0; k < 3; k++) pts[k] = a0[k] + e * u[k];
+        double t = seg_point_t(b0, v, C, pts);
+        double d2 = seg_seg_d2(a0, u, b0, v, (double)e, t);
+        if (d2 < best) best = d2;
+        for (int k = 0; k < 3; k++) pts[k] = b0[k] + e * v[k];
+        double s = seg_point_t(a0, u, A, pts);
+        d2 = seg_seg_d2(a0, u, b0, v, s, (double)e);
+        if (d2 < best) best = d2;
+    }
+    *dist = sqrt(best) - ra - rb;
+}
+
+/* Unit quaternion (w, x, y, z) of a rotation matrix (row-major): the
+ * largest of 4w^2 = 1 + tr, 4x^2 = 1 + R00 - R11 - R22, ... is taken
+ * from the diagonal and the other three components from the off-diagonal
+ * sums and differences; w >= 0. */
+void or_rot_to_quat(const double *R, double *q) {
+    double tr = R[0] + R[4] + R[8];
+    double c[4] = {1.0 + tr, 1.0 + R[0] - R[4] - R[8], 1.0 - R[0] + R[4] - R[8], 1.0 - R[0] - R[4] + R[8]};
+    int i = 0;
+    for (int k = 1; k < 4; k++)
+        if (c[k] > c[i]) i = k;
+    double s = 0.5 / sqrt(c[i]);
+    if (i == 0) { q[0] = 0.5 * sqrt(c[0]); q[1] = (R[7] - R[5]) * s; q[2] = (R[2] - R[6]) * s; q[3] = (R[3] - R[1]) * s; }
+    else if (i == 1) { q[1] = 0.5 * sqrt(c[1]); q[0] = (R[7] - R[5]) * s; q[2] = (R[1] + R[3]) * s; q[3] = (R[2] + R[6]) * s; }
+    else if (i == 2) { q[2] = 0.5 * sqrt(c[2]); q[0] = (R[2] - R[6]) * s; q[1] = (R[1] + R[3]) * s; q[3] = (R[5] + R[7]) * s; }
+    else { q[3] = 0.5 * sqrt(c[3]); q[0] = (R[3] - R[1]) * s; q[1] = (R[2] + R[6]) * s; q[2] = (R[5] + R[7]) * s; }
+    if (q[0] < 0.0) for (int k = 0; k < 4; k++) q[k] = -q[k];
+}
+
+/* End-effector state of both arms: position = distal end of the last
+ * capsule, orientation = the last link frame as a quaternion, linear
+ * velocity = J(q) qdot of that point.  ee = 20 values:
+ * p1[3] p2[3] v1[3] v2[3] q1[4] q2[4]. */
+void or_ee_state(const or_model *m, const double *x, double *ee) {
+    or_fk f;
+    or_forward_kinematics(m, x, &f);
+    int na = m->na, nv = m->nv;
+    const double *qd = x + m->nq;
+    double J[3 * OR_MAXNV];
+    for (int a = 0; a < 2; a++) {
+        const double *p = f.a1[a][na - 1];
+        memcpy(ee + 3 * a, p, 3 * sizeof(double));
+        point_jacobian_link(m, &f, a, na - 1, p, J);
+        for (int r = 0; r < 3; r++) {
+            double s = 0.0;
+            for (int j = 0; j < nv; j++) s += J[r * nv + j] * qd[j];
+            ee[6 + 3 * a + r] = s;
+        }
+        or_rot_to_quat(f.R[a][na - 1], ee + 12 + 4 * a);
+    }
+}
+
+/* Signed distances of the collision cost's pairs at state x: every link
+ * against every box (link-major), every link against the ball (pick phase
+ * only), every left link against every right link.  Returns the count. */
+int or_pair_distances(const or_model *m, const double *x, int phase, double *d) {
+    or_fk f;
+    or_forward_kinematics(m, x, &f);
+    int na = m->na, n = 0;
+    double tmp[3], tmp2[3];
+    for (int a = 0; a < 2; a++)
+        for (int i = 0; i < na; i++)
+            for (int b = 0; b < m->nb; b++)
+                or_capsule_box(f.a0[a][i], f.a1[a][i], m->L[a][i].rcap, m->bc[b], m->bh[b], &d[n++], tmp, tmp2, NULL);
+    if (phase == 0) {
+        const double *c = x + 2 * na;
+        for (int a = 0; a < 2; a++)
+            for (int i = 0; i < na; i++)
+                or_sphere_capsule(c, m->rb, f.a0[a][i], f.a1[a][i], m->L[a][i].rcap, &d[n++], tmp, tmp2);
+    }
+    for (int i = 0; i < na; i++)
+        for (int j = 0; j < na; j++)
+            or_capsule_capsule(f.a0[0][i], f.a1[0][i], m->L[0][i].rcap, f.a0[1][j], f.a1[1][j], m->L[1][j].rcap,
+                               &d[n++]);
+    return n;
+}
+
+static double qdist(const double *q, const double *qs) {
+    double c = fabs(q[0] * qs[0] + q[1] * qs[1] + q[2] * qs[2] + q[3] * qs[3]);
+    return 2.0 * acos(c > 1.0 ? 1.0 : c);
+}
+
+/* The task cost from per-state features of x_0..x_H: D ((H+1) x B pair
+ * distances), TH ((H+1) x nu joint positions), EE ((H+1) x 20 as
+ * or_ee_state writes).  Every state term sums over the states x_1..x_H that
+ * the H controls produce; the barrier sums over the H transitions
+ * x_k -> x_{k+1}, k = 0..H-1, and the penetration indicator over x_1..x_H.
+ * terms (optional, 8): C_c, C_theta, C_yz, C_v, C_r, C_l, C_eef_obj,
+ * C_obj_targ.  Returns the weighted total. */
+double or_task_cost_features(const double *task, int nu, int B, int H, const double *D, const double *TH,
+                             const double *EE, double *terms) {
+    const int phase = (int)task[0];
+    const double gamma = task[2];
+    double Cc = 0.0, Cth = 0.0, Cyz = 0.0, Cv2 = 0.0, Cr = 0.0, Cl = 0.0, Ceo = 0.0, Cot = 0.0;
+    for (int k = 0; k < H; k++)
+        for (int b = 0; b < B; b++) {
+            double g = -D[(size_t)(k + 1) * B + b] + (1.0 - gamma) * D[(size_t)k * B + b];
+            if (g > 0.0) Cc += g;
+        }
+    for (int k = 1; k <= H; k++) {
+        for (int b = 0; b < B; b++)
+            if (D[(size_t)k * B + b] < 0.0) Cc += 1.0;
+        const double *th = TH + (size_t)k * nu, *e = EE + (size_t)k * 20;
+        const double *p1 = e, *p2 = e + 3, *v1 = e + 6, *v2 = e + 9, *q1 = e + 12, *q2 = e + 16;
+        double s = 0.0;
+        for (int j = 0; j < nu; j++) s += (th[j] - task[OR_TASK_N + j]) * (th[j] - task[OR_TASK_N + j]);
+        Cth += sqrt(s);
+        Cyz += sqrt((p1[1] - p2[1]) * (p1[1] - p2[1]) + (p1[2] - p2[2]) * (p1[2] - p2[2]));
+        double dp[3], dv[3];
+        v3_sub(p1, p2, dp);
+        v3_sub(v1, v2, dv);
+        double rv = v3_dot(dp, dv);
+        Cv2 += rv * rv;
+        Cr += 0.5 * (qdist(q1, task + 18) + qdist(q2, task + 22));
+        double l = v3_norm(dp) - task[8];
+        Cl += l * l;
+        double c[3] = {0.5 * (p1[0] + p2[0]), 0.5 * (p1[1] + p2[1]), 0.5 * (p1[2] + p2[2])};
+        double eo[3] = {c[0] - task[12], c[1] - task[13], c[2] - (task[14] - task[11])};
+        Ceo += v3_norm(eo);
+        double ot[3] = {c[0] - task[15], c[1] - task[16], c[2] + task[11] - task[17]};
+        Cot += v3_norm(ot);
+    }
+    double Cv = sqrt(Cv2);
+    double wpick = phase == 0 ? 1.0 : 0.0, wmove = phase == 0 ? 0.0 : 1.0;
+    if (terms) {
+        terms[0] = Cc; terms[1] = Cth; terms[2] = Cyz; terms[3] = Cv;
+        terms[4] = Cr; terms[5] = Cl; terms[6] = Ceo; terms[7] = Cot;
+    }
+    return wpick * (task[1] * Cc + task[9] * Ceo) + wmove * (task[1] * Cc + task[10] * Cot) + task[3] * Cth +
+           task[4] * Cyz + task[5] * Cv + task[6] * Cr + task[7] * Cl;
+}
+
+/* Task cost of a trajectory x_0..x_H ((H+1) x nx). */
+double or_task_cost(const or_model *m, const double *task, const double *traj, int H, double *terms) {
+    int nx = m->nq + m->nv, nu = m->nu, phase = (int)task[0];
+    double *D = (double *)malloc(sizeof(double) * (size_t)(H + 1) * OR_MAXPAIRS);
+    double *TH = (double *)malloc(sizeof(double) * (size_t)(H + 1) * nu);
+    double *EE = (double *)malloc(sizeof(double) * (size_t)(H + 1) * 20);
+    int B = 0;
+    for (int k = 0; k <= H; k++) {
+        const double *x = traj + (size_t)k * nx;
+        double d[OR_MAXPAIRS];
+        B = or_pair_distances(m, x, phase, d);
+        for (int b = 0; b < B; b++) D[(size_t)k * B + b] = d[b];
+        memcpy(TH + (size_t)k * nu, x, sizeof(double) * nu);
+        or_ee_state(m, x, EE + (size_t)k * 20);
+    }
+    double c = or_task_cost_features(task, nu, B, H, D, TH, EE, terms);
+    free(D); free(TH); free(EE);
+    return c;
+}
+
+/* Roll out H steps from x with controls U and score the trajectory with
+ * the task cost (in place of the stage cost).  traj (optional) receives
+ * the H+1 states. */
+double or_rollout_task(const or_model *m, const double *task, const double *x, const double *U, int H,
+                       double *traj_out, double *terms) {
+    int nx = m->nq + m->nv;
+    double *traj = (double *)malloc(sizeof(double) * (size_t)(H + 1) * nx);
+    memcpy(traj, x, sizeof(double) * nx);
+    for (int h = 0; h < H; h++) {
+        or_step_info info;
+        if (or_step(m, traj + (size_t)h * nx, U + (size_t)h * m->nu, traj + (size_t)(h + 1) * nx, &info) != 0) {
+            free(traj);
+            return NAN;
+        }
+    }
+    double c = or_task_cost(m, task, traj, H, terms);
+    if (traj_out) memcpy(traj_out, traj, sizeof(double) * (size_t)(H + 1) * nx);
+    free(traj);
+    return c;
+}

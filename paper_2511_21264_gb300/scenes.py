@@ -478,3 +478,30 @@ def projection_bounds(scene: Scene, pos_margin: float = 1.0, vel: float = math.p
         b[j] = [q_home[j] - pos_margin, q_home[j] + pos_margin, max(ln.u_lo, -vel), min(ln.u_hi, vel),
                 -acc, acc, -jerk, jerk]
     return b
+
+
+TASK_N = 26  # task parameters before theta_home
+
+
+def ball_task(scene: Scene, phase: int = 0, w_c: float = 1.0, gamma: float = 0.2, w_theta: float = 0.1,
+              w_yz: float = 1.0, w_v: float = 1.0, w_r: float = 0.2, w_l: float = 5.0, w_eef_obj: float = 5.0,
+              w_obj_targ: float = 5.0, eps: float = 0.02, l_ball: Optional[float] = None) -> np.ndarray:
+    """Parameters of the ball-task cost suite (Sec. IV-B) as the flat array
+    the library and the oracle read: phase (0 pick, 1 move), weights, the
+    barrier rate gamma, the EE distance l_ball, the vertical offset eps, the
+    ball position before the pick (the scene's start), the target (the
+    scene's goal), the target EE orientations and theta_home (the scene's
+    home pose).  The paper tunes its weights by hand and prints none; these
+    defaults weight each term to the same order of magnitude on the scenes
+    here.  Target orientations: the last link frames turned +-90 degrees
+    about the world y axis (fixed constants, w first)."""
+    r = scene.ball_r
+    lb = 1.8 * r if l_ball is None else l_ball  # contact points 0.9 of a diameter apart
+    c = math.cos(math.pi / 4)
+    v = [float(phase), w_c, gamma, w_theta, w_yz, w_v, w_r, w_l, lb, w_eef_obj, w_obj_targ, eps]
+    v += list(scene.x0[scene.nu:scene.nu + 3])        # ball position before the pick
+    v += list(scene.goal)                              # target
+    v += [c, 0.0, c, 0.0, c, 0.0, -c, 0.0]             # q1*, q2*
+    v += list(scene.x0[:scene.nu])                     # theta_home
+    assert len(v) == TASK_N + scene.nu
+    return np.array(v, dtype=np.float64)
