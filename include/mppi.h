@@ -218,6 +218,36 @@ int mppi_set_projection(mppi_ctx *c, const float *bounds, int iters, float rho, 
  * clamped samples.  Needs the sample buffer. */
 int mppi_get_samples(mppi_ctx *c, float *U, void *stream);
 
+/* --------------------------------------------------- ball-task cost suite */
+/* The paper's cost for lifting and transporting the ball (Sec. IV-B), in
+ * place of the scene's stage cost for every rollout of the handle
+ * (mppi_step, mppi_solve, rollout_batch):
+ *   C = w_pick (w_c C_c + w_eo C_eef-obj) + w_move (w_c C_c + w_ot C_obj-targ)
+ *       + w_theta C_theta + w_yz C_yz + w_v C_v + w_r C_r + w_l C_l,
+ * w_pick = 1, w_move = 0 in the pick phase and the reverse in the move
+ * phase.  With x_0 the present state and x_1..x_H the states the controls
+ * produce, p_i the distal end of arm i's last capsule, q_i its last link
+ * frame as a quaternion and c = (p_1 + p_2)/2:
+ *   C_c       = sum over the H transitions and every pair b of
+ *               max(-d_{k+1,b} + (1 - gamma) d_{k,b}, 0)  +  the number of
+ *               (state k >= 1, pair) with d_{k,b} < 0; pairs: every link x
+ *               every box, every link x the ball (pick phase only), every
+ *               left link x every right link (signed distances)
+ *   C_theta   = sum_k |theta_k - theta_home|
+ *   C_yz      = sum_k |(p_1 - p_2) in y and z|
+ *   C_v       = sqrt(sum_k ((p_1 - p_2) . (pdot_1 - pdot_2))^2)
+ *   C_r       = sum_k (acos|<q_1, q_1*>| + acos|<q_2, q_2*>|)
+ *   C_l       = sum_k (|p_1 - p_2| - l_ball)^2
+ *   C_eef-obj = sum_k |c - (p_ball0 - (0, 0, eps))|
+ *   C_obj-targ= sum_k |c + (0, 0, eps) - p_target|
+ * params (HOST, MPPI_TASK_N + nu floats): [0] phase (0 pick, 1 move),
+ * [1] w_c, [2] gamma in [0, 1), [3] w_theta, [4] w_yz, [5] w_v, [6] w_r,
+ * [7] w_l, [8] l_ball, [9] w_eo, [10] w_ot, [11] eps, [12..14] p_ball0,
+ * [15..17] p_target, [18..21] q_1*, [22..25] q_2* (unit, w first),
+ * [26..26+nu) theta_home.  params = NULL turns the suite off. */
+#define MPPI_TASK_N 26
+int mppi_set_task_cost(mppi_ctx *c, const float *params, int n);
+
 /* Launch shape: samples (warps) per CTA for the rollout kernels, 1..16
  * (0 = the library default).  Used by the autotuner. */
 int mppi_set_launch(mppi_ctx *c, int samples_per_cta);

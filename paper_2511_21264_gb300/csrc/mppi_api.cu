@@ -24,6 +24,7 @@
 #include "mppi_device.cuh"
 #include "mppi_internal.h"
 #include "mppi_kernels.cuh"
+#include "mppi_task.cuh"
 
 using namespace mppi;
 
@@ -32,16 +33,23 @@ using namespace mppi;
 // ---------------------------------------------------------------------------
 namespace mppi {
 
-template <int NA, int MODE>
+template <int NA, int MODE, bool TASK>
 __global__ void __launch_bounds__(512) rollout_kernel(RolloutArgs args) {
     using d = Dims<NA>;
     extern __shared__ __align__(16) unsigned char smem[];
     DevModel& M = *reinterpret_cast<DevModel*>(smem);
-    float* unom_s = reinterpret_cast<float*>(smem + sizeof(DevModel));
+    constexpr size_t task_b = TASK ? sizeof(DevTask) : 0;
+    DevTask* task_s = reinterpret_cast<DevTask*>(smem + sizeof(DevModel));
+    float* unom_s = reinterpret_cast<float*>(smem + sizeof(DevModel) + task_b);
     const int unom_n = (MODE == 1 && args.stage_unom) ? args.H * d::NU : 0;
-    const size_t ws_off = sizeof(DevModel) + ((size_t)unom_n * sizeof(float) + 15) / 16 * 16;
+    const size_t ws_off = sizeof(DevModel) + task_b + ((size_t)unom_n * sizeof(float) + 15) / 16 * 16;
     WarpWS<NA>* wsb = reinterpret_cast<WarpWS<NA>*>(smem + ws_off);
     stage_model(smem, args.model, unom_s, args.u_nom, unom_n);
+    if constexpr (TASK) {
+        const float4* src = reinterpret_cast<const float4*>(args.task);
+        float4* dst = reinterpret_cast<float4*>(task_s);
+        for (int t = threadIdx.x; t < (int)(sizeof(DevTask) / 16); t += blockDim.x) dst[t] = src[t];
+    }
     __syncthreads();
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -53,6 +61,7 @@ __global__ void __launch_bounds__(512) rollout_kernel(RolloutArgs args) {
     io.H = args.H;
     io.err = args.err;
     io.stats = args.stats;
+    io.task = TASK ? task_s : nullptr;
     io.x_out = args.states_out ? args.states_out + (size_t)k * d::NX : nullptr;
     io.U_store = MODE == 1 ? args.U_store : nullptr;
     io.Kn = args.n;
@@ -75,7 +84,7 @@ __global__ void __launch_bounds__(512) rollout_kernel(RolloutArgs args) {
             io.u_stride = d::NU;
         }
     }
-    const float cost = rollout_sample<NA, MODE>(M, wsb[warp], lane, io);
+    const float cost = rollout_sample<NA, MODE, TASK>(M, wsb[warp], lane, io);
     if (lane == 0) args.costs[k] = cost;
 }
 
@@ -180,16 +189,17 @@ int cuda_fail(cudaError_t e) {
 }
 
 template <int NA>
-size_t rollout_smem(int spc, int unom_floats) {
-    return sizeof(DevModel) + ((size_t)unom_floats * sizeof(float) + 15) / 16 * 16 + (size_t)spc * sizeof(WarpWS<NA>);
+size_t rollout_smem(int spc, int unom_floats, bool task = false) {
+    return sizeof(DevModel) + (task ? sizeof(DevTask) : 0) + ((size_t)unom_floats * sizeof(float) + 15) / 16 * 16 +
+           (size_t)spc * sizeof(WarpWS<NA>);
 }
 
-template <int NA, int MODE>
+template <int NA, int MODE, bool TASK>
 int launch_rollout_t(const RolloutArgs& a, int spc, cudaStream_t s) {
     const int unom = (MODE == 1 && a.stage_unom) ? a.H * Dims<NA>::NU : 0;
-    const size_t sm = rollout_smem<NA>(spc, unom);
+    const size_t sm = rollout_smem<NA>(spc, unom, TASK);
     static int max_set[17] = {0};
-    auto fn = rollout_kernel<NA, MODE>;
+    auto fn = rollout_kernel<NA, MODE, TASK>;
     if (sm > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return cuda_fail(e);
@@ -206,8 +216,13 @@ namespace mppi {
 
 int launch_rollout(int na, int mode, const RolloutArgs& a, int spc, cudaStream_t s) {
     if (a.n <= 0) return MPPI_OK;
-    if (na == 3) return mode ? launch_rollout_t<3, 1>(a, spc, s) : launch_rollout_t<3, 0>(a, spc, s);
-    if (na == 7) return mode ? launch_rollout_t<7, 1>(a, spc, s) : launch_rollout_t<7, 0>(a, spc, s);
+    if (a.task) {
+        if (na == 3) return mode ? launch_rollout_t<3, 1, true>(a, spc, s) : launch_rollout_t<3, 0, true>(a, spc, s);
+        if (na == 7) return mode ? launch_rollout_t<7, 1, true>(a, spc, s) : launch_rollout_t<7, 0, true>(a, spc, s);
+        return MPPI_ERR_UNSUPPORTED;
+    }
+    if (na == 3) return mode ? launch_rollout_t<3, 1, false>(a, spc, s) : launch_rollout_t<3, 0, false>(a, spc, s);
+    if (na == 7) return mode ? launch_rollout_t<7, 1, false>(a, spc, s) : launch_rollout_t<7, 0, false>(a, spc, s);
     return MPPI_ERR_UNSUPPORTED;
 }
 
@@ -366,6 +381,9 @@ struct mppi_ctx {
     float qp_dt = 0.0f;
     void* d_qp = nullptr;  // nu QPClass records, then per joint the inverse (H <= 32) or 2H band rows
     size_t qp_bytes = 0;
+    // ball-task cost suite (Sec. IV-B)
+    DevTask* d_task = nullptr;
+    int task_on = 0;
 };
 
 namespace mppi {
@@ -448,6 +466,7 @@ int mppi_destroy(mppi_ctx* c) {
     cudaFree(c->d_sel);
     cudaFree(c->d_eidx);
     cudaFree(c->d_qp);
+    cudaFree(c->d_task);
     cudaFree(c->d_bestU);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->graph) cudaGraphDestroy(c->graph);
@@ -696,6 +715,7 @@ static RolloutArgs philox_args(mppi_ctx* c, const float* state, const float* u_n
     a.stage_unom = c->H * 2 * c->m->info.na <= 2048;
     a.U_store = c->d_U;
     a.Lfac = c->cov_sampling ? c->d_L : nullptr;
+    a.task = c->task_on ? c->d_task : nullptr;
     return a;
 }
 
@@ -783,6 +803,55 @@ int mppi_set_projection(mppi_ctx* c, const float* bounds, int iters, float rho, 
     c->qp_iters = iters;
     c->qp_dt = dt;
     drop_graph(c);  // a captured solve holds the old launches
+    return MPPI_OK;
+}
+
+int mppi_set_task_cost(mppi_ctx* c, const float* p, int n) {
+    if (!c) return MPPI_ERR_INVALID_ARG;
+    if (!p) {
+        if (c->task_on) drop_graph(c);
+        c->task_on = 0;
+        return MPPI_OK;
+    }
+    const int nu = 2 * c->m->info.na;
+    if (n != MPPI_TASK_N + nu) return MPPI_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return MPPI_ERR_INVALID_ARG;
+    if (!(p[0] == 0.0f || p[0] == 1.0f) || !(p[2] >= 0.0f && p[2] < 1.0f) || !(p[8] >= 0.0f)) return MPPI_ERR_INVALID_ARG;
+    for (int q = 18; q <= 22; q += 4) {
+        const float nn = p[q] * p[q] + p[q + 1] * p[q + 1] + p[q + 2] * p[q + 2] + p[q + 3] * p[q + 3];
+        if (std::fabs(nn - 1.0f) > 1e-3f) return MPPI_ERR_INVALID_ARG;
+    }
+    DevTask t{};
+    t.phase = (int)p[0];
+    t.w_c = p[1];
+    t.gamma = p[2];
+    t.w_theta = p[3];
+    t.w_yz = p[4];
+    t.w_v = p[5];
+    t.w_r = p[6];
+    t.w_l = p[7];
+    t.l_ball = p[8];
+    t.w_eo = p[9];
+    t.w_ot = p[10];
+    t.eps = p[11];
+    for (int k = 0; k < 3; ++k) {
+        t.pb0[k] = p[12 + k];
+        t.ptg[k] = p[15 + k];
+    }
+    for (int k = 0; k < 4; ++k) {
+        t.q1s[k] = p[18 + k];
+        t.q2s[k] = p[22 + k];
+    }
+    for (int j = 0; j < nu; ++j) t.home[j] = p[MPPI_TASK_N + j];
+    if (!c->d_task) {
+        cudaError_t e = cudaMalloc(&c->d_task, sizeof(DevTask));
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    cudaError_t e = cudaMemcpy(c->d_task, &t, sizeof t, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e);
+    c->task_on = 1;
+    drop_graph(c);
     return MPPI_OK;
 }
 
@@ -970,6 +1039,7 @@ int rollout_batch(mppi_ctx* c, int n, const float* states, const float* U, float
     a.costs = costs;
     a.states_out = states_out;
     a.err = c->d_err;
+    a.task = c->task_on ? c->d_task : nullptr;
     return launch_rollout(c->m->info.na, 0, a, c->spc, (cudaStream_t)stream);
 }
 

@@ -100,6 +100,7 @@ struct __align__(16) WarpWS {
     int nact;
     float pen_all;
     float pen_box;
+    float ee[2][10];  // task cost: end-effector position, velocity, quaternion per arm
     union Phase {
         struct {
             short surv[2 * MAXL * MAXB];  // capsule-box pairs that pass the cull

@@ -24,6 +24,7 @@ constexpr int ERRB_CHOLESKY = 2;
 constexpr int ERRB_TIMEOUT = 4;
 
 struct DevModel;
+struct DevTask;
 
 struct HostModelInfo {
     int na = 0, nb = 0;
@@ -51,6 +52,7 @@ struct RolloutArgs {
     float* U_store;              // optional: sampled controls, H x n x nu (h-major), MODE 1
     int U_hmajor;                // MODE 0: U is H x n x nu (h-major) instead of n x H x nu
     const float* Lfac;           // optional: covariance factors H x nu x nu (MODE 1), else diagonal sigma
+    const DevTask* task;         // optional: the ball-task cost suite replaces the stage cost
 };
 
 // Arguments of the weighted-mean update (one CTA per horizon step).

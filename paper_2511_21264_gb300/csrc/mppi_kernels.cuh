@@ -3,6 +3,7 @@
 #pragma once
 #include "mppi_device.cuh"
 #include "mppi_internal.h"
+#include "mppi_task.cuh"
 
 namespace mppi {
 
@@ -22,6 +23,7 @@ struct SampleIO {
     const float* Lfac;         // optional: H x nu x nu factors of the sampling covariance blocks
     int* err;                  // error word
     unsigned long long* stats; // optional [sample-steps, contacts, exact box tests]
+    const DevTask* task;       // ball-task cost suite (TASK rollouts), in place of the stage cost
 };
 
 // Copy the scene model (and optionally u_nom) into shared memory.
@@ -33,9 +35,10 @@ __device__ __forceinline__ void stage_model(unsigned char* smem, const DevModel*
     for (int t = threadIdx.x; t < unom_n; t += blockDim.x) unom_s[t] = u_nom[t];
 }
 
-// H simulator steps of one sample with its stage costs; the warp's state
-// stays in shared memory throughout.  Returns the summed cost on every lane.
-template <int NA, int MODE>
+// H simulator steps of one sample with its stage costs (TASK: the ball-task
+// cost suite instead); the warp's state stays in shared memory throughout.
+// Returns the summed cost on every lane.
+template <int NA, int MODE, bool TASK = false>
 __device__ __forceinline__ float rollout_sample(const DevModel& M, WarpWS<NA>& w, int lane, const SampleIO& io) {
     using d = Dims<NA>;
     const int k = io.k;
@@ -45,6 +48,12 @@ __device__ __forceinline__ float rollout_sample(const DevModel& M, WarpWS<NA>& w
     float cost = 0.0f;
     const float* gb = M.goal;
     unsigned n_exact = 0, n_con = 0;
+    TaskAcc<NA> tacc;
+    if constexpr (TASK) {
+#pragma unroll
+        for (int s = 0; s < TaskDims<NA>::SLOTS; ++s) tacc.prev[s] = 0.0f;
+        tacc.c = tacc.th = tacc.yz = tacc.v2 = tacc.r = tacc.l = tacc.eo = tacc.ot = 0.0f;
+    }
     for (int h = 0; h < io.H; ++h) {
         if (MODE == 1) {
             // every 8 steps the 32 lanes draw one Philox block each: 8 steps x
@@ -76,14 +85,18 @@ __device__ __forceinline__ float rollout_sample(const DevModel& M, WarpWS<NA>& w
         float Rl[9], cl[3];  // this lane's link rotation and COM, kept for the dynamics
         forward_kinematics<NA>(M, w, lane, Rl, cl);
         __syncwarp();
-        if (h > 0 && lane == 0 && M.w_grasp != 0.0f) cost += M.w_grasp * grasp_term<NA>(w);
+        if constexpr (TASK) {
+            task_state<NA>(M, *io.task, w, lane, Rl, h == 0, tacc);
+        } else {
+            if (h > 0 && lane == 0 && M.w_grasp != 0.0f) cost += M.w_grasp * grasp_term<NA>(w);
+        }
         n_exact += collide<NA>(M, w, lane);
         __syncwarp();
         n_con += w.ncon;
         dynamics<NA>(M, w, lane, io.err, Rl, cl);
         contacts<NA>(M, w, lane);
         integrate<NA>(M, w, lane);
-        if (lane == 0) {
+        if (!TASK && lane == 0) {
             const float* pb = &w.q[d::B];
             const float e0 = pb[0] - gb[0], e1 = pb[1] - gb[1], e2 = pb[2] - gb[2];
             float uu = 0.0f;
@@ -94,7 +107,13 @@ __device__ __forceinline__ float rollout_sample(const DevModel& M, WarpWS<NA>& w
         }
         __syncwarp();
     }
-    if (M.w_grasp != 0.0f) {
+    if constexpr (TASK) {
+        float Rl[9], cl[3];
+        forward_kinematics<NA>(M, w, lane, Rl, cl);
+        __syncwarp();
+        task_state<NA>(M, *io.task, w, lane, Rl, false, tacc);
+        cost = task_total<NA>(*io.task, tacc);
+    } else if (M.w_grasp != 0.0f) {
         float Rl[9], cl[3];
         forward_kinematics<NA>(M, w, lane, Rl, cl);
         __syncwarp();

@@ -77,3 +77,19 @@ def qp_flops(H: int, iters: int) -> float:
     FMA = 2, min/max = 1 each.  The start point (prefix sums, B^T vt) adds
     3 per step; sampling is not counted."""
     return float(iters) * 59.0 * H + 3.0 * H
+
+
+def task_flops(scene, phase: int) -> float:
+    """Algorithmic FP32 operations of the ball-task cost suite (Sec. IV-B)
+    per state: every collision pair's signed distance -- capsule-box over
+    its 43 candidate minimisers (about 12 for the candidate's parameter and
+    22 for the box distance at it: 34 each), sphere-capsule 25,
+    capsule-capsule 90 -- plus 4 for the barrier per pair, the end effectors'
+    velocities (6 per joint) and quaternions (25 each), and the per-state
+    terms (about 80)."""
+    na, nb = scene.n_a, scene.n_boxes
+    pairs_box = 2 * na * nb
+    pairs_ball = 2 * na if phase == 0 else 0
+    pairs_arm = na * na
+    dist = pairs_box * 43 * 34 + pairs_ball * 25 + pairs_arm * 90
+    return float(dist + 4 * (pairs_box + pairs_ball + pairs_arm) + 2 * na * 6 + 2 * 25 + 80)

@@ -150,6 +150,7 @@ def lib():
     _decl(L, "mppi_qp_project", i, [i, i, C.c_float, fp, i, C.c_float, fp, fp, fp, fp, fp, vp])
     _decl(L, "mppi_set_projection", i, [vp, fp, i, C.c_float, fp])
     _decl(L, "mppi_get_samples", i, [vp, fp, vp])
+    _decl(L, "mppi_set_task_cost", i, [vp, fp, i])
     _lib = L
     return L
 
@@ -518,6 +519,16 @@ class Controller:
         sc = None if scales is None else _host_f32(scales, 4)
         _check(lib().mppi_set_projection(self._h, b.ctypes.data, int(iters), float(rho),
                                          None if sc is None else sc.ctypes.data), "mppi_set_projection")
+
+    def set_task_cost(self, params=None):
+        """The paper's ball-task cost suite (Sec. IV-B) in place of the
+        scene's stage cost: params is the MPPI_TASK_N + nu array that
+        scenes.ball_task builds; None turns it off."""
+        if params is None:
+            _check(lib().mppi_set_task_cost(self._h, None, 0), "mppi_set_task_cost")
+            return
+        p = _host_f32(params)
+        _check(lib().mppi_set_task_cost(self._h, p.ctypes.data, int(p.size)), "mppi_set_task_cost")
 
     def samples(self, out, stream=None):
         """The last iteration's samples as rolled out (H x K x nu)."""
