@@ -501,17 +501,81 @@ def run_serve(args):
     return 0
 
 
+def run_closed_loop(args):
+    """Closed-loop receding horizon as the paper evaluates it (Sec. IV-A):
+    N_runs = args.runs episodes of the planar ball lift with randomised
+    goals (ball start + (U(-0.1, 0.1), 0, U(0.15, 0.3)) m), K = args.k
+    samples, H = 16, M = 10 iterations per planning step, the first 4 steps
+    of the best sequence averaged and executed, 8 s of simulated time per
+    run.  Reports the success rate, task time (mean and standard deviation
+    over successful runs) and planning compute time (mean and standard
+    deviation over every planning step)."""
+    import numpy as np
+    import torch
+    from paper_2511_21264_gb300 import native
+    rank, world, local = _dist_setup(args.gpus)
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    native.build() if rank == 0 and world == 1 else None
+    native.lib()
+    rng = np.random.default_rng(1000 + rank)
+    K, H, M, n_avg, max_steps = args.k, 16, 10, 4, 800
+    results = []
+    stream = torch.cuda.Stream(device=dev)
+    with ClockSampler(local) as clk:
+        for run in range(args.runs):
+            sc = scenes.config(1, seed=run)
+            start = np.array(sc.x0[sc.nu:sc.nu + 3])
+            sc.goal = tuple(start + np.array([rng.uniform(-0.1, 0.1), 0.0, rng.uniform(0.15, 0.3)]))
+            m = native.Model(sc.to_blob())
+            ctl = native.Controller(m, K, H, sc.lam, sc.sigma_vec(), scenes.controller_key(run, rank))
+            u = torch.zeros((H, sc.nu), device=dev)
+            with torch.cuda.stream(stream):
+                ep = ctl.run_episode(sc.x0, u, iters=M, n_avg=n_avg, max_steps=max_steps, goal_tol=0.03,
+                                     lift_dz=0.05, drop_dz=0.05, record=True, stream=stream)
+            results.append(ep)
+            ctl.close()
+            m.close()
+    if rank != 0:
+        return 0
+    ok = [r for r in results if r["outcome_name"] == "success"]
+    comp = np.concatenate([r["comp_ms"] for r in results])
+    tt = np.array([r["task_time_s"] for r in ok]) if ok else np.zeros(0)
+    outcomes = {}
+    for r in results:
+        outcomes[r["outcome_name"]] = outcomes.get(r["outcome_name"], 0) + 1
+    line = {
+        "metric": "closed-loop success rate (%) of the planar ball lift, receding horizon (Sec. IV-A metrics)",
+        "value": 100.0 * len(ok) / len(results), "unit": "%", "n_gpus": world, "steps": None, "warmup": 0,
+        "ms_per_step": float(comp.mean()), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"planar 3-link bimanual ball lift, {args.runs} runs with randomised goals, K={K}, "
+                               f"H={H}, M={M} iterations per plan, first {n_avg} steps averaged and executed, "
+                               f"{max_steps} world steps ({max_steps * 0.01:g} s) per run"},
+        "task_time_s": {"mean": float(tt.mean()) if tt.size else None, "std": float(tt.std()) if tt.size else None,
+                        "n_success": len(ok)},
+        "comp_time_ms": {"mean": float(comp.mean()), "std": float(comp.std()), "n_plans": int(comp.size)},
+        "outcomes": outcomes,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=("lift", "transfer", "batched", "serve"), default="lift",
+    ap.add_argument("--workload", choices=("lift", "transfer", "batched", "serve", "closed_loop"), default="lift",
                     help="lift: 7-DoF ball lift K=1024 H=32 (default); transfer: 8-box transfer K=4096 "
                          "H=64; batched: 64 instances (K 256..4096, H 16..64, 0..16 boxes) in one "
                          "persistent launch vs 64 sequential plain launches; serve: Poisson replan "
-                         "requests over 256 scenes, batched server vs one-at-a-time server")
+                         "requests over 256 scenes, batched server vs one-at-a-time server; closed_loop: "
+                         "receding-horizon episodes with the paper's success / task-time / compute-time metrics")
+    ap.add_argument("--runs", type=int, default=20, help="closed_loop: episodes (the paper's N_runs = 20)")
+    ap.add_argument("--k", type=int, default=1024, help="closed_loop: samples per iteration")
     ap.add_argument("--elite", type=int, default=0, help="elite set size (0 = all samples: the plain update)")
     ap.add_argument("--eta", type=float, default=1.0, help="learning rate of Eq. 8 (elite mode)")
     ap.add_argument("--cov", action="store_true", help="update the per-step covariance blocks (Eq. 8b/8c)")
@@ -534,6 +598,8 @@ def main(argv=None):
         return run_batched(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "closed_loop":
+        return run_closed_loop(args)
     return run_ours(args)
 
 

@@ -248,6 +248,54 @@ int mppi_get_samples(mppi_ctx *c, float *U, void *stream);
 #define MPPI_TASK_N 26
 int mppi_set_task_cost(mppi_ctx *c, const float *params, int n);
 
+/* ------------------------------------------------ closed-loop episodes */
+/* Receding-horizon control as the paper runs it (Sec. III-A, Alg. 1 and
+ * the text after Eq. 8; metrics of Sec. IV-A): the simulator itself stands
+ * in for the robot ("world").  Each planning step
+ *   1. runs cfg->iters optimiser iterations (mppi_solve) from the world
+ *      state on the warm-started nominal sequence;
+ *   2. takes the lowest-cost sequence of the last iteration (the elite
+ *      update's best sequence, or the lowest-cost sample of the plain
+ *      update) and averages its first cfg->n_avg steps;
+ *   3. applies that average for cfg->n_avg world steps;
+ *   4. shifts the nominal sequence (and the covariance blocks, when the
+ *      full Eq. 8 update is on) by cfg->n_avg steps, repeating the last.
+ * After every world step the state is checked: success when the ball
+ * centre is within cfg->goal_tol of the goal (the task's target when the
+ * ball-task cost suite is on, else the scene's goal); failure on a
+ * collision (a link penetrating a box or a link of the other arm), on the
+ * ball falling (its centre more than cfg->drop_dz below the highest point
+ * it reached once it was cfg->lift_dz above its start) or on reaching
+ * cfg->max_steps world steps.  With the task suite on and cfg->pick_tol > 0
+ * the pick phase switches to the move phase once the end effectors'
+ * midpoint is within pick_tol of the pick point.  Synchronises the stream
+ * at every planning step. */
+typedef struct {
+    int iters;       /* optimiser iterations per planning step, >= 1 */
+    int n_avg;       /* steps averaged and executed per planning step, 1..H */
+    int max_steps;   /* world steps before a timeout, >= 1 */
+    float goal_tol;  /* m */
+    float lift_dz;   /* m */
+    float drop_dz;   /* m */
+    float pick_tol;  /* m; 0 = never switch */
+} mppi_episode_config;
+enum { MPPI_EP_SUCCESS = 0, MPPI_EP_TIMEOUT = 1, MPPI_EP_COLLISION = 2, MPPI_EP_DROPPED = 3 };
+typedef struct {
+    int outcome;           /* MPPI_EP_* */
+    int plans;             /* planning steps (N_steps) */
+    int steps;             /* world steps executed */
+    int switch_step;       /* world step of the pick -> move switch, -1 if none */
+    double task_time_s;    /* steps x dt */
+    double comp_mean_ms;   /* mean and standard deviation of the planning */
+    double comp_std_ms;    /* steps' compute time (steps 1-2, CUDA events) */
+} mppi_episode_result;
+/* x0: HOST, nx floats (the world's start).  u_nom: device, H x nu, the
+ * warm start on entry, the last nominal sequence on return.  Optional HOST
+ * outputs: traj ((max_steps + 1) x nx world states), u_exec (max_steps x nu
+ * executed controls), comp_ms (per planning step, up to max_steps). */
+int mppi_run_episode(mppi_ctx *c, const float *x0, float *u_nom, const mppi_episode_config *cfg, float *traj,
+                     float *u_exec, float *comp_ms, mppi_episode_result *res, void *stream);
+
 /* Launch shape: samples (warps) per CTA for the rollout kernels, 1..16
  * (0 = the library default).  Used by the autotuner. */
 int mppi_set_launch(mppi_ctx *c, int samples_per_cta);

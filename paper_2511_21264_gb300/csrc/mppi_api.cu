@@ -1112,3 +1112,136 @@ int mppi_sync(mppi_ctx* c, void* stream) {
 }
 
 }  // extern "C"
+
+int mppi_run_episode(mppi_ctx* c, const float* x0, float* u, const mppi_episode_config* cfg, float* traj,
+                     float* u_exec, float* comp_ms, mppi_episode_result* res, void* stream) {
+    if (!c || !x0 || !u || !cfg || !res) return MPPI_ERR_INVALID_ARG;
+    if (cfg->iters < 1 || cfg->n_avg < 1 || cfg->n_avg > c->H || cfg->max_steps < 1 || !(cfg->goal_tol > 0.0f) ||
+        !(cfg->lift_dz >= 0.0f) || !(cfg->drop_dz > 0.0f) || !(cfg->pick_tol >= 0.0f))
+        return MPPI_ERR_INVALID_ARG;
+    const bool elite = elite_mode(c);
+    if (!elite && !c->d_U) return MPPI_ERR_UNSUPPORTED;  // the best sample is read from the sample buffer
+    NvtxRange r("mppi_run_episode");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int na = c->m->info.na, nu = 2 * na, nq = 2 * na + 7, nx = nq + 2 * na + 6;
+    float* d_world = nullptr;  // world state (nx), executed control (nu), probe (8)
+    cudaError_t e = cudaMalloc(&d_world, (size_t)(nx + nu + 8) * sizeof(float));
+    if (e != cudaSuccess) return cuda_fail(e);
+    float* d_u1 = d_world + nx;
+    float* d_probe = d_u1 + nu;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    cudaEventCreate(&ev[0]);
+    cudaEventCreate(&ev[1]);
+    int rc = cuda_fail(cudaMemcpyAsync(d_world, x0, (size_t)nx * sizeof(float), cudaMemcpyHostToDevice, s));
+    DevTask task{};
+    bool switching = false;
+    float goal[3] = {c->m->host.goal[0], c->m->host.goal[1], c->m->host.goal[2]};
+    if (rc == MPPI_OK && c->task_on) {
+        rc = cuda_fail(cudaMemcpy(&task, c->d_task, sizeof task, cudaMemcpyDeviceToHost));
+        for (int k = 0; k < 3; ++k) goal[k] = task.ptg[k];
+        switching = task.phase == 0 && cfg->pick_tol > 0.0f;
+    }
+    if (traj) std::memcpy(traj, x0, (size_t)nx * sizeof(float));
+    mppi_episode_result out{};
+    out.outcome = MPPI_EP_TIMEOUT;
+    out.switch_step = -1;
+    const float z0 = x0[2 * na + 2];
+    float zmax = z0;
+    bool lifted = false;
+    float arm0 = 0.0f;  // left-right link distance at the start: arms already crossing are exempt
+    double sum = 0.0, sum2 = 0.0;
+    float probe[8];
+    if (rc == MPPI_OK) rc = launch_probe(na, c->m->dev, d_world, d_probe, s);
+    if (rc == MPPI_OK) rc = cuda_fail(cudaMemcpyAsync(probe, d_probe, sizeof probe, cudaMemcpyDeviceToHost, s));
+    if (rc == MPPI_OK) rc = cuda_fail(cudaStreamSynchronize(s));
+    arm0 = probe[1];
+    bool done = false;
+    while (rc == MPPI_OK && !done && out.steps < cfg->max_steps) {
+        cudaEventRecord(ev[0], s);
+        rc = mppi_solve(c, d_world, u, cfg->iters, c->d_best, s);
+        if (rc == MPPI_OK)
+            rc = launch_best_average(c->d_U, c->d_best, elite ? c->d_bestU : nullptr, c->K, nu, cfg->n_avg, d_u1, s);
+        cudaEventRecord(ev[1], s);
+        if (rc != MPPI_OK) break;
+        for (int i = 0; i < cfg->n_avg && out.steps < cfg->max_steps && rc == MPPI_OK; ++i) {
+            rc = sim_step(c, 1, d_world, d_u1, s);
+            if (rc == MPPI_OK) rc = launch_probe(na, c->m->dev, d_world, d_probe, s);
+            if (rc == MPPI_OK) rc = cuda_fail(cudaMemcpyAsync(probe, d_probe, sizeof probe, cudaMemcpyDeviceToHost, s));
+            if (rc == MPPI_OK && (traj || u_exec)) {
+                if (traj)
+                    rc = cuda_fail(cudaMemcpyAsync(traj + (size_t)(out.steps + 1) * nx, d_world, (size_t)nx * sizeof(float),
+                                                   cudaMemcpyDeviceToHost, s));
+                if (rc == MPPI_OK && u_exec)
+                    rc = cuda_fail(cudaMemcpyAsync(u_exec + (size_t)out.steps * nu, d_u1, (size_t)nu * sizeof(float),
+                                                   cudaMemcpyDeviceToHost, s));
+            }
+            if (rc == MPPI_OK) rc = cuda_fail(cudaStreamSynchronize(s));
+            if (rc != MPPI_OK) break;
+            ++out.steps;
+            const float bz = probe[4];
+            if (!lifted && bz > z0 + cfg->lift_dz) lifted = true;
+            zmax = fmaxf(zmax, bz);
+            const float g0 = probe[2] - goal[0], g1 = probe[3] - goal[1], g2 = probe[4] - goal[2];
+            if (probe[0] < 0.0f || (arm0 >= 0.0f && probe[1] < 0.0f)) {
+                out.outcome = MPPI_EP_COLLISION;
+                done = true;
+            } else if (std::sqrt(g0 * g0 + g1 * g1 + g2 * g2) < cfg->goal_tol) {
+                out.outcome = MPPI_EP_SUCCESS;
+                done = true;
+            } else if (lifted && bz < zmax - cfg->drop_dz) {
+                out.outcome = MPPI_EP_DROPPED;
+                done = true;
+            }
+            if (done) break;
+            if (switching) {  // pick -> move once the end effectors reach the pick point
+                const float m0 = probe[5] - task.pb0[0], m1 = probe[6] - task.pb0[1],
+                            m2 = probe[7] - (task.pb0[2] - task.eps);
+                if (std::sqrt(m0 * m0 + m1 * m1 + m2 * m2) < cfg->pick_tol) {
+                    std::vector<float> p(MPPI_TASK_N + nu);
+                    p[0] = 1.0f;
+                    p[1] = task.w_c; p[2] = task.gamma; p[3] = task.w_theta; p[4] = task.w_yz; p[5] = task.w_v;
+                    p[6] = task.w_r; p[7] = task.w_l; p[8] = task.l_ball; p[9] = task.w_eo; p[10] = task.w_ot;
+                    p[11] = task.eps;
+                    for (int k = 0; k < 3; ++k) {
+                        p[12 + k] = task.pb0[k];
+                        p[15 + k] = task.ptg[k];
+                    }
+                    for (int k = 0; k < 4; ++k) {
+                        p[18 + k] = task.q1s[k];
+                        p[22 + k] = task.q2s[k];
+                    }
+                    for (int j = 0; j < nu; ++j) p[MPPI_TASK_N + j] = task.home[j];
+                    rc = mppi_set_task_cost(c, p.data(), (int)p.size());
+                    switching = false;
+                    out.switch_step = out.steps;
+                }
+            }
+        }
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, ev[0], ev[1]) == cudaSuccess) {
+            if (comp_ms && out.plans < cfg->max_steps) comp_ms[out.plans] = ms;
+            sum += ms;
+            sum2 += (double)ms * ms;
+        }
+        ++out.plans;
+        if (done || rc != MPPI_OK) break;
+        // warm start: shift the nominal sequence and the covariance blocks
+        rc = launch_shift_rows(u, c->H, nu, cfg->n_avg, s);
+        if (rc == MPPI_OK && c->update_cov) {
+            rc = launch_shift_rows(c->d_Sigma, c->H, nu * nu, cfg->n_avg, s);
+            if (rc == MPPI_OK) rc = launch_shift_rows(c->d_L, c->H, nu * nu, cfg->n_avg, s);
+        }
+    }
+    if (rc == MPPI_OK) rc = cuda_fail(cudaStreamSynchronize(s));
+    out.task_time_s = out.steps * (double)c->m->host.dt;
+    if (out.plans > 0) {
+        out.comp_mean_ms = sum / out.plans;
+        const double var = sum2 / out.plans - out.comp_mean_ms * out.comp_mean_ms;
+        out.comp_std_ms = var > 0.0 ? std::sqrt(var) : 0.0;
+    }
+    *res = out;
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    cudaFree(d_world);
+    return rc;
+}

@@ -166,6 +166,12 @@ void qp_make_class(const float b[8], const float sc[4], float rho, QPClass* c);
 int qp_validate(const float b[8], const float sc[4], float rho);
 int launch_qp(const QPArgs& a, cudaStream_t s);
 
+// closed-loop episode helpers
+int launch_best_average(const float* U, const float* best, const float* bestU, int K, int nu, int n, float* u1,
+                        cudaStream_t s);
+int launch_shift_rows(float* u, int H, int row, int n, cudaStream_t s);
+int launch_probe(int na, const DevModel* model, const float* x, float* out, cudaStream_t s);
+
 int parse_model_blob(const void* blob, size_t len, DevModel* out, HostModelInfo* info);
 int launch_rollout(int na, int mode, const RolloutArgs& a, int spc, cudaStream_t s);
 int launch_update(int nu, const UpdateArgs& a, int H, cudaStream_t s);

@@ -33,10 +33,82 @@ struct TaskAcc {
     float th, yz, v2, r, l, eo, ot;   // per-state terms (lane 0)
 };
 
+// Exact distance between a capsule (segment a0-a1, radius rcap) and a box:
+// the minimum over t in [0,1] of the box SDF f(t) at a0 + t (a1 - a0), minus
+// the radius.  f is convex; its kinks along the segment are where a
+// coordinate crosses a slab plane or the box's mid-plane, plus, inside the
+// box, where two face distances cross.  f is evaluated at the nine crossing
+// parameters and both ends; by convexity the minimiser lies in one of the
+// two pieces next to the best of them.  On a piece outside the box f is the
+// root of a quadratic (exceeded slabs and signs fixed), minimised at its
+// stationary point; inside, f is the largest of three linear face
+// distances, minimised at a pairwise crossing or an end.
 __device__ __forceinline__ float capsule_box_distance(const float* a0, const float* a1, float rcap, const float* box) {
     const float dd[3] = {a1[0] - a0[0], a1[1] - a0[1], a1[2] - a0[2]};
-    float best = INFINITY;
-    for (int id = 0; id < CB_CANDIDATES; ++id) best = fminf(best, box_sdf_only(a0, dd, capsule_box_candidate(id, a0, dd, box), box));
+    float T[11];
+    T[0] = 0.0f;
+    T[1] = 1.0f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const bool mv = dd[k] != 0.0f;
+        const float inv = mv ? 1.0f / dd[k] : 0.0f;
+        const float t0 = (box[k] - box[3 + k] - a0[k]) * inv, t1 = (box[k] + box[3 + k] - a0[k]) * inv;
+        const float tc = (box[k] - a0[k]) * inv;
+        T[2 + 3 * k] = mv ? fminf(fmaxf(t0, 0.0f), 1.0f) : 0.0f;
+        T[3 + 3 * k] = mv ? fminf(fmaxf(t1, 0.0f), 1.0f) : 0.0f;
+        T[4 + 3 * k] = mv ? fminf(fmaxf(tc, 0.0f), 1.0f) : 0.0f;
+    }
+    float best = INFINITY, tb = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 11; ++i) {
+        const float f = box_sdf_only(a0, dd, T[i], box);
+        if (f < best) {
+            best = f;
+            tb = T[i];
+        }
+    }
+    float tl = 0.0f, tr = 1.0f;
+#pragma unroll
+    for (int i = 0; i < 11; ++i) {
+        if (T[i] < tb) tl = fmaxf(tl, T[i]);
+        if (T[i] > tb) tr = fminf(tr, T[i]);
+    }
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        const float lo = side == 0 ? tl : tb, hi = side == 0 ? tb : tr;
+        if (!(hi > lo)) continue;
+        const float tm = 0.5f * (lo + hi);
+        float al[3], be[3], num = 0.0f, den = 0.0f;
+        bool outside = false;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float xk = a0[k] + tm * dd[k] - box[k];
+            const float sg = xk >= 0.0f ? 1.0f : -1.0f;
+            al[k] = sg * (a0[k] - box[k]) - box[3 + k];
+            be[k] = sg * dd[k];
+            if (sg * xk - box[3 + k] > 0.0f) {  // slab k exceeded on this piece
+                outside = true;
+                num += al[k] * be[k];
+                den += be[k] * be[k];
+            }
+        }
+        if (outside) {
+            if (den > 0.0f) {
+                const float t = fminf(fmaxf(-num / den, lo), hi);
+                best = fminf(best, box_sdf_only(a0, dd, t, box));
+            }
+        } else {
+#pragma unroll
+            for (int p = 0; p < 3; ++p) {
+                const int j = p, k = (p + 1) % 3;
+                const float dn = be[k] - be[j];
+                if (dn != 0.0f) {
+                    const float t = fminf(fmaxf((al[j] - al[k]) / dn, lo), hi);
+                    best = fminf(best, box_sdf_only(a0, dd, t, box));
+                }
+            }
+        }
+    }
     return best - rcap;
 }
 

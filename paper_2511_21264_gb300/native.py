@@ -151,6 +151,7 @@ def lib():
     _decl(L, "mppi_set_projection", i, [vp, fp, i, C.c_float, fp])
     _decl(L, "mppi_get_samples", i, [vp, fp, vp])
     _decl(L, "mppi_set_task_cost", i, [vp, fp, i])
+    _decl(L, "mppi_run_episode", i, [vp, fp, fp, C.POINTER(EpisodeConfig), fp, fp, fp, C.POINTER(EpisodeResult), vp])
     _lib = L
     return L
 
@@ -231,6 +232,19 @@ def qp_project(v_in, bounds, q0, qd0, dt: float, iters: int = 30, rho: float = 1
                                  None if sc is None else sc.ctypes.data, _ptr(q0), _ptr(qd0), _ptr(v_in),
                                  _ptr(v_out), _stream(stream)), "mppi_qp_project")
     return v_out
+
+
+class EpisodeConfig(C.Structure):
+    _fields_ = [("iters", C.c_int), ("n_avg", C.c_int), ("max_steps", C.c_int), ("goal_tol", C.c_float),
+                ("lift_dz", C.c_float), ("drop_dz", C.c_float), ("pick_tol", C.c_float)]
+
+
+class EpisodeResult(C.Structure):
+    _fields_ = [("outcome", C.c_int), ("plans", C.c_int), ("steps", C.c_int), ("switch_step", C.c_int),
+                ("task_time_s", C.c_double), ("comp_mean_ms", C.c_double), ("comp_std_ms", C.c_double)]
+
+
+EPISODE_OUTCOMES = {0: "success", 1: "timeout", 2: "collision", 3: "dropped"}
 
 
 class ServerConfig(C.Structure):
@@ -529,6 +543,34 @@ class Controller:
             return
         p = _host_f32(params)
         _check(lib().mppi_set_task_cost(self._h, p.ctypes.data, int(p.size)), "mppi_set_task_cost")
+
+    def run_episode(self, x0, u_nom, iters=10, n_avg=4, max_steps=500, goal_tol=0.03, lift_dz=0.05, drop_dz=0.05,
+                    pick_tol=0.0, record=True, stream=None):
+        """One closed-loop receding-horizon run (mppi_run_episode) from the
+        host state x0 with the CUDA warm start u_nom (H x nu, updated).
+        Returns a dict with the outcome and metrics, and with record the
+        world trajectory, executed controls and per-plan compute times."""
+        import numpy as np
+        x = np.ascontiguousarray(np.asarray(x0, dtype=np.float32))
+        cfg = EpisodeConfig(int(iters), int(n_avg), int(max_steps), float(goal_tol), float(lift_dz), float(drop_dz),
+                            float(pick_tol))
+        nx, nu = self.model.nx, self.model.nu
+        traj = np.zeros((max_steps + 1, nx), np.float32) if record else None
+        uex = np.zeros((max_steps, nu), np.float32) if record else None
+        comp = np.zeros(max_steps, np.float32) if record else None
+        res = EpisodeResult()
+        _check(lib().mppi_run_episode(self._h, x.ctypes.data, _ptr(u_nom), C.byref(cfg),
+                                      None if traj is None else traj.ctypes.data,
+                                      None if uex is None else uex.ctypes.data,
+                                      None if comp is None else comp.ctypes.data, C.byref(res), _stream(stream)),
+               "mppi_run_episode")
+        out = {n: getattr(res, n) for n, _ in EpisodeResult._fields_}
+        out["outcome_name"] = EPISODE_OUTCOMES.get(res.outcome, str(res.outcome))
+        if record:
+            out["traj"] = traj[:res.steps + 1]
+            out["u_exec"] = uex[:res.steps]
+            out["comp_ms"] = comp[:res.plans]
+        return out
 
     def samples(self, out, stream=None):
         """The last iteration's samples as rolled out (H x K x nu)."""
