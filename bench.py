@@ -529,10 +529,17 @@ def run_closed_loop(args):
             sc.goal = tuple(start + np.array([rng.uniform(-0.1, 0.1), 0.0, rng.uniform(0.15, 0.3)]))
             m = native.Model(sc.to_blob())
             ctl = native.Controller(m, K, H, sc.lam, sc.sigma_vec(), scenes.controller_key(run, rank))
+            if args.elite or args.eta != 1.0 or args.cov:
+                ctl.set_update(args.elite or K, args.eta, args.cov, 1e-6)
+            if args.qp:
+                ctl.set_projection(scenes.projection_bounds(sc), iters=args.qp)
+            if args.task is not None:
+                ctl.set_task_cost(scenes.ball_task(sc, phase=args.task))
             u = torch.zeros((H, sc.nu), device=dev)
             with torch.cuda.stream(stream):
                 ep = ctl.run_episode(sc.x0, u, iters=M, n_avg=n_avg, max_steps=max_steps, goal_tol=0.03,
-                                     lift_dz=0.05, drop_dz=0.05, record=True, stream=stream)
+                                     lift_dz=0.05, drop_dz=0.05, pick_tol=0.03 if args.task == 0 else 0.0,
+                                     record=True, stream=stream)
             results.append(ep)
             ctl.close()
             m.close()
@@ -551,7 +558,11 @@ def run_closed_loop(args):
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"planar 3-link bimanual ball lift, {args.runs} runs with randomised goals, K={K}, "
                                f"H={H}, M={M} iterations per plan, first {n_avg} steps averaged and executed, "
-                               f"{max_steps} world steps ({max_steps * 0.01:g} s) per run"},
+                               f"{max_steps} world steps ({max_steps * 0.01:g} s) per run",
+                   "update": {"n_elite": args.elite or K, "eta": args.eta, "covariance": bool(args.cov)},
+                   "projection_iters": args.qp,
+                   "cost": "ball-task suite (Sec. IV-B), pick then move" if args.task == 0 else
+                           ("ball-task suite, move" if args.task == 1 else "scene stage cost")},
         "task_time_s": {"mean": float(tt.mean()) if tt.size else None, "std": float(tt.std()) if tt.size else None,
                         "n_success": len(ok)},
         "comp_time_ms": {"mean": float(comp.mean()), "std": float(comp.std()), "n_plans": int(comp.size)},

@@ -491,12 +491,15 @@ def ball_task(scene: Scene, phase: int = 0, w_c: float = 1.0, gamma: float = 0.2
     barrier rate gamma, the EE distance l_ball, the vertical offset eps, the
     ball position before the pick (the scene's start), the target (the
     scene's goal), the target EE orientations and theta_home (the scene's
-    home pose).  The paper tunes its weights by hand and prints none; these
+    home pose).  l_ball defaults to the end effectors 5 mm inside the ball's
+    surface on opposite sides.  The paper tunes its weights by hand and prints none; these
     defaults weight each term to the same order of magnitude on the scenes
     here.  Target orientations: the last link frames turned +-90 degrees
     about the world y axis (fixed constants, w first)."""
-    r = scene.ball_r
-    lb = 1.8 * r if l_ball is None else l_ball  # contact points 0.9 of a diameter apart
+    # end effectors pressing 5 mm into the ball on opposite sides: the EE
+    # points sit a ball radius plus a capsule radius from the centre at contact
+    rc = scene.links[0][scene.n_a - 1].radius
+    lb = 2.0 * (scene.ball_r + rc) - 0.01 if l_ball is None else l_ball
     c = math.cos(math.pi / 4)
     v = [float(phase), w_c, gamma, w_theta, w_yz, w_v, w_r, w_l, lb, w_eef_obj, w_obj_targ, eps]
     v += list(scene.x0[scene.nu:scene.nu + 3])        # ball position before the pick
