@@ -889,6 +889,106 @@ __device__ __forceinline__ void contact_frame_row(const float* n, int k, float* 
 }
 
 
+// One or two contacts that touch only the ball (floor, boxes): the rows act
+// on the ball's six velocities alone and its mass matrix is diag(m, m, m,
+// I, I, I), so every lane forms the whole problem in registers -- row
+// directions e (signed by the ball's side) and d = (p - c) x e, Delassus
+// G_rs = e_r.e_s / m + d_r.d_s / I, b_r = e_r.v_f + d_r.w_f -- runs the
+// sweeps and applies the impulse, with no shared-memory rows or factor.
+// The same iteration as the general path, summed in a different order.
+template <int NA, int NC>
+__device__ __forceinline__ void contacts_ball(const DevModel& M, WarpWS<NA>& w, int lane) {
+    using d = Dims<NA>;
+    constexpr int NR = 3 * NC;
+    const float im = 1.0f / M.mb, iI = 1.0f / M.Ib, regc = (1.0f - M.imp) / M.imp;
+    const float* bc = &w.q[d::B];
+    const float* vl = &w.vf[d::B];
+    const float* va = &w.vf[d::B + 3];
+    float E[NR][3], D[NR][3], bb[NR], vs[NR];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const float sgn = w.cA[c] == d::B ? 1.0f : -1.0f;
+        const float* p = w.cp[c];
+        const float dd[3] = {p[0] - bc[0], p[1] - bc[1], p[2] - bc[2]};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int r = 3 * c + k;
+            float e[3], de[3];
+            contact_frame_row<NA>(w.cn[c], k, e);
+            cross3(dd, e, de);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                E[r][q] = sgn * e[q];
+                D[r][q] = sgn * de[q];
+            }
+            bb[r] = dot3(E[r], vl) + dot3(D[r], va);
+            vs[r] = k == 0 ? (M.erp / M.dt) * w.cdep[c] : 0.0f;
+        }
+    }
+    float G[NR][NR], R[NR], iA[NR], lam[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+#pragma unroll
+        for (int q = r; q < NR; ++q) {
+            const float g = im * dot3(E[r], E[q]) + iI * dot3(D[r], D[q]);
+            G[r][q] = g;
+            G[q][r] = g;
+        }
+        R[r] = regc * G[r][r];
+        iA[r] = 1.0f / (G[r][r] + R[r]);
+        lam[r] = 0.0f;
+    }
+    for (int sw = 0; sw < M.sweeps; ++sw) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const int rn = 3 * c;
+            float res = bb[rn] + R[rn] * lam[rn] - vs[rn];
+#pragma unroll
+            for (int q = 0; q < NR; ++q) res += G[rn][q] * lam[q];
+            const float ln = fmaxf(lam[rn] - res * iA[rn], 0.0f);
+            lam[rn] = ln;
+            float r1 = bb[rn + 1] + R[rn + 1] * lam[rn + 1];
+            float r2 = bb[rn + 2] + R[rn + 2] * lam[rn + 2];
+#pragma unroll
+            for (int q = 0; q < NR; ++q) {
+                r1 += G[rn + 1][q] * lam[q];
+                r2 += G[rn + 2][q] * lam[q];
+            }
+            float l1 = lam[rn + 1] - r1 * iA[rn + 1];
+            float l2 = lam[rn + 2] - r2 * iA[rn + 2];
+            const float n2 = l1 * l1 + l2 * l2, lim = M.mu * ln;
+            if (n2 > lim * lim) {
+                const float sc = lim * rsqrtf(n2);
+                l1 *= sc;
+                l2 *= sc;
+            }
+            lam[rn + 1] = l1;
+            lam[rn + 2] = l2;
+        }
+    }
+    // v = v_f + M^-1 J^T lambda on the ball, v_f elsewhere
+    float dv[6];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float sl = 0.0f, sa = 0.0f;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            sl += E[r][k] * lam[r];
+            sa += D[r][k] * lam[r];
+        }
+        dv[k] = im * sl;
+        dv[3 + k] = iI * sa;
+    }
+    if (lane < d::NV) {
+        float add = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            if (lane == d::B + k) add = dv[k];
+        w.v[lane] = w.vf[lane] + add;
+    }
+    __syncwarp();
+}
+
 // Projected Gauss-Seidel for one or two contacts with the Delassus block in
 // registers: every lane runs the same sweeps (no shuffles, no shared-memory
 // round trips), then lane r stores lambda_r.  The same iteration as the
@@ -966,6 +1066,11 @@ __device__ __forceinline__ void contacts(const DevModel& M, WarpWS<NA>& w, int l
         if (Bb >= 0 && Bb < d::B) tb |= 1 << (Bb / NA);
     }
     tb = (int)__reduce_or_sync(FULL, (unsigned)tb);
+    if (tb == 4 && nc <= 2) {  // ball against static geometry only
+        if (nc == 1) contacts_ball<NA, 1>(M, w, lane);
+        else contacts_ball<NA, 2>(M, w, lane);
+        return;
+    }
     // z_f = L^T v_f (one lane per arm coordinate; lane 15 the ball)
     {
         const int a = lane >> 4, i = lane & 15;
