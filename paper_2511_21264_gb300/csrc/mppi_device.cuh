@@ -152,6 +152,19 @@ __device__ __forceinline__ float block_normal(uint4 w, int t) {
     return __fmul_rn(r, (t & 1) ? s : c);
 }
 
+// All four normals of a Philox block, each word pair's radius and angle
+// computed once (the values block_normal gives for t = 0..3).
+__device__ __forceinline__ void block_normals4(uint4 w, float (&z)[4]) {
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const float r = sqrtf(__fmul_rn(-2.0f, logf(u01_23(p ? w.z : w.x))));
+        float s, c;
+        sincospif(__fmul_rn(2.0f, u01_23(p ? w.w : w.y)), &s, &c);
+        z[2 * p] = __fmul_rn(r, c);
+        z[2 * p + 1] = __fmul_rn(r, s);
+    }
+}
+
 // Sampled control U[k,h,j] = clamp(u_nom[h,j] + sigma_j z, lo, hi) with z
 // from counter (j/4, h, k, iteration).  Written with explicit rounding so the
 // rollout and the update kernels regenerate identical values.
@@ -910,11 +923,17 @@ __device__ __forceinline__ void contacts_ball(const DevModel& M, WarpWS<NA>& w, 
         const float sgn = w.cA[c] == d::B ? 1.0f : -1.0f;
         const float* p = w.cp[c];
         const float dd[3] = {p[0] - bc[0], p[1] - bc[1], p[2] - bc[2]};
+        const float nrm[3] = {w.cn[c][0], w.cn[c][1], w.cn[c][2]};
+        float fr[3][3];  // n, t1, t2 (the rows contact_frame_row gives)
+        contact_frame_row<NA>(nrm, 1, fr[1]);
+        cross3(nrm, fr[1], fr[2]);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) fr[0][q] = nrm[q];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             const int r = 3 * c + k;
-            float e[3], de[3];
-            contact_frame_row<NA>(w.cn[c], k, e);
+            const float* e = fr[k];
+            float de[3];
             cross3(dd, e, de);
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
@@ -938,7 +957,7 @@ __device__ __forceinline__ void contacts_ball(const DevModel& M, WarpWS<NA>& w, 
         iA[r] = 1.0f / (G[r][r] + R[r]);
         lam[r] = 0.0f;
     }
-    for (int sw = 0; sw < M.sweeps; ++sw) {
+    auto sweep = [&]() {
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
             const int rn = 3 * c;
@@ -965,6 +984,18 @@ __device__ __forceinline__ void contacts_ball(const DevModel& M, WarpWS<NA>& w, 
             lam[rn + 1] = l1;
             lam[rn + 2] = l2;
         }
+    };
+    if (M.sweeps == 4) {  // the scenes' sweep counts, unrolled
+        sweep();
+        sweep();
+        sweep();
+        sweep();
+    } else if (M.sweeps == 3) {
+        sweep();
+        sweep();
+        sweep();
+    } else {
+        for (int sw = 0; sw < M.sweeps; ++sw) sweep();
     }
     // v = v_f + M^-1 J^T lambda on the ball, v_f elsewhere
     float dv[6];

@@ -63,8 +63,10 @@ __device__ __forceinline__ float rollout_sample(const DevModel& M, WarpWS<NA>& w
                 const int jb = lane & 3, hs = h + (lane >> 2);
                 if (4 * jb < d::NU && hs < io.H) {
                     const uint4 wv = philox4x32_10(make_uint4((uint32_t)jb, (uint32_t)hs, (uint32_t)k, io.iter), io.key);
+                    float z4[4];
+                    block_normals4(wv, z4);
 #pragma unroll
-                    for (int t = 0; t < 4; ++t) w.zn[lane >> 2][4 * jb + t] = block_normal(wv, t);
+                    for (int t = 0; t < 4; ++t) w.zn[lane >> 2][4 * jb + t] = z4[t];
                 }
                 __syncwarp();
             }
@@ -209,11 +211,13 @@ __device__ __forceinline__ void update_step(const UpdateArgs& a, int h, UpdateSm
 #pragma unroll
                 for (int jb = 0; jb < (NU + 3) / 4; ++jb) {
                     const uint4 wv = philox4x32_10(make_uint4((uint32_t)jb, (uint32_t)h, (uint32_t)k, iter), key);
+                    float z4[4];
+                    block_normals4(wv, z4);
 #pragma unroll
                     for (int t = 0; t < 4; ++t) {
                         const int j = 4 * jb + t;
                         if (j < NU) {
-                            const float z = block_normal(wv, t);
+                            const float z = z4[t];
                             const float u = fminf(fmaxf(__fmaf_rn(sg[j], z, un[j]), lo[j]), hi[j]);
                             acc[j] += wk * u;
                         }
@@ -280,9 +284,11 @@ __device__ __forceinline__ void sample_row(uint2 key, uint32_t iter, int k, int 
 #pragma unroll
     for (int jb = 0; jb < (NU + 3) / 4; ++jb) {
         const uint4 wv = philox4x32_10(make_uint4((uint32_t)jb, (uint32_t)h, (uint32_t)k, iter), key);
+        float z4[4];
+        block_normals4(wv, z4);
 #pragma unroll
         for (int t = 0; t < 4; ++t)
-            if (4 * jb + t < NU) z[4 * jb + t] = block_normal(wv, t);
+            if (4 * jb + t < NU) z[4 * jb + t] = z4[t];
     }
 #pragma unroll
     for (int j = 0; j < NU; ++j) {
