@@ -36,6 +36,10 @@ namespace mppi {
 template <int NA, int MODE, bool TASK>
 __global__ void __launch_bounds__(512) rollout_kernel(RolloutArgs args) {
     using d = Dims<NA>;
+    // launched as a programmatic dependent: wait for the previous kernel's
+    // results (u_nom, the counter), then let the next kernel launch early
+    cudaGridDependencySynchronize();
+    cudaTriggerProgrammaticLaunchCompletion();
     extern __shared__ __align__(16) unsigned char smem[];
     DevModel& M = *reinterpret_cast<DevModel*>(smem);
     constexpr size_t task_b = TASK ? sizeof(DevTask) : 0;
@@ -90,6 +94,8 @@ __global__ void __launch_bounds__(512) rollout_kernel(RolloutArgs args) {
 
 template <int NU>
 __global__ void __launch_bounds__(256) update_kernel(UpdateArgs a) {
+    cudaGridDependencySynchronize();  // the rollout's costs and samples
+    cudaTriggerProgrammaticLaunchCompletion();
     __shared__ UpdateSmem<NU> sm;
     update_step<NU>(a, blockIdx.x, sm);
     update_finish<NU>(a, gridDim.x, sm);
@@ -188,6 +194,25 @@ int cuda_fail(cudaError_t e) {
     return MPPI_ERR_CUDA;
 }
 
+// Kernel launch, optionally as a programmatic dependent of the stream's
+// previous kernel (its launch overlaps that kernel's tail; the kernel waits
+// in cudaGridDependencySynchronize before reading what that kernel wrote).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_kernel(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, bool pdl,
+                          Args... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = pdl ? at : nullptr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 template <int NA>
 size_t rollout_smem(int spc, int unom_floats, bool task = false) {
     return sizeof(DevModel) + (task ? sizeof(DevTask) : 0) + ((size_t)unom_floats * sizeof(float) + 15) / 16 * 16 +
@@ -206,8 +231,8 @@ int launch_rollout_t(const RolloutArgs& a, int spc, cudaStream_t s) {
     }
     (void)max_set;
     const int grid = (a.n + spc - 1) / spc;
-    fn<<<grid, spc * 32, sm, s>>>(a);
-    return cuda_fail(cudaGetLastError());
+    cudaError_t e = launch_kernel(fn, dim3(grid), dim3(spc * 32), sm, s, a.pdl != 0, a);
+    return cuda_fail(e != cudaSuccess ? e : cudaGetLastError());
 }
 
 }  // namespace
@@ -227,10 +252,11 @@ int launch_rollout(int na, int mode, const RolloutArgs& a, int spc, cudaStream_t
 }
 
 int launch_update(int nu, const UpdateArgs& a, int H, cudaStream_t s) {
-    if (nu == 6) update_kernel<6><<<H, 256, 0, s>>>(a);
-    else if (nu == 14) update_kernel<14><<<H, 256, 0, s>>>(a);
+    cudaError_t e;
+    if (nu == 6) e = launch_kernel(update_kernel<6>, dim3(H), dim3(256), 0, s, a.pdl != 0, a);
+    else if (nu == 14) e = launch_kernel(update_kernel<14>, dim3(H), dim3(256), 0, s, a.pdl != 0, a);
     else return MPPI_ERR_UNSUPPORTED;
-    return cuda_fail(cudaGetLastError());
+    return cuda_fail(e != cudaSuccess ? e : cudaGetLastError());
 }
 
 int launch_noise(int nu, const NoiseArgs& a, cudaStream_t s) {
@@ -950,6 +976,7 @@ static int enqueue_step(mppi_ctx* c, const float* state, const float* u_nom, flo
         mode = 0;
     }
     if (prof) cudaEventRecord(ev[1], s);
+    a.pdl = !prof;  // event records between the kernels would break the overlap anyway
     rc = launch_rollout(c->m->info.na, mode, a, c->spc, s);
     if (rc != MPPI_OK) return rc;
     if (prof) cudaEventRecord(ev[2], s);
@@ -958,6 +985,7 @@ static int enqueue_step(mppi_ctx* c, const float* state, const float* u_nom, flo
     } else {
         UpdateArgs u = update_args(c, c->d_costs, u_nom, u_out, 1, best);
         u.U_stored = c->d_U;
+        u.pdl = !prof;
         rc = launch_update(2 * c->m->info.na, u, c->H, s);
     }
     if (prof) {

@@ -801,7 +801,16 @@ __device__ __forceinline__ void dynamics(const DevModel& M, WarpWS<NA>& w, int l
         }
     }
     __syncwarp();
-    // (6) Cholesky of each arm block (in registers), the free velocity; ball
+    // (6) Cholesky of each arm block (in registers), the free velocity; ball.
+    //     The factor is kept only for arms a contact touches (the contact
+    //     solve's rows need it there).
+    int armc = 0;
+    if (lane < w.ncon) {
+        const int A = w.cA[lane], Bb = w.cB[lane];
+        if (A >= 0 && A < d::B) armc |= 1 << (A / NA);
+        if (Bb >= 0 && Bb < d::B) armc |= 1 << (Bb / NA);
+    }
+    armc = (int)__reduce_or_sync(FULL, (unsigned)armc);
     if (i == 0) {
         float A[NA][NA];
 #pragma unroll
@@ -846,11 +855,14 @@ __device__ __forceinline__ void dynamics(const DevModel& M, WarpWS<NA>& w, int l
             y[r] = sr * di[r];
         }
 #pragma unroll
-        for (int r = 0; r < NA; ++r) {
-            w.vf[a * NA + r] = w.qd[a * NA + r] + M.dt * y[r];
-            w.Ldi[a][r] = di[r];
+        for (int r = 0; r < NA; ++r) w.vf[a * NA + r] = w.qd[a * NA + r] + M.dt * y[r];
+        if ((armc >> a) & 1) {
 #pragma unroll
-            for (int cc = 0; cc <= r; ++cc) w.L[a][r][cc] = A[r][cc];
+            for (int r = 0; r < NA; ++r) {
+                w.Ldi[a][r] = di[r];
+#pragma unroll
+                for (int cc = 0; cc <= r; ++cc) w.L[a][r][cc] = A[r][cc];
+            }
         }
         if (!ok) atomicOr(err, ERRB_CHOLESKY);
     }

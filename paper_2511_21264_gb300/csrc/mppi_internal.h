@@ -53,6 +53,7 @@ struct RolloutArgs {
     int U_hmajor;                // MODE 0: U is H x n x nu (h-major) instead of n x H x nu
     const float* Lfac;           // optional: covariance factors H x nu x nu (MODE 1), else diagonal sigma
     const DevTask* task;         // optional: the ball-task cost suite replaces the stage cost
+    int pdl;                     // launch as a programmatic dependent of the previous kernel
 };
 
 // Arguments of the weighted-mean update (one CTA per horizon step).
@@ -73,6 +74,7 @@ struct UpdateArgs {
     int advance;        // last CTA increments *iter_ptr
     unsigned int* done; // CTA completion counter (reset by the last CTA)
     const float* U_stored;  // optional: the rollout's sampled controls (H x K x nu), else regenerated
+    int pdl;                // launch as a programmatic dependent of the previous kernel
 };
 
 struct NoiseArgs {

@@ -166,20 +166,30 @@ __device__ __forceinline__ void update_step(const UpdateArgs& a, int h, UpdateSm
             ci = k;
         }
     }
-    sm.rmin[tid] = cm;
-    sm.ridx[tid] = ci;
-    __syncthreads();
-    for (int st = T / 2; st > 0; st >>= 1) {
-        if (tid < st) {
-            const float o = sm.rmin[tid + st];
-            const int oi = sm.ridx[tid + st];
-            if (o < sm.rmin[tid] || (o == sm.rmin[tid] && oi < sm.ridx[tid])) {
-                sm.rmin[tid] = o;
-                sm.ridx[tid] = oi;
-            }
+    // lowest (cost, index): butterfly within each warp, then the 8 warp
+    // results in order
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const float o = __shfl_xor_sync(0xffffffffu, cm, off);
+        const int oi = __shfl_xor_sync(0xffffffffu, ci, off);
+        if (o < cm || (o == cm && oi < ci)) {
+            cm = o;
+            ci = oi;
         }
-        __syncthreads();
     }
+    if ((tid & 31) == 0) {
+        sm.rmin[tid >> 5] = cm;
+        sm.ridx[tid >> 5] = ci;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int q = 1; q < T / 32; ++q)
+            if (sm.rmin[q] < sm.rmin[0] || (sm.rmin[q] == sm.rmin[0] && sm.ridx[q] < sm.ridx[0])) {
+                sm.rmin[0] = sm.rmin[q];
+                sm.ridx[0] = sm.ridx[q];
+            }
+    }
+    __syncthreads();
     const float cmin = sm.rmin[0];
     const int cidx = sm.ridx[0];
     __syncthreads();
@@ -226,17 +236,25 @@ __device__ __forceinline__ void update_step(const UpdateArgs& a, int h, UpdateSm
             }
         }
     }
+    // fixed-order sums: butterfly within each warp, then the warps in order
 #pragma unroll
-    for (int j = 0; j < NU; ++j) sm.red[j][tid] = acc[j];
-    sm.red[NU][tid] = Z;
-    __syncthreads();
-    for (int st = T / 2; st > 0; st >>= 1) {
-        if (tid < st) {
+    for (int off = 16; off > 0; off >>= 1) {
 #pragma unroll
-            for (int j = 0; j <= NU; ++j) sm.red[j][tid] += sm.red[j][tid + st];
-        }
-        __syncthreads();
+        for (int j = 0; j < NU; ++j) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], off);
+        Z += __shfl_xor_sync(0xffffffffu, Z, off);
     }
+    if ((tid & 31) == 0) {
+#pragma unroll
+        for (int j = 0; j < NU; ++j) sm.red[j][tid >> 5] = acc[j];
+        sm.red[NU][tid >> 5] = Z;
+    }
+    __syncthreads();
+    if (tid <= NU) {
+        float t = sm.red[tid][0];
+        for (int q = 1; q < T / 32; ++q) t += sm.red[tid][q];
+        sm.red[tid][0] = t;
+    }
+    __syncthreads();
     if (tid < NU) a.u_out[h * NU + tid] = any ? sm.red[tid][0] / sm.red[NU][0] : un[tid];
     if (h == 0 && tid == 0) {
         if (!any) atomicOr(a.err, ERRB_NONFINITE);
@@ -387,17 +405,25 @@ __device__ __forceinline__ void elite_update_step(const EliteArgs& a, int h, Eli
 #pragma unroll
         for (int j = 0; j < NU; ++j) acc[j] += wk * u[j];
     }
+    // fixed-order sums: butterfly within each warp, then the warps in order
 #pragma unroll
-    for (int j = 0; j < NU; ++j) sm.red[j][tid] = acc[j];
-    sm.red[NU][tid] = Z;
-    __syncthreads();
-    for (int st = T / 2; st > 0; st >>= 1) {
-        if (tid < st) {
+    for (int off = 16; off > 0; off >>= 1) {
 #pragma unroll
-            for (int j = 0; j <= NU; ++j) sm.red[j][tid] += sm.red[j][tid + st];
-        }
-        __syncthreads();
+        for (int j = 0; j < NU; ++j) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], off);
+        Z += __shfl_xor_sync(0xffffffffu, Z, off);
     }
+    if ((tid & 31) == 0) {
+#pragma unroll
+        for (int j = 0; j < NU; ++j) sm.red[j][tid >> 5] = acc[j];
+        sm.red[NU][tid >> 5] = Z;
+    }
+    __syncthreads();
+    if (tid <= NU) {
+        float t = sm.red[tid][0];
+        for (int q = 1; q < T / 32; ++q) t += sm.red[tid][q];
+        sm.red[tid][0] = t;
+    }
+    __syncthreads();
     const float Zs = sm.red[NU][0];
     if (tid < NU) {
         const float m = any ? sm.red[tid][0] / Zs : unom_h[tid];
