@@ -277,6 +277,11 @@ def run_ours(args):
     roll_ms = kt["rollout_ms"] / max(1, kt["iterations"])
     achieved = fl * K * H / (roll_ms * 1e-3) / 1e12
     elite = bool(args.elite or args.eta != 1.0 or args.cov)
+    # dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of the
+    # current rollout_kernel<7,1,0> on the lift workload (80.4 KB + 0)
+    traffic = args.traffic
+    if traffic is None and args.workload == "lift" and not (elite or args.qp or args.task is not None):
+        traffic = 80384.0
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -287,7 +292,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": int(4 * u.numel())},
         "gpu_launches": (2 + (1 if elite else 0) + (1 if args.qp else 0)) * args.steps,
         "roofline": {"bound": "alu", "kernel": "rollout_kernel<7,1>", "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": args.traffic,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (median SM clock "
                                    f"sampled during the timed steps)",
                      "flops_per_sample_step": fl, "rollout_ms": roll_ms,
@@ -599,7 +604,8 @@ def main(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--traffic", type=float, default=None,
-                    help="DRAM bytes per rollout launch from an ncu capture (else null)")
+                    help="DRAM bytes per rollout launch from an ncu capture (default: the lift workload's "
+                         "capture of the current rollout kernel; null for the others)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
