@@ -297,7 +297,8 @@ int mppi_run_episode(mppi_ctx *c, const float *x0, float *u_nom, const mppi_epis
                      float *u_exec, float *comp_ms, mppi_episode_result *res, void *stream);
 
 /* Launch shape: samples (warps) per CTA for the rollout kernels, 1..16
- * (0 = the library default).  Used by the autotuner. */
+ * (0 = the library default: 1 when K < 8 x the SM count, else 4).  Used by
+ * the autotuner. */
 int mppi_set_launch(mppi_ctx *c, int samples_per_cta);
 
 /* ---------------------------------------------------------------- batch */

@@ -508,6 +508,17 @@ int mppi_destroy(mppi_ctx* c) {
     return MPPI_OK;
 }
 
+// Samples (warps) per rollout CTA when the caller sets none: one when K / 4
+// CTAs would give the SMs fewer than two each (the uneven split then sets the
+// kernel's length), four otherwise.
+static int default_spc(int K) {
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0)
+        return 4;
+    return K < 8 * nsm ? 1 : 4;
+}
+
 int mppi_create(const mppi_model* m, int K, int H, float lambda, const float* sigma, uint64_t seed, mppi_ctx** out) {
     if (!m || !out || !sigma || K < 1 || K > (1 << 20) || H < 1 || H > 1024 || !(lambda > 0.0f))
         return MPPI_ERR_INVALID_ARG;
@@ -521,6 +532,7 @@ int mppi_create(const mppi_model* m, int K, int H, float lambda, const float* si
     c->lambda = lambda;
     c->seed = seed;
     c->n_elite = K;
+    c->spc = default_spc(K);
     const int nu = 2 * m->info.na;
     std::vector<float> lo(nu), hi(nu);
     for (int j = 0; j < nu; ++j) {
@@ -721,7 +733,7 @@ int mppi_best_controls(mppi_ctx* c, float* U_best, void* stream) {
 
 int mppi_set_launch(mppi_ctx* c, int spc) {
     if (!c || spc < 0 || spc > 16) return MPPI_ERR_INVALID_ARG;
-    c->spc = spc == 0 ? 4 : spc;
+    c->spc = spc == 0 ? default_spc(c->K) : spc;
     return MPPI_OK;
 }
 

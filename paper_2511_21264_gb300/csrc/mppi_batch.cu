@@ -41,7 +41,7 @@ __device__ __forceinline__ int owner(const BatchInst* insts, int n, int t, bool 
 }
 
 template <int NA>
-__global__ void __launch_bounds__(256, 3) batch_rollout_kernel(const BatchInst* insts, int n, int ntiles, BatchCtl* ctl,
+__global__ void __launch_bounds__(256, 2) batch_rollout_kernel(const BatchInst* insts, int n, int ntiles, BatchCtl* ctl,
                                                              int max_unom) {
     using d = Dims<NA>;
     extern __shared__ __align__(16) unsigned char smem[];

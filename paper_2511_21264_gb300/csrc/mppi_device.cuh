@@ -369,44 +369,47 @@ __device__ __forceinline__ float box_sdf_only(const float* a, const float* d, fl
 // two face distances cross.  43 candidates in all; each is clamped to [0,1].
 constexpr int CB_CANDIDATES = 43;
 __device__ __forceinline__ float capsule_box_candidate(int id, const float* a, const float* d, const float* box) {
+    // per-lane axis choices are applied by selects over the three axes, so
+    // that the caller's small arrays stay in registers
     float t = 0.0f;
     if (id == 1) {
         t = 1.0f;
-    } else if (id >= 2 && id < 8) {  // slab planes x_k = c_k +- h_k
-        const int k = (id - 2) >> 1;
-        const float sg = (id & 1) ? -1.0f : 1.0f;
-        t = (box[k] + sg * box[3 + k] - a[k]) / d[k];
-    } else if (id >= 8 && id < 11) {  // axis centres x_k = c_k
-        const int k = id - 8;
-        t = (box[k] - a[k]) / d[k];
+    } else if (id >= 2 && id < 11) {  // slab planes x_k = c_k +- h_k, axis centres x_k = c_k
+        const int k = id < 8 ? (id - 2) >> 1 : id - 8;
+        const float sg = id >= 8 ? 0.0f : ((id & 1) ? -1.0f : 1.0f);
+        float ak = a[0], dk = d[0], ck = box[0], hk = box[3];
+#pragma unroll
+        for (int q = 1; q < 3; ++q)
+            if (k == q) {
+                ak = a[q];
+                dk = d[q];
+                ck = box[q];
+                hk = box[3 + q];
+            }
+        t = (ck + sg * hk - ak) / dk;
     } else if (id >= 11) {
         float al[3], be[3];
         int use = 7;
         bool cross = false;
-        int q;
         float sgn[3] = {1.0f, 1.0f, 1.0f};
-        if (id < 23) {  // two exceeded slabs (edge regions)
-            q = id - 11;
-            const int pair = q >> 2;
-            use = pair == 0 ? 3 : (pair == 1 ? 5 : 6);
-            int first = pair == 2 ? 1 : 0;
-            int second = pair == 0 ? 1 : 2;
-            sgn[first] = (q & 1) ? -1.0f : 1.0f;
-            sgn[second] = (q & 2) ? -1.0f : 1.0f;
-        } else if (id < 31) {  // three exceeded slabs (vertex regions)
-            q = id - 23;
+        if (id < 31 && id >= 23) {  // three exceeded slabs (vertex regions)
+            const int q = id - 23;
             sgn[0] = (q & 1) ? -1.0f : 1.0f;
             sgn[1] = (q & 2) ? -1.0f : 1.0f;
             sgn[2] = (q & 4) ? -1.0f : 1.0f;
-        } else {  // two face distances equal inside the box
-            q = id - 31;
+        } else {  // two exceeded slabs (edge regions, id < 23), or two face
+                  // distances equal inside the box (id >= 31)
+            const int q = id < 23 ? id - 11 : id - 31;
             const int pair = q >> 2;
             use = pair == 0 ? 3 : (pair == 1 ? 5 : 6);
-            int first = pair == 2 ? 1 : 0;
-            int second = pair == 0 ? 1 : 2;
-            sgn[first] = (q & 1) ? -1.0f : 1.0f;
-            sgn[second] = (q & 2) ? -1.0f : 1.0f;
-            cross = true;
+            const int first = pair == 2 ? 1 : 0;
+            const int second = pair == 0 ? 1 : 2;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                if (k == first) sgn[k] = (q & 1) ? -1.0f : 1.0f;
+                if (k == second) sgn[k] = (q & 2) ? -1.0f : 1.0f;
+            }
+            cross = id >= 31;
         }
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -423,14 +426,22 @@ __device__ __forceinline__ float capsule_box_candidate(int id, const float* a, c
                 }
             t = -num / den;
         } else {
-            int j = -1, k2 = -1;
+            // the two axes in use, lower (j) and higher (k2)
+            float alj = 0.0f, bej = 0.0f, alk = 0.0f, bek = 0.0f;
+            bool seen = false;
 #pragma unroll
             for (int k = 0; k < 3; ++k)
                 if (use & (1 << k)) {
-                    if (j < 0) j = k;
-                    else k2 = k;
+                    if (!seen) {
+                        alj = al[k];
+                        bej = be[k];
+                    } else {
+                        alk = al[k];
+                        bek = be[k];
+                    }
+                    seen = true;
                 }
-            t = (al[k2] - al[j]) / (be[j] - be[k2]);
+            t = (alk - alj) / (bej - bek);
         }
     }
     if (!(t >= 0.0f)) t = 0.0f;  // also maps NaN from degenerate directions
@@ -896,10 +907,11 @@ __device__ __forceinline__ void contact_frame_row(const float* n, int k, float* 
         ia = 1;
     }
     if (az < best) ia = 2;
-    float ev[3] = {0, 0, 0};
-    ev[ia] = 1.0f;
+    // n x e_ia, written out per axis (no dynamically indexed local array)
     float t1[3];
-    cross3(n, ev, t1);
+    t1[0] = ia == 0 ? 0.0f : (ia == 1 ? -n[2] : n[1]);
+    t1[1] = ia == 0 ? n[2] : (ia == 1 ? 0.0f : -n[0]);
+    t1[2] = ia == 0 ? -n[1] : (ia == 1 ? n[0] : 0.0f);
     const float il = rsqrtf(dot3(t1, t1));
     t1[0] *= il;
     t1[1] *= il;

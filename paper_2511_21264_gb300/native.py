@@ -19,6 +19,12 @@ BUILD = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(BUILD, "libmppi.so")
 INCLUDE = os.path.join(os.path.dirname(_HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# FP32 division and square root by the hardware's approximate forms (errors of
+# a few ulp) rather than the correctly rounded sequences; denormals are kept.
+# The divisions and square roots sit on the rollout's dependent chains (contact
+# normals, capsule parameters, PGS row inverses), and the parity bounds against
+# the FP64 oracle are orders of magnitude above that.
+FP_FLAGS = ["-prec-div=false", "-prec-sqrt=false"]
 
 ERRORS = {0: "MPPI_OK", 1: "MPPI_ERR_INVALID_ARG", 2: "MPPI_ERR_OOM", 3: "MPPI_ERR_CUDA",
           4: "MPPI_ERR_NONFINITE", 5: "MPPI_ERR_TIMEOUT", 6: "MPPI_ERR_ADMISSION",
@@ -53,7 +59,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     objs, procs = [], []
     for src in _sources():
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-        cmd = ["nvcc", "-O3", "-std=c++17", "-Xcompiler", "-fPIC", *ARCH, "-lineinfo",
+        cmd = ["nvcc", "-O3", *FP_FLAGS, "-std=c++17", "-Xcompiler", "-fPIC", *ARCH, "-lineinfo",
                "-I", INCLUDE, "-c", src, "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
