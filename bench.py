@@ -277,11 +277,17 @@ def run_ours(args):
     roll_ms = kt["rollout_ms"] / max(1, kt["iterations"])
     achieved = fl * K * H / (roll_ms * 1e-3) / 1e12
     elite = bool(args.elite or args.eta != 1.0 or args.cov)
-    # dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of the
-    # current rollout_kernel<7,1,0> on the lift workload (80.4 KB + 0)
-    traffic = args.traffic
-    if traffic is None and args.workload == "lift" and not (elite or args.qp or args.task is not None):
-        traffic = 80384.0
+    # From one ncu capture of the current rollout_kernel<7,1,0> per workload
+    # (the fourth launch of `bench.py --steps 4 --warmup 3`): DRAM traffic
+    # dram__bytes_read.sum + dram__bytes_write.sum, and the FP32 operations
+    # the kernel executed, 2 x FFMA + FADD + FMUL thread instructions
+    # (sm__sass_thread_inst_executed_op_{ffma,fadd,fmul}_pred_on.sum), which
+    # count redundant lanes too; null for the other configurations.
+    plain = not (elite or args.qp or args.task is not None)
+    captured = {"lift": (78336.0, 1108017448.0), "transfer": (86528.0, 9602228856.0)}
+    traffic, exec_flops = captured.get(args.workload, (None, None)) if plain else (None, None)
+    if args.traffic is not None:
+        traffic = args.traffic
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -301,6 +307,12 @@ def run_ours(args):
                      "box_tests_per_step": kt["box_tests_per_step"]},
         "clocks": clocks,
     }
+    if exec_flops is not None:
+        ex = exec_flops / (roll_ms * 1e-3) / 1e12
+        line["roofline"]["ncu_executed"] = {
+            "flops_per_launch": exec_flops, "achieved": ex, "frac": ex / peak,
+            "per_sample_step": exec_flops / (K * H),
+            "basis": "ncu FP32 thread instructions of one launch (2 x FFMA + FADD + FMUL) / live mean duration"}
     if args.workload != "lift":
         line["metric"] = METRIC.replace("MPPI iteration", "MPPI iteration, " + args.workload)
     if elite:
