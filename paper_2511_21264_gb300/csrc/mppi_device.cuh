@@ -223,7 +223,9 @@ __device__ __forceinline__ void forward_kinematics(const DevModel& M, WarpWS<NA>
     if (act) {
         const DevLink& L = M.link[a][i];
         float sn, cs;
-        sincosf(w.q[a * NA + i], &sn, &cs);
+        // the hardware sine and cosine: absolute error about 1e-6 for joint
+        // angles of a few radians, growing slowly with the angle
+        __sincosf(w.q[a * NA + i], &sn, &cs);
 #pragma unroll
         for (int cc = 0; cc < 3; ++cc) {
             R[cc] = cs * L.FR[cc] - sn * L.FR[3 + cc];
@@ -941,10 +943,13 @@ __device__ __forceinline__ void contacts_ball(const DevModel& M, WarpWS<NA>& w, 
     const float* bc = &w.q[d::B];
     const float* vl = &w.vf[d::B];
     const float* va = &w.vf[d::B + 3];
-    float E[NR][3], D[NR][3], bb[NR], vs[NR];
+    // rows without the side sign s_c (+1 when the ball is body A): it enters
+    // b, the cross-contact Delassus entries and the applied impulse
+    float E[NR][3], D[NR][3], bb[NR], vs[NR], sg[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
         const float sgn = w.cA[c] == d::B ? 1.0f : -1.0f;
+        sg[c] = sgn;
         const float* p = w.cp[c];
         const float dd[3] = {p[0] - bc[0], p[1] - bc[1], p[2] - bc[2]};
         const float nrm[3] = {w.cn[c][0], w.cn[c][1], w.cn[c][2]};
@@ -961,10 +966,10 @@ __device__ __forceinline__ void contacts_ball(const DevModel& M, WarpWS<NA>& w, 
             cross3(dd, e, de);
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
-                E[r][q] = sgn * e[q];
-                D[r][q] = sgn * de[q];
+                E[r][q] = e[q];
+                D[r][q] = de[q];
             }
-            bb[r] = dot3(E[r], vl) + dot3(D[r], va);
+            bb[r] = sgn * (dot3(E[r], vl) + dot3(D[r], va));
             vs[r] = k == 0 ? (M.erp / M.dt) * w.cdep[c] : 0.0f;
         }
     }
@@ -973,7 +978,10 @@ __device__ __forceinline__ void contacts_ball(const DevModel& M, WarpWS<NA>& w, 
     for (int r = 0; r < NR; ++r) {
 #pragma unroll
         for (int q = r; q < NR; ++q) {
-            const float g = im * dot3(E[r], E[q]) + iI * dot3(D[r], D[q]);
+            // one contact's frame is orthonormal: e_r . e_q = delta_rq
+            float g;
+            if (r / 3 == q / 3) g = (r == q ? im : 0.0f) + iI * dot3(D[r], D[q]);
+            else g = sg[r / 3] * sg[q / 3] * (im * dot3(E[r], E[q]) + iI * dot3(D[r], D[q]));
             G[r][q] = g;
             G[q][r] = g;
         }
@@ -1028,8 +1036,9 @@ __device__ __forceinline__ void contacts_ball(const DevModel& M, WarpWS<NA>& w, 
         float sl = 0.0f, sa = 0.0f;
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
-            sl += E[r][k] * lam[r];
-            sa += D[r][k] * lam[r];
+            const float sl_r = sg[r / 3] * lam[r];
+            sl += E[r][k] * sl_r;
+            sa += D[r][k] * sl_r;
         }
         dv[k] = im * sl;
         dv[3 + k] = iI * sa;
