@@ -621,10 +621,15 @@ __device__ __forceinline__ int collide(const DevModel& M, WarpWS<NA>& w, int lan
             ++base;
         }
     }
+    if (nb > 0) {
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        pa += __shfl_xor_sync(FULL, pa, off);
-        pbox += __shfl_xor_sync(FULL, pbox, off);
+        for (int off = 16; off > 0; off >>= 1) {
+            pa += __shfl_xor_sync(FULL, pa, off);
+            pbox += __shfl_xor_sync(FULL, pbox, off);
+        }
+    } else {  // no boxes: no box penetration
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) pa += __shfl_xor_sync(FULL, pa, off);
     }
     if (lane == 0) {
         w.ncon = base < M.maxc ? base : M.maxc;
@@ -1395,17 +1400,22 @@ __device__ __forceinline__ void integrate(const DevModel& M, WarpWS<NA>& w, int 
     if (lane == 31) {
         const float* om = &w.v[d::B + 3];
         const float th[3] = {om[0] * dt, om[1] * dt, om[2] * dt};
-        const float ang = sqrtf(dot3(th, th));
-        float dq0 = 1.0f, dq1 = 0.0f, dq2 = 0.0f, dq3 = 0.0f;
-        if (ang > 0.0f) {
+        // dq = (cos x, th sin(x) / (2x)) with x = |th| / 2.  For x < 1/2 both
+        // factors are their Taylor series in x^2 to the x^8 term (truncation
+        // below 3e-10), which needs neither the square root nor the sine.
+        const float a2 = dot3(th, th), x2 = 0.25f * a2;
+        float dq0, kq;
+        if (x2 < 0.25f) {
+            dq0 = 1.0f + x2 * (-0.5f + x2 * (1.0f / 24.0f + x2 * (-1.0f / 720.0f + x2 * (1.0f / 40320.0f))));
+            kq = 0.5f + x2 * (-1.0f / 12.0f + x2 * (1.0f / 240.0f + x2 * (-1.0f / 10080.0f + x2 * (1.0f / 725760.0f))));
+        } else {
+            const float ang = sqrtf(a2);
             float s, c;
             sincosf(0.5f * ang, &s, &c);
-            const float k = s / ang;
             dq0 = c;
-            dq1 = th[0] * k;
-            dq2 = th[1] * k;
-            dq3 = th[2] * k;
+            kq = s / ang;
         }
+        const float dq1 = th[0] * kq, dq2 = th[1] * kq, dq3 = th[2] * kq;
         float* qq = &w.q[d::B + 3];
         const float w0 = qq[0], x0 = qq[1], y0 = qq[2], z0 = qq[3];
         float nw = dq0 * w0 - dq1 * x0 - dq2 * y0 - dq3 * z0;

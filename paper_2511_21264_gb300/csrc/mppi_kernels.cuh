@@ -48,6 +48,7 @@ __device__ __forceinline__ float rollout_sample(const DevModel& M, WarpWS<NA>& w
     float cost = 0.0f;
     const float* gb = M.goal;
     unsigned n_exact = 0, n_con = 0;
+    float uacc = 0.0f;  // this lane's control's sum of squares over the horizon
     TaskAcc<NA> tacc;
     if constexpr (TASK) {
 #pragma unroll
@@ -78,11 +79,15 @@ __device__ __forceinline__ float rollout_sample(const DevModel& M, WarpWS<NA>& w
                 } else {
                     acc = __fmaf_rn(io.sig, w.zn[h & 7][lane], acc);
                 }
-                w.u[lane] = fminf(fmaxf(acc, io.lo), io.hi);
-                if (io.U_store) io.U_store[((size_t)h * io.Kn + k) * d::NU + lane] = w.u[lane];
+                const float uv = fminf(fmaxf(acc, io.lo), io.hi);
+                w.u[lane] = uv;
+                uacc = __fmaf_rn(uv, uv, uacc);
+                if (io.U_store) io.U_store[((size_t)h * io.Kn + k) * d::NU + lane] = uv;
             }
         } else if (lane < d::NU) {
-            w.u[lane] = io.U[h * io.u_stride + lane];
+            const float uv = io.U[h * io.u_stride + lane];
+            w.u[lane] = uv;
+            uacc = __fmaf_rn(uv, uv, uacc);
         }
         float Rl[9], cl[3];  // this lane's link rotation and COM, kept for the dynamics
         forward_kinematics<NA>(M, w, lane, Rl, cl);
@@ -98,14 +103,10 @@ __device__ __forceinline__ float rollout_sample(const DevModel& M, WarpWS<NA>& w
         dynamics<NA>(M, w, lane, io.err, Rl, cl);
         contacts<NA>(M, w, lane);
         integrate<NA>(M, w, lane);
-        if (!TASK && lane == 0) {
+        if (!TASK && lane == 0) {  // the control term is added after the horizon
             const float* pb = &w.q[d::B];
             const float e0 = pb[0] - gb[0], e1 = pb[1] - gb[1], e2 = pb[2] - gb[2];
-            float uu = 0.0f;
-#pragma unroll
-            for (int j = 0; j < d::NU; ++j) uu += w.u[j] * w.u[j];
-            cost += M.w_goal * (e0 * e0 + e1 * e1 + e2 * e2) + M.w_u * uu + M.w_pen * w.pen_all +
-                    M.w_obst * w.pen_box;
+            cost += M.w_goal * (e0 * e0 + e1 * e1 + e2 * e2) + M.w_pen * w.pen_all + M.w_obst * w.pen_box;
         }
         __syncwarp();
     }
@@ -120,6 +121,11 @@ __device__ __forceinline__ float rollout_sample(const DevModel& M, WarpWS<NA>& w
         forward_kinematics<NA>(M, w, lane, Rl, cl);
         __syncwarp();
         if (lane == 0) cost += M.w_grasp * grasp_term<NA>(w);
+    }
+    if constexpr (!TASK) {  // w_u sum_h |u_h|^2: the lanes' sums, in a fixed tree
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) uacc += __shfl_xor_sync(FULL, uacc, off);
+        cost += M.w_u * uacc;
     }
     // a non-finite state poisons the sample's cost (weight 0 in the update)
     const bool bad = (lane < d::NQ && !isfinite(w.q[lane])) || (lane < d::NV && !isfinite(w.qd[lane]));
