@@ -528,15 +528,19 @@ __device__ __forceinline__ int collide(const DevModel& M, WarpWS<NA>& w, int lan
         }
         base += __popc(mask);
     }
-    // capsule-box: one lane per link tests its capsule against every box
-    // (bounding sphere and axis-aligned overlap, both conservative); the
-    // survivors are placed link-major, box-minor by a warp prefix sum
+    // capsule-box: lanes l and 16 + l test link l's capsule against the first
+    // and the second half of the boxes (bounding sphere and axis-aligned
+    // overlap, both conservative); the survivors are placed link-major,
+    // box-minor by a prefix sum over the links
     if (nb > 0) {
+        const int l = lane & 15, half = lane >> 4;
+        const int bsplit = (nb + 1) >> 1;
+        const int b0 = half ? bsplit : 0, b1 = half ? nb : bsplit;
         unsigned smask = 0u;
-        if (lane < d::NL) {
-            const float* a0 = w.a0[lane];
-            const float* a1 = w.a1[lane];
-            const float rc = M.link[lane / NA][lane % NA].rcap;
+        if (l < d::NL) {
+            const float* a0 = w.a0[l];
+            const float* a1 = w.a1[l];
+            const float rc = M.link[l / NA][l % NA].rcap;
             float mid[3], lo[3], hi[3];
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
@@ -546,7 +550,7 @@ __device__ __forceinline__ int collide(const DevModel& M, WarpWS<NA>& w, int lan
             }
             const float dx = a1[0] - a0[0], dy = a1[1] - a0[1], dz = a1[2] - a0[2];
             const float rad = 0.5f * sqrtf(dx * dx + dy * dy + dz * dz) + rc;
-            for (int bi = 0; bi < nb; ++bi) {
+            for (int bi = b0; bi < b1; ++bi) {
                 const float* box = M.box[bi];
                 float lb2 = 0.0f;
                 bool ov = true;
@@ -560,19 +564,20 @@ __device__ __forceinline__ int collide(const DevModel& M, WarpWS<NA>& w, int lan
             }
         }
         const int cnt = __popc(smask);
-        int pre = cnt;  // inclusive prefix over lanes
+        const int cnt_link = cnt + __shfl_xor_sync(FULL, cnt, 16);  // both halves of link l
+        int pre = cnt_link;  // inclusive prefix over the links (both half-warps alike)
 #pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const int o = __shfl_up_sync(FULL, pre, off);
-            if (lane >= off) pre += o;
+        for (int off = 1; off < 16; off <<= 1) {
+            const int o = __shfl_up_sync(FULL, pre, off, 16);
+            if (l >= off) pre += o;
         }
-        int pos = pre - cnt;
+        int pos = pre - cnt_link + (half ? cnt_link - cnt : 0);
         while (smask) {
             const int bi = __ffs(smask) - 1;
             smask &= smask - 1u;
-            w.ph.col.surv[pos++] = (short)(lane * nb + bi);
+            w.ph.col.surv[pos++] = (short)(l * nb + bi);
         }
-        nsurv = __shfl_sync(FULL, pre, 31);
+        nsurv = __shfl_sync(FULL, pre, 15);
     }
     __syncwarp();
     for (int si = 0; si < nsurv; ++si) {
