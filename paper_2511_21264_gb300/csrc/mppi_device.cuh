@@ -98,8 +98,6 @@ struct __align__(16) WarpWS {
     int cB[MAXC];
     int ncon;
     int nact;
-    float pen_all;
-    float pen_box;
     float ee[2][10];  // task cost: end-effector position, velocity, quaternion per arm
     union Phase {
         struct {
@@ -455,17 +453,17 @@ __device__ __forceinline__ float capsule_box_candidate(int id, const float* a, c
 // links x boxes).  Ball pairs: one lane per pair, exact, compacted with a
 // ballot.  Capsule-box pairs: a conservative bounding-sphere cull per lane,
 // then each surviving pair (in pair order) is minimised by the whole warp
-// over the candidate set above.  Returns the number of exact capsule-box
-// tests on lane 0 (0 on the other lanes).
+// over the candidate set above.  Each lane adds the depths of the contacts
+// it found to pa (all) and pbox (against boxes).  Returns the number of
+// exact capsule-box tests on lane 0 (0 on the other lanes).
 template <int NA>
-__device__ __forceinline__ int collide(const DevModel& M, WarpWS<NA>& w, int lane) {
+__device__ __forceinline__ int collide(const DevModel& M, WarpWS<NA>& w, int lane, float& pa, float& pbox) {
     using d = Dims<NA>;
     const int nb = M.nb;
     const int nball = 1 + d::NL + nb;
     const float* pb = &w.q[d::B];
     const float rb = M.rb;
     int base = 0, nsurv = 0;
-    float pa = 0.0f, pbox = 0.0f;
     for (int p0 = 0; p0 < nball; p0 += 32) {
         const int p = p0 + lane;
         bool active = false, isbox = false;
@@ -626,21 +624,9 @@ __device__ __forceinline__ int collide(const DevModel& M, WarpWS<NA>& w, int lan
             ++base;
         }
     }
-    if (nb > 0) {
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            pa += __shfl_xor_sync(FULL, pa, off);
-            pbox += __shfl_xor_sync(FULL, pbox, off);
-        }
-    } else {  // no boxes: no box penetration
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) pa += __shfl_xor_sync(FULL, pa, off);
-    }
     if (lane == 0) {
         w.ncon = base < M.maxc ? base : M.maxc;
         w.nact = base;
-        w.pen_all = pa;
-        w.pen_box = pbox;
     }
     return lane == 0 ? nsurv : 0;
 }

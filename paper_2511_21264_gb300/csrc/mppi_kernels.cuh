@@ -49,6 +49,7 @@ __device__ __forceinline__ float rollout_sample(const DevModel& M, WarpWS<NA>& w
     const float* gb = M.goal;
     unsigned n_exact = 0, n_con = 0;
     float uacc = 0.0f;  // this lane's control's sum of squares over the horizon
+    float pacc = 0.0f, pbacc = 0.0f;  // this lane's contacts' depths (all, against boxes) over the horizon
     TaskAcc<NA> tacc;
     if constexpr (TASK) {
 #pragma unroll
@@ -97,16 +98,16 @@ __device__ __forceinline__ float rollout_sample(const DevModel& M, WarpWS<NA>& w
         } else {
             if (h > 0 && lane == 0 && M.w_grasp != 0.0f) cost += M.w_grasp * grasp_term<NA>(w);
         }
-        n_exact += collide<NA>(M, w, lane);
+        n_exact += collide<NA>(M, w, lane, pacc, pbacc);
         __syncwarp();
         n_con += w.ncon;
         dynamics<NA>(M, w, lane, io.err, Rl, cl);
         contacts<NA>(M, w, lane);
         integrate<NA>(M, w, lane);
-        if (!TASK && lane == 0) {  // the control term is added after the horizon
+        if (!TASK && lane == 0) {  // the control and penetration terms are added after the horizon
             const float* pb = &w.q[d::B];
             const float e0 = pb[0] - gb[0], e1 = pb[1] - gb[1], e2 = pb[2] - gb[2];
-            cost += M.w_goal * (e0 * e0 + e1 * e1 + e2 * e2) + M.w_pen * w.pen_all + M.w_obst * w.pen_box;
+            cost += M.w_goal * (e0 * e0 + e1 * e1 + e2 * e2);
         }
         __syncwarp();
     }
@@ -122,10 +123,16 @@ __device__ __forceinline__ float rollout_sample(const DevModel& M, WarpWS<NA>& w
         __syncwarp();
         if (lane == 0) cost += M.w_grasp * grasp_term<NA>(w);
     }
-    if constexpr (!TASK) {  // w_u sum_h |u_h|^2: the lanes' sums, in a fixed tree
+    if constexpr (!TASK) {
+        // w_u sum_h |u_h|^2 + w_pen sum_h pen_h + w_obst sum_h pen_box_h from
+        // the lanes' sums, each reduced in a fixed butterfly order
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) uacc += __shfl_xor_sync(FULL, uacc, off);
-        cost += M.w_u * uacc;
+        for (int off = 16; off > 0; off >>= 1) {
+            uacc += __shfl_xor_sync(FULL, uacc, off);
+            pacc += __shfl_xor_sync(FULL, pacc, off);
+            pbacc += __shfl_xor_sync(FULL, pbacc, off);
+        }
+        cost += M.w_u * uacc + M.w_pen * pacc + M.w_obst * pbacc;
     }
     // a non-finite state poisons the sample's cost (weight 0 in the update)
     const bool bad = (lane < d::NQ && !isfinite(w.q[lane])) || (lane < d::NV && !isfinite(w.qd[lane]));
