@@ -1424,20 +1424,14 @@ __device__ __forceinline__ void integrate(const DevModel& M, WarpWS<NA>& w, int 
     __syncwarp();
 }
 
-// grasp-maintenance term || p_L + p_R - 2 p_ball ||^2 on the current FK
+// coordinate k of the grasp-maintenance error p_L + p_R - 2 p_ball, squared,
+// on the current FK
 template <int NA>
-__device__ __forceinline__ float grasp_term(const WarpWS<NA>& w) {
+__device__ __forceinline__ float grasp_coord(const WarpWS<NA>& w, int k) {
     using d = Dims<NA>;
-    const float* pl = w.a1[NA - 1];
-    const float* pr = w.a1[2 * NA - 1];
-    const float* pb = &w.q[d::B];
-    float s = 0.0f;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const float e = pl[k] + pr[k] - 2.0f * pb[k];
-        s += e * e;
-    }
-    return s;
+    const float e = w.a1[NA - 1][k] + w.a1[2 * NA - 1][k] - 2.0f * w.q[d::B + k];
+    return e * e;
 }
+
 
 }  // namespace mppi

@@ -50,6 +50,8 @@ __device__ __forceinline__ float rollout_sample(const DevModel& M, WarpWS<NA>& w
     unsigned n_exact = 0, n_con = 0;
     float uacc = 0.0f;  // this lane's control's sum of squares over the horizon
     float pacc = 0.0f, pbacc = 0.0f;  // this lane's contacts' depths (all, against boxes) over the horizon
+    float gacc = 0.0f;  // squared goal error of this lane's ball coordinate over the horizon
+    float kacc = 0.0f;  // squared grasp error (p_L + p_R - 2 p_ball) of this lane's coordinate
     TaskAcc<NA> tacc;
     if constexpr (TASK) {
 #pragma unroll
@@ -96,7 +98,7 @@ __device__ __forceinline__ float rollout_sample(const DevModel& M, WarpWS<NA>& w
         if constexpr (TASK) {
             task_state<NA>(M, *io.task, w, lane, Rl, h == 0, tacc);
         } else {
-            if (h > 0 && lane == 0 && M.w_grasp != 0.0f) cost += M.w_grasp * grasp_term<NA>(w);
+            if (h > 0 && lane < 3 && M.w_grasp != 0.0f) kacc += grasp_coord<NA>(w, lane);
         }
         n_exact += collide<NA>(M, w, lane, pacc, pbacc);
         __syncwarp();
@@ -104,10 +106,9 @@ __device__ __forceinline__ float rollout_sample(const DevModel& M, WarpWS<NA>& w
         dynamics<NA>(M, w, lane, io.err, Rl, cl);
         contacts<NA>(M, w, lane);
         integrate<NA>(M, w, lane);
-        if (!TASK && lane == 0) {  // the control and penetration terms are added after the horizon
-            const float* pb = &w.q[d::B];
-            const float e0 = pb[0] - gb[0], e1 = pb[1] - gb[1], e2 = pb[2] - gb[2];
-            cost += M.w_goal * (e0 * e0 + e1 * e1 + e2 * e2);
+        if (!TASK && lane >= d::B && lane < d::B + 3) {  // the ball coordinate this lane integrated
+            const float e = w.q[lane] - gb[lane - d::B];
+            gacc = __fmaf_rn(e, e, gacc);
         }
         __syncwarp();
     }
@@ -121,18 +122,21 @@ __device__ __forceinline__ float rollout_sample(const DevModel& M, WarpWS<NA>& w
         float Rl[9], cl[3];
         forward_kinematics<NA>(M, w, lane, Rl, cl);
         __syncwarp();
-        if (lane == 0) cost += M.w_grasp * grasp_term<NA>(w);
+        if (lane < 3) kacc += grasp_coord<NA>(w, lane);
     }
     if constexpr (!TASK) {
-        // w_u sum_h |u_h|^2 + w_pen sum_h pen_h + w_obst sum_h pen_box_h from
-        // the lanes' sums, each reduced in a fixed butterfly order
+        // w_goal sum_h |p_ball - goal|^2 + w_u sum_h |u_h|^2 + w_pen sum_h pen_h
+        // + w_obst sum_h pen_box_h + w_grasp sum_h |p_L + p_R - 2 p_ball|^2
+        // from the lanes' sums, each reduced in a fixed butterfly order
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
+            gacc += __shfl_xor_sync(FULL, gacc, off);
             uacc += __shfl_xor_sync(FULL, uacc, off);
             pacc += __shfl_xor_sync(FULL, pacc, off);
             pbacc += __shfl_xor_sync(FULL, pbacc, off);
+            kacc += __shfl_xor_sync(FULL, kacc, off);
         }
-        cost += M.w_u * uacc + M.w_pen * pacc + M.w_obst * pbacc;
+        cost += M.w_goal * gacc + M.w_u * uacc + M.w_pen * pacc + M.w_obst * pbacc + M.w_grasp * kacc;
     }
     // a non-finite state poisons the sample's cost (weight 0 in the update)
     const bool bad = (lane < d::NQ && !isfinite(w.q[lane])) || (lane < d::NV && !isfinite(w.qd[lane]));
