@@ -731,9 +731,13 @@ int mppi_best_controls(mppi_ctx* c, float* U_best, void* stream) {
                                      (cudaStream_t)stream));
 }
 
+static void drop_graph(mppi_ctx* c);
+
 int mppi_set_launch(mppi_ctx* c, int spc) {
     if (!c || spc < 0 || spc > 16) return MPPI_ERR_INVALID_ARG;
-    c->spc = spc == 0 ? default_spc(c->K) : spc;
+    const int v = spc == 0 ? default_spc(c->K) : spc;
+    if (v != c->spc) drop_graph(c);  // a captured solve holds the old launch shape
+    c->spc = v;
     return MPPI_OK;
 }
 

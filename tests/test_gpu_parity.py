@@ -114,6 +114,35 @@ def test_single_step_parity(native, cfg):
     assert np.mean(np.array(ncon) > 0) > 0.5
 
 
+def test_fast_ball_spin_rotation_step(native):
+    # the ball's rotation step is a Taylor series below |w| dt / 2 = 1/2 and
+    # the sine/cosine form above it: spins from 10 to 300 rad/s about random
+    # axes, ball lifted clear of every contact, against the oracle's step
+    n = 64
+    sc, gm, om, ctl, _ = _setup(2, K=n, H=1)
+    X = scenes.random_states(sc, n, seed=7, ball_lift=3.0)
+    rng = np.random.default_rng(7)
+    axis = rng.normal(size=(n, 3))
+    axis /= np.linalg.norm(axis, axis=1, keepdims=True)
+    speed = np.geomspace(10.0, 300.0, n)
+    w0 = sc.nq + 2 * sc.n_a + 3
+    X[:, w0:w0 + 3] = axis * speed[:, None]
+    X = _f32(X)
+    half = speed * sc.dt / 2
+    assert (half < 0.5).any() and (half >= 0.5).any()
+    U1 = np.zeros((n, sc.nu))
+    xs = _t(X)
+    ctl.sim_step(xs, _t(U1))
+    assert ctl.sync() == 0
+    G = xs.cpu().numpy().astype(np.float64)
+    q0 = 2 * sc.n_a + 3
+    for i in range(n):
+        xo, info = om.step(X[i], U1[i])
+        assert info.ncon == 0
+        assert np.abs(G[i, q0:q0 + 4] - xo[q0:q0 + 4]).max() <= 1e-5, (i, speed[i])
+        assert np.abs(G[i] - xo).max() <= 1e-4 * max(1.0, np.abs(xo).max()), (i, speed[i])
+
+
 def _traj_ok(om, x, U, gap=1e-5):
     c, T = om.rollout(x, U, traj=True)
     return all(om.min_abs_dist(T[h]) > gap for h in range(T.shape[0] - 1)), c, T
@@ -240,6 +269,33 @@ def test_step_aliasing_and_graph_replay_are_deterministic(native):
     s.synchronize()
     assert torch.equal(u1, u2) and torch.equal(u2, u3)
     assert float(u1.abs().max()) > 0
+
+
+def test_launch_shape_does_not_change_results(native):
+    # one sample per CTA (the default below 8 x the SM count, plain launches)
+    # and 2, 4 or 16 samples per CTA (programmatic dependent launches): the
+    # same iterations, bitwise, eager and from the captured graph
+    K, H = 1024, 32
+    sc, gm, om, ctl, key = _setup(2, K=K, H=H)
+    x = _t(_f32(sc.x0))
+    s = torch.cuda.Stream()
+    outs = []
+    with torch.cuda.stream(s):
+        for spc in (0, 1, 2, 4, 16):
+            ctl.set_launch(spc)
+            for graph in (False, True):
+                ctl.set_iteration(0, stream=s)
+                u = torch.zeros((H, sc.nu), device=DEV)
+                if graph:
+                    ctl.solve(x, u, 3, stream=s)
+                else:
+                    for _ in range(3):
+                        ctl.step(x, u, u, stream=s)
+                outs.append(u)
+        assert ctl.sync(stream=s) == 0
+    s.synchronize()
+    assert all(torch.equal(outs[0], o) for o in outs[1:])
+    assert float(outs[0].abs().max()) > 0.0
 
 
 def test_edge_cases(native):
