@@ -98,6 +98,7 @@ struct __align__(16) WarpWS {
     int cB[MAXC];
     int ncon;
     int nact;
+    int tb;  // blocks the stored contacts touch: 1 left arm, 2 right arm, 4 ball
     float ee[2][10];  // task cost: end-effector position, velocity, quaternion per arm
     union Phase {
         struct {
@@ -464,6 +465,7 @@ __device__ __forceinline__ int collide(const DevModel& M, WarpWS<NA>& w, int lan
     const float* pb = &w.q[d::B];
     const float rb = M.rb;
     int base = 0, nsurv = 0;
+    unsigned tbits = 0u;  // blocks the stored contacts touch
     for (int p0 = 0; p0 < nball; p0 += 32) {
         const int p = p0 + lane;
         bool active = false, isbox = false;
@@ -514,6 +516,7 @@ __device__ __forceinline__ int collide(const DevModel& M, WarpWS<NA>& w, int lan
             pa += -dist;
             if (isbox) pbox += -dist;
             if (pos < M.maxc) {
+                tbits |= 4u | (Bb >= 0 ? 1u << (Bb / NA) : 0u);
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
                     w.cp[pos][k] = cp[k];
@@ -611,6 +614,7 @@ __device__ __forceinline__ int collide(const DevModel& M, WarpWS<NA>& w, int lan
                 pa += -dist;
                 pbox += -dist;
                 if (base < M.maxc) {
+                    tbits |= 1u << (l / NA);
 #pragma unroll
                     for (int k = 0; k < 3; ++k) {
                         w.cp[base][k] = 0.5f * ((x[k] - rc * nn[k]) + surf[k]);
@@ -624,9 +628,11 @@ __device__ __forceinline__ int collide(const DevModel& M, WarpWS<NA>& w, int lan
             ++base;
         }
     }
+    tbits = __reduce_or_sync(FULL, tbits);
     if (lane == 0) {
         w.ncon = base < M.maxc ? base : M.maxc;
         w.nact = base;
+        w.tb = (int)tbits;
     }
     return lane == 0 ? nsurv : 0;
 }
@@ -813,13 +819,7 @@ __device__ __forceinline__ void dynamics(const DevModel& M, WarpWS<NA>& w, int l
     // (6) Cholesky of each arm block (in registers), the free velocity; ball.
     //     The factor is kept only for arms a contact touches (the contact
     //     solve's rows need it there).
-    int armc = 0;
-    if (lane < w.ncon) {
-        const int A = w.cA[lane], Bb = w.cB[lane];
-        if (A >= 0 && A < d::B) armc |= 1 << (A / NA);
-        if (Bb >= 0 && Bb < d::B) armc |= 1 << (Bb / NA);
-    }
-    armc = (int)__reduce_or_sync(FULL, (unsigned)armc);
+    const int armc = w.tb & 3;
     if (i == 0) {
         float A[NA][NA];
 #pragma unroll
@@ -1116,16 +1116,10 @@ __device__ __forceinline__ void contacts(const DevModel& M, WarpWS<NA>& w, int l
         return;
     }
     const float ismb = rsqrtf(M.mb), isIb = rsqrtf(M.Ib);
-    // blocks any contact touches (warp-uniform): 1 left arm, 2 right arm,
-    // 4 ball.  Untouched blocks keep v = v_f and skip the z-space work.
-    int tb = 0;
-    if (lane < nc) {
-        const int A = w.cA[lane], Bb = w.cB[lane];
-        if (A == d::B || Bb == d::B) tb |= 4;
-        if (A >= 0 && A < d::B) tb |= 1 << (A / NA);
-        if (Bb >= 0 && Bb < d::B) tb |= 1 << (Bb / NA);
-    }
-    tb = (int)__reduce_or_sync(FULL, (unsigned)tb);
+    // blocks any contact touches (warp-uniform, from the narrow phase): 1
+    // left arm, 2 right arm, 4 ball.  Untouched blocks keep v = v_f and skip
+    // the z-space work.
+    const int tb = w.tb;
     if (tb == 4 && nc <= 2) {  // ball against static geometry only
         if (nc == 1) contacts_ball<NA, 1>(M, w, lane);
         else contacts_ball<NA, 2>(M, w, lane);
