@@ -98,7 +98,6 @@ struct __align__(16) WarpWS {
     int cB[MAXC];
     int ncon;
     int nact;
-    int tb;  // blocks the stored contacts touch: 1 left arm, 2 right arm, 4 ball
     float ee[2][10];  // task cost: end-effector position, velocity, quaternion per arm
     union Phase {
         struct {
@@ -455,10 +454,13 @@ __device__ __forceinline__ float capsule_box_candidate(int id, const float* a, c
 // ballot.  Capsule-box pairs: a conservative bounding-sphere cull per lane,
 // then each surviving pair (in pair order) is minimised by the whole warp
 // over the candidate set above.  Each lane adds the depths of the contacts
-// it found to pa (all) and pbox (against boxes).  Returns the number of
-// exact capsule-box tests on lane 0 (0 on the other lanes).
+// it found to pa (all) and pbox (against boxes); every lane gets the number
+// of stored contacts (ncon) and the blocks they touch (tb: 1 left arm, 2
+// right arm, 4 ball).  Returns the number of exact capsule-box tests on
+// lane 0 (0 on the other lanes).
 template <int NA>
-__device__ __forceinline__ int collide(const DevModel& M, WarpWS<NA>& w, int lane, float& pa, float& pbox) {
+__device__ __forceinline__ int collide(const DevModel& M, WarpWS<NA>& w, int lane, float& pa, float& pbox, int& ncon,
+                                      int& tb) {
     using d = Dims<NA>;
     const int nb = M.nb;
     const int nball = 1 + d::NL + nb;
@@ -628,11 +630,11 @@ __device__ __forceinline__ int collide(const DevModel& M, WarpWS<NA>& w, int lan
             ++base;
         }
     }
-    tbits = __reduce_or_sync(FULL, tbits);
+    tb = (int)__reduce_or_sync(FULL, tbits);
+    ncon = base < M.maxc ? base : M.maxc;
     if (lane == 0) {
-        w.ncon = base < M.maxc ? base : M.maxc;
+        w.ncon = ncon;
         w.nact = base;
-        w.tb = (int)tbits;
     }
     return lane == 0 ? nsurv : 0;
 }
@@ -670,7 +672,7 @@ __device__ __forceinline__ void seg_prefix_sum(float (&v)[N], int i, int nlinks)
 
 template <int NA>
 __device__ __forceinline__ void dynamics(const DevModel& M, WarpWS<NA>& w, int lane, int* err, const float (&R)[9],
-                                         const float (&cl)[3]) {
+                                         const float (&cl)[3], int tb) {
     using d = Dims<NA>;
     const int a = lane >> 4, i = lane & 15;
     const bool act = i < NA;
@@ -819,7 +821,7 @@ __device__ __forceinline__ void dynamics(const DevModel& M, WarpWS<NA>& w, int l
     // (6) Cholesky of each arm block (in registers), the free velocity; ball.
     //     The factor is kept only for arms a contact touches (the contact
     //     solve's rows need it there).
-    const int armc = w.tb & 3;
+    const int armc = tb & 3;
     if (i == 0) {
         float A[NA][NA];
 #pragma unroll
@@ -1107,19 +1109,16 @@ __device__ __forceinline__ void pgs_small(const DevModel& M, WarpWS<NA>& w, int 
 // v_f; after the sweeps v = L^-T (z_f + Y^T lambda).  This is the same
 // iteration as updating v row by row (J_r v = b_r + (G lambda)_r).
 template <int NA>
-__device__ __forceinline__ void contacts(const DevModel& M, WarpWS<NA>& w, int lane) {
+__device__ __forceinline__ void contacts(const DevModel& M, WarpWS<NA>& w, int lane, int nc, int tb) {
     using d = Dims<NA>;
-    const int nc = w.ncon;
     if (nc == 0) {
         if (lane < d::NV) w.v[lane] = w.vf[lane];
         __syncwarp();
         return;
     }
     const float ismb = rsqrtf(M.mb), isIb = rsqrtf(M.Ib);
-    // blocks any contact touches (warp-uniform, from the narrow phase): 1
-    // left arm, 2 right arm, 4 ball.  Untouched blocks keep v = v_f and skip
-    // the z-space work.
-    const int tb = w.tb;
+    // tb: the blocks any contact touches (warp-uniform, from the narrow
+    // phase).  Untouched blocks keep v = v_f and skip the z-space work.
     if (tb == 4 && nc <= 2) {  // ball against static geometry only
         if (nc == 1) contacts_ball<NA, 1>(M, w, lane);
         else contacts_ball<NA, 2>(M, w, lane);

@@ -100,11 +100,12 @@ __device__ __forceinline__ float rollout_sample(const DevModel& M, WarpWS<NA>& w
         } else {
             if (h > 0 && lane < 3 && M.w_grasp != 0.0f) kacc += grasp_coord<NA>(w, lane);
         }
-        n_exact += collide<NA>(M, w, lane, pacc, pbacc);
+        int ncon, tb;
+        n_exact += collide<NA>(M, w, lane, pacc, pbacc, ncon, tb);
         __syncwarp();
-        n_con += w.ncon;
-        dynamics<NA>(M, w, lane, io.err, Rl, cl);
-        contacts<NA>(M, w, lane);
+        n_con += ncon;
+        dynamics<NA>(M, w, lane, io.err, Rl, cl, tb);
+        contacts<NA>(M, w, lane, ncon, tb);
         integrate<NA>(M, w, lane);
         if (!TASK && lane >= d::B && lane < d::B + 3) {  // the ball coordinate this lane integrated
             const float e = w.q[lane] - gb[lane - d::B];
