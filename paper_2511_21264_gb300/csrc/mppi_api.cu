@@ -121,6 +121,44 @@ __global__ void __launch_bounds__(1024) elite_select_kernel(const float* costs, 
                                                             unsigned long long* sel, int* eidx) {
     extern __shared__ unsigned long long keys[];
     __shared__ int nfin;
+    if (P <= 1024) {
+        // one key per thread (padding keys sort last): the same bitonic
+        // network in registers, partners by shuffles below stride 32 and
+        // through a double-buffered shared array above
+        const int t = threadIdx.x;
+        unsigned long long x = ~0ull;
+        bool fin = false;
+        if (t < K) {
+            const float c = costs[t];
+            x = cost_key(c, t);
+            fin = isfinite(c);
+        }
+        const int nf = __syncthreads_count(fin);
+        int buf = 0;
+        for (int size = 2; size <= 1024; size <<= 1)
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                unsigned long long y;
+                if (stride >= 32) {
+                    keys[buf * 1024 + t] = x;
+                    __syncthreads();
+                    y = keys[buf * 1024 + (t ^ stride)];
+                    buf ^= 1;
+                } else {
+                    y = __shfl_xor_sync(0xffffffffu, x, stride);
+                }
+                const bool asc = (t & size) == 0, lower = (t & stride) == 0;
+                x = (lower == asc) ? (x < y ? x : y) : (x < y ? y : x);
+            }
+        const int ne = nf == 0 ? 0 : (n_elite < nf ? n_elite : nf);
+        if (t < ne) eidx[t] = (int)(x & 0xFFFFFFFFull);
+        if (t == 0) {
+            sel[1] = x;
+            sel[2] = (unsigned long long)nf;
+            if (ne == 0) sel[0] = 0ull;
+        }
+        if (ne > 0 && t == ne - 1) sel[0] = x;
+        return;
+    }
     if (threadIdx.x == 0) nfin = 0;
     __syncthreads();
     int mine = 0;
@@ -913,7 +951,9 @@ static int launch_elite(mppi_ctx* c, const float* costs, const float* u_nom, flo
     const int nu = 2 * c->m->info.na;
     int P = 1;
     while (P < c->K) P <<= 1;
-    const size_t sm = (size_t)P * sizeof(unsigned long long);
+    // keys in shared memory: all P of them, or the two 1024-key buffers of
+    // the register network (P <= 1024)
+    const size_t sm = (size_t)(P <= 1024 ? 2048 : P) * sizeof(unsigned long long);
     if (sm > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(elite_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return cuda_fail(e);

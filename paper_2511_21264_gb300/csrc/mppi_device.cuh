@@ -96,8 +96,6 @@ struct __align__(16) WarpWS {
     float cdep[MAXC];
     int cA[MAXC];
     int cB[MAXC];
-    int ncon;
-    int nact;
     float ee[2][10];  // task cost: end-effector position, velocity, quaternion per arm
     union Phase {
         struct {
@@ -632,10 +630,6 @@ __device__ __forceinline__ int collide(const DevModel& M, WarpWS<NA>& w, int lan
     }
     tb = (int)__reduce_or_sync(FULL, tbits);
     ncon = base < M.maxc ? base : M.maxc;
-    if (lane == 0) {
-        w.ncon = ncon;
-        w.nact = base;
-    }
     return lane == 0 ? nsurv : 0;
 }
 
