@@ -241,22 +241,17 @@ def run_ours(args):
         qp_ms = ctl.profile_projection() / max(1, kt["iterations"])
         ctl.profile(0)
 
-        # end to end through the public API with host buffers: pinned H2D
-        # copy of (state, u_nom), the iteration, D2H read of u_nom'
-        xh = torch.tensor(model.home()).pin_memory()
-        uh = torch.zeros((H, sc.nu)).pin_memory()
-        uo = torch.empty((H, sc.nu)).pin_memory()
-        xd, ud = torch.empty_like(x), torch.empty_like(u)
+        # end to end through the C ABI with host buffers (mppi_step_host): per
+        # step one H2D copy of (state, u_nom) through the handle's pinned
+        # staging buffer, the iteration, one D2H copy of u_nom', synchronised
+        xh = np.asarray(model.home(), np.float32)
+        uh = np.zeros((H, sc.nu), np.float32)
+        ctl.step_host(xh, uh, uh, stream=stream)  # allocates the staging buffers
         _barrier(world)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for i in range(args.steps):
-            xd.copy_(xh, non_blocking=True)
-            ud.copy_(uh, non_blocking=True)
-            ctl.step(xd, ud, ud, stream=stream)
-            uo.copy_(ud, non_blocking=True)
-            stream.synchronize()
-            uh.copy_(uo)
+            ctl.step_host(xh, uh, uh, stream=stream)
         e1.record(stream)
         stream.synchronize()
         e2e_ms = _max_over_ranks(e0.elapsed_time(e1), world)

@@ -94,6 +94,13 @@ int mppi_destroy(mppi_ctx *c);
  * handle's iteration counter (on the device) by one. */
 int mppi_step(mppi_ctx *c, const float *state, const float *u_nom, float *u_nom_out, void *stream);
 
+/* The same iteration with HOST buffers (state: nx floats, u_nom and
+ * u_nom_out: H x nu floats, may alias): one copy of (state, u_nom) to the
+ * device through a pinned staging buffer the handle owns (allocated on the
+ * first call), the iteration, one copy of u_nom' back; returns after the
+ * stream has synchronised.  Not capturable. */
+int mppi_step_host(mppi_ctx *c, const float *state, const float *u_nom, float *u_nom_out, void *stream);
+
 /* `iters` iterations of mppi_step in place on u_nom_inout (Alg. 1, M =
  * iters).  best_cost_out (optional, 2 floats): lowest sample cost of the
  * last iteration and its sample index (as float).  After the first call

@@ -411,6 +411,8 @@ struct mppi_ctx {
     float lambda = 1.0f;
     uint64_t seed = 0;
     float* d_sigma = nullptr;
+    float* h_stage = nullptr;  // pinned staging of mppi_step_host: state, u_nom, u_nom_out
+    float* d_stage = nullptr;  // its device copy: state, u_nom (updated in place)
     float* d_ulo = nullptr;
     float* d_uhi = nullptr;
     float* d_costs = nullptr;
@@ -535,6 +537,8 @@ int mppi_destroy(mppi_ctx* c) {
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->graph) cudaGraphDestroy(c->graph);
     cudaFree(c->d_sigma);
+    cudaFreeHost(c->h_stage);
+    cudaFree(c->d_stage);
     cudaFree(c->d_ulo);
     cudaFree(c->d_uhi);
     cudaFree(c->d_costs);
@@ -1061,6 +1065,36 @@ int mppi_step(mppi_ctx* c, const float* state, const float* u_nom, float* u_nom_
     if (!c || !state || !u_nom || !u_nom_out) return MPPI_ERR_INVALID_ARG;
     NvtxRange r("mppi_step");
     return enqueue_step(c, state, u_nom, u_nom_out, c->d_best, (cudaStream_t)stream);
+}
+
+int mppi_step_host(mppi_ctx* c, const float* state, const float* u_nom, float* u_nom_out, void* stream) {
+    if (!c || !state || !u_nom || !u_nom_out) return MPPI_ERR_INVALID_ARG;
+    NvtxRange r("mppi_step_host");
+    const int na = c->m->info.na, nx = 4 * na + 13, nu_h = c->H * 2 * na;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    if (!c->h_stage) {
+        e = cudaMallocHost(&c->h_stage, (size_t)(nx + 2 * nu_h) * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc(&c->d_stage, (size_t)(nx + nu_h) * sizeof(float));
+        if (e != cudaSuccess) {
+            cudaFreeHost(c->h_stage);
+            c->h_stage = nullptr;
+            return e == cudaErrorMemoryAllocation ? MPPI_ERR_OOM : cuda_fail(e);
+        }
+    }
+    // one H2D copy of (state, u_nom), the iteration in place, one D2H copy
+    std::memcpy(c->h_stage, state, (size_t)nx * sizeof(float));
+    std::memcpy(c->h_stage + nx, u_nom, (size_t)nu_h * sizeof(float));
+    e = cudaMemcpyAsync(c->d_stage, c->h_stage, (size_t)(nx + nu_h) * sizeof(float), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    int rc = enqueue_step(c, c->d_stage, c->d_stage + nx, c->d_stage + nx, c->d_best, s);
+    if (rc != MPPI_OK) return rc;
+    e = cudaMemcpyAsync(c->h_stage + nx + nu_h, c->d_stage + nx, (size_t)nu_h * sizeof(float), cudaMemcpyDeviceToHost,
+                        s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    std::memcpy(u_nom_out, c->h_stage + nx + nu_h, (size_t)nu_h * sizeof(float));
+    return MPPI_OK;
 }
 
 int mppi_solve(mppi_ctx* c, const float* state, float* u, int iters, float* best_out, void* stream) {

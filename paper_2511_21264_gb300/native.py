@@ -110,6 +110,7 @@ def lib():
     _decl(L, "mppi_create", i, [vp, i, i, C.c_float, fp, u64, C.POINTER(vp)])
     _decl(L, "mppi_destroy", i, [vp])
     _decl(L, "mppi_step", i, [vp, fp, fp, fp, vp])
+    _decl(L, "mppi_step_host", i, [vp, vp, vp, vp, vp])
     _decl(L, "mppi_solve", i, [vp, fp, fp, i, fp, vp])
     _decl(L, "mppi_update", i, [vp, fp, fp, fp, vp])
     _decl(L, "rollout_batch", i, [vp, i, fp, fp, fp, fp, vp])
@@ -460,6 +461,21 @@ class Controller:
         u_out = u_nom if u_out is None else u_out
         _check(lib().mppi_step(self._h, _ptr(state), _ptr(u_nom), _ptr(u_out), _stream(stream)), "mppi_step")
         return u_out
+
+    def step_host(self, state, u_nom, u_out=None, stream=None):
+        """One iteration with host arrays (numpy float32: state nx, u_nom
+        H x nu); returns u_out (a new array unless given).  The library
+        stages the copies and synchronises the stream."""
+        import numpy as np
+        x = _host_f32(state, self.model.nx)
+        u = _host_f32(u_nom, self.H * self.model.nu)
+        out = np.empty((self.H, self.model.nu), np.float32) if u_out is None else u_out
+        if not (isinstance(out, np.ndarray) and out.dtype == np.float32 and out.flags.c_contiguous
+                and out.size == self.H * self.model.nu):
+            raise ValueError("u_out: C-contiguous float32 array of H x nu values")
+        _check(lib().mppi_step_host(self._h, x.ctypes.data, u.ctypes.data, out.ctypes.data, _stream(stream)),
+               "mppi_step_host")
+        return out
 
     def solve(self, state, u_nom_inout, iters: int, best=None, stream=None):
         _check(lib().mppi_solve(self._h, _ptr(state), _ptr(u_nom_inout), int(iters), _ptr(best), _stream(stream)),

@@ -271,6 +271,26 @@ def test_step_aliasing_and_graph_replay_are_deterministic(native):
     assert float(u1.abs().max()) > 0
 
 
+def test_step_with_host_buffers_matches_device_step(native):
+    # mppi_step_host (host arrays, staged copies) against mppi_step on device
+    # buffers: the same iterations, bitwise, also in place
+    K, H = 256, 16
+    sc, gm, om, ctl, key = _setup(2, K=K, H=H)
+    x = np.asarray(sc.x0, np.float32)
+    ud = torch.zeros((H, sc.nu), device=DEV)
+    for _ in range(3):
+        ctl.step(_t(x), ud, ud)
+    assert ctl.sync() == 0
+    ctl.set_iteration(0)
+    uh = np.zeros((H, sc.nu), np.float32)
+    uh = ctl.step_host(x, uh)
+    ctl.step_host(x, uh, uh)
+    ctl.step_host(x, uh, uh)
+    assert ctl.sync() == 0
+    np.testing.assert_array_equal(uh, ud.cpu().numpy())
+    assert ctl.iteration() == 3
+
+
 def test_launch_shape_does_not_change_results(native):
     # one sample per CTA (the default below 8 x the SM count, plain launches)
     # and 2, 4 or 16 samples per CTA (programmatic dependent launches): the
