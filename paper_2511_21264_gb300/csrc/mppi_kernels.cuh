@@ -77,8 +77,11 @@ __device__ __forceinline__ float rollout_sample(const DevModel& M, WarpWS<NA>& w
             if (lane < d::NU) {
                 float acc = io.unom[h * d::NU + lane];
                 if (io.Lfac) {  // u = nu + L_h z, FMAs in the order sample_row uses
+                    // (unrolled over the row so that its loads are issued together)
                     const float* Lr = io.Lfac + ((size_t)h * d::NU + lane) * d::NU;
-                    for (int i = 0; i <= lane; ++i) acc = __fmaf_rn(Lr[i], w.zn[h & 7][i], acc);
+#pragma unroll
+                    for (int i = 0; i < d::NU; ++i)
+                        if (i <= lane) acc = __fmaf_rn(Lr[i], w.zn[h & 7][i], acc);
                 } else {
                     acc = __fmaf_rn(io.sig, w.zn[h & 7][lane], acc);
                 }
@@ -414,6 +417,7 @@ __device__ __forceinline__ void elite_update_step(const EliteArgs& a, int h, Eli
 #pragma unroll
     for (int j = 0; j < NU; ++j) acc[j] = 0.0f;
     float Z = 0.0f;
+    const bool cached = ne <= 64;  // the covariance pass then reuses the rows kept here
     for (int e = tid; e < ne; e += T) {
         const int k = a.eidx[e];
         const float wk = expf(-(a.costs[k] - cmin) * inv_beta);
@@ -422,6 +426,11 @@ __device__ __forceinline__ void elite_update_step(const EliteArgs& a, int h, Eli
         Z += wk;
 #pragma unroll
         for (int j = 0; j < NU; ++j) acc[j] += wk * u[j];
+        if (cached) {
+#pragma unroll
+            for (int j = 0; j < NU; ++j) sm.d[e][j] = u[j];
+            sm.d[e][NU] = wk;
+        }
     }
     // fixed-order sums: butterfly within each warp, then the warps in order
 #pragma unroll
@@ -477,9 +486,15 @@ __device__ __forceinline__ void elite_update_step(const EliteArgs& a, int h, Eli
 #pragma unroll
                 for (int j = 0; j < NU; ++j) u[j] = sm.mean[j];
                 if (e < ne) {
-                    const int k = a.eidx[e];
-                    wk = expf(-(a.costs[k] - cmin) * inv_beta);
-                    elite_row<NU>(a, h, k, key, iter, unom_h, u);
+                    if (cached) {  // this thread's own row from the mean pass
+#pragma unroll
+                        for (int j = 0; j < NU; ++j) u[j] = sm.d[tid][j];
+                        wk = sm.d[tid][NU];
+                    } else {
+                        const int k = a.eidx[e];
+                        wk = expf(-(a.costs[k] - cmin) * inv_beta);
+                        elite_row<NU>(a, h, k, key, iter, unom_h, u);
+                    }
                 }
 #pragma unroll
                 for (int j = 0; j < NU; ++j) sm.d[tid][j] = u[j] - sm.mean[j];
