@@ -58,6 +58,8 @@ __device__ __forceinline__ float rollout_sample(const DevModel& M, WarpWS<NA>& w
         for (int s = 0; s < TaskDims<NA>::SLOTS; ++s) tacc.prev[s] = 0.0f;
         tacc.c = tacc.th = tacc.yz = tacc.v2 = tacc.r = tacc.l = tacc.eo = tacc.ot = 0.0f;
     }
+    float upre = 0.0f;  // explicit controls: the next step's value
+    if (MODE == 0 && lane < d::NU) upre = io.U[lane];
     for (int h = 0; h < io.H; ++h) {
         if (MODE == 1) {
             // every 8 steps the 32 lanes draw one Philox block each: 8 steps x
@@ -91,7 +93,8 @@ __device__ __forceinline__ float rollout_sample(const DevModel& M, WarpWS<NA>& w
                 if (io.U_store) io.U_store[((size_t)h * io.Kn + k) * d::NU + lane] = uv;
             }
         } else if (lane < d::NU) {
-            const float uv = io.U[h * io.u_stride + lane];
+            const float uv = upre;  // read one step ahead: its latency overlaps the step
+            if (h + 1 < io.H) upre = io.U[(h + 1) * io.u_stride + lane];
             w.u[lane] = uv;
             uacc = __fmaf_rn(uv, uv, uacc);
         }
