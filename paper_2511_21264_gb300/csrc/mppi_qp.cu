@@ -229,6 +229,9 @@ __device__ void qp_admm(const QPClass& c, const float4* __restrict__ band, int H
         float d1p = 0.0f, d2p = 0.0f;            // first and second differences at t-1
         float r0 = 0.0f, r1 = 0.0f, r2 = 0.0f;   // rhs of x_{t-2}, x_{t-1}, x_t
         float z1 = 0.0f, z2 = 0.0f, z3 = 0.0f;   // z_{i-1}, z_{i-2}, z_{i-3} of the substitution
+        // unrolled so that the next steps' loads are in flight during the
+        // substitution chain (the operations and their order are unchanged)
+#pragma unroll 4
         for (int t = 0; t < H; ++t) {
             const float2 xv = xb[(size_t)t * T];
             float4 y = yv[(size_t)t * T];
@@ -273,6 +276,7 @@ __device__ void qp_admm(const QPClass& c, const float4* __restrict__ band, int H
         }
         // backward substitution L^T x = z
         float p1 = 0.0f, p2 = 0.0f, p3 = 0.0f;  // x_{i+1}, x_{i+2}, x_{i+3}
+#pragma unroll 4
         for (int i = H; i >= 1; --i) {
             const float4 L = __ldg(&bb[i - 1]);
             float* slot = &xb[(size_t)(i - 1) * T].x;
