@@ -664,9 +664,56 @@ __device__ __forceinline__ void seg_prefix_sum(float (&v)[N], int i, int nlinks)
     }
 }
 
+// Cholesky factor of arm a's block of (M + dt D) (lower triangle of w.L[a]
+// on entry) and the solution y of (M + dt D) y = rhs for that arm, in
+// registers; ok is false on a finite non-positive pivot.
+template <int NA>
+__device__ __forceinline__ void arm_solve(const WarpWS<NA>& w, int a, float (&A)[NA][NA], float (&di)[NA],
+                                          float (&y)[NA], bool& ok) {
+#pragma unroll
+    for (int r = 0; r < NA; ++r)
+#pragma unroll
+        for (int cc = 0; cc <= r; ++cc) A[r][cc] = w.L[a][r][cc];
+    ok = true;
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+        float sj = A[j][j];
+#pragma unroll
+        for (int k = 0; k < j; ++k) sj -= A[j][k] * A[j][k];
+        // a NaN pivot comes from a non-finite state (reported through the
+        // cost); only a finite non-positive pivot is a loss of positive
+        // definiteness
+        ok = ok && !(sj <= 0.0f);
+        const float inv = rsqrtf(sj);
+        A[j][j] = sj * inv;
+        di[j] = inv;
+#pragma unroll
+        for (int r = j + 1; r < NA; ++r) {
+            float t = A[r][j];
+#pragma unroll
+            for (int k = 0; k < j; ++k) t -= A[r][k] * A[j][k];
+            A[r][j] = t * inv;
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < NA; ++r) {
+        float sr = w.rhs[a * NA + r];
+#pragma unroll
+        for (int k = 0; k < r; ++k) sr -= A[r][k] * y[k];
+        y[r] = sr * di[r];
+    }
+#pragma unroll
+    for (int r = NA - 1; r >= 0; --r) {
+        float sr = y[r];
+#pragma unroll
+        for (int k = r + 1; k < NA; ++k) sr -= A[k][r] * y[k];
+        y[r] = sr * di[r];
+    }
+}
+
 template <int NA>
 __device__ __forceinline__ void dynamics(const DevModel& M, WarpWS<NA>& w, int lane, int* err, const float (&R)[9],
-                                         const float (&cl)[3], int tb) {
+                                         const float (&cl)[3], int tb, bool solve) {
     using d = Dims<NA>;
     const int a = lane >> 4, i = lane & 15;
     const bool act = i < NA;
@@ -814,51 +861,14 @@ __device__ __forceinline__ void dynamics(const DevModel& M, WarpWS<NA>& w, int l
     __syncwarp();
     // (6) Cholesky of each arm block (in registers), the free velocity; ball.
     //     The factor is kept only for arms a contact touches (the contact
-    //     solve's rows need it there).
+    //     solve's rows need it there).  Skipped (solve = false) when the
+    //     caller solves the arms together with a ball-only contact problem.
+    if (!solve) return;
     const int armc = tb & 3;
     if (i == 0) {
-        float A[NA][NA];
-#pragma unroll
-        for (int r = 0; r < NA; ++r)
-#pragma unroll
-            for (int cc = 0; cc <= r; ++cc) A[r][cc] = w.L[a][r][cc];
-        bool ok = true;
-        float di[NA];
-#pragma unroll
-        for (int j = 0; j < NA; ++j) {
-            float sj = A[j][j];
-#pragma unroll
-            for (int k = 0; k < j; ++k) sj -= A[j][k] * A[j][k];
-            // a NaN pivot comes from a non-finite state (reported through the
-            // cost); only a finite non-positive pivot is a loss of
-            // positive definiteness
-            ok = ok && !(sj <= 0.0f);
-            const float inv = rsqrtf(sj);
-            A[j][j] = sj * inv;
-            di[j] = inv;
-#pragma unroll
-            for (int r = j + 1; r < NA; ++r) {
-                float t = A[r][j];
-#pragma unroll
-                for (int k = 0; k < j; ++k) t -= A[r][k] * A[j][k];
-                A[r][j] = t * inv;
-            }
-        }
-        float y[NA];
-#pragma unroll
-        for (int r = 0; r < NA; ++r) {
-            float sr = w.rhs[a * NA + r];
-#pragma unroll
-            for (int k = 0; k < r; ++k) sr -= A[r][k] * y[k];
-            y[r] = sr * di[r];
-        }
-#pragma unroll
-        for (int r = NA - 1; r >= 0; --r) {
-            float sr = y[r];
-#pragma unroll
-            for (int k = r + 1; k < NA; ++k) sr -= A[k][r] * y[k];
-            y[r] = sr * di[r];
-        }
+        float A[NA][NA], di[NA], y[NA];
+        bool ok;
+        arm_solve<NA>(w, a, A, di, y, ok);
 #pragma unroll
         for (int r = 0; r < NA; ++r) w.vf[a * NA + r] = w.qd[a * NA + r] + M.dt * y[r];
         if ((armc >> a) & 1) {
@@ -927,14 +937,13 @@ __device__ __forceinline__ void contact_frame_row(const float* n, int k, float* 
 // G_rs = e_r.e_s / m + d_r.d_s / I, b_r = e_r.v_f + d_r.w_f -- runs the
 // sweeps and applies the impulse, with no shared-memory rows or factor.
 // The same iteration as the general path, summed in a different order.
-template <int NA, int NC>
-__device__ __forceinline__ void contacts_ball(const DevModel& M, WarpWS<NA>& w, int lane) {
+template <int NA, int NC, int SW>
+__device__ __forceinline__ void ball_contact_dv(const DevModel& M, const WarpWS<NA>& w, const float* vl,
+                                                const float* va, float (&dv)[6]) {
     using d = Dims<NA>;
     constexpr int NR = 3 * NC;
     const float im = 1.0f / M.mb, iI = 1.0f / M.Ib, regc = (1.0f - M.imp) / M.imp;
     const float* bc = &w.q[d::B];
-    const float* vl = &w.vf[d::B];
-    const float* va = &w.vf[d::B + 3];
     // rows without the side sign s_c (+1 when the ball is body A): it enters
     // b, the cross-contact Delassus entries and the applied impulse
     float E[NR][3], D[NR][3], bb[NR], vs[NR], sg[NC];
@@ -1009,7 +1018,10 @@ __device__ __forceinline__ void contacts_ball(const DevModel& M, WarpWS<NA>& w, 
             lam[rn + 2] = l2;
         }
     };
-    if (M.sweeps == 4) {  // the scenes' sweep counts, unrolled
+    if (SW > 0) {  // a sweep count fixed at compile time, unrolled
+#pragma unroll
+        for (int sw = 0; sw < SW; ++sw) sweep();
+    } else if (M.sweeps == 4) {  // the scenes' sweep counts, unrolled
         sweep();
         sweep();
         sweep();
@@ -1021,8 +1033,7 @@ __device__ __forceinline__ void contacts_ball(const DevModel& M, WarpWS<NA>& w, 
     } else {
         for (int sw = 0; sw < M.sweeps; ++sw) sweep();
     }
-    // v = v_f + M^-1 J^T lambda on the ball, v_f elsewhere
-    float dv[6];
+    // M^-1 J^T lambda on the ball
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         float sl = 0.0f, sa = 0.0f;
@@ -1035,12 +1046,64 @@ __device__ __forceinline__ void contacts_ball(const DevModel& M, WarpWS<NA>& w, 
         dv[k] = im * sl;
         dv[3 + k] = iI * sa;
     }
+}
+
+// v = v_f + M^-1 J^T lambda on the ball, v_f elsewhere.
+template <int NA, int NC>
+__device__ __forceinline__ void contacts_ball(const DevModel& M, WarpWS<NA>& w, int lane) {
+    using d = Dims<NA>;
+    float dv[6];
+    ball_contact_dv<NA, NC, 0>(M, w, &w.vf[d::B], &w.vf[d::B + 3], dv);
     if (lane < d::NV) {
         float add = 0.0f;
 #pragma unroll
         for (int k = 0; k < 6; ++k)
             if (lane == d::B + k) add = dv[k];
         w.v[lane] = w.vf[lane] + add;
+    }
+    __syncwarp();
+}
+
+// The free velocity and a ball-only contact solve together (one or two
+// contacts of the ball with static geometry, SW sweeps).  Every lane of an
+// arm's half-warp factors that arm's block and solves for its free velocity
+// (the operations of the one-lane factor in dynamics) while every lane runs
+// the contact solve: with no divergence between them the two independent
+// chains share the issue slots.  Writes v: the arms' free velocities and the
+// ball's after the impulses (the values dynamics and contacts_ball give).
+template <int NA, int NC, int SW>
+__device__ __forceinline__ void solve_ball_contacts(const DevModel& M, WarpWS<NA>& w, int lane, int* err) {
+    using d = Dims<NA>;
+    const int a = lane >> 4, i = lane & 15;
+    float vb[6];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        vb[r] = w.qd[d::B + r] + M.dt * M.g[r];
+        vb[3 + r] = w.qd[d::B + 3 + r];
+    }
+    float A[NA][NA], di[NA], y[NA];
+    bool ok;
+    arm_solve<NA>(w, a, A, di, y, ok);
+    float dv[6];
+    ball_contact_dv<NA, NC, SW>(M, w, vb, vb + 3, dv);
+    if (i == 0 && !ok) atomicOr(err, ERRB_CHOLESKY);
+    if (i < NA) {
+        float yi = y[0];
+#pragma unroll
+        for (int r = 1; r < NA; ++r)
+            if (i == r) yi = y[r];
+        const float vf = w.qd[a * NA + i] + M.dt * yi;
+        w.v[a * NA + i] = vf + 0.0f;
+    } else if (a == 0 && i < NA + 6) {
+        const int k = i - NA;
+        float vk = vb[0], dk = dv[0];
+#pragma unroll
+        for (int r = 1; r < 6; ++r)
+            if (k == r) {
+                vk = vb[r];
+                dk = dv[r];
+            }
+        w.v[d::B + k] = vk + dk;
     }
     __syncwarp();
 }

@@ -110,8 +110,16 @@ __device__ __forceinline__ float rollout_sample(const DevModel& M, WarpWS<NA>& w
         n_exact += collide<NA>(M, w, lane, pacc, pbacc, ncon, tb);
         __syncwarp();
         n_con += ncon;
-        dynamics<NA>(M, w, lane, io.err, Rl, cl, tb);
-        contacts<NA>(M, w, lane, ncon, tb);
+        // one ball contact with static geometry (the lift's common case):
+        // the arms' solve and the contact solve run side by side
+        const bool fast = tb == 4 && ncon == 1 && (M.sweeps == 4 || M.sweeps == 3);
+        dynamics<NA>(M, w, lane, io.err, Rl, cl, tb, !fast);
+        if (fast) {
+            if (M.sweeps == 4) solve_ball_contacts<NA, 1, 4>(M, w, lane, io.err);
+            else solve_ball_contacts<NA, 1, 3>(M, w, lane, io.err);
+        } else {
+            contacts<NA>(M, w, lane, ncon, tb);
+        }
         integrate<NA>(M, w, lane);
         if (!TASK && lane >= d::B && lane < d::B + 3) {  // the ball coordinate this lane integrated
             const float e = w.q[lane] - gb[lane - d::B];
