@@ -466,7 +466,57 @@ __device__ __forceinline__ int collide(const DevModel& M, WarpWS<NA>& w, int lan
     const float rb = M.rb;
     int base = 0, nsurv = 0;
     unsigned tbits = 0u;  // blocks the stored contacts touch
-    for (int p0 = 0; p0 < nball; p0 += 32) {
+    if (nb == 0) {  // floor and link capsules only (one pass): every lane runs both tests, no divergence
+        const int p = lane;
+        const int l = min(max(p - 1, 0), d::NL - 1);
+        const float* a0 = w.a0[l];
+        const float* a1 = w.a1[l];
+        float dd[3] = {a1[0] - a0[0], a1[1] - a0[1], a1[2] - a0[2]};
+        float ac[3] = {pb[0] - a0[0], pb[1] - a0[1], pb[2] - a0[2]};
+        const float den = dot3(dd, dd);
+        float t = den > 0.0f ? dot3(ac, dd) / den : 0.0f;
+        t = fminf(fmaxf(t, 0.0f), 1.0f);
+        float sp[3] = {a0[0] + t * dd[0], a0[1] + t * dd[1], a0[2] + t * dd[2]};
+        float df[3] = {pb[0] - sp[0], pb[1] - sp[1], pb[2] - sp[2]};
+        const float len = sqrtf(dot3(df, df));
+        const float il = 1.0f / len;
+        const bool isf = p == 0, isc = p >= 1 && p <= d::NL;
+        float nn[3];
+        nn[0] = !isf && len > 0.0f ? df[0] * il : 0.0f;
+        nn[1] = !isf && len > 0.0f ? df[1] * il : 0.0f;
+        nn[2] = !isf && len > 0.0f ? df[2] * il : 1.0f;
+        const float rc = M.link[l / NA][l % NA].rcap;
+        float cp[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) cp[k] = 0.5f * ((pb[k] - rb * nn[k]) + (sp[k] + rc * nn[k]));
+        float dist = len - rb - rc;
+        if (isf) {  // ball - floor
+            dist = (pb[2] - M.floor_z) - rb;
+            cp[0] = pb[0];
+            cp[1] = pb[1];
+            cp[2] = 0.5f * ((pb[2] - rb) + M.floor_z);
+        }
+        const int Bb = isc ? l : -1;
+        const bool active = (isf || isc) && dist < 0.0f;
+        const unsigned mask = __ballot_sync(FULL, active);
+        if (active) {
+            const int pos = __popc(mask & ((1u << lane) - 1u));
+            pa += -dist;
+            if (pos < M.maxc) {
+                tbits |= 4u | (Bb >= 0 ? 1u << (Bb / NA) : 0u);
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    w.cp[pos][k] = cp[k];
+                    w.cn[pos][k] = nn[k];
+                }
+                w.cdep[pos] = -dist;
+                w.cA[pos] = d::B;
+                w.cB[pos] = Bb;
+            }
+        }
+        base = __popc(mask);
+    }
+    for (int p0 = 0; nb > 0 && p0 < nball; p0 += 32) {
         const int p = p0 + lane;
         bool active = false, isbox = false;
         float dist = 1.0f, cp[3] = {0, 0, 0}, nn[3] = {0, 0, 1};
