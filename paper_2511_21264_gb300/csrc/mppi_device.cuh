@@ -216,12 +216,16 @@ __device__ __forceinline__ void forward_kinematics(const DevModel& M, WarpWS<NA>
     const int a = lane >> 4, i = lane & 15;
     const bool act = i < NA;
     float R[9], p[3];
-    if (act) {
-        const DevLink& L = M.link[a][i];
+    {
+        // every lane forms a local transform, with no divergent branch: lanes
+        // past the last link use the last link's data (the prefix products of
+        // the links' lanes never read theirs)
+        const int ic = act ? i : NA - 1;
+        const DevLink& L = M.link[a][ic];
         float sn, cs;
         // the hardware sine and cosine: absolute error about 1e-6 for joint
         // angles of a few radians, growing slowly with the angle
-        __sincosf(w.q[a * NA + i], &sn, &cs);
+        __sincosf(w.q[a * NA + ic], &sn, &cs);
 #pragma unroll
         for (int cc = 0; cc < 3; ++cc) {
             R[cc] = cs * L.FR[cc] - sn * L.FR[3 + cc];
@@ -231,10 +235,6 @@ __device__ __forceinline__ void forward_kinematics(const DevModel& M, WarpWS<NA>
         p[0] = cs * L.Fp[0] - sn * L.Fp[1];
         p[1] = sn * L.Fp[0] + cs * L.Fp[1];
         p[2] = L.Fp[2];
-    } else {
-#pragma unroll
-        for (int k = 0; k < 9; ++k) R[k] = (k % 4 == 0) ? 1.0f : 0.0f;
-        p[0] = p[1] = p[2] = 0.0f;
     }
 #pragma unroll
     for (int off = 1; off < NA; off <<= 1) {
@@ -1488,7 +1488,7 @@ template <int NA>
 __device__ __forceinline__ void integrate(const DevModel& M, WarpWS<NA>& w, int lane) {
     using d = Dims<NA>;
     const float dt = M.dt;
-    if (lane == 31) {
+    {  // every lane forms the new orientation (no divergent branch); lane 31 stores it
         const float* om = &w.v[d::B + 3];
         const float th[3] = {om[0] * dt, om[1] * dt, om[2] * dt};
         // dq = (cos x, th sin(x) / (2x)) with x = |th| / 2.  For x < 1/2 both
@@ -1514,10 +1514,13 @@ __device__ __forceinline__ void integrate(const DevModel& M, WarpWS<NA>& w, int 
         float ny = dq0 * y0 - dq1 * z0 + dq2 * w0 + dq3 * x0;
         float nz = dq0 * z0 + dq1 * y0 - dq2 * x0 + dq3 * w0;
         const float inv = rsqrtf(nw * nw + nx * nx + ny * ny + nz * nz);
-        qq[0] = nw * inv;
-        qq[1] = nx * inv;
-        qq[2] = ny * inv;
-        qq[3] = nz * inv;
+        __syncwarp();  // every lane has read the old orientation
+        if (lane == 31) {
+            qq[0] = nw * inv;
+            qq[1] = nx * inv;
+            qq[2] = ny * inv;
+            qq[3] = nz * inv;
+        }
     }
     if (lane < d::NV) w.qd[lane] = w.v[lane];
     if (lane < d::B + 3) w.q[lane] += dt * w.v[lane];
