@@ -697,7 +697,7 @@ __device__ __forceinline__ void seg_suffix_sum(float (&v)[N], int i, int nlinks)
 #pragma unroll
         for (int t = 0; t < N; ++t) {
             const float o = __shfl_down_sync(FULL, v[t], off, 16);
-            if (i + off < 16) v[t] += o;
+            if (i + off < nlinks) v[t] += o;  // lanes past the last link never enter
         }
     }
 }
@@ -771,14 +771,13 @@ __device__ __forceinline__ void dynamics(const DevModel& M, WarpWS<NA>& w, int l
     // (1) per link (lane i): spatial inertia about the world origin
     //     (m, h = m c, J = R I R^T + m(|c|^2 E - c c^T)), joint motion axis
     //     S = (z, o x z), velocity term S qd
+    //     Every lane computes (no divergent branch); lanes past the last
+    //     link work on link 0's data, and the scans below never pass their
+    //     values to a link's lane.
     float Is[10], S[6], sq[6];
-#pragma unroll
-    for (int t = 0; t < 10; ++t) Is[t] = 0.0f;
-#pragma unroll
-    for (int t = 0; t < 6; ++t) S[t] = sq[t] = 0.0f;
-    float qdi = 0.0f;
-    if (act) {
-        const DevLink& L = M.link[a][i];
+    float qdi;
+    {
+        const DevLink& L = M.link[a][l - a * NA];
         const float* Ib = L.I;
         const float B9[9] = {Ib[0], Ib[3], Ib[4], Ib[3], Ib[1], Ib[5], Ib[4], Ib[5], Ib[2]};
         float T[9];
@@ -804,7 +803,7 @@ __device__ __forceinline__ void dynamics(const DevModel& M, WarpWS<NA>& w, int l
         S[1] = w.z[l][1];
         S[2] = w.z[l][2];
         cross3(w.o[l], w.z[l], S + 3);
-        qdi = w.qd[a * NA + i];
+        qdi = w.qd[l];
 #pragma unroll
         for (int t = 0; t < 6; ++t) sq[t] = S[t] * qdi;
     }
@@ -840,16 +839,12 @@ __device__ __forceinline__ void dynamics(const DevModel& M, WarpWS<NA>& w, int l
         Aa[4] = t2[1] + t3[1];
         Aa[5] = t2[2] + t3[2];
     }
-    if (!act) {
-#pragma unroll
-        for (int t = 0; t < 6; ++t) Aa[t] = 0.0f;
-    }
     seg_prefix_sum<6>(Aa, i, NA);
     // bias force of link i: I_i (A_i + a_g) + V_i x* (I_i V_i), gravity as a
     // base acceleration -g on links without compensation
     float f[6];
     {
-        const float gw = act ? 1.0f - M.link[a][i].gravcomp : 0.0f;
+        const float gw = act ? 1.0f - M.link[a][l - a * NA].gravcomp : 0.0f;
         Aa[3] -= gw * M.g[0];
         Aa[4] -= gw * M.g[1];
         Aa[5] -= gw * M.g[2];
@@ -866,10 +861,6 @@ __device__ __forceinline__ void dynamics(const DevModel& M, WarpWS<NA>& w, int l
         f[3] = IA[3] + f1[0];
         f[4] = IA[4] + f1[1];
         f[5] = IA[5] + f1[2];
-        if (!act) {
-#pragma unroll
-            for (int t = 0; t < 6; ++t) f[t] = 0.0f;
-        }
     }
     // (4) bias torque S_i . (subtree force); drive; implicit damping
     seg_suffix_sum<6>(f, i, NA);
