@@ -864,16 +864,18 @@ __device__ __forceinline__ void dynamics(const DevModel& M, WarpWS<NA>& w, int l
     }
     // (4) bias torque S_i . (subtree force); drive; implicit damping
     seg_suffix_sum<6>(f, i, NA);
-    if (act) {
+    {  // every lane computes, the links' lanes store
         const float tb = S[0] * f[0] + S[1] * f[1] + S[2] * f[2] + S[3] * f[3] + S[4] * f[4] + S[5] * f[5];
-        const DevLink& L = M.link[a][i];
-        const int dof = a * NA + i;
-        const float td = fminf(fmaxf(L.gear * w.u[dof], -L.tau_max), L.tau_max);
-        w.rhs[dof] = td - tb - L.D * qdi;
+        const DevLink& L = M.link[a][l - a * NA];
+        const float td = fminf(fmaxf(L.gear * w.u[l], -L.tau_max), L.tau_max);
+        const float rhs = td - tb - L.D * qdi;
+        if (act) {
+            w.rhs[l] = rhs;
 #pragma unroll
-        for (int t = 0; t < 6; ++t) {
-            w.ph.dyn.S[l][t] = S[t];
-            w.ph.dyn.F[l][t] = F[t];
+            for (int t = 0; t < 6; ++t) {
+                w.ph.dyn.S[l][t] = S[t];
+                w.ph.dyn.F[l][t] = F[t];
+            }
         }
     }
     __syncwarp();
@@ -883,8 +885,8 @@ __device__ __forceinline__ void dynamics(const DevModel& M, WarpWS<NA>& w, int l
 #pragma unroll
     for (int e0 = 0; e0 < NENT; e0 += 16) {
         const int e = e0 + i;
-        if (e < NENT) {
-            int c = 0, rem = e;
+        {  // every lane computes (past the last entry on the last one), the entries' lanes store
+            int c = 0, rem = e < NENT ? e : NENT - 1;
 #pragma unroll
             for (int cc = 0; cc < NA; ++cc)
                 if (rem > c) {
@@ -896,7 +898,7 @@ __device__ __forceinline__ void dynamics(const DevModel& M, WarpWS<NA>& w, int l
             const float* Fc = w.ph.dyn.F[a * NA + c];
             float mv = Sr[0] * Fc[0] + Sr[1] * Fc[1] + Sr[2] * Fc[2] + Sr[3] * Fc[3] + Sr[4] * Fc[4] + Sr[5] * Fc[5];
             if (r == c) mv += M.dt * M.link[a][c].D;
-            w.L[a][c][r] = mv;
+            if (e < NENT) w.L[a][c][r] = mv;
         }
     }
     __syncwarp();

@@ -76,21 +76,24 @@ __device__ __forceinline__ float rollout_sample(const DevModel& M, WarpWS<NA>& w
                 }
                 __syncwarp();
             }
-            if (lane < d::NU) {
-                float acc = io.unom[h * d::NU + lane];
+            {  // every lane computes (past the controls on the last one), the controls' lanes store
+                const int jc = lane < d::NU ? lane : d::NU - 1;
+                float acc = io.unom[h * d::NU + jc];
                 if (io.Lfac) {  // u = nu + L_h z, FMAs in the order sample_row uses
                     // (unrolled over the row so that its loads are issued together)
-                    const float* Lr = io.Lfac + ((size_t)h * d::NU + lane) * d::NU;
+                    const float* Lr = io.Lfac + ((size_t)h * d::NU + jc) * d::NU;
 #pragma unroll
                     for (int i = 0; i < d::NU; ++i)
-                        if (i <= lane) acc = __fmaf_rn(Lr[i], w.zn[h & 7][i], acc);
+                        if (i <= jc) acc = __fmaf_rn(Lr[i], w.zn[h & 7][i], acc);
                 } else {
-                    acc = __fmaf_rn(io.sig, w.zn[h & 7][lane], acc);
+                    acc = __fmaf_rn(io.sig, w.zn[h & 7][jc], acc);
                 }
                 const float uv = fminf(fmaxf(acc, io.lo), io.hi);
-                w.u[lane] = uv;
-                uacc = __fmaf_rn(uv, uv, uacc);
-                if (io.U_store) io.U_store[((size_t)h * io.Kn + k) * d::NU + lane] = uv;
+                if (lane < d::NU) {
+                    w.u[lane] = uv;
+                    uacc = __fmaf_rn(uv, uv, uacc);
+                    if (io.U_store) io.U_store[((size_t)h * io.Kn + k) * d::NU + lane] = uv;
+                }
             }
         } else if (lane < d::NU) {
             const float uv = upre;  // read one step ahead: its latency overlaps the step
