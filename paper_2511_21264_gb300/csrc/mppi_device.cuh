@@ -280,18 +280,27 @@ __device__ __forceinline__ void forward_kinematics(const DevModel& M, WarpWS<NA>
             op[r] = M.basep[a][r];
         }
     }
-    if (act) {
-        const DevLink& L = M.link[a][i];
-        const int l = a * NA + i;
+    {  // every lane computes (lanes past the last link on its data), the links' lanes store
+        const int ic = act ? i : NA - 1;
+        const DevLink& L = M.link[a][ic];
+        const int l = a * NA + ic;
 #pragma unroll
         for (int k = 0; k < 9; ++k) Rl[k] = Rw[k];
+        float c0[3], c1[3];
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
-            w.z[l][r] = zp[r];
-            w.o[l][r] = op[r];
             cl[r] = Rw[3 * r] * L.com[0] + Rw[3 * r + 1] * L.com[1] + Rw[3 * r + 2] * L.com[2] + pw[r];
-            w.a0[l][r] = Rw[3 * r] * L.s0[0] + Rw[3 * r + 1] * L.s0[1] + Rw[3 * r + 2] * L.s0[2] + pw[r];
-            w.a1[l][r] = Rw[3 * r] * L.s1[0] + Rw[3 * r + 1] * L.s1[1] + Rw[3 * r + 2] * L.s1[2] + pw[r];
+            c0[r] = Rw[3 * r] * L.s0[0] + Rw[3 * r + 1] * L.s0[1] + Rw[3 * r + 2] * L.s0[2] + pw[r];
+            c1[r] = Rw[3 * r] * L.s1[0] + Rw[3 * r + 1] * L.s1[1] + Rw[3 * r + 2] * L.s1[2] + pw[r];
+        }
+        if (act) {
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                w.z[l][r] = zp[r];
+                w.o[l][r] = op[r];
+                w.a0[l][r] = c0[r];
+                w.a1[l][r] = c1[r];
+            }
         }
     }
 }
