@@ -508,20 +508,19 @@ __device__ __forceinline__ int collide(const DevModel& M, WarpWS<NA>& w, int lan
         const int Bb = isc ? l : -1;
         const bool active = (isf || isc) && dist < 0.0f;
         const unsigned mask = __ballot_sync(FULL, active);
-        if (active) {
-            const int pos = __popc(mask & ((1u << lane) - 1u));
-            pa += -dist;
-            if (pos < M.maxc) {
-                tbits |= 4u | (Bb >= 0 ? 1u << (Bb / NA) : 0u);
+        const int pos = __popc(mask & ((1u << lane) - 1u));
+        const bool keep = active && pos < M.maxc;
+        pa += active ? -dist : 0.0f;
+        tbits |= keep ? 4u | (Bb >= 0 ? 1u << (Bb / NA) : 0u) : 0u;
+        if (keep) {
 #pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    w.cp[pos][k] = cp[k];
-                    w.cn[pos][k] = nn[k];
-                }
-                w.cdep[pos] = -dist;
-                w.cA[pos] = d::B;
-                w.cB[pos] = Bb;
+            for (int k = 0; k < 3; ++k) {
+                w.cp[pos][k] = cp[k];
+                w.cn[pos][k] = nn[k];
             }
+            w.cdep[pos] = -dist;
+            w.cA[pos] = d::B;
+            w.cB[pos] = Bb;
         }
         base = __popc(mask);
     }
@@ -1139,24 +1138,23 @@ __device__ __forceinline__ void solve_ball_contacts(const DevModel& M, WarpWS<NA
     float dv[6];
     ball_contact_dv<NA, NC, SW>(M, w, vb, vb + 3, dv);
     if (i == 0 && !ok) atomicOr(err, ERRB_CHOLESKY);
-    if (i < NA) {
-        float yi = y[0];
+    // lane 16a + i < NA: the arm's velocity i; lanes NA..NA+5 of half 0: the
+    // ball's six (both values formed on every lane, one stored)
+    float yi = y[0], vk = vb[0], dk = dv[0];
+    const int k = i - NA;
 #pragma unroll
-        for (int r = 1; r < NA; ++r)
-            if (i == r) yi = y[r];
-        const float vf = w.qd[a * NA + i] + M.dt * yi;
-        w.v[a * NA + i] = vf + 0.0f;
-    } else if (a == 0 && i < NA + 6) {
-        const int k = i - NA;
-        float vk = vb[0], dk = dv[0];
+    for (int r = 1; r < NA; ++r)
+        if (i == r) yi = y[r];
 #pragma unroll
-        for (int r = 1; r < 6; ++r)
-            if (k == r) {
-                vk = vb[r];
-                dk = dv[r];
-            }
-        w.v[d::B + k] = vk + dk;
-    }
+    for (int r = 1; r < 6; ++r)
+        if (k == r) {
+            vk = vb[r];
+            dk = dv[r];
+        }
+    const float vf = w.qd[a * NA + (i < NA ? i : 0)] + M.dt * yi;
+    const float va = vf + 0.0f, vbk = vk + dk;
+    if (i < NA) w.v[a * NA + i] = va;
+    else if (a == 0 && i < NA + 6) w.v[d::B + k] = vbk;
     __syncwarp();
 }
 
