@@ -475,7 +475,11 @@ __device__ __forceinline__ int collide(const DevModel& M, WarpWS<NA>& w, int lan
     const float rb = M.rb;
     int base = 0, nsurv = 0;
     unsigned tbits = 0u;  // blocks the stored contacts touch
-    if (nb == 0) {  // floor and link capsules only (one pass): every lane runs both tests, no divergence
+    // ball pairs in one pass (1 + 2 n_a + n_b <= 32): every lane runs the
+    // floor, capsule and (with boxes) box tests on its own or clamped
+    // operands and keeps the one its pair needs -- no divergent branches
+    static_assert(1 + 2 * MAXL + MAXB <= 32, "ball pairs must fit one warp");
+    {
         const int p = lane;
         const int l = min(max(p - 1, 0), d::NL - 1);
         const float* a0 = w.a0[l];
@@ -489,7 +493,7 @@ __device__ __forceinline__ int collide(const DevModel& M, WarpWS<NA>& w, int lan
         float df[3] = {pb[0] - sp[0], pb[1] - sp[1], pb[2] - sp[2]};
         const float len = sqrtf(dot3(df, df));
         const float il = 1.0f / len;
-        const bool isf = p == 0, isc = p >= 1 && p <= d::NL;
+        const bool isf = p == 0, isc = p >= 1 && p <= d::NL, isb = p > d::NL && p < nball;
         float nn[3];
         nn[0] = !isf && len > 0.0f ? df[0] * il : 0.0f;
         nn[1] = !isf && len > 0.0f ? df[1] * il : 0.0f;
@@ -505,12 +509,26 @@ __device__ __forceinline__ int collide(const DevModel& M, WarpWS<NA>& w, int lan
             cp[1] = pb[1];
             cp[2] = 0.5f * ((pb[2] - rb) + M.floor_z);
         }
+        if (nb > 0) {  // ball - box (warp-uniform test)
+            const float* box = M.box[min(max(p - 1 - d::NL, 0), nb - 1)];
+            float nb3[3], surf[3];
+            const float db = box_sdf(pb, box, nb3, surf) - rb;
+            if (isb) {
+                dist = db;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    nn[k] = nb3[k];
+                    cp[k] = 0.5f * ((pb[k] - rb * nn[k]) + surf[k]);
+                }
+            }
+        }
         const int Bb = isc ? l : -1;
-        const bool active = (isf || isc) && dist < 0.0f;
+        const bool active = (isf || isc || isb) && dist < 0.0f;
         const unsigned mask = __ballot_sync(FULL, active);
         const int pos = __popc(mask & ((1u << lane) - 1u));
         const bool keep = active && pos < M.maxc;
         pa += active ? -dist : 0.0f;
+        pbox += active && isb ? -dist : 0.0f;
         tbits |= keep ? 4u | (Bb >= 0 ? 1u << (Bb / NA) : 0u) : 0u;
         if (keep) {
 #pragma unroll
@@ -523,69 +541,6 @@ __device__ __forceinline__ int collide(const DevModel& M, WarpWS<NA>& w, int lan
             w.cB[pos] = Bb;
         }
         base = __popc(mask);
-    }
-    for (int p0 = 0; nb > 0 && p0 < nball; p0 += 32) {
-        const int p = p0 + lane;
-        bool active = false, isbox = false;
-        float dist = 1.0f, cp[3] = {0, 0, 0}, nn[3] = {0, 0, 1};
-        int Bb = -1;
-        if (p < nball) {
-            if (p == 0) {  // ball - floor
-                dist = (pb[2] - M.floor_z) - rb;
-                cp[0] = pb[0];
-                cp[1] = pb[1];
-                cp[2] = 0.5f * ((pb[2] - rb) + M.floor_z);
-            } else if (p < 1 + d::NL) {  // ball - link capsule
-                const int l = p - 1;
-                const float* a0 = w.a0[l];
-                const float* a1 = w.a1[l];
-                float dd[3] = {a1[0] - a0[0], a1[1] - a0[1], a1[2] - a0[2]};
-                float ac[3] = {pb[0] - a0[0], pb[1] - a0[1], pb[2] - a0[2]};
-                const float den = dot3(dd, dd);
-                float t = den > 0.0f ? dot3(ac, dd) / den : 0.0f;
-                t = fminf(fmaxf(t, 0.0f), 1.0f);
-                float sp[3] = {a0[0] + t * dd[0], a0[1] + t * dd[1], a0[2] + t * dd[2]};
-                float df[3] = {pb[0] - sp[0], pb[1] - sp[1], pb[2] - sp[2]};
-                const float len = sqrtf(dot3(df, df));
-                if (len > 0.0f) {
-                    const float il = 1.0f / len;
-                    nn[0] = df[0] * il;
-                    nn[1] = df[1] * il;
-                    nn[2] = df[2] * il;
-                }
-                const float rc = M.link[l / NA][l % NA].rcap;
-                dist = len - rb - rc;
-#pragma unroll
-                for (int k = 0; k < 3; ++k) cp[k] = 0.5f * ((pb[k] - rb * nn[k]) + (sp[k] + rc * nn[k]));
-                Bb = l;
-            } else {  // ball - box
-                const float* box = M.box[p - 1 - d::NL];
-                float surf[3];
-                dist = box_sdf(pb, box, nn, surf) - rb;
-#pragma unroll
-                for (int k = 0; k < 3; ++k) cp[k] = 0.5f * ((pb[k] - rb * nn[k]) + surf[k]);
-                isbox = true;
-            }
-            active = dist < 0.0f;
-        }
-        const unsigned mask = __ballot_sync(FULL, active);
-        if (active) {
-            const int pos = base + __popc(mask & ((1u << lane) - 1u));
-            pa += -dist;
-            if (isbox) pbox += -dist;
-            if (pos < M.maxc) {
-                tbits |= 4u | (Bb >= 0 ? 1u << (Bb / NA) : 0u);
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    w.cp[pos][k] = cp[k];
-                    w.cn[pos][k] = nn[k];
-                }
-                w.cdep[pos] = -dist;
-                w.cA[pos] = d::B;
-                w.cB[pos] = Bb;
-            }
-        }
-        base += __popc(mask);
     }
     // capsule-box: lanes l and 16 + l test link l's capsule against the first
     // and the second half of the boxes (bounding sphere and axis-aligned
