@@ -161,17 +161,6 @@ __device__ __forceinline__ void block_normals4(uint4 w, float (&z)[4]) {
     }
 }
 
-// Sampled control U[k,h,j] = clamp(u_nom[h,j] + sigma_j z, lo, hi) with z
-// from counter (j/4, h, k, iteration).  Written with explicit rounding so the
-// rollout and the update kernels regenerate identical values.
-__device__ __forceinline__ float sample_control(uint2 key, uint32_t iter, int k, int h, int j, float unom,
-                                                float sigma, float lo, float hi) {
-    const uint4 w = philox4x32_10(make_uint4((uint32_t)(j >> 2), (uint32_t)h, (uint32_t)k, iter), key);
-    const float z = block_normal(w, j & 3);
-    const float u = __fmaf_rn(sigma, z, unom);
-    return fminf(fmaxf(u, lo), hi);
-}
-
 // ---------------------------------------------------------------------------
 // small vector helpers
 // ---------------------------------------------------------------------------

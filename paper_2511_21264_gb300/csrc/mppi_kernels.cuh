@@ -63,8 +63,9 @@ __device__ __forceinline__ float rollout_sample(const DevModel& M, WarpWS<NA>& w
     for (int h = 0; h < io.H; ++h) {
         if (MODE == 1) {
             // every 8 steps the 32 lanes draw one Philox block each: 8 steps x
-            // 16 controls of standard normals (the same values sample_control
-            // draws one at a time)
+            // 16 controls of standard normals, counter (j/4, h, k, iteration),
+            // Box-Muller on the word pairs (the values sample_row and the
+            // debug draw give)
             if ((h & 7) == 0) {
                 const int jb = lane & 3, hs = h + (lane >> 2);
                 if (4 * jb < d::NU && hs < io.H) {
