@@ -96,7 +96,7 @@ struct __align__(16) WarpWS {
     float cdep[MAXC];
     int cA[MAXC];
     int cB[MAXC];
-    float ee[2][10];  // task cost: end-effector position, velocity, quaternion per arm
+    float ee[2][6];   // task cost: end-effector position and velocity per arm
     union Phase {
         struct {
             short surv[2 * MAXL * MAXB];  // capsule-box pairs that pass the cull

@@ -55,7 +55,9 @@ __device__ __forceinline__ float rollout_sample(const DevModel& M, WarpWS<NA>& w
     TaskAcc<NA> tacc;
     if constexpr (TASK) {
 #pragma unroll
-        for (int s = 0; s < TaskDims<NA>::SLOTS; ++s) tacc.prev[s] = 0.0f;
+        for (int s = 0; s < TaskDims<NA>::CB; ++s) tacc.prevb[s] = 0.0f;
+#pragma unroll
+        for (int s = 0; s < TaskDims<NA>::CC; ++s) tacc.prevc[s] = 0.0f;
         tacc.c = tacc.th = tacc.yz = tacc.v2 = tacc.r = tacc.l = tacc.eo = tacc.ot = 0.0f;
     }
     float upre = 0.0f;  // explicit controls: the next step's value

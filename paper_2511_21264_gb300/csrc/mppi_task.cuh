@@ -19,23 +19,25 @@ struct __align__(16) DevTask {
     float home[16];        // theta_home
 };
 
-// pairs: links x boxes (link-major), links x ball (pick), left x right links
+// pairs: links x boxes (link-major) in the first lane passes, then links x
+// ball (pick) and left x right links, so that every pass evaluates one kind
 template <int NA>
 struct TaskDims {
-    static constexpr int MAXPAIRS = 2 * NA * MAXB + 2 * NA + NA * NA;
-    static constexpr int SLOTS = (MAXPAIRS + 31) / 32;
+    static constexpr int CB = (2 * NA * MAXB + 31) / 32;  // capsule-box passes at most
+    static constexpr int CC = (2 * NA + NA * NA + 31) / 32;
 };
 
 template <int NA>
 struct TaskAcc {
-    float prev[TaskDims<NA>::SLOTS];  // each slot's pair distance at the previous state (this lane)
-    float c;                          // barrier + penetration count (this lane)
-    float th, yz, v2, r, l, eo, ot;   // per-state terms (lane 0)
+    float prevb[TaskDims<NA>::CB];  // each pass's pair distance at the previous state (this lane)
+    float prevc[TaskDims<NA>::CC];
+    float c;                        // barrier + penetration count (this lane)
+    float r;                        // orientation error (the end-effector lanes)
+    float th, yz, v2, l, eo, ot;    // per-state terms (lane 0)
 };
 
-// Exact distance between a capsule (segment a0-a1, radius rcap) and a box:
-// the minimum over t in [0,1] of the box SDF f(t) at a0 + t (a1 - a0), minus
-// the radius.  f is convex; its kinks along the segment are where a
+// Minimum over t in [0,1] of the box SDF f(t) at a0 + t dd, for any segment
+// (the piece walk).  f is convex; its kinks along the segment are where a
 // coordinate crosses a slab plane or the box's mid-plane, plus, inside the
 // box, where two face distances cross.  f is evaluated at the nine crossing
 // parameters and both ends; by convexity the minimiser lies in one of the
@@ -43,8 +45,7 @@ struct TaskAcc {
 // root of a quadratic (exceeded slabs and signs fixed), minimised at its
 // stationary point; inside, f is the largest of three linear face
 // distances, minimised at a pairwise crossing or an end.
-__device__ __forceinline__ float capsule_box_distance(const float* a0, const float* a1, float rcap, const float* box) {
-    const float dd[3] = {a1[0] - a0[0], a1[1] - a0[1], a1[2] - a0[2]};
+__device__ __forceinline__ float segment_box_sdf_min(const float* a0, const float (&dd)[3], const float* box) {
     float T[11];
     T[0] = 0.0f;
     T[1] = 1.0f;
@@ -109,26 +110,72 @@ __device__ __forceinline__ float capsule_box_distance(const float* a0, const flo
             }
         }
     }
-    return best - rcap;
+    return best;
 }
 
-__device__ __forceinline__ float seg_clamp_t(const float* p0, const float* d, float dd, float x0, float x1, float x2) {
-    if (!(dd > 0.0f)) return 0.0f;
-    const float t = ((x0 - p0[0]) * d[0] + (x1 - p0[1]) * d[1] + (x2 - p0[2]) * d[2]) / dd;
-    return fminf(fmaxf(t, 0.0f), 1.0f);
-}
-
-__device__ __forceinline__ float sphere_capsule_distance(const float* c, float r, const float* a0, const float* a1,
-                                                         float rcap) {
-    const float d[3] = {a1[0] - a0[0], a1[1] - a0[1], a1[2] - a0[2]};
-    const float t = seg_clamp_t(a0, d, d[0] * d[0] + d[1] * d[1] + d[2] * d[2], c[0], c[1], c[2]);
-    const float e0 = c[0] - a0[0] - t * d[0], e1 = c[1] - a0[1] - t * d[1], e2 = c[2] - a0[2] - t * d[2];
-    return sqrtf(e0 * e0 + e1 * e1 + e2 * e2) - r - rcap;
+// Exact distance between a capsule (segment a0-a1, radius rcap) and a box
+// (centre, half extents): the minimum of the box SDF along the segment,
+// minus the radius.  A segment that misses the box (the slab intervals of
+// the three axes have no common t in [0,1]) stays outside it, where the
+// squared distance g(t) = sum_k e_k(t)^2, e_k the excess of coordinate k
+// past its slab (zero within it), is a convex piecewise quadratic: g'/2 =
+// sum_k e_k d_k is continuous, nondecreasing, and linear between the slab
+// crossings.  g' at the six crossings and both ends brackets its zero
+// between two candidates with no crossing in between, where one linear
+// interpolation gives the minimiser.  A segment that meets the box takes the
+// piece walk above.
+__device__ __forceinline__ float capsule_box_distance(const float* a0, const float* a1, float rcap, const float* box) {
+    float y0[3], dd[3], h[3], tc[6];
+    float tin = 0.0f, tout = 1.0f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        y0[k] = a0[k] - box[k];
+        dd[k] = a1[k] - a0[k];
+        h[k] = box[3 + k];
+        const bool mv = dd[k] != 0.0f;
+        const float inv = 1.0f / (mv ? dd[k] : 1.0f);
+        const float ta = (-h[k] - y0[k]) * inv, tb = (h[k] - y0[k]) * inv;
+        tin = mv ? fmaxf(tin, fminf(ta, tb)) : (fabsf(y0[k]) > h[k] ? 2.0f : tin);
+        tout = mv ? fminf(tout, fmaxf(ta, tb)) : tout;
+        tc[2 * k] = mv ? fminf(fmaxf(ta, 0.0f), 1.0f) : 0.0f;
+        tc[2 * k + 1] = mv ? fminf(fmaxf(tb, 0.0f), 1.0f) : 0.0f;
+    }
+    if (tin <= tout) return segment_box_sdf_min(a0, dd, box) - rcap;
+    auto gp = [&](float t) {
+        float s = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float y = __fmaf_rn(t, dd[k], y0[k]);
+            s = __fmaf_rn(y - fminf(fmaxf(y, -h[k]), h[k]), dd[k], s);
+        }
+        return s;
+    };
+    // tl: the last candidate with g' <= 0, tr: the first with g' > 0
+    float tl = 0.0f, gl = gp(0.0f), tr = 1.0f, gr = gp(1.0f);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        const float v = gp(tc[c]);
+        const bool lo = v <= 0.0f && tc[c] > tl, hi = v > 0.0f && tc[c] < tr;
+        tl = lo ? tc[c] : tl;
+        gl = lo ? v : gl;
+        tr = hi ? tc[c] : tr;
+        gr = hi ? v : gr;
+    }
+    const float t = gl >= 0.0f ? tl : (gr <= 0.0f ? tr : tl - gl * (tr - tl) / (gr - gl));
+    float g = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float y = __fmaf_rn(t, dd[k], y0[k]);
+        const float e = y - fminf(fmaxf(y, -h[k]), h[k]);
+        g = __fmaf_rn(e, e, g);
+    }
+    return sqrtf(g) - rcap;
 }
 
 // Segment-segment distance minus both radii: the squared distance is a
 // convex quadratic on [0,1]^2; take the interior stationary point if it lies
-// inside, and every edge's clamped minimum.
+// inside, and every edge's clamped minimum.  A segment of zero length (a
+// sphere) leaves only the projection onto the other segment and its ends.
 __device__ __forceinline__ float capsule_capsule_distance(const float* a0, const float* a1, float ra, const float* b0,
                                                           const float* b1, float rb) {
     float u[3], v[3], w0[3];
@@ -150,18 +197,22 @@ __device__ __forceinline__ float capsule_capsule_distance(const float* a0, const
         }
         return r;
     };
-    float best = INFINITY;
+    // the interior candidate (masked unless it lies in the square) and the
+    // four edges' clamped minimisers, each edge's projection formed from the
+    // dot products above
     const float den = A * Cq - Bq * Bq;
-    if (den > 1e-7f * A * Cq) {
-        const float s = (Bq * E - Cq * D) / den, t = (A * E - Bq * D) / den;
-        if (s >= 0.0f && s <= 1.0f && t >= 0.0f && t <= 1.0f) best = d2(s, t);
-    }
+    const bool inner = den > 1e-7f * A * Cq;
+    const float idn = inner ? 1.0f / den : 0.0f;
+    const float si = (Bq * E - Cq * D) * idn, ti = (A * E - Bq * D) * idn;
+    const bool in_sq = inner && si >= 0.0f && si <= 1.0f && ti >= 0.0f && ti <= 1.0f;
+    float best = in_sq ? d2(si, ti) : INFINITY;
+    const float ia = A > 0.0f ? 1.0f / A : 0.0f, ic = Cq > 0.0f ? 1.0f / Cq : 0.0f;
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
         const float fe = (float)e;
-        const float t = seg_clamp_t(b0, v, Cq, a0[0] + fe * u[0], a0[1] + fe * u[1], a0[2] + fe * u[2]);
+        const float t = fminf(fmaxf((E + fe * Bq) * ic, 0.0f), 1.0f);
         best = fminf(best, d2(fe, t));
-        const float s = seg_clamp_t(a0, u, A, b0[0] + fe * v[0], b0[1] + fe * v[1], b0[2] + fe * v[2]);
+        const float s = fminf(fmaxf((fe * Bq - D) * ia, 0.0f), 1.0f);
         best = fminf(best, d2(s, fe));
     }
     return sqrtf(best) - ra - rb;
@@ -202,26 +253,40 @@ __device__ __forceinline__ void task_state(const DevModel& M, const DevTask& T, 
                                            const float (&Rl)[9], bool first, TaskAcc<NA>& acc) {
     using d = Dims<NA>;
     const int nlb = 2 * NA * M.nb;
+    const int ncb = (nlb + 31) >> 5;  // capsule-box passes
     const int nball = T.phase == 0 ? 2 * NA : 0;
-    const int np = nlb + nball + NA * NA;
-#pragma unroll
-    for (int s = 0; s < TaskDims<NA>::SLOTS; ++s) {
+    const int ncc = nball + NA * NA;
+    const float keep = 1.0f - T.gamma;
+    // capsule-box passes: one copy of the code, the pass's previous
+    // distance picked out of the register array by selects
+#pragma unroll 1
+    for (int s = 0; s < ncb; ++s) {
         const int b = lane + 32 * s;
-        if (b < np) {
-            float dist;
-            if (b < nlb) {
-                const int l = b / M.nb, bx = b - l * M.nb;
-                dist = capsule_box_distance(w.a0[l], w.a1[l], M.link[l / NA][l % NA].rcap, M.box[bx]);
-            } else if (b < nlb + nball) {
-                const int l = b - nlb;
-                dist = sphere_capsule_distance(&w.q[d::B], M.rb, w.a0[l], w.a1[l], M.link[l / NA][l % NA].rcap);
-            } else {
-                const int r = b - nlb - nball, i = r / NA, j = r - i * NA;
-                dist = capsule_capsule_distance(w.a0[i], w.a1[i], M.link[0][i].rcap, w.a0[NA + j], w.a1[NA + j],
-                                                M.link[1][j].rcap);
-            }
-            if (!first) acc.c += fmaxf(-dist + (1.0f - T.gamma) * acc.prev[s], 0.0f) + (dist < 0.0f ? 1.0f : 0.0f);
-            acc.prev[s] = dist;
+        if (b < nlb) {
+            const int l = b / M.nb, bx = b - l * M.nb;
+            const float dist = capsule_box_distance(w.a0[l], w.a1[l], M.link[l / NA][l % NA].rcap, M.box[bx]);
+            float pv = acc.prevb[0];
+#pragma unroll
+            for (int k = 1; k < TaskDims<NA>::CB; ++k) pv = s == k ? acc.prevb[k] : pv;
+            if (!first) acc.c += fmaxf(-dist + keep * pv, 0.0f) + (dist < 0.0f ? 1.0f : 0.0f);
+#pragma unroll
+            for (int k = 0; k < TaskDims<NA>::CB; ++k) acc.prevb[k] = s == k ? dist : acc.prevb[k];
+        }
+    }
+    // ball-link and link-link passes (the ball is a capsule of zero length)
+#pragma unroll
+    for (int s = 0; s < TaskDims<NA>::CC; ++s) {
+        const int b = lane + 32 * s;
+        if (b < ncc) {
+            const bool ball = b < nball;
+            const int r = b - nball, i = r / NA, j = r - i * NA;
+            const int la = ball ? b : i, lb = ball ? 0 : NA + j;
+            const float* c0 = ball ? &w.q[d::B] : w.a0[lb];
+            const float* c1 = ball ? &w.q[d::B] : w.a1[lb];
+            const float rb = ball ? M.rb : M.link[1][j].rcap;
+            const float dist = capsule_capsule_distance(w.a0[la], w.a1[la], M.link[la / NA][la % NA].rcap, c0, c1, rb);
+            if (!first) acc.c += fmaxf(-dist + keep * acc.prevc[s], 0.0f) + (dist < 0.0f ? 1.0f : 0.0f);
+            acc.prevc[s] = dist;
         }
     }
     if (first) return;
@@ -251,7 +316,10 @@ __device__ __forceinline__ void task_state(const DevModel& M, const DevTask& T, 
         e[3] = vx;
         e[4] = vy;
         e[5] = vz;
-        rot_to_quat(Rl, e + 6);
+        // orientation error against this arm's target, on this lane
+        float qe[4];
+        rot_to_quat(Rl, qe);
+        acc.r += 0.5f * quat_angle(qe, a == 0 ? T.q1s : T.q2s);
     }
     float th = 0.0f;
     if (lane < d::NU) {
@@ -271,7 +339,6 @@ __device__ __forceinline__ void task_state(const DevModel& M, const DevTask& T, 
         acc.th += sqrtf(th);
         acc.yz += sqrtf(dp1 * dp1 + dp2 * dp2);
         acc.v2 += rv * rv;
-        acc.r += 0.5f * (quat_angle(e1 + 6, T.q1s) + quat_angle(e2 + 6, T.q2s));
         acc.l += lerr * lerr;
         const float o0 = c0 - T.pb0[0], o1 = c1 - T.pb0[1], o2 = c2 - (T.pb0[2] - T.eps);
         acc.eo += sqrtf(o0 * o0 + o1 * o1 + o2 * o2);
@@ -281,16 +348,19 @@ __device__ __forceinline__ void task_state(const DevModel& M, const DevTask& T, 
     __syncwarp();
 }
 
-// Weighted total on lane 0 after the last state (the barrier sums reduced
-// over the warp).
+// Weighted total after the last state (the barrier and orientation sums
+// reduced over the warp; the other terms from lane 0).
 template <int NA>
 __device__ __forceinline__ float task_total(const DevTask& T, TaskAcc<NA>& acc) {
-    float c = acc.c;
+    float c = acc.c, r = acc.r;
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(FULL, c, off);
+    for (int off = 16; off > 0; off >>= 1) {
+        c += __shfl_xor_sync(FULL, c, off);
+        r += __shfl_xor_sync(FULL, r, off);
+    }
     const float pick = T.phase == 0 ? 1.0f : 0.0f, move = 1.0f - pick;
     return pick * (T.w_c * c + T.w_eo * acc.eo) + move * (T.w_c * c + T.w_ot * acc.ot) + T.w_theta * acc.th +
-           T.w_yz * acc.yz + T.w_v * sqrtf(acc.v2) + T.w_r * acc.r + T.w_l * acc.l;
+           T.w_yz * acc.yz + T.w_v * sqrtf(acc.v2) + T.w_r * r + T.w_l * acc.l;
 }
 
 }  // namespace mppi

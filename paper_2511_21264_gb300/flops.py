@@ -81,16 +81,17 @@ def qp_flops(H: int, iters: int) -> float:
 
 def task_flops(scene, phase: int) -> float:
     """Algorithmic FP32 operations of the ball-task cost suite (Sec. IV-B)
-    per state: every collision pair's signed distance -- capsule-box by the
-    piece walk (nine crossing parameters, 27; the box distance at those and
-    the two ends, 11 x 22; the neighbour search, 22; two pieces' stationary
-    points and their distances, about 2 x 45: 430 in all), sphere-capsule
-    25, capsule-capsule 90 -- plus 4 for the barrier per pair, the end
-    effectors' velocities (6 per joint) and quaternions (25 each), and the
-    per-state terms (about 80)."""
+    per state: every collision pair's signed distance -- capsule-box for a
+    segment that misses the box (the slab intervals, 21; the squared
+    distance's derivative at the six crossings and both ends, 8 x 15; the
+    interpolated minimiser, 6; the distance there, 17: 165 in all; segments
+    that meet the box take the longer piece walk, not counted),
+    sphere-capsule 25, capsule-capsule 90 -- plus 4 for the barrier per
+    pair, the end effectors' velocities (6 per joint) and quaternions (25
+    each), and the per-state terms (about 80)."""
     na, nb = scene.n_a, scene.n_boxes
     pairs_box = 2 * na * nb
     pairs_ball = 2 * na if phase == 0 else 0
     pairs_arm = na * na
-    dist = pairs_box * 430 + pairs_ball * 25 + pairs_arm * 90
+    dist = pairs_box * 165 + pairs_ball * 25 + pairs_arm * 90
     return float(dist + 4 * (pairs_box + pairs_ball + pairs_arm) + 2 * na * 6 + 2 * 25 + 80)
