@@ -153,6 +153,14 @@ int mppi_sync(mppi_ctx *c, void *stream);
 int mppi_profile(mppi_ctx *c, int n);
 int mppi_profile_read(mppi_ctx *c, int *n, float *rollout_ms, float *update_ms, double *contacts_per_step,
                       double *box_tests_per_step);
+/* Of the recorded sample-steps, the fraction whose only contact is the
+ * ball against static geometry (floor or box): the Delassus block of such a
+ * contact is diagonal (its point lies on the normal through the ball's
+ * centre), so projected Gauss-Seidel is at its fixed point after one sweep
+ * and the rollout solves it directly.  Counted on the device with the
+ * statistics of mppi_profile; synchronous.  Errors: MPPI_ERR_INVALID_ARG for
+ * a NULL handle or output. */
+int mppi_profile_lone_contacts(mppi_ctx *c, double *lone_per_step);
 /* Total time (ms) of the QP projection launches over the recorded
  * iterations (0 when the projection is off); synchronises the events. */
 int mppi_profile_projection(mppi_ctx *c, float *qp_ms);

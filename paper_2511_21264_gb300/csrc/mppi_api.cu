@@ -654,6 +654,17 @@ int mppi_profile_read(mppi_ctx* c, int* n, float* rollout_ms, float* update_ms, 
     return MPPI_OK;
 }
 
+int mppi_profile_lone_contacts(mppi_ctx* c, double* lone_per_step) {
+    if (!c || !lone_per_step) return MPPI_ERR_INVALID_ARG;
+    unsigned long long st[4] = {0, 0, 0, 0};
+    if (c->d_stats) {
+        cudaError_t e = cudaMemcpy(st, c->d_stats, sizeof st, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    *lone_per_step = st[0] ? (double)st[3] / (double)st[0] : 0.0;
+    return MPPI_OK;
+}
+
 int mppi_profile_projection(mppi_ctx* c, float* qp_ms) {
     if (!c || !qp_ms) return MPPI_ERR_INVALID_ARG;
     float tq = 0.0f;

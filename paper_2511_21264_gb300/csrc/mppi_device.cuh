@@ -974,9 +974,11 @@ __device__ __forceinline__ void ball_contact_dv(const DevModel& M, const WarpWS<
     for (int r = 0; r < NR; ++r) {
 #pragma unroll
         for (int q = r; q < NR; ++q) {
-            // one contact's frame is orthonormal: e_r . e_q = delta_rq
+            // one contact's frame is orthonormal: e_r . e_q = delta_rq; a
+            // lone contact's block is diagonal (below)
             float g;
-            if (r / 3 == q / 3) g = (r == q ? im : 0.0f) + iI * dot3(D[r], D[q]);
+            if (NC == 1 && r != q) g = 0.0f;
+            else if (r / 3 == q / 3) g = (r == q ? im : 0.0f) + iI * dot3(D[r], D[q]);
             else g = sg[r / 3] * sg[q / 3] * (im * dot3(E[r], E[q]) + iI * dot3(D[r], D[q]));
             G[r][q] = g;
             G[q][r] = g;
@@ -1013,7 +1015,28 @@ __device__ __forceinline__ void ball_contact_dv(const DevModel& M, const WarpWS<
             lam[rn + 2] = l2;
         }
     };
-    if (SW > 0) {  // a sweep count fixed at compile time, unrolled
+    if constexpr (NC == 1) {
+        // One contact of the ball with static geometry (floor or box): the
+        // contact point lies on the normal through the ball's centre, so the
+        // normal row has no angular part and the tangent rows' angular parts
+        // are orthogonal -- the Delassus block is diagonal.  The first sweep
+        // then puts every row at its own minimiser (the friction disk's
+        // scaling depends on lambda_n alone) and later sweeps leave lambda
+        // there: the sweeps reduce to this one.
+        if (M.sweeps > 0) {
+            const float ln = fmaxf((vs[0] - bb[0]) * iA[0], 0.0f);
+            float l1 = -bb[1] * iA[1], l2 = -bb[2] * iA[2];
+            const float n2 = l1 * l1 + l2 * l2, lim = M.mu * ln;
+            if (n2 > lim * lim) {
+                const float sc = lim * rsqrtf(n2);
+                l1 *= sc;
+                l2 *= sc;
+            }
+            lam[0] = ln;
+            lam[1] = l1;
+            lam[2] = l2;
+        }
+    } else if (SW > 0) {  // a sweep count fixed at compile time, unrolled
 #pragma unroll
         for (int sw = 0; sw < SW; ++sw) sweep();
     } else if (M.sweeps == 4) {  // the scenes' sweep counts, unrolled
@@ -1060,7 +1083,7 @@ __device__ __forceinline__ void contacts_ball(const DevModel& M, WarpWS<NA>& w, 
 }
 
 // The free velocity and a ball-only contact solve together (one or two
-// contacts of the ball with static geometry, SW sweeps).  Every lane of an
+// contacts of the ball with static geometry; SW sweeps for two).  Every lane of an
 // arm's half-warp factors that arm's block and solves for its free velocity
 // (the operations of the one-lane factor in dynamics) while every lane runs
 // the contact solve: with no divergence between them the two independent

@@ -47,7 +47,7 @@ __device__ __forceinline__ float rollout_sample(const DevModel& M, WarpWS<NA>& w
     __syncwarp();
     float cost = 0.0f;
     const float* gb = M.goal;
-    unsigned n_exact = 0, n_con = 0;
+    unsigned n_exact = 0, n_con = 0, n_lone = 0;
     float uacc = 0.0f;  // this lane's control's sum of squares over the horizon
     float pacc = 0.0f, pbacc = 0.0f;  // this lane's contacts' depths (all, against boxes) over the horizon
     float gacc = 0.0f;  // squared goal error of this lane's ball coordinate over the horizon
@@ -118,11 +118,11 @@ __device__ __forceinline__ float rollout_sample(const DevModel& M, WarpWS<NA>& w
         n_con += ncon;
         // one ball contact with static geometry (the lift's common case):
         // the arms' solve and the contact solve run side by side
-        const bool fast = tb == 4 && ncon == 1 && (M.sweeps == 4 || M.sweeps == 3);
+        const bool fast = tb == 4 && ncon == 1;
+        n_lone += fast ? 1u : 0u;
         dynamics<NA>(M, w, lane, io.err, Rl, cl, tb, !fast);
         if (fast) {
-            if (M.sweeps == 4) solve_ball_contacts<NA, 1, 4>(M, w, lane, io.err);
-            else solve_ball_contacts<NA, 1, 3>(M, w, lane, io.err);
+            solve_ball_contacts<NA, 1, 0>(M, w, lane, io.err);
         } else {
             contacts<NA>(M, w, lane, ncon, tb);
         }
@@ -168,6 +168,7 @@ __device__ __forceinline__ float rollout_sample(const DevModel& M, WarpWS<NA>& w
         atomicAdd(&io.stats[0], (unsigned long long)io.H);
         atomicAdd(&io.stats[1], (unsigned long long)n_con);
         atomicAdd(&io.stats[2], (unsigned long long)n_exact);
+        atomicAdd(&io.stats[3], (unsigned long long)n_lone);
     }
     if (io.x_out) {
         if (lane < d::NQ) io.x_out[lane] = w.q[lane];

@@ -11,13 +11,19 @@ divisions, trigonometric, exponential and logarithmic functions run on the
 special-function units and are not FP32 FLOPs; Philox is integer work.
 
 The data-dependent terms (active contacts per step, capsule-box pairs that
-pass the bounding-sphere cull) are measured on the device during the timed
-run (mppi_profile_read).
+pass the bounding-sphere cull, steps whose only contact is the ball against
+static geometry) are measured on the device during the timed run
+(mppi_profile_read, mppi_profile_lone_contacts).
 """
 from __future__ import annotations
 
 
-def per_sample_step(scene, contacts: float, box_tests: float, breakdown: bool = False):
+def per_sample_step(scene, contacts: float, box_tests: float, lone: float = 0.0, breakdown: bool = False):
+    """lone: the sample-steps (per sample-step) whose only contact is the ball
+    against the floor or a box.  Such a contact touches the ball's six
+    coordinates alone and its Delassus block is diagonal, so it costs its
+    three rows and one projected sweep; the other contacts are charged as
+    rows over the ball and one arm chain with `sweeps` sweeps."""
     na = scene.n_a
     nl, nv, nu, nb = 2 * na, 2 * na + 6, 2 * na, scene.n_boxes
     sweeps = scene.sweeps
@@ -45,13 +51,20 @@ def per_sample_step(scene, contacts: float, box_tests: float, breakdown: bool = 
     parts["cholesky"] = 2 * (chol + solve) + 6
     # a7 contact rows: frame, Jacobian of the touched bodies (ball + one
     #    link chain), half-solve with one arm factor, diagonal, reference
+    general = max(contacts - lone, 0.0)
     touched = na + 6
     row = 12 + 18 + 19 * (na + 1) // 2 + na * (na - 1) + 2 * touched + 4
-    zf = 2 * na * (na + 1) + 6 if contacts > 0 else 0
-    back = 2 * na * (na - 1) if contacts > 0 else 0
-    parts["contact_rows"] = zf + 3 * row * contacts + back
-    # a8 PGS: per contact and sweep, normal (dot, update) and tangent pair
-    parts["pgs"] = sweeps * contacts * (12 * touched + 16)
+    zf = 2 * na * (na + 1) + 6 if general > 0 else 0
+    back = 2 * na * (na - 1) if general > 0 else 0
+    # a lone ball contact: frame (t1 10, t2 = n x t1 6), lever arm 3, Baumgarte
+    #    term 2, per row the lever-arm cross product 9, b = e.v + (d x e).w with
+    #    the side sign 12, the diagonal entry, regularisation and sum 9; the
+    #    impulse on the ball M^-1 J^T lambda 39
+    ball_rows = 16 + 3 + 2 + 3 * (9 + 12 + 9) + 39
+    parts["contact_rows"] = zf + 3 * row * general + back + ball_rows * lone
+    # a8 PGS: per contact and sweep, normal (dot, update) and tangent pair; a
+    #    lone ball contact's one sweep: normal 2, tangents 2, friction disk 8
+    parts["pgs"] = sweeps * general * (12 * touched + 16) + 12 * lone
     # a9 integration (coordinates, quaternion)
     parts["integrate"] = 2 * (2 * na + 3) + 50
     # a10 stage cost

@@ -154,6 +154,7 @@ def lib():
     _decl(L, "mppi_profile_read", i, [vp, C.POINTER(i), C.POINTER(C.c_float), C.POINTER(C.c_float),
                                        C.POINTER(C.c_double), C.POINTER(C.c_double)])
     _decl(L, "mppi_profile_projection", i, [vp, C.POINTER(C.c_float)])
+    _decl(L, "mppi_profile_lone_contacts", i, [vp, C.POINTER(C.c_double)])
     _decl(L, "mppi_qp_project", i, [i, i, C.c_float, fp, i, C.c_float, fp, fp, fp, fp, fp, vp])
     _decl(L, "mppi_set_projection", i, [vp, fp, i, C.c_float, fp])
     _decl(L, "mppi_get_samples", i, [vp, fp, vp])
@@ -519,11 +520,13 @@ class Controller:
 
     def profile_read(self):
         n, tr, tu = C.c_int(), C.c_float(), C.c_float()
-        cps, bps = C.c_double(), C.c_double()
+        cps, bps, lps = C.c_double(), C.c_double(), C.c_double()
         _check(lib().mppi_profile_read(self._h, C.byref(n), C.byref(tr), C.byref(tu), C.byref(cps),
                                        C.byref(bps)), "mppi_profile_read")
+        _check(lib().mppi_profile_lone_contacts(self._h, C.byref(lps)), "mppi_profile_lone_contacts")
         return {"iterations": n.value, "rollout_ms": tr.value, "update_ms": tu.value,
-                "contacts_per_step": cps.value, "box_tests_per_step": bps.value}
+                "contacts_per_step": cps.value, "box_tests_per_step": bps.value,
+                "lone_ball_per_step": lps.value}
 
     def set_update(self, n_elite: int, eta: float = 1.0, update_cov: bool = False, cov_floor: float = 0.0):
         """The paper's full Eq. 8: elite set size, learning rate, covariance update."""

@@ -250,6 +250,40 @@ def test_mppi_step_parity_planar(native):
     np.testing.assert_allclose(out.cpu().numpy(), ref["u_nom"], atol=1e-3, rtol=0)
 
 
+@pytest.mark.parametrize("cfg,lift", [(1, 0.03), (3, 0.0)])
+def test_profile_contact_counts_match_oracle_rollouts(native, cfg, lift):
+    # mppi_profile's device counts against the oracle's rollouts of the same
+    # Philox samples: active contacts per sample-step, and the steps whose
+    # only contact is the ball against static geometry (the lone-contact
+    # solve).  The start states mix steps with no contact, a lone ball
+    # contact and arm contacts.  Contact activation at |distance| ~ 0 may
+    # differ between FP32 and FP64, so the means agree to 2% of the steps.
+    K, H = 64, 16
+    sc, gm, om, ctl, key = _setup(cfg, K=K, H=H)
+    x = _f32(scenes.random_states(sc, 1, 1, ball_lift=lift)[0])
+    u0 = np.zeros((H, sc.nu))
+    ctl.profile(1)
+    out = _t(u0)
+    ctl.step(_t(x), _t(u0), out)
+    assert ctl.sync() == 0
+    kt = ctl.profile_read()
+    ctl.profile(0)
+    U = om.mppi_iteration(x, u0, K, sc.lam, _f32(sc.sigma_vec()), key, 0, want_samples=True)["U"]
+    ball = 2 * sc.n_a
+    con = lone = 0
+    for k in range(K):
+        xk = x
+        for h in range(H):
+            xk, info, lam, cl = om.step(xk, U[k, h], want_contacts=True)
+            con += info.ncon
+            lone += int(info.ncon == 1 and cl[0]["bodyA"] == ball and cl[0]["bodyB"] == -1)
+    assert kt["iterations"] == 1
+    assert abs(kt["contacts_per_step"] - con / (K * H)) <= 0.02, (kt, con / (K * H))
+    assert abs(kt["lone_ball_per_step"] - lone / (K * H)) <= 0.02, (kt, lone / (K * H))
+    assert 0.2 < lone / (K * H) < 0.8  # both kinds of step occur
+    assert kt["lone_ball_per_step"] <= kt["contacts_per_step"] + 1e-12
+
+
 def test_step_aliasing_and_graph_replay_are_deterministic(native):
     K, H = 96, 8
     sc, gm, om, ctl, key = _setup(2, K=K, H=H)
