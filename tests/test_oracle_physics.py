@@ -172,3 +172,74 @@ def test_velocity_servo_settles_at_commanded_rate():
             x, _ = m.step(x, u)
         assert x[sc.nq + 0] == pytest.approx(expect, rel=1e-9)
         assert x[sc.nq + 1] == pytest.approx(-expect, rel=1e-9)
+
+
+def _sweep_pair(sc):
+    one, four = copy.deepcopy(sc), copy.deepcopy(sc)
+    one.sweeps, four.sweeps = 1, 4
+    return oracle.Model(one.to_blob()), oracle.Model(four.to_blob())
+
+
+def _first_box_at(sc, c, h):
+    sc = copy.deepcopy(sc)
+    bc, bh = np.array(sc.boxes_c), np.array(sc.boxes_h)
+    bc[0], bh[0] = c, h
+    sc.boxes_c, sc.boxes_h = bc, bh
+    return sc
+
+
+def test_lone_ball_contact_is_solved_by_one_sweep():
+    """A lone contact of the ball with the floor or a box has its point on
+    the normal through the ball's centre, so its Delassus block is diagonal
+    and projected Gauss-Seidel stops moving after the first sweep: one sweep
+    and four give the same step (the reading behind the rollout's one-sweep
+    solve of this case).  Two coupled contacts (the ball pressed into the
+    floor and a box side) do depend on the sweep count."""
+    rng = np.random.default_rng(11)
+    worst = 0.0
+    # the floor, the ball sliding and spinning in any direction
+    sc = helpers.ball_far(scenes.config(1), pos=(0.0, 3.0, 0.1))
+    m1, m4 = _sweep_pair(sc)
+    b = 2 * sc.n_a
+    for _ in range(20):
+        x = sc.x0.copy()
+        x[b + 2] = sc.ball_r - 1e-3 * rng.uniform()
+        x[sc.nq + b:sc.nq + b + 6] = rng.normal(size=6)
+        x1, i1, _, c1 = m1.step(x, np.zeros(sc.nu), want_contacts=True)
+        x4, _ = m4.step(x, np.zeros(sc.nu))
+        assert i1.ncon == 1 and c1[0]["bodyB"] == -1 and c1[0]["box"] == -1
+        worst = max(worst, np.abs(x1 - x4).max())
+    # a box face from outside, and the centre inside the box
+    base = helpers.ball_far(scenes.config(3), pos=(0.0, 3.0, 1.0))
+    b, r = 2 * base.n_a, base.ball_r
+    c, h = np.array((0.0, 3.0, 1.0)), np.array((0.1, 0.08, 0.12))
+    sc = _first_box_at(base, c, h)
+    m1, m4 = _sweep_pair(sc)
+    for t in range(30):
+        x = sc.x0.copy()
+        off = rng.uniform(-0.5, 0.5, size=3) * h
+        if t % 5 != 4:
+            ax = t % 3
+            off[ax] = (1 if t % 2 == 0 else -1) * (h[ax] + r - 1e-3 * rng.uniform())
+        x[b:b + 3] = c + off
+        x[sc.nq + b:sc.nq + b + 6] = rng.normal(size=6)
+        x1, i1, _, c1 = m1.step(x, np.zeros(sc.nu), want_contacts=True)
+        x4, _ = m4.step(x, np.zeros(sc.nu))
+        assert i1.ncon == 1 and c1[0]["bodyB"] == -1 and c1[0]["box"] == 0
+        worst = max(worst, np.abs(x1 - x4).max())
+    assert worst < 1e-12, worst
+    # control: floor and a box side together
+    sc = _first_box_at(base, (0.0, 3.0, h[2] + 0.05), h)
+    m1, m4 = _sweep_pair(sc)
+    gap = 0.0
+    for _ in range(5):
+        x = sc.x0.copy()
+        x[b:b + 3] = (h[0] + r - 1e-3, 3.0, r - 1e-3)
+        v = rng.normal(size=6)
+        v[0], v[2] = -abs(v[0]) - 0.5, -abs(v[2]) - 0.5
+        x[sc.nq + b:sc.nq + b + 6] = v
+        x1, i1 = m1.step(x, np.zeros(sc.nu))
+        x4, _ = m4.step(x, np.zeros(sc.nu))
+        assert i1.ncon == 2
+        gap = max(gap, np.abs(x1 - x4).max())
+    assert gap > 1e-2, gap
