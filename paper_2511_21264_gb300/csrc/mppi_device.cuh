@@ -232,20 +232,21 @@ __device__ __forceinline__ void forward_kinematics(const DevModel& M, WarpWS<NA>
         for (int k = 0; k < 9; ++k) Rp[k] = __shfl_up_sync(FULL, R[k], off, 16);
 #pragma unroll
         for (int k = 0; k < 3; ++k) pp[k] = __shfl_up_sync(FULL, p[k], off, 16);
-        if (i >= off) {
-            float Rn[9], pn[3];
+        // every lane forms the product; lanes with no predecessor this far
+        // back keep their transform (a select, no divergent branch)
+        const bool take = i >= off;
+        float Rn[9], pn[3];
 #pragma unroll
-            for (int r = 0; r < 3; ++r) {
+        for (int r = 0; r < 3; ++r) {
 #pragma unroll
-                for (int cc = 0; cc < 3; ++cc)
-                    Rn[3 * r + cc] = Rp[3 * r] * R[cc] + Rp[3 * r + 1] * R[3 + cc] + Rp[3 * r + 2] * R[6 + cc];
-                pn[r] = Rp[3 * r] * p[0] + Rp[3 * r + 1] * p[1] + Rp[3 * r + 2] * p[2] + pp[r];
-            }
-#pragma unroll
-            for (int k = 0; k < 9; ++k) R[k] = Rn[k];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) p[k] = pn[k];
+            for (int cc = 0; cc < 3; ++cc)
+                Rn[3 * r + cc] = Rp[3 * r] * R[cc] + Rp[3 * r + 1] * R[3 + cc] + Rp[3 * r + 2] * R[6 + cc];
+            pn[r] = Rp[3 * r] * p[0] + Rp[3 * r + 1] * p[1] + Rp[3 * r + 2] * p[2] + pp[r];
         }
+#pragma unroll
+        for (int k = 0; k < 9; ++k) R[k] = take ? Rn[k] : R[k];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) p[k] = take ? pn[k] : p[k];
     }
     // world frame: base * chain
     const float* B = M.baseR[a];
