@@ -279,7 +279,7 @@ def run_ours(args):
     # (sm__sass_thread_inst_executed_op_{ffma,fadd,fmul}_pred_on.sum), which
     # count redundant lanes too; null for the other configurations.
     plain = not (elite or args.qp or args.task is not None)
-    captured = {"lift": (78592.0, 1315668264.0), "transfer": (84992.0, 11437105784.0)}
+    captured = {"lift": (78848.0, 1334935848.0), "transfer": (129280.0, 11593654904.0)}
     traffic, exec_flops = captured.get(args.workload, (None, None)) if plain else (None, None)
     if args.traffic is not None:
         traffic = args.traffic
