@@ -60,8 +60,10 @@ typedef struct mppi_ctx mppi_ctx;
 const char *mppi_strerror(int code);
 
 /* ---------------------------------------------------------------- model */
-/* Parse a scene blob (host memory, `len` bytes; layout: u32 magic
- * 0x4950504D, u32 version 1, u32 count, u32 0, then `count` float64 values
+/* The world model f of Eq. 1b (Sec. III): the simulator that maps a state
+ * and one control to the next state.  Parse a scene blob (host memory,
+ * `len` bytes; layout: u32 magic 0x4950504D, u32 version 1, u32 count,
+ * u32 0, then `count` float64 values
  * -- kinematics, inertias, capsule geometry, contact constants, boxes, cost
  * weights, home state) and upload it to the current device.  The blob is
  * copied; the caller keeps ownership of it.  *out receives an immutable
@@ -115,18 +117,22 @@ int mppi_solve(mppi_ctx *c, const float *state, float *u_nom_inout, int iters, f
  * advance the counter. */
 int mppi_update(mppi_ctx *c, const float *costs, const float *u_nom, float *u_out, void *stream);
 
-/* Roll out n explicit control sequences: states (n x nx), U (n x H x nu),
+/* The world model f of Eq. 1b (Sec. III) applied H times per sequence, with
+ * the stage costs summed as in Alg. 1's rollout and cost step.
+ * Roll out n explicit control sequences: states (n x nx), U (n x H x nu),
  * costs (n) -- the same simulator and stage costs as mppi_step with the
  * controls given instead of sampled.  states_out (optional, n x nx): the
  * state after the last step.  n <= K of the handle. */
 int rollout_batch(mppi_ctx *c, int n, const float *states, const float *U, float *costs,
                   float *states_out, void *stream);
 
-/* One simulator step for n states in place: states_inout (n x nx), U1
+/* One application of the world model f of Eq. 1b (Sec. III): x' = f(x, u).
+ * One simulator step for n states in place: states_inout (n x nx), U1
  * (n x nu).  n <= K. */
 int sim_step(mppi_ctx *c, int n, float *states_inout, const float *U1, void *stream);
 
-/* Materialise the Philox noise of iteration `iteration`: eps_out
+/* Alg. 1's sampling step (control perturbations drawn from N(0, Sigma)).
+ * Materialise the Philox noise of iteration `iteration`: eps_out
  * (K x H x nu).  For tests. */
 int mppi_debug_noise(mppi_ctx *c, uint64_t iteration, float *eps_out, void *stream);
 
