@@ -2,12 +2,15 @@
 
 A step is one MPPI iteration (Alg. 1 loop body: Philox sampling, H-step
 contact rollouts of K samples, stage costs, softmax weights, weighted-mean
-update) of the two 7-DoF arms / 0.12 m ball lift scene with K = 1024
-samples and H = 32 steps (dt = 0.01 s, 4 PGS sweeps), on synthetic seeded
-inputs.  value = simulated sample-steps/s = K * H * steps / time over all
-ranks (each rank runs its own independent controller: weak scaling).
+update).  The headline workload is the largest single-controller one: two
+7-DoF arms carrying a 0.10 m ball past 8 static boxes, K = 4096 samples,
+H = 64 steps (dt = 0.01 s, 4 PGS sweeps), on synthetic seeded inputs; the
+line also carries the smaller ball lift (K = 1024, H = 32) under "lift".
+value = simulated sample-steps/s = K * H * steps / time over all ranks (each
+rank runs its own independent controller: weak scaling).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload transfer|lift|batched|serve|closed_loop]
 
 --impl reference times the FP64 CPU oracle on the host cores on a bounded
 sample of the same workload (the comparison arm for this project).
@@ -42,7 +45,7 @@ WORKLOADS = {
 }
 
 
-def _config_json(sc, n_gpus, workload="lift"):
+def _config_json(sc, n_gpus, workload="transfer"):
     return {"workload": WORKLOADS[workload], "scene": sc.name, "K": sc.K, "H": sc.H, "nv": sc.nv, "n_boxes": sc.n_boxes,
             "lambda": sc.lam, "sigma": sc.sigma, "per_rank": "one independent controller (own Philox key)",
             "parallelism": f"replicas x{n_gpus}",
@@ -163,11 +166,63 @@ def cpu_baseline(sc, seconds=15.0, nthreads=None):
                       f"of K'={K1}"}
 
 
+def _scene(workload):
+    if workload in ("lift", "transfer"):
+        return scenes.config(3 if workload == "transfer" else 2)
+    raise ValueError(workload)
+
+
+def _metric(workload):
+    return METRIC if workload == "lift" else METRIC.replace("MPPI iteration", "MPPI iteration, " + workload)
+
+
+PROFILE_FILES = {"transfer": "rollout_kernel_dh7_transfer_K4096_H64.md",
+                 "lift": "rollout_kernel_dh7_lift_K1024_H32.md"}
+KERNEL_SOURCES = ("mppi_device.cuh", "mppi_kernels.cuh", "mppi_task.cuh", "mppi_internal.h")
+
+
+def kernel_source_hash():
+    """sha256 over the source files that make up the rollout kernel (and the
+    floating-point flags they are compiled with)."""
+    import hashlib
+    from paper_2511_21264_gb300 import native
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2511_21264_gb300", "csrc")
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + b"\0" + f.read())
+    h.update(" ".join(native.FP_FLAGS).encode())
+    return h.hexdigest()[:16]
+
+
+def profile_counters(workload):
+    """DRAM traffic and executed FP32 operations of one rollout launch from
+    the committed ncu summary of this workload.  The summary carries one
+    line `counters: {json}` with the kernel-source hash it was taken at;
+    when the sources have changed since, the counters are stale and
+    (None, None, reason) is returned."""
+    name = PROFILE_FILES.get(workload)
+    if name is None:
+        return None, None, "no ncu summary for this workload"
+    path = os.path.join(ROOT, "profiles", name)
+    try:
+        with open(path) as f:
+            rows = [ln for ln in f if ln.startswith("counters: ")]
+    except OSError:
+        return None, None, f"profiles/{name} missing"
+    if not rows:
+        return None, None, f"profiles/{name} has no counters line"
+    c = json.loads(rows[-1][len("counters: "):])
+    if c.get("source_hash") != kernel_source_hash():
+        return None, None, f"profiles/{name}: kernel sources changed since the capture"
+    return float(c["dram_bytes_per_launch"]), float(c["fp32_flops_per_launch"]), f"profiles/{name}"
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", 0))
     if rank != 0:
         return 0
-    sc = scenes.config(2)
+    sc = _scene(args.workload)
     nthreads = os.cpu_count() or 1
     import oracle
     om = oracle.Model(sc.to_blob())
@@ -181,10 +236,10 @@ def run_reference(args):
         om.mppi_iteration(x, u, Kp, sc.lam, sc.sigma_vec(), 1, args.warmup + s, nthreads=nthreads)
     el = time.perf_counter() - t0
     value = Kp * sc.H * args.steps / el
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+    line = {"impl": "reference", "metric": _metric(args.workload), "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": _config_json(sc, args.gpus),
+            "data": "synthetic", "config": _config_json(sc, args.gpus, args.workload),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthreads, "kind": "oracle",
                              "sample": f"each step: one MPPI iteration with K'={Kp} of K={sc.K} samples"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -192,16 +247,13 @@ def run_reference(args):
     return 0
 
 
-def run_ours(args):
+def _measure(args, workload, steps, dev, stream, flush, world, local, rank):
+    """Times `steps` MPPI iterations of one workload (per-step CUDA events,
+    L2 flushed between steps), then the same iterations end to end through
+    mppi_step_host with host buffers.  Returns the numbers of the line."""
     import torch
     from paper_2511_21264_gb300 import native
-
-    rank, world, local = _dist_setup(args.gpus)
-    dev = torch.device(f"cuda:{local}")
-    torch.cuda.set_device(dev)
-    native.build() if rank == 0 and world == 1 else None
-    native.lib()
-    sc = scenes.config(3 if args.workload == "transfer" else 2)
+    sc = _scene(workload)
     K, H = sc.K, sc.H
     model = native.Model(sc.to_blob())
     ctl = native.Controller(model, K, H, sc.lam, sc.sigma_vec(), scenes.controller_key(sc.seed, rank))
@@ -213,20 +265,18 @@ def run_ours(args):
         ctl.set_projection(scenes.projection_bounds(sc), iters=args.qp)
     if args.task is not None:
         ctl.set_task_cost(scenes.ball_task(sc, phase=args.task))
-    stream = torch.cuda.Stream(device=dev)
     x = torch.tensor(model.home(), device=dev)
     u = torch.zeros((H, sc.nu), device=dev)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             ctl.step(x, u, u, stream=stream)
         stream.synchronize()
         _barrier(world)
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        ctl.profile(args.steps)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        ctl.profile(steps)
         with ClockSampler(local) as clk:
             time.sleep(0.3)
-            for i in range(args.steps):
+            for i in range(steps):
                 flush.fill_(i & 0xFF)
                 ev[i][0].record(stream)
                 ctl.step(x, u, u, stream=stream)
@@ -250,18 +300,13 @@ def run_ours(args):
         _barrier(world)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for i in range(args.steps):
+        for i in range(steps):
             ctl.step_host(xh, uh, uh, stream=stream)
         e1.record(stream)
         stream.synchronize()
         e2e_ms = _max_over_ranks(e0.elapsed_time(e1), world)
-
-    units = K * H * args.steps * world
-    value = units / (total_ms * 1e-3)
-    e2e = units / (e2e_ms * 1e-3)
+    units = K * H * steps * world
     clocks = clk.summary()
-    if rank != 0:
-        return 0
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
     sm_mhz = clocks["sm_mhz"] or 1477.0
@@ -272,45 +317,72 @@ def run_ours(args):
     roll_ms = kt["rollout_ms"] / max(1, kt["iterations"])
     achieved = fl * K * H / (roll_ms * 1e-3) / 1e12
     elite = bool(args.elite or args.eta != 1.0 or args.cov)
-    # From one ncu capture of the current rollout_kernel<7,1,0> per workload
-    # (the fourth launch of `bench.py --steps 4 --warmup 3`): DRAM traffic
-    # dram__bytes_read.sum + dram__bytes_write.sum, and the FP32 operations
-    # the kernel executed, 2 x FFMA + FADD + FMUL thread instructions
-    # (sm__sass_thread_inst_executed_op_{ffma,fadd,fmul}_pred_on.sum), which
-    # count redundant lanes too; null for the other configurations.
     plain = not (elite or args.qp or args.task is not None)
-    captured = {"lift": (78848.0, 1334935848.0), "transfer": (129280.0, 11593654904.0)}
-    traffic, exec_flops = captured.get(args.workload, (None, None)) if plain else (None, None)
-    if args.traffic is not None:
-        traffic = args.traffic
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": _config_json(sc, world, args.workload),
-        "iters_per_s": args.steps * world / (total_ms * 1e-3),
-        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(4 * (x.numel() + u.numel())),
-                "d2h_bytes_per_step": int(4 * u.numel())},
-        "gpu_launches": (2 + (1 if elite else 0) + (1 if args.qp else 0)) * args.steps,
-        "roofline": {"bound": "alu", "kernel": "rollout_kernel<7,1>", "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
-                     "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (median SM clock "
-                                   f"sampled during the timed steps)",
-                     "flops_per_sample_step": fl, "rollout_ms": roll_ms,
-                     "update_ms": kt["update_ms"] / max(1, kt["iterations"]),
-                     "contacts_per_step": kt["contacts_per_step"],
-                     "box_tests_per_step": kt["box_tests_per_step"],
-                     "lone_ball_per_step": kt["lone_ball_per_step"]},
-        "clocks": clocks,
-    }
+    # DRAM traffic and executed FP32 operations of one rollout launch come
+    # from the committed ncu summary of the workload, taken at the current
+    # kernel sources; null when there is none or it is stale
+    traffic, exec_flops, source = profile_counters(workload) if plain else (None, None, "not captured")
+    roof = {"bound": "alu", "kernel": "rollout_kernel<7,1>", "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic, "traffic_source": source,
+            "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (median SM clock "
+                          f"sampled during the timed steps)",
+            "flops_per_sample_step": fl, "rollout_ms": roll_ms,
+            "update_ms": kt["update_ms"] / max(1, kt["iterations"]),
+            "contacts_per_step": kt["contacts_per_step"],
+            "box_tests_per_step": kt["box_tests_per_step"],
+            "lone_ball_per_step": kt["lone_ball_per_step"]}
     if exec_flops is not None:
         ex = exec_flops / (roll_ms * 1e-3) / 1e12
-        line["roofline"]["ncu_executed"] = {
+        roof["ncu_executed"] = {
             "flops_per_launch": exec_flops, "achieved": ex, "frac": ex / peak,
             "per_sample_step": exec_flops / (K * H),
             "basis": "ncu FP32 thread instructions of one launch (2 x FFMA + FADD + FMUL) / live mean duration"}
-    if args.workload != "lift":
-        line["metric"] = METRIC.replace("MPPI iteration", "MPPI iteration, " + args.workload)
+    return {"sc": sc, "value": units / (total_ms * 1e-3), "e2e": units / (e2e_ms * 1e-3),
+            "ms_per_step": total_ms / steps, "iters_per_s": steps * world / (total_ms * 1e-3),
+            "h2d": int(4 * (x.numel() + u.numel())), "d2h": int(4 * u.numel()),
+            "roofline": roof, "clocks": clocks, "qp_ms": qp_ms, "peak": peak, "elite": elite}
+
+
+def run_ours(args):
+    import torch
+    from paper_2511_21264_gb300 import native
+
+    rank, world, local = _dist_setup(args.gpus)
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    native.build() if rank == 0 and world == 1 else None
+    native.lib()
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    m = _measure(args, args.workload, args.steps, dev, stream, flush, world, local, rank)
+    extra = None
+    plain = not (m["elite"] or args.qp or args.task is not None)
+    if args.workload == "transfer" and plain and not args.no_lift:
+        # the smaller single-controller workload, reported beside the headline
+        extra = _measure(args, "lift", max(args.steps, 200), dev, stream, flush, world, local, rank)
+    if rank != 0:
+        return 0
+    sc = m["sc"]
+    K, H = sc.K, sc.H
+    elite = m["elite"]
+    line = {
+        "metric": _metric(args.workload), "value": m["value"], "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": _config_json(sc, world, args.workload),
+        "iters_per_s": m["iters_per_s"],
+        "e2e": {"value": m["e2e"], "unit": UNIT, "h2d_bytes_per_step": m["h2d"], "d2h_bytes_per_step": m["d2h"]},
+        "gpu_launches": (2 + (1 if elite else 0) + (1 if args.qp else 0)) * args.steps,
+        "roofline": m["roofline"],
+        "clocks": m["clocks"],
+    }
+    if extra is not None:
+        line["lift"] = {"workload": WORKLOADS["lift"], "value": extra["value"], "unit": UNIT,
+                        "ms_per_step": extra["ms_per_step"], "iters_per_s": extra["iters_per_s"],
+                        "e2e": extra["e2e"], "roofline_frac": extra["roofline"]["frac"],
+                        "rollout_ms": extra["roofline"]["rollout_ms"],
+                        "flops_per_sample_step": extra["roofline"]["flops_per_sample_step"],
+                        "traffic": extra["roofline"]["traffic"], "clocks": extra["clocks"]}
     if elite:
         line["config"]["update"] = {"n_elite": args.elite or K, "eta": args.eta, "covariance": bool(args.cov)}
         line["metric"] = line["metric"].replace("weights + update", "elite set + Eq. 8 update")
@@ -319,10 +391,10 @@ def run_ours(args):
         line["config"]["projection"] = {"iters": args.qp, "rho": 1.0,
                                         "bounds": "home +-1 rad, +-pi rad/s, +-10 rad/s^2, +-300 rad/s^3"}
         line["metric"] = line["metric"].replace("sample + rollout", "sample + QP projection + rollout")
-        qa = qfl * K * sc.nu / (qp_ms * 1e-3) / 1e12
-        line["qp_projection"] = {"kernel": "qp_project_kernel", "ms": qp_ms, "bound": "alu",
-                                 "flops_per_sequence": qfl, "achieved": qa, "peak": peak, "unit": "TFLOP/s",
-                                 "frac": qa / peak}
+        qa = qfl * K * sc.nu / (m["qp_ms"] * 1e-3) / 1e12
+        line["qp_projection"] = {"kernel": "qp_project_kernel", "ms": m["qp_ms"], "bound": "alu",
+                                 "flops_per_sequence": qfl, "achieved": qa, "peak": m["peak"],
+                                 "unit": "TFLOP/s", "frac": qa / m["peak"]}
     if args.task is not None:
         line["config"]["cost"] = {"suite": "ball task (Sec. IV-B)", "phase": "pick" if args.task == 0 else "move"}
         line["metric"] = line["metric"].replace("+ cost +", "+ ball-task cost suite +")
@@ -594,9 +666,10 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=("lift", "transfer", "batched", "serve", "closed_loop"), default="lift",
-                    help="lift: 7-DoF ball lift K=1024 H=32 (default); transfer: 8-box transfer K=4096 "
-                         "H=64; batched: 64 instances (K 256..4096, H 16..64, 0..16 boxes) in one "
+    ap.add_argument("--workload", choices=("lift", "transfer", "batched", "serve", "closed_loop"),
+                    default="transfer",
+                    help="transfer: 8-box transfer K=4096 H=64 (default; the line also carries the lift); "
+                         "lift: 7-DoF ball lift K=1024 H=32; batched: 64 instances (K 256..4096, H 16..64, 0..16 boxes) in one "
                          "persistent launch vs 64 sequential plain launches; serve: Poisson replan "
                          "requests over 256 scenes, batched server vs one-at-a-time server; closed_loop: "
                          "receding-horizon episodes with the paper's success / task-time / compute-time metrics")
@@ -613,9 +686,7 @@ def main(argv=None):
     ap.add_argument("--spc", type=int, default=0, help="samples per CTA (0 = library default)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--traffic", type=float, default=None,
-                    help="DRAM bytes per rollout launch from an ncu capture (default: the lift workload's "
-                         "capture of the current rollout kernel; null for the others)")
+    ap.add_argument("--no-lift", action="store_true", help="transfer: skip the extra lift measurement")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -452,9 +452,14 @@ int srv_run_load(mppi_server *s, double rate_hz, double duration_s, uint64_t see
  *   state (device, nx), u_nom, u_nom_out (device, H x nu; may alias)
  *   status_out  optional host int: when non-NULL the call synchronises
  *               `stream` and stores the device status (MPPI_OK,
- *               MPPI_ERR_NONFINITE, MPPI_ERR_CHOLESKY)
+ *               MPPI_ERR_NONFINITE, MPPI_ERR_CHOLESKY); when NULL the call
+ *               only enqueues work and does not wait for the stream
+ * The model and parameters reach the device as a kernel parameter of the
+ * call's first launch, so no host buffer is read after the call returns.
  * The first call on a device looks up the array's device address with that
- * device current; make that first call before any stream capture.  Every
+ * device current and keeps it for the life of the process; make that first
+ * call before any stream capture, and do not use this entry point after a
+ * cudaDeviceReset on that device (the kept address would be stale).  Every
  * call shares the array and it keeps the last call's contents (the error
  * word is cleared at the start of each call): calls that overlap on the GPU
  * -- on different streams, or from different host threads -- race. */

@@ -314,15 +314,21 @@ size_t rollout_smem_bytes(int na, int spc, int unom_floats) {
 
 // Parse the scene blob into the device representation.
 int parse_model_blob(const void* blob, size_t len, DevModel* out, HostModelInfo* info) {
-    if (!blob || len < 16) return MPPI_ERR_INVALID_ARG;
+    // Values are read one at a time with memcpy (the blob need not be
+    // 8-byte aligned) and nothing is allocated unless `info` is given.
+    if (!blob || !out || len < 16) return MPPI_ERR_INVALID_ARG;
+    const unsigned char* raw = static_cast<const unsigned char*>(blob);
     uint32_t h[4];
-    std::memcpy(h, blob, 16);
+    std::memcpy(h, raw, 16);
     if (h[0] != 0x4950504Du || h[1] != 1u) return MPPI_ERR_INVALID_ARG;
     const size_t n = h[2];
     if (n < 23 || len < 16 + 8 * n) return MPPI_ERR_INVALID_ARG;
-    std::vector<double> v(n);
-    std::memcpy(v.data(), static_cast<const unsigned char*>(blob) + 16, 8 * n);
-    const int na = (int)v[0], nb = (int)v[1], maxc = (int)v[2];
+    auto v = [raw](size_t i) {
+        double x;
+        std::memcpy(&x, raw + 16 + 8 * i, 8);
+        return x;
+    };
+    const int na = (int)v(0), nb = (int)v(1), maxc = (int)v(2);
     if (na < 1 || na > MAXL || nb < 0 || nb > MAXB || maxc < 1 || maxc > 16) return MPPI_ERR_INVALID_ARG;
     if (maxc > MAXC) return MPPI_ERR_UNSUPPORTED;  // more contacts than the device solver keeps
     const int nq = 2 * na + 7, nv = 2 * na + 6;
@@ -332,62 +338,62 @@ int parse_model_blob(const void* blob, size_t len, DevModel* out, HostModelInfo*
     M.na = na;
     M.nb = nb;
     M.maxc = maxc;
-    M.dt = (float)v[3];
-    M.sweeps = (int)v[4];
-    M.mu = (float)v[5];
-    M.imp = (float)v[6];
-    M.erp = (float)v[7];
-    for (int k = 0; k < 3; ++k) M.g[k] = (float)v[8 + k];
-    M.floor_z = (float)v[11];
-    M.rb = (float)v[12];
-    M.mb = (float)v[13];
-    M.Ib = (float)v[14];
-    for (int k = 0; k < 3; ++k) M.goal[k] = (float)v[15 + k];
-    M.w_goal = (float)v[18];
-    M.w_u = (float)v[19];
-    M.w_pen = (float)v[20];
-    M.w_obst = (float)v[21];
-    M.w_grasp = (float)v[22];
+    M.dt = (float)v(3);
+    M.sweeps = (int)v(4);
+    M.mu = (float)v(5);
+    M.imp = (float)v(6);
+    M.erp = (float)v(7);
+    for (int k = 0; k < 3; ++k) M.g[k] = (float)v(8 + k);
+    M.floor_z = (float)v(11);
+    M.rb = (float)v(12);
+    M.mb = (float)v(13);
+    M.Ib = (float)v(14);
+    for (int k = 0; k < 3; ++k) M.goal[k] = (float)v(15 + k);
+    M.w_goal = (float)v(18);
+    M.w_u = (float)v(19);
+    M.w_pen = (float)v(20);
+    M.w_obst = (float)v(21);
+    M.w_grasp = (float)v(22);
     if (!(M.dt > 0) || M.sweeps < 0 || M.sweeps > 1000 || !(M.imp > 0 && M.imp <= 1) || !(M.mb > 0) || !(M.Ib > 0))
         return MPPI_ERR_INVALID_ARG;
     size_t o = 23;
     for (int a = 0; a < 2; ++a) {
-        for (int k = 0; k < 9; ++k) M.baseR[a][k] = (float)v[o++];
-        for (int k = 0; k < 3; ++k) M.basep[a][k] = (float)v[o++];
+        for (int k = 0; k < 9; ++k) M.baseR[a][k] = (float)v(o++);
+        for (int k = 0; k < 3; ++k) M.basep[a][k] = (float)v(o++);
         for (int i = 0; i < na; ++i) {
             DevLink& L = M.link[a][i];
-            for (int k = 0; k < 9; ++k) L.FR[k] = (float)v[o++];
-            for (int k = 0; k < 3; ++k) L.Fp[k] = (float)v[o++];
-            L.mass = (float)v[o++];
-            for (int k = 0; k < 3; ++k) L.com[k] = (float)v[o++];
+            for (int k = 0; k < 9; ++k) L.FR[k] = (float)v(o++);
+            for (int k = 0; k < 3; ++k) L.Fp[k] = (float)v(o++);
+            L.mass = (float)v(o++);
+            for (int k = 0; k < 3; ++k) L.com[k] = (float)v(o++);
             double I[9];
-            for (int k = 0; k < 9; ++k) I[k] = v[o++];
+            for (int k = 0; k < 9; ++k) I[k] = v(o++);
             L.I[0] = (float)I[0];
             L.I[1] = (float)I[4];
             L.I[2] = (float)I[8];
             L.I[3] = (float)(0.5 * (I[1] + I[3]));
             L.I[4] = (float)(0.5 * (I[2] + I[6]));
             L.I[5] = (float)(0.5 * (I[5] + I[7]));
-            for (int k = 0; k < 3; ++k) L.s0[k] = (float)v[o++];
-            for (int k = 0; k < 3; ++k) L.s1[k] = (float)v[o++];
-            L.rcap = (float)v[o++];
-            const double damping = v[o++], kv = v[o++];
+            for (int k = 0; k < 3; ++k) L.s0[k] = (float)v(o++);
+            for (int k = 0; k < 3; ++k) L.s1[k] = (float)v(o++);
+            L.rcap = (float)v(o++);
+            const double damping = v(o++), kv = v(o++);
             L.D = (float)(damping + kv);
-            L.gear = (float)v[o++];
-            L.tau_max = (float)v[o++];
-            L.u_lo = (float)v[o++];
-            L.u_hi = (float)v[o++];
-            L.gravcomp = (float)v[o++];
+            L.gear = (float)v(o++);
+            L.tau_max = (float)v(o++);
+            L.u_lo = (float)v(o++);
+            L.u_hi = (float)v(o++);
+            L.gravcomp = (float)v(o++);
             if (!(L.mass > 0)) return MPPI_ERR_INVALID_ARG;
         }
     }
     for (int b = 0; b < nb; ++b)
-        for (int k = 0; k < 6; ++k) M.box[b][k] = (float)v[o++];
+        for (int k = 0; k < 6; ++k) M.box[b][k] = (float)v(o++);
     if (info) {
         info->na = na;
         info->nb = nb;
         info->x0.assign(nq + nv, 0.0f);
-        for (int k = 0; k < nq + nv; ++k) info->x0[k] = (float)v[o + k];
+        for (int k = 0; k < nq + nv; ++k) info->x0[k] = (float)v(o + k);
     }
     *out = M;
     return MPPI_OK;

@@ -35,6 +35,16 @@ constexpr int MAX_DEVICES = 64;
 std::mutex g_mu;
 unsigned char* g_dev_ptr[MAX_DEVICES] = {nullptr};
 
+// What one call uploads, passed by value as a kernel parameter: the launch
+// copies it, so the call never reads host memory after it returns and needs
+// no host-to-device copy (a copy from pageable memory would first wait for
+// the stream).
+struct NoallocUpload {
+    DevModel model;
+    float params[48];  // sigma, u_lo, u_hi at 0, 16, 32
+};
+static_assert(sizeof(NoallocUpload) <= 4000, "kernel parameter block too large");
+
 }  // namespace
 
 // Shared by every call on a device; keeps the last call's contents.
@@ -42,9 +52,22 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[SCRATCH_BYTES];
 
 namespace {
 
+// Writes the call's model and parameters into the scratch array and clears
+// the error word; one CTA, word by word.
+__global__ void noalloc_upload_kernel(NoallocUpload up, unsigned char* base) {
+    const int t = threadIdx.x;
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(&up.model);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(base + OFF_MODEL);
+    for (int i = t; i < (int)(sizeof(DevModel) / 4); i += blockDim.x) dst[i] = src[i];
+    float* p = reinterpret_cast<float*>(base + OFF_PARAMS);
+    for (int i = t; i < 48; i += blockDim.x) p[i] = up.params[i];
+    if (t == 0) *reinterpret_cast<int*>(base + OFF_WORDS) = 0;
+}
+
 // Device address of the scratch array on the current device.  In host code
 // the array's name is only a host-side stand-in, so the address is looked up
-// once per device (with that device current) and cached.
+// once per device (with that device current) and cached for the life of the
+// process.
 int scratch_address(unsigned char** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -61,86 +84,6 @@ int scratch_address(unsigned char** out) {
     return MPPI_OK;
 }
 
-double blob_value(const unsigned char* b, size_t i) {
-    double v;
-    std::memcpy(&v, b + 16 + 8 * i, 8);
-    return v;
-}
-
-// Blob -> device model representation without any heap allocation (the same
-// format mppi_model_load reads).
-int parse_blob_noalloc(const void* blob, size_t len, DevModel* M) {
-    if (!blob || len < 16) return MPPI_ERR_INVALID_ARG;
-    const unsigned char* b = static_cast<const unsigned char*>(blob);
-    uint32_t h[4];
-    std::memcpy(h, b, 16);
-    if (h[0] != 0x4950504Du || h[1] != 1u) return MPPI_ERR_INVALID_ARG;
-    const size_t n = h[2];
-    if (n < 23 || len < 16 + 8 * n) return MPPI_ERR_INVALID_ARG;
-    const int na = (int)blob_value(b, 0), nb = (int)blob_value(b, 1), maxc = (int)blob_value(b, 2);
-    if (na < 1 || na > MAXL || nb < 0 || nb > MAXB || maxc < 1 || maxc > 16) return MPPI_ERR_INVALID_ARG;
-    if (maxc > MAXC) return MPPI_ERR_UNSUPPORTED;  // more contacts than the device solver keeps
-    const int nq = 2 * na + 7, nv = 2 * na + 6;
-    if (n != 23 + 2 * (12 + 39 * (size_t)na) + 6 * (size_t)nb + (size_t)(nq + nv)) return MPPI_ERR_INVALID_ARG;
-    std::memset(M, 0, sizeof *M);
-    M->na = na;
-    M->nb = nb;
-    M->maxc = maxc;
-    M->dt = (float)blob_value(b, 3);
-    M->sweeps = (int)blob_value(b, 4);
-    M->mu = (float)blob_value(b, 5);
-    M->imp = (float)blob_value(b, 6);
-    M->erp = (float)blob_value(b, 7);
-    for (int k = 0; k < 3; ++k) M->g[k] = (float)blob_value(b, 8 + k);
-    M->floor_z = (float)blob_value(b, 11);
-    M->rb = (float)blob_value(b, 12);
-    M->mb = (float)blob_value(b, 13);
-    M->Ib = (float)blob_value(b, 14);
-    for (int k = 0; k < 3; ++k) M->goal[k] = (float)blob_value(b, 15 + k);
-    M->w_goal = (float)blob_value(b, 18);
-    M->w_u = (float)blob_value(b, 19);
-    M->w_pen = (float)blob_value(b, 20);
-    M->w_obst = (float)blob_value(b, 21);
-    M->w_grasp = (float)blob_value(b, 22);
-    if (!(M->dt > 0) || M->sweeps < 0 || M->sweeps > 1000 || !(M->imp > 0 && M->imp <= 1) || !(M->mb > 0) ||
-        !(M->Ib > 0))
-        return MPPI_ERR_INVALID_ARG;
-    size_t o = 23;
-    for (int a = 0; a < 2; ++a) {
-        for (int k = 0; k < 9; ++k) M->baseR[a][k] = (float)blob_value(b, o++);
-        for (int k = 0; k < 3; ++k) M->basep[a][k] = (float)blob_value(b, o++);
-        for (int i = 0; i < na; ++i) {
-            DevLink& L = M->link[a][i];
-            for (int k = 0; k < 9; ++k) L.FR[k] = (float)blob_value(b, o++);
-            for (int k = 0; k < 3; ++k) L.Fp[k] = (float)blob_value(b, o++);
-            L.mass = (float)blob_value(b, o++);
-            for (int k = 0; k < 3; ++k) L.com[k] = (float)blob_value(b, o++);
-            double I[9];
-            for (int k = 0; k < 9; ++k) I[k] = blob_value(b, o++);
-            L.I[0] = (float)I[0];
-            L.I[1] = (float)I[4];
-            L.I[2] = (float)I[8];
-            L.I[3] = (float)(0.5 * (I[1] + I[3]));
-            L.I[4] = (float)(0.5 * (I[2] + I[6]));
-            L.I[5] = (float)(0.5 * (I[5] + I[7]));
-            for (int k = 0; k < 3; ++k) L.s0[k] = (float)blob_value(b, o++);
-            for (int k = 0; k < 3; ++k) L.s1[k] = (float)blob_value(b, o++);
-            L.rcap = (float)blob_value(b, o++);
-            const double damping = blob_value(b, o++), kv = blob_value(b, o++);
-            L.D = (float)(damping + kv);
-            L.gear = (float)blob_value(b, o++);
-            L.tau_max = (float)blob_value(b, o++);
-            L.u_lo = (float)blob_value(b, o++);
-            L.u_hi = (float)blob_value(b, o++);
-            L.gravcomp = (float)blob_value(b, o++);
-            if (!(L.mass > 0)) return MPPI_ERR_INVALID_ARG;
-        }
-    }
-    for (int bi = 0; bi < nb; ++bi)
-        for (int k = 0; k < 6; ++k) M->box[bi][k] = (float)blob_value(b, o++);
-    return MPPI_OK;
-}
-
 int cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return MPPI_OK;
     return MPPI_ERR_CUDA;
@@ -153,26 +96,25 @@ extern "C" int mppi_step_noalloc(const void* blob, size_t len, int K, int H, flo
                                  float* u_nom_out, int* status_out, void* stream) {
     if (!blob || !sigma || !state || !u_nom || !u_nom_out || !(lambda > 0.0f)) return MPPI_ERR_INVALID_ARG;
     if (K < 1 || K > NOALLOC_MAX_K || H < 1 || H > NOALLOC_MAX_H) return MPPI_ERR_INVALID_ARG;
-    DevModel M;
-    int rc = parse_blob_noalloc(blob, len, &M);
+    NoallocUpload up;
+    std::memset(&up, 0, sizeof up);
+    // the same parser as mppi_model_load; without the host info it allocates nothing
+    int rc = parse_model_blob(blob, len, &up.model, nullptr);
     if (rc != MPPI_OK) return rc;
+    const DevModel& M = up.model;
     if (M.na != 3 && M.na != 7) return MPPI_ERR_UNSUPPORTED;
     const int nu = 2 * M.na;
     unsigned char* base = nullptr;
     rc = scratch_address(&base);
     if (rc != MPPI_OK) return rc;
-    float params[48];
-    std::memset(params, 0, sizeof params);
     for (int j = 0; j < nu; ++j) {
-        params[j] = sigma[j];
-        params[16 + j] = M.link[j / M.na][j % M.na].u_lo;
-        params[32 + j] = M.link[j / M.na][j % M.na].u_hi;
+        up.params[j] = sigma[j];
+        up.params[16 + j] = M.link[j / M.na][j % M.na].u_lo;
+        up.params[32 + j] = M.link[j / M.na][j % M.na].u_hi;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    // host buffers are pageable: each copy returns once the data are staged
-    cudaError_t e = cudaMemcpyAsync(base + OFF_MODEL, &M, sizeof M, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(base + OFF_PARAMS, params, sizeof params, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(base + OFF_WORDS, 0, 256, s);  // error word starts at zero
+    noalloc_upload_kernel<<<1, 256, 0, s>>>(up, base);
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_status(e);
     const float* d_params = reinterpret_cast<const float*>(base + OFF_PARAMS);
     int* d_err = reinterpret_cast<int*>(base + OFF_WORDS);
@@ -213,6 +155,7 @@ extern "C" int mppi_step_noalloc(const void* blob, size_t len, int K, int H, flo
     rc = launch_update(nu, u, H, s);
     if (rc != MPPI_OK) return rc;
     if (status_out) {
+        // device -> pageable host copy, then wait: this branch synchronises the stream
         int err = 0;
         e = cudaMemcpyAsync(&err, d_err, sizeof err, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -7,7 +7,8 @@ Checked against the handle-based entry point (mppi_step) on two calls in a
 row: same scene, seed and iteration counter, so the same samples; the
 updated nominal controls must agree within the tolerance the parity tests
 use for the control update (1e-3; the kernels are the same, so the match is
-in fact exact).  This file is collected last on purpose."""
+in fact exact).  A warm call must leave the device's free memory unchanged,
+and u_nom_out may alias u_nom.  This file is collected last on purpose."""
 import ctypes as C
 
 import numpy as np
@@ -50,6 +51,49 @@ def test_noalloc_step_matches_handle_step_on_two_calls():
         assert float(out_na.abs().max()) > 0
         u_ref.copy_(out_ref)
         u_na.copy_(out_na)
+
+
+def test_noalloc_warm_call_allocates_nothing_and_may_alias():
+    # After a warm call, a second call leaves the device's free memory
+    # unchanged, and u_nom_out may be u_nom itself.
+    from paper_2511_21264_gb300 import native
+    native.build()
+    L = native.lib()
+    sc = scenes.config(1)
+    K, H = 256, 12
+    blob = sc.to_blob()
+    buf = C.create_string_buffer(blob, len(blob))
+    sig = np.ascontiguousarray(sc.sigma_vec().astype(np.float32))
+    seed = scenes.controller_key(3, 1)
+    model = native.Model(blob)
+    x = torch.tensor(model.home(), device="cuda")
+    rng = np.random.default_rng(5)
+    u0 = torch.tensor(rng.normal(scale=0.1, size=(H, sc.nu)).astype(np.float32), device="cuda")
+    u_in = u0.clone()
+    u_out = torch.empty_like(u0)
+    stream = torch.cuda.current_stream().cuda_stream or None
+
+    def call(src, dst, it):
+        st = C.c_int(-1)
+        rc = L.mppi_step_noalloc(buf, len(blob), K, H, C.c_float(sc.lam), sig.ctypes.data, C.c_uint64(seed),
+                                 C.c_uint64(it), x.data_ptr(), src.data_ptr(), dst.data_ptr(), C.byref(st), stream)
+        assert rc == 0 and st.value == 0
+
+    call(u_in, u_out, 0)                       # warm: address lookup, module load
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    call(u_in, u_out, 1)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    # aliased: the update written over its own input
+    u_alias = u0.clone()
+    u_in.copy_(u0)
+    call(u_in, u_out, 2)
+    call(u_alias, u_alias, 2)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(u_alias.cpu().numpy(), u_out.cpu().numpy())
+    assert float((u_out - u0).abs().max()) > 0
 
 
 def test_noalloc_rejects_sizes_beyond_the_maximum():
