@@ -257,6 +257,8 @@ def _measure(args, workload, steps, dev, stream, flush, world, local, rank):
     K, H = sc.K, sc.H
     model = native.Model(sc.to_blob())
     ctl = native.Controller(model, K, H, sc.lam, sc.sigma_vec(), scenes.controller_key(sc.seed, rank))
+    if args.lps or args.place:
+        ctl.set_layout(args.lps or 32, args.place)
     if args.spc:
         ctl.set_launch(args.spc)
     if args.elite or args.eta != 1.0 or args.cov:
@@ -337,6 +339,9 @@ def _measure(args, workload, steps, dev, stream, flush, world, local, rank):
             "flops_per_launch": exec_flops, "achieved": ex, "frac": ex / peak,
             "per_sample_step": exec_flops / (K * H),
             "basis": "ncu FP32 thread instructions of one launch (2 x FFMA + FADD + FMUL) / live mean duration"}
+    lay = ctl.get_layout()
+    roof["layout"] = {"lanes_per_sample": lay[0], "placement": "fused" if lay[1] == 0 else "after the factor",
+                      "samples_per_cta": lay[2]}
     return {"sc": sc, "value": units / (total_ms * 1e-3), "e2e": units / (e2e_ms * 1e-3),
             "ms_per_step": total_ms / steps, "iters_per_s": steps * world / (total_ms * 1e-3),
             "h2d": int(4 * (x.numel() + u.numel())), "d2h": int(4 * u.numel()),
@@ -684,6 +689,8 @@ def main(argv=None):
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="arrival window per rate (serve)")
     ap.add_argument("--serve-rates", type=str, default="50,200,1000")
     ap.add_argument("--spc", type=int, default=0, help="samples per CTA (0 = library default)")
+    ap.add_argument("--lps", type=int, default=0, help="lanes per sample: 32, 16 (0 = library default)")
+    ap.add_argument("--place", type=int, default=0, help="lone ball contact solve: 0 fused, 1 after the factor")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-lift", action="store_true", help="transfer: skip the extra lift measurement")

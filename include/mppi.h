@@ -317,10 +317,27 @@ typedef struct {
 int mppi_run_episode(mppi_ctx *c, const float *x0, float *u_nom, const mppi_episode_config *cfg, float *traj,
                      float *u_exec, float *comp_ms, mppi_episode_result *res, void *stream);
 
-/* Launch shape: samples (warps) per CTA for the rollout kernels, 1..16
- * (0 = the library default: 1 when K < 8 x the SM count, else 4).  Used by
- * the autotuner. */
+/* Launch shape: samples per CTA for the rollout kernels, 1..32, rounded up
+ * to whole warps, at most 512 threads (0 = the library default: the shape
+ * that puts the K samples on the SMs in the fewest waves of CTAs with the
+ * least load on the busiest SM, from the kernel's occupancy; it follows
+ * later layout changes).  A shape whose per-sample workspaces do not fit
+ * one CTA's shared memory makes the stepping calls return
+ * MPPI_ERR_INVALID_ARG.  Used by the autotuner. */
 int mppi_set_launch(mppi_ctx *c, int samples_per_cta);
+
+/* Layout of the rollout kernels.  lanes_per_sample: 32 (one sample per
+ * warp), 16 (two) or 8 (four; 3-link arms only); 0 = 32.  The default of a
+ * new controller is 16 when K exceeds 16 x the SM count (32-lane groups'
+ * registers then cannot hold all samples at once), else 32.  placement of the
+ * solve of a lone ball contact with static geometry: 0 = fused with the
+ * arms' factorisation (every lane runs both chains), 1 = after it.  Every
+ * layout gives bitwise the same samples, costs and updates.  The ball-task
+ * cost suite always runs on 32 lanes per sample.  Errors:
+ * MPPI_ERR_INVALID_ARG for other values or more than 512 threads per CTA,
+ * MPPI_ERR_UNSUPPORTED for 8 lanes with 7-link arms. */
+int mppi_set_layout(mppi_ctx *c, int lanes_per_sample, int placement);
+int mppi_get_layout(const mppi_ctx *c, int *lanes_per_sample, int *placement, int *samples_per_cta);
 
 /* ---------------------------------------------------------------- batch */
 /* Many independent controllers advanced together (the paper runs one
@@ -331,7 +348,8 @@ int mppi_set_launch(mppi_ctx *c, int samples_per_cta);
  * items from a device counter, longest instances first -- and one update
  * launch with a CTA per (instance, horizon step).  Each instance's result
  * is bitwise the one mppi_step gives it alone: a sample's rollout is one
- * warp's work and the update reduces in a fixed order. */
+ * lane group's work, reduced in a layout-independent order, and the update
+ * reduces in a fixed order. */
 typedef struct mppi_batch mppi_batch;
 typedef struct {
     const mppi_model *model; /* kept alive by the caller for the batch's lifetime */
@@ -360,23 +378,30 @@ int mppi_batch_iteration(mppi_batch *b, int i, uint64_t *iteration, void *stream
 int mppi_batch_set_iteration(mppi_batch *b, int i, uint64_t iteration, void *stream);
 /* Device pointer to instance i's K sample costs of the last iteration. */
 const float *mppi_batch_costs(const mppi_batch *b, int i);
-/* Launch shape: samples (warps) per CTA 1..8; order 0 = as given,
- * 1 = longest instances first. */
+/* Launch shape: samples per tile (CTA) 1..32, rounded up to whole warps,
+ * at most 256 threads; order 0 = as given, 1 = longest instances first. */
 int mppi_batch_set_launch(mppi_batch *b, int samples_per_cta, int order);
 int mppi_batch_get_launch(const mppi_batch *b, int *samples_per_cta, int *order);
-/* Autotuner: times `reps` iterations of every shape (samples per CTA in
- * {1,2,4,8} x both orders) on the given buffers (u is modified: pass
- * scratch copies), keeps the fastest, restores the iteration counters and
- * appends the choice to the tuning table under a key of (nv, box-count
- * bucket, instances, total K, longest H); mppi_batch_create applies a
- * stored choice for its key.  best_ms (optional): time of one iteration. */
+/* Layout: lanes per sample (32, 16, or 8 for 3-link arms; 0 = 32) and the
+ * placement of the lone ball contact's solve (as mppi_set_layout). */
+int mppi_batch_set_layout(mppi_batch *b, int lanes_per_sample, int placement);
+int mppi_batch_get_layout(const mppi_batch *b, int *lanes_per_sample, int *placement);
+/* Autotuner: times `reps` iterations of every shape -- lanes per sample
+ * {32, 16, and 8 for 3-link arms} x placement {fused, after} x samples per
+ * CTA {1, 2, 4, 8} warps' worth x both orders -- on the given buffers (u is
+ * modified: pass scratch copies), keeps the fastest, restores the iteration
+ * counters and appends the choice to the tuning table under a key of (nv,
+ * box-count bucket, instances, total K, longest H); mppi_batch_create
+ * applies a stored choice for its key.  best_ms (optional): time of one
+ * iteration. */
 int mppi_batch_autotune(mppi_batch *b, const float *const *states, float *const *u, int reps, void *stream,
                         float *best_ms);
-/* Tuning table: text file of "key spc order ms" lines at $MPPI_TUNE_FILE
- * (default ~/.cache/mppi_tune.txt); the last entry of a key wins.  Host
- * only; no GPU needed. */
-int mppi_tune_store(const char *key, int samples_per_cta, int order, float ms);
-int mppi_tune_lookup(const char *key, int *samples_per_cta, int *order);
+/* Tuning table: text file of "key spc order lps placement ms" lines at
+ * $MPPI_TUNE_FILE (default ~/.cache/mppi_tune.txt); the last entry of a
+ * key wins.  Host only; no GPU needed. */
+int mppi_tune_store(const char *key, int samples_per_cta, int order, int lanes_per_sample, int placement,
+                    float ms);
+int mppi_tune_lookup(const char *key, int *samples_per_cta, int *order, int *lanes_per_sample, int *placement);
 
 /* --------------------------------------------------------------- server */
 /* Replanning with continuous batching.  Registered scenes keep their

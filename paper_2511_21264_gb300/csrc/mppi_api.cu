@@ -1,11 +1,9 @@
 // Kernels and C ABI of libmppi (see include/mppi.h).
 //
 // Kernels
-//   rollout_kernel<NA, MODE>  one warp per sample: H simulator steps with the
-//                             state resident in shared memory, stage costs,
-//                             cost[k].  MODE 0 reads explicit controls, MODE 1
-//                             samples them in-kernel from Philox (Alg. 1,
-//                             sampling + rollout + cost).
+//   rollout_kernel            (mppi_rollout.cuh) one lane group per sample: H
+//                             simulator steps with the state resident in
+//                             shared memory, stage costs, cost[k].
 //   update_kernel<NU>         one CTA per horizon step h: min cost, weights
 //                             exp(-(c - c_min)/lambda), sum_k w_k U_k[h,:]
 //                             with the samples regenerated from Philox,
@@ -24,6 +22,7 @@
 #include "mppi_device.cuh"
 #include "mppi_internal.h"
 #include "mppi_kernels.cuh"
+#include "mppi_rollout.cuh"
 #include "mppi_task.cuh"
 
 using namespace mppi;
@@ -32,65 +31,6 @@ using namespace mppi;
 // kernels
 // ---------------------------------------------------------------------------
 namespace mppi {
-
-template <int NA, int MODE, bool TASK>
-__global__ void __launch_bounds__(512) rollout_kernel(RolloutArgs args) {
-    using d = Dims<NA>;
-    // launched as a programmatic dependent: wait for the previous kernel's
-    // results (u_nom, the counter), then let the next kernel launch early
-    cudaGridDependencySynchronize();
-    cudaTriggerProgrammaticLaunchCompletion();
-    extern __shared__ __align__(16) unsigned char smem[];
-    DevModel& M = *reinterpret_cast<DevModel*>(smem);
-    constexpr size_t task_b = TASK ? sizeof(DevTask) : 0;
-    DevTask* task_s = reinterpret_cast<DevTask*>(smem + sizeof(DevModel));
-    float* unom_s = reinterpret_cast<float*>(smem + sizeof(DevModel) + task_b);
-    const int unom_n = (MODE == 1 && args.stage_unom) ? args.H * d::NU : 0;
-    const size_t ws_off = sizeof(DevModel) + task_b + ((size_t)unom_n * sizeof(float) + 15) / 16 * 16;
-    WarpWS<NA>* wsb = reinterpret_cast<WarpWS<NA>*>(smem + ws_off);
-    stage_model(smem, args.model, unom_s, args.u_nom, unom_n);
-    if constexpr (TASK) {
-        const float4* src = reinterpret_cast<const float4*>(args.task);
-        float4* dst = reinterpret_cast<float4*>(task_s);
-        for (int t = threadIdx.x; t < (int)(sizeof(DevTask) / 16); t += blockDim.x) dst[t] = src[t];
-    }
-    __syncthreads();
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int k = blockIdx.x * (blockDim.x >> 5) + warp;
-    if (k >= args.n) return;
-    SampleIO io{};
-    io.x = args.states + (size_t)k * args.state_stride;
-    io.k = k;
-    io.H = args.H;
-    io.err = args.err;
-    io.stats = args.stats;
-    io.task = TASK ? task_s : nullptr;
-    io.x_out = args.states_out ? args.states_out + (size_t)k * d::NX : nullptr;
-    io.U_store = MODE == 1 ? args.U_store : nullptr;
-    io.Kn = args.n;
-    io.Lfac = MODE == 1 ? args.Lfac : nullptr;
-    if (MODE == 1) {
-        io.unom = unom_n ? unom_s : args.u_nom;
-        io.iter = (uint32_t)(args.iter_ptr ? *args.iter_ptr : args.iter_val);
-        io.key = make_uint2((uint32_t)args.seed, (uint32_t)(args.seed >> 32));
-        if (lane < d::NU) {
-            io.sig = args.sigma[lane];
-            io.lo = M.link[lane / NA][lane % NA].u_lo;
-            io.hi = M.link[lane / NA][lane % NA].u_hi;
-        }
-    } else {
-        if (args.U_hmajor) {
-            io.U = args.U + (size_t)k * d::NU;
-            io.u_stride = (long long)args.n * d::NU;
-        } else {
-            io.U = args.U + (size_t)k * args.H * d::NU;
-            io.u_stride = d::NU;
-        }
-    }
-    const float cost = rollout_sample<NA, MODE, TASK>(M, wsb[warp], lane, io);
-    if (lane == 0) args.costs[k] = cost;
-}
 
 template <int NU>
 __global__ void __launch_bounds__(256) update_kernel(UpdateArgs a) {
@@ -251,41 +191,14 @@ cudaError_t launch_kernel(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t 
     return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
-template <int NA>
-size_t rollout_smem(int spc, int unom_floats, bool task = false) {
-    return sizeof(DevModel) + (task ? sizeof(DevTask) : 0) + ((size_t)unom_floats * sizeof(float) + 15) / 16 * 16 +
-           (size_t)spc * sizeof(WarpWS<NA>);
-}
-
-template <int NA, int MODE, bool TASK>
-int launch_rollout_t(const RolloutArgs& a, int spc, cudaStream_t s) {
-    const int unom = (MODE == 1 && a.stage_unom) ? a.H * Dims<NA>::NU : 0;
-    const size_t sm = rollout_smem<NA>(spc, unom, TASK);
-    static int max_set[17] = {0};
-    auto fn = rollout_kernel<NA, MODE, TASK>;
-    if (sm > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return cuda_fail(e);
-    }
-    (void)max_set;
-    const int grid = (a.n + spc - 1) / spc;
-    cudaError_t e = launch_kernel(fn, dim3(grid), dim3(spc * 32), sm, s, a.pdl != 0, a);
-    return cuda_fail(e != cudaSuccess ? e : cudaGetLastError());
-}
-
 }  // namespace
 
 namespace mppi {
 
 int launch_rollout(int na, int mode, const RolloutArgs& a, int spc, cudaStream_t s) {
     if (a.n <= 0) return MPPI_OK;
-    if (a.task) {
-        if (na == 3) return mode ? launch_rollout_t<3, 1, true>(a, spc, s) : launch_rollout_t<3, 0, true>(a, spc, s);
-        if (na == 7) return mode ? launch_rollout_t<7, 1, true>(a, spc, s) : launch_rollout_t<7, 0, true>(a, spc, s);
-        return MPPI_ERR_UNSUPPORTED;
-    }
-    if (na == 3) return mode ? launch_rollout_t<3, 1, false>(a, spc, s) : launch_rollout_t<3, 0, false>(a, spc, s);
-    if (na == 7) return mode ? launch_rollout_t<7, 1, false>(a, spc, s) : launch_rollout_t<7, 0, false>(a, spc, s);
+    if (na == 3) return launch_rollout_na3(mode, a, spc, s);
+    if (na == 7) return launch_rollout_na7(mode, a, spc, s);
     return MPPI_ERR_UNSUPPORTED;
 }
 
@@ -306,11 +219,7 @@ int launch_noise(int nu, const NoiseArgs& a, cudaStream_t s) {
     return cuda_fail(cudaGetLastError());
 }
 
-size_t rollout_smem_bytes(int na, int spc, int unom_floats) {
-    if (na == 3) return rollout_smem<3>(spc, unom_floats);
-    if (na == 7) return rollout_smem<7>(spc, unom_floats);
-    return 0;
-}
+
 
 // Parse the scene blob into the device representation.
 int parse_model_blob(const void* blob, size_t len, DevModel* out, HostModelInfo* info) {
@@ -414,6 +323,8 @@ struct mppi_model {
 struct mppi_ctx {
     const mppi_model* m = nullptr;
     int K = 0, H = 0, spc = 4;
+    int lps = 32, place = 0;  // lanes per sample, placement of the lone ball contact's solve
+    bool spc_auto = true;     // spc is the library's choice for the layout
     float lambda = 1.0f;
     uint64_t seed = 0;
     float* d_sigma = nullptr;
@@ -556,15 +467,12 @@ int mppi_destroy(mppi_ctx* c) {
     return MPPI_OK;
 }
 
-// Samples (warps) per rollout CTA when the caller sets none: one when K / 4
-// CTAs would give the SMs fewer than two each (the uneven split then sets the
-// kernel's length), four otherwise.
-static int default_spc(int K) {
-    int dev = 0, nsm = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0)
-        return 4;
-    return K < 8 * nsm ? 1 : 4;
+// Samples per rollout CTA when the caller sets none: the shape that puts
+// the K samples on the SMs in the fewest waves with the least load on the
+// busiest SM (occupancy of the sampling rollout kernel of the layout).
+static int default_spc(const mppi_ctx* c) {
+    const int unom = c->H * 2 * c->m->info.na <= 2048 ? c->H * 2 * c->m->info.na : 0;
+    return c->m->info.na == 3 ? choose_spc_na3(c->lps, c->K, unom) : choose_spc_na7(c->lps, c->K, unom);
 }
 
 int mppi_create(const mppi_model* m, int K, int H, float lambda, const float* sigma, uint64_t seed, mppi_ctx** out) {
@@ -580,7 +488,8 @@ int mppi_create(const mppi_model* m, int K, int H, float lambda, const float* si
     c->lambda = lambda;
     c->seed = seed;
     c->n_elite = K;
-    c->spc = default_spc(K);
+    c->lps = default_lps(K);
+    c->spc = default_spc(c);
     const int nu = 2 * m->info.na;
     std::vector<float> lo(nu), hi(nu);
     for (int j = 0; j < nu; ++j) {
@@ -793,10 +702,33 @@ int mppi_best_controls(mppi_ctx* c, float* U_best, void* stream) {
 static void drop_graph(mppi_ctx* c);
 
 int mppi_set_launch(mppi_ctx* c, int spc) {
-    if (!c || spc < 0 || spc > 16) return MPPI_ERR_INVALID_ARG;
-    const int v = spc == 0 ? default_spc(c->K) : spc;
+    if (!c || spc < 0 || spc > 32) return MPPI_ERR_INVALID_ARG;
+    const int v = spc == 0 ? default_spc(c) : spc;
+    if (v * c->lps > 512) return MPPI_ERR_INVALID_ARG;
     if (v != c->spc) drop_graph(c);  // a captured solve holds the old launch shape
     c->spc = v;
+    c->spc_auto = spc == 0;
+    return MPPI_OK;
+}
+
+int mppi_set_layout(mppi_ctx* c, int lps, int place) {
+    if (!c) return MPPI_ERR_INVALID_ARG;
+    if (lps == 0) lps = 32;
+    if ((lps != 8 && lps != 16 && lps != 32) || place < 0 || place > 1) return MPPI_ERR_INVALID_ARG;
+    if (lps == 8 && c->m->info.na != 3) return MPPI_ERR_UNSUPPORTED;  // a 7-link arm needs 8 lanes per arm
+    if (!c->spc_auto && c->spc * lps > 512) return MPPI_ERR_INVALID_ARG;
+    if (lps != c->lps || place != c->place) drop_graph(c);
+    c->lps = lps;
+    c->place = place;
+    if (c->spc_auto) c->spc = default_spc(c);  // the default shape follows the layout
+    return MPPI_OK;
+}
+
+int mppi_get_layout(const mppi_ctx* c, int* lps, int* place, int* spc) {
+    if (!c) return MPPI_ERR_INVALID_ARG;
+    if (lps) *lps = c->lps;
+    if (place) *place = c->place;
+    if (spc) *spc = c->spc;
     return MPPI_OK;
 }
 
@@ -817,6 +749,8 @@ static RolloutArgs philox_args(mppi_ctx* c, const float* state, const float* u_n
     a.U_store = c->d_U;
     a.Lfac = c->cov_sampling ? c->d_L : nullptr;
     a.task = c->task_on ? c->d_task : nullptr;
+    a.lps = a.task ? 32 : c->lps;  // the ball-task suite runs on 32 lanes per sample
+    a.place = a.task ? 0 : c->place;
     return a;
 }
 
@@ -1058,7 +992,7 @@ static int enqueue_step(mppi_ctx* c, const float* state, const float* u_nom, flo
     // dependent CTAs cost more than the overlap saves (lift, K = 1024: 0.146
     // ms per iteration without, 0.168 with), so they are used with wider CTAs
     // only; event records between the kernels would break the overlap anyway.
-    const bool pdl = !prof && c->spc > 1;
+    const bool pdl = !prof && c->spc * a.lps > 32;
     a.pdl = pdl;
     rc = launch_rollout(c->m->info.na, mode, a, c->spc, s);
     if (rc != MPPI_OK) return rc;
@@ -1181,6 +1115,7 @@ int rollout_batch(mppi_ctx* c, int n, const float* states, const float* U, float
     a.states_out = states_out;
     a.err = c->d_err;
     a.task = c->task_on ? c->d_task : nullptr;
+    a.lps = a.task ? 32 : c->lps;
     return launch_rollout(c->m->info.na, 0, a, c->spc, (cudaStream_t)stream);
 }
 
@@ -1194,8 +1129,9 @@ int sim_step(mppi_ctx* c, int n, float* states, const float* U1, void* stream) {
     a.state_stride = 4 * c->m->info.na + 13;
     a.U = U1;
     a.costs = c->d_costs;
-    a.states_out = states;  // each warp reads its state before writing it back
+    a.states_out = states;  // each lane group reads its state before writing it back
     a.err = c->d_err;
+    a.lps = c->lps;
     return launch_rollout(c->m->info.na, 0, a, c->spc, (cudaStream_t)stream);
 }
 

@@ -19,6 +19,7 @@
 #include "mppi_device.cuh"
 #include "mppi_internal.h"
 #include "mppi_kernels.cuh"
+#include "mppi_rollout.cuh"
 
 using namespace mppi;
 
@@ -40,7 +41,7 @@ __device__ __forceinline__ int owner(const BatchInst* insts, int n, int t, bool 
     return lo;
 }
 
-template <int NA>
+template <int NA, int LPS, int PLACE>
 __global__ void __launch_bounds__(256, 2) batch_rollout_kernel(const BatchInst* insts, int n, int ntiles, BatchCtl* ctl,
                                                              int max_unom) {
     using d = Dims<NA>;
@@ -48,9 +49,10 @@ __global__ void __launch_bounds__(256, 2) batch_rollout_kernel(const BatchInst* 
     __shared__ int s_tile;
     DevModel& M = *reinterpret_cast<DevModel*>(smem);
     float* unom_s = reinterpret_cast<float*>(smem + sizeof(DevModel));
-    WarpWS<NA>* wsb =
-        reinterpret_cast<WarpWS<NA>*>(smem + sizeof(DevModel) + ((size_t)max_unom * sizeof(float) + 15) / 16 * 16);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char* wsb = smem + sizeof(DevModel) + ((size_t)max_unom * sizeof(float) + 15) / 16 * 16;
+    const int spc = blockDim.x / LPS, gi = threadIdx.x / LPS;
+    const Lanes<LPS> g(threadIdx.x & 31);
+    WarpWS<NA>& w = *reinterpret_cast<WarpWS<NA>*>(wsb + (size_t)gi * ws_stride<NA, LPS>());
     int staged = -1;
     for (;;) {
         if (threadIdx.x == 0) s_tile = (int)atomicAdd(&ctl->next, 1u);
@@ -65,7 +67,7 @@ __global__ void __launch_bounds__(256, 2) batch_rollout_kernel(const BatchInst* 
             staged = inst;
         }
         __syncthreads();
-        const int k = (t - I.tile0) * (int)(blockDim.x >> 5) + warp;
+        const int k = (t - I.tile0) * spc + gi;
         if (k < I.K) {
             SampleIO io{};
             io.x = I.state;
@@ -75,13 +77,13 @@ __global__ void __launch_bounds__(256, 2) batch_rollout_kernel(const BatchInst* 
             io.unom = unom_n ? unom_s : I.u;
             io.iter = (uint32_t)(*I.iter);
             io.key = make_uint2((uint32_t)I.seed, (uint32_t)(I.seed >> 32));
-            if (lane < d::NU) {
-                io.sig = I.sigma[lane];
-                io.lo = I.u_lo[lane];
-                io.hi = I.u_hi[lane];
+            if (g.sl < d::NU) {
+                io.sig = I.sigma[g.sl];
+                io.lo = I.u_lo[g.sl];
+                io.hi = I.u_hi[g.sl];
             }
-            const float cost = rollout_sample<NA, 1>(M, wsb[warp], lane, io);
-            if (lane == 0) I.costs[k] = cost;
+            const float cost = rollout_sample<NA, LPS, 1, false, PLACE>(M, w, g, io);
+            if (g.sl == 0) I.costs[k] = cost;
         }
         __syncthreads();
     }
@@ -130,28 +132,56 @@ __global__ void shift_kernel(float* u, int H, int nu) {
     }
 }
 
+using BatchFn = void (*)(const BatchInst*, int, int, BatchCtl*, int);
+
 template <int NA>
-int batch_shape_t(int spc, int max_h, BatchLaunch* L) {
+BatchFn batch_fn(int lps, int place) {
+    if (lps == 32) return place ? batch_rollout_kernel<NA, 32, 1> : batch_rollout_kernel<NA, 32, 0>;
+    if (lps == 16) return place ? batch_rollout_kernel<NA, 16, 1> : batch_rollout_kernel<NA, 16, 0>;
+    if constexpr (Lanes<8>::SEG > NA) {
+        if (lps == 8) return place ? batch_rollout_kernel<NA, 8, 1> : batch_rollout_kernel<NA, 8, 0>;
+    }
+    return nullptr;
+}
+
+template <int NA>
+size_t batch_ws_stride(int lps) {
+    if (lps == 16) return ws_stride<NA, 16>();
+    if (lps == 8) return ws_stride<NA, 8>();
+    return ws_stride<NA, 32>();
+}
+
+template <int NA>
+int batch_shape_t(int spc, int lps, int place, int max_h, BatchLaunch* L) {
+    BatchFn fn = batch_fn<NA>(lps, place);
+    if (!fn) return MPPI_ERR_UNSUPPORTED;
+    const int spw = 32 / lps;
+    spc = (spc + spw - 1) / spw * spw;
+    if (spc * lps > 256) return MPPI_ERR_INVALID_ARG;
     const int max_unom = max_h * Dims<NA>::NU <= 2048 ? max_h * Dims<NA>::NU : 0;
     L->max_unom = max_unom;
-    L->smem = sizeof(DevModel) + ((size_t)max_unom * sizeof(float) + 15) / 16 * 16 + (size_t)spc * sizeof(WarpWS<NA>);
-    auto fn = batch_rollout_kernel<NA>;
+    L->smem = sizeof(DevModel) + ((size_t)max_unom * sizeof(float) + 15) / 16 * 16 + (size_t)spc * batch_ws_stride<NA>(lps);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L->smem);
     if (e != cudaSuccess) return MPPI_ERR_CUDA;
     int per_sm = 0, dev = 0, sms = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, spc * 32, L->smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, spc * lps, L->smem);
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return MPPI_ERR_CUDA;
     L->grid = (per_sm > 0 ? per_sm : 1) * sms;
     L->spc = spc;
+    L->lps = lps;
+    L->place = place;
     L->na = NA;
     return MPPI_OK;
 }
 
-int batch_shape(int na, int spc, int max_h, BatchLaunch* L) {
-    if (na == 3) return batch_shape_t<3>(spc, max_h, L);
-    if (na == 7) return batch_shape_t<7>(spc, max_h, L);
+int batch_shape(int na, int spc, int lps, int place, int max_h, BatchLaunch* L) {
+    if (lps == 0) lps = 32;
+    if (lps != 8 && lps != 16 && lps != 32) return MPPI_ERR_INVALID_ARG;
+    if (place < 0 || place > 1) return MPPI_ERR_INVALID_ARG;
+    if (na == 3) return batch_shape_t<3>(spc, lps, place, max_h, L);
+    if (na == 7) return batch_shape_t<7>(spc, lps, place, max_h, L);
     return MPPI_ERR_UNSUPPORTED;
 }
 
@@ -160,10 +190,9 @@ int batch_shape(int na, int spc, int max_h, BatchLaunch* L) {
 int launch_batch_iteration(const BatchInst* insts, int n, int ntiles, int nrows, BatchCtl* ctl, const BatchLaunch& L,
                            cudaStream_t s) {
     if (n <= 0) return MPPI_OK;
-    if (L.na == 3)
-        batch_rollout_kernel<3><<<L.grid, L.spc * 32, L.smem, s>>>(insts, n, ntiles, ctl, L.max_unom);
-    else
-        batch_rollout_kernel<7><<<L.grid, L.spc * 32, L.smem, s>>>(insts, n, ntiles, ctl, L.max_unom);
+    BatchFn fn = L.na == 3 ? batch_fn<3>(L.lps, L.place) : batch_fn<7>(L.lps, L.place);
+    if (!fn) return MPPI_ERR_UNSUPPORTED;
+    fn<<<L.grid, L.spc * L.lps, L.smem, s>>>(insts, n, ntiles, ctl, L.max_unom);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return MPPI_ERR_CUDA;
     if (L.na == 3) batch_update_kernel<6><<<nrows, 256, 0, s>>>(insts, n);
@@ -179,7 +208,7 @@ int launch_shift(float* u, int H, int nu, cudaStream_t s) {
 }  // namespace mppi
 
 // ---------------------------------------------------------------------------
-// autotuner table: "key spc order ms" lines in a text file
+// autotuner table: "key spc order lps place ms" lines in a text file
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -194,19 +223,21 @@ std::string tune_path() {
 
 }  // namespace
 
-extern "C" int mppi_tune_lookup(const char* key, int* spc, int* order) {
-    if (!key || !spc || !order) return MPPI_ERR_INVALID_ARG;
+extern "C" int mppi_tune_lookup(const char* key, int* spc, int* order, int* lps, int* place) {
+    if (!key || !spc || !order || !lps || !place) return MPPI_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lock(g_tune_mu);
     FILE* f = std::fopen(tune_path().c_str(), "r");
     if (!f) return MPPI_ERR_INVALID_ARG;
     char k[256];
-    int s = 0, o = 0;
+    int s = 0, o = 0, l = 0, pl = 0;
     float ms = 0.0f;
     int found = MPPI_ERR_INVALID_ARG;
-    while (std::fscanf(f, "%255s %d %d %f", k, &s, &o, &ms) == 4) {
+    while (std::fscanf(f, "%255s %d %d %d %d %f", k, &s, &o, &l, &pl, &ms) == 6) {
         if (std::strcmp(k, key) == 0) {  // the last entry for a key wins
             *spc = s;
             *order = o;
+            *lps = l;
+            *place = pl;
             found = MPPI_OK;
         }
     }
@@ -214,9 +245,9 @@ extern "C" int mppi_tune_lookup(const char* key, int* spc, int* order) {
     return found;
 }
 
-extern "C" int mppi_tune_store(const char* key, int spc, int order, float ms) {
-    if (!key || !*key || std::strlen(key) > 255 || std::strchr(key, ' ') || spc < 1 || spc > 16 || order < 0 ||
-        order > 1)
+extern "C" int mppi_tune_store(const char* key, int spc, int order, int lps, int place, float ms) {
+    if (!key || !*key || std::strlen(key) > 255 || std::strchr(key, ' ') || spc < 1 || spc > 32 || order < 0 ||
+        order > 1 || (lps != 8 && lps != 16 && lps != 32) || place < 0 || place > 1)
         return MPPI_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lock(g_tune_mu);
     const std::string path = tune_path();
@@ -233,7 +264,7 @@ extern "C" int mppi_tune_store(const char* key, int spc, int order, float ms) {
     }
     FILE* f = std::fopen(path.c_str(), "a");
     if (!f) return MPPI_ERR_INVALID_ARG;
-    std::fprintf(f, "%s %d %d %.6f\n", key, spc, order, ms);
+    std::fprintf(f, "%s %d %d %d %d %.6f\n", key, spc, order, lps, place, ms);
     std::fclose(f);
     return MPPI_OK;
 }
@@ -242,7 +273,7 @@ extern "C" int mppi_tune_store(const char* key, int spc, int order, float ms) {
 // batch handle
 // ---------------------------------------------------------------------------
 struct mppi_batch {
-    int n = 0, na = 0, nu = 0, max_h = 0, spc = 4, order = 1;
+    int n = 0, na = 0, nu = 0, max_h = 0, spc = 4, order = 1, lps = 32, place = 0;
     std::vector<mppi_batch_desc> desc;
     std::vector<BatchInst> inst;  // per user instance
     std::vector<int> perm;        // execution order -> user instance
@@ -300,8 +331,9 @@ void build_order(mppi_batch* b) {
 }
 
 int reshape(mppi_batch* b) {
-    int rc = batch_shape(b->na, b->spc, b->max_h, &b->L);
+    int rc = batch_shape(b->na, b->spc, b->lps, b->place, b->max_h, &b->L);
     if (rc != MPPI_OK) return rc;
+    b->spc = b->L.spc;  // rounded up to whole warps
     build_order(b);
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     if (b->graph) cudaGraphDestroy(b->graph);
@@ -434,10 +466,12 @@ int mppi_batch_create(const mppi_batch_desc* desc, int n, mppi_batch** out) {
     std::snprintf(key, sizeof key, "nv%d_nb%d_n%d_K%lld_H%d", 2 * na + 6, boxes <= 0 ? 0 : (boxes <= 8 ? 8 : 16), n,
                   ksum, b->max_h);
     b->key = key;
-    int spc = 0, order = 0;
-    if (mppi_tune_lookup(key, &spc, &order) == MPPI_OK) {
+    int spc = 0, order = 0, lps = 0, place = 0;
+    if (mppi_tune_lookup(key, &spc, &order, &lps, &place) == MPPI_OK) {
         b->spc = spc;
         b->order = order;
+        b->lps = lps;
+        b->place = place;
     }
     int rc = reshape(b);
     if (rc != MPPI_OK) {
@@ -449,16 +483,47 @@ int mppi_batch_create(const mppi_batch_desc* desc, int n, mppi_batch** out) {
 }
 
 int mppi_batch_set_launch(mppi_batch* b, int spc, int order) {
-    if (!b || spc < 1 || spc > 8 || order < 0 || order > 1) return MPPI_ERR_INVALID_ARG;
+    if (!b || spc < 1 || spc > 32 || order < 0 || order > 1) return MPPI_ERR_INVALID_ARG;
+    const int os = b->spc, oo = b->order;
     b->spc = spc;
     b->order = order;
-    return reshape(b);
+    const int rc = reshape(b);
+    if (rc != MPPI_OK) {
+        b->spc = os;
+        b->order = oo;
+        reshape(b);
+    }
+    return rc;
 }
 
 int mppi_batch_get_launch(const mppi_batch* b, int* spc, int* order) {
     if (!b) return MPPI_ERR_INVALID_ARG;
     if (spc) *spc = b->spc;
     if (order) *order = b->order;
+    return MPPI_OK;
+}
+
+int mppi_batch_set_layout(mppi_batch* b, int lps, int place) {
+    if (!b) return MPPI_ERR_INVALID_ARG;
+    if (lps == 0) lps = 32;
+    if ((lps != 8 && lps != 16 && lps != 32) || place < 0 || place > 1) return MPPI_ERR_INVALID_ARG;
+    const int ol = b->lps, op = b->place, os = b->spc;
+    b->lps = lps;
+    b->place = place;
+    const int rc = reshape(b);
+    if (rc != MPPI_OK) {
+        b->lps = ol;
+        b->place = op;
+        b->spc = os;
+        reshape(b);
+    }
+    return rc;
+}
+
+int mppi_batch_get_layout(const mppi_batch* b, int* lps, int* place) {
+    if (!b) return MPPI_ERR_INVALID_ARG;
+    if (lps) *lps = b->lps;
+    if (place) *place = b->place;
     return MPPI_OK;
 }
 
@@ -579,35 +644,51 @@ int mppi_batch_autotune(mppi_batch* b, const float* const* states, float* const*
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
-    int bs = b->spc, bo = b->order;
-    const int spcs[4] = {1, 2, 4, 8};
+    int bs = b->spc, bo = b->order, bl = b->lps, bp = b->place;
+    // lanes per sample (8 only for the 3-link arms) x placement of the lone
+    // ball contact's solve x samples per CTA (whole warps, <= 256 threads)
+    // x instance order
+    const int lpss[3] = {32, 16, 8};
     int rc = MPPI_OK;
-    for (int si = 0; si < 4 && rc == MPPI_OK; ++si)
-        for (int o = 0; o < 2 && rc == MPPI_OK; ++o) {
-            b->spc = spcs[si];
-            b->order = o;
-            rc = reshape(b);
-            if (rc != MPPI_OK) break;
-            rc = mppi_batch_step(b, states, u, stream);  // warm-up
-            if (rc != MPPI_OK) break;
-            cudaEventRecord(e0, s);
-            for (int r = 0; r < reps && rc == MPPI_OK; ++r) rc = mppi_batch_step(b, states, u, stream);
-            cudaEventRecord(e1, s);
-            e = cudaEventSynchronize(e1);
-            float ms = 0.0f;
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-            if (e != cudaSuccess) rc = cuda_rc(e);
-            ms /= reps;
-            if (ms < best) {
-                best = ms;
-                bs = spcs[si];
-                bo = o;
-            }
-        }
+    for (int li = 0; li < 3 && rc == MPPI_OK; ++li) {
+        const int lps = lpss[li];
+        if (lps == 8 && b->na != 3) continue;
+        const int spw = 32 / lps;
+        for (int pl = 0; pl < 2 && rc == MPPI_OK; ++pl)
+            for (int sm = 1; sm <= 8 && rc == MPPI_OK; sm <<= 1)
+                for (int o = 0; o < 2 && rc == MPPI_OK; ++o) {
+                    const int spc = sm * spw;
+                    b->spc = spc;
+                    b->order = o;
+                    b->lps = lps;
+                    b->place = pl;
+                    rc = reshape(b);
+                    if (rc != MPPI_OK) break;
+                    rc = mppi_batch_step(b, states, u, stream);  // warm-up
+                    if (rc != MPPI_OK) break;
+                    cudaEventRecord(e0, s);
+                    for (int r = 0; r < reps && rc == MPPI_OK; ++r) rc = mppi_batch_step(b, states, u, stream);
+                    cudaEventRecord(e1, s);
+                    e = cudaEventSynchronize(e1);
+                    float ms = 0.0f;
+                    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                    if (e != cudaSuccess) rc = cuda_rc(e);
+                    ms /= reps;
+                    if (ms < best) {
+                        best = ms;
+                        bs = spc;
+                        bo = o;
+                        bl = lps;
+                        bp = pl;
+                    }
+                }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     b->spc = bs;
     b->order = bo;
+    b->lps = bl;
+    b->place = bp;
     if (rc == MPPI_OK) rc = reshape(b);
     // the tuning iterations do not count: restore the counters
     if (rc == MPPI_OK) {
@@ -615,7 +696,7 @@ int mppi_batch_autotune(mppi_batch* b, const float* const* states, float* const*
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) rc = cuda_rc(e);
     }
-    if (rc == MPPI_OK) mppi_tune_store(b->key.c_str(), bs, bo, best);
+    if (rc == MPPI_OK) mppi_tune_store(b->key.c_str(), bs, bo, bl, bp, best);
     if (best_ms) *best_ms = best;
     return rc;
 }

@@ -1,22 +1,29 @@
 // Device side of the MPPI + contact-rollout path (sm_103a, FP32, CUDA cores).
 //
-// One warp simulates one sample.  The sample's articulated state, link frames,
-// contact set and solver scratch live in the warp's slice of shared memory for
-// all H steps; the scene model is staged once per CTA.  Lane roles inside a
-// step:
+// A group of LPS lanes of one warp simulates one sample: LPS = 32 (one
+// sample per warp), 16 (two) or 8 (four; the planar 3-link arms).  The
+// sample's articulated state, link frames, contact set and solver scratch
+// live in the group's slice of shared memory for all H steps; the scene
+// model is staged once per CTA.  Every synchronisation (shuffle, ballot,
+// __syncwarp) names the group's lanes only, so the samples of one warp may
+// take different branches.  Lane roles inside a step (SEG = LPS / 2 lanes
+// per arm segment):
 //   - controls: lane j < nu draws its Gaussian from Philox4x32-10 (or reads
 //     the explicit control);
 //   - kinematics: one lane per link, prefix product of the link transforms;
 //   - collision: one lane per ball pair and per capsule-box cull, each
-//     surviving capsule-box pair minimised by the whole warp over a closed
+//     surviving capsule-box pair minimised by the whole group over a closed
 //     candidate set, contacts compacted with ballots in canonical order;
-//   - dynamics: lane 16a + i owns link i of arm a (spatial inertia, composite
-//     inertia, mass-matrix column, Newton-Euler bias force), lane 16a factors
-//     the arm's (M + dt D) block, lane 15 handles the ball;
+//   - dynamics: lane SEG*a + i owns link i of arm a (spatial inertia,
+//     composite inertia, mass-matrix column, Newton-Euler bias force), lane
+//     SEG*a factors the arm's (M + dt D) block, lane SEG-1 handles the ball;
 //   - contact rows: one lane per Jacobian row (half-solved by the Cholesky
-//     factor), the Delassus block across lanes, projected Gauss-Seidel by
-//     lane 0 in contact space;
-//   - integration: one lane per coordinate.
+//     factor), the Delassus block across lanes, projected Gauss-Seidel in
+//     contact space;
+//   - integration: one lane per coordinate (strided when nv > LPS).
+// Every reduction follows the order of a 32-slot tree whatever LPS is (a
+// lane of a narrower group folds its slots in that order), so the result of
+// a sample does not depend on the layout it ran in.
 // The formulation (world-frame spatial algebra, composite-rigid-body mass
 // matrix, recursive bias, half-solved contact rows) is independent of the
 // FP64 oracle, which builds the same quantities from Jacobian definitions.
@@ -66,6 +73,64 @@ struct Dims {
     static constexpr int NL = 2 * NA, NV = 2 * NA + 6, NQ = 2 * NA + 7, NU = 2 * NA;
     static constexpr int NX = NQ + NV, B = 2 * NA;
 };
+
+// The lanes of one warp that simulate one sample.  Arm a's links sit on
+// group lanes SEG*a .. SEG*a + NA - 1; group lane SEG - 1 (past the first
+// arm's links) is the ball's lane.
+template <int LPS>
+struct Lanes {
+    static_assert(LPS == 8 || LPS == 16 || LPS == 32, "lanes per sample: 8, 16 or 32");
+    static constexpr int SEG = LPS / 2;  // lanes per arm segment
+    static constexpr int SPW = 32 / LPS;  // samples per warp
+    int sl;       // lane within the group
+    int base;     // the group's first lane in the warp
+    unsigned gm;  // the group's lanes
+    int a, i;     // arm segment, lane within it
+    __device__ __forceinline__ explicit Lanes(int lane) {
+        sl = lane & (LPS - 1);
+        base = lane & ~(LPS - 1);
+        gm = LPS == 32 ? FULL : (((1u << (LPS & 31)) - 1u) << base);
+        a = sl / SEG;
+        i = sl & (SEG - 1);
+    }
+    __device__ __forceinline__ void sync() const { __syncwarp(gm); }
+    // the group's ballot, bit t = group lane t
+    __device__ __forceinline__ unsigned ballot(bool p) const {
+        const unsigned b = __ballot_sync(gm, p) & gm;
+        return LPS == 32 ? b : b >> base;
+    }
+    __device__ __forceinline__ bool any(bool p) const { return ballot(p) != 0u; }
+    __device__ __forceinline__ float shfl(float v, int src) const { return __shfl_sync(gm, v, src, LPS); }
+    __device__ __forceinline__ int shfl(int v, int src) const { return __shfl_sync(gm, v, src, LPS); }
+    __device__ __forceinline__ float xor_(float v, int off) const { return __shfl_xor_sync(gm, v, off, LPS); }
+    __device__ __forceinline__ int xor_(int v, int off) const { return __shfl_xor_sync(gm, v, off, LPS); }
+    // within the lane's arm segment
+    __device__ __forceinline__ float up_seg(float v, int off) const { return __shfl_up_sync(gm, v, off, SEG); }
+    __device__ __forceinline__ float down_seg(float v, int off) const { return __shfl_down_sync(gm, v, off, SEG); }
+};
+
+// Sum over the 32 slots of a sample, slot t held by group lane t % LPS as
+// element t / LPS of v: the order of a 32-lane xor butterfly with offsets
+// 16, 8, 4, 2, 1 (in-lane folds for the offsets >= LPS), on every lane.
+template <int LPS, int PS>
+__device__ __forceinline__ float slot_sum(const Lanes<LPS>& g, float (&v)[PS]) {
+    static_assert(PS * LPS == 32, "32 slots");
+#pragma unroll
+    for (int n = PS; n > 1; n >>= 1)
+#pragma unroll
+        for (int t = 0; t < n / 2; ++t) v[t] = v[t] + v[t + n / 2];
+    float s = v[0];
+#pragma unroll
+    for (int off = LPS / 2; off > 0; off >>= 1) s += g.xor_(s, off);
+    return s;
+}
+// The same for a value that only slots < LPS hold (the others are zero).
+template <int LPS>
+__device__ __forceinline__ float group_sum(const Lanes<LPS>& g, float v) {
+#pragma unroll
+    for (int off = LPS / 2; off > 0; off >>= 1) v += g.xor_(v, off);
+    return v;
+}
 
 // Per-warp (per-sample) workspace in shared memory.  Scratch that lives in
 // one phase only shares storage: the capsule-box survivor list (collision),
@@ -192,17 +257,18 @@ __device__ __forceinline__ void spatial_inertia_apply(const float* I, const floa
 }
 
 // ---------------------------------------------------------------------------
-// kinematics: lane 16a walks arm a
+// kinematics: the lanes of arm segment a walk arm a
 // ---------------------------------------------------------------------------
-template <int NA>
-__device__ __forceinline__ void forward_kinematics(const DevModel& M, WarpWS<NA>& w, int lane, float (&Rl)[9],
-                                                   float (&cl)[3]) {
-    // Lane 16a + i owns link i of arm a.  Each lane forms its local transform
-    // Rz(q_i) F_i; an inclusive prefix product over the 16-lane segment
+template <int NA, int LPS>
+__device__ __forceinline__ void forward_kinematics(const DevModel& M, WarpWS<NA>& w, const Lanes<LPS>& g,
+                                                   float (&Rl)[9], float (&cl)[3]) {
+    // Lane i of segment a owns link i of arm a.  Each lane forms its local
+    // transform Rz(q_i) F_i; an inclusive prefix product over the segment
     // (Hillis-Steele, log2(n_a) shuffle rounds) gives the chain to link i;
     // the base transform is applied last.  The joint axis and origin of link
     // i are the previous link's frame (the base for i = 0).
-    const int a = lane >> 4, i = lane & 15;
+    static_assert(Lanes<LPS>::SEG > NA, "an arm segment holds the arm's links and one spare lane");
+    const int a = g.a, i = g.i;
     const bool act = i < NA;
     float R[9], p[3];
     {
@@ -229,9 +295,9 @@ __device__ __forceinline__ void forward_kinematics(const DevModel& M, WarpWS<NA>
     for (int off = 1; off < NA; off <<= 1) {
         float Rp[9], pp[3];
 #pragma unroll
-        for (int k = 0; k < 9; ++k) Rp[k] = __shfl_up_sync(FULL, R[k], off, 16);
+        for (int k = 0; k < 9; ++k) Rp[k] = g.up_seg(R[k], off);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) pp[k] = __shfl_up_sync(FULL, p[k], off, 16);
+        for (int k = 0; k < 3; ++k) pp[k] = g.up_seg(p[k], off);
         // every lane forms the product; lanes with no predecessor this far
         // back keep their transform (a select, no divergent branch)
         const bool take = i >= off;
@@ -260,8 +326,8 @@ __device__ __forceinline__ void forward_kinematics(const DevModel& M, WarpWS<NA>
     float zp[3], op[3];
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
-        zp[r] = __shfl_up_sync(FULL, Rw[3 * r + 2], 1, 16);
-        op[r] = __shfl_up_sync(FULL, pw[r], 1, 16);
+        zp[r] = g.up_seg(Rw[3 * r + 2], 1);
+        op[r] = g.up_seg(pw[r], 1);
     }
     if (i == 0) {
 #pragma unroll
@@ -446,32 +512,33 @@ __device__ __forceinline__ float capsule_box_candidate(int id, const float* a, c
     return t;
 }
 
-// Narrow phase in canonical pair order (ball-floor, ball-links, ball-boxes,
-// links x boxes).  Ball pairs: one lane per pair, exact, compacted with a
-// ballot.  Capsule-box pairs: a conservative bounding-sphere cull per lane,
-// then each surviving pair (in pair order) is minimised by the whole warp
-// over the candidate set above.  Each lane adds the depths of the contacts
-// it found to pa (all) and pbox (against boxes); every lane gets the number
-// of stored contacts (ncon) and the blocks they touch (tb: 1 left arm, 2
-// right arm, 4 ball).  Returns the number of exact capsule-box tests on
-// lane 0 (0 on the other lanes).
-template <int NA>
-__device__ __forceinline__ int collide(const DevModel& M, WarpWS<NA>& w, int lane, float& pa, float& pbox, int& ncon,
-                                      int& tb) {
+// Ball pairs live in 32 fixed slots: slot 0 the floor, slot 1 + l link l
+// (l < 2 n_a <= 14), slot 16 + b box b (b < 16); slot t sits on group lane
+// t % LPS as element t / LPS of the lane's depth sums.  One pass covers the
+// LPS slots of one element: a pass that holds floor and link slots only runs
+// the capsule test, one that holds box slots only runs the box test, and the
+// single pass of a 32-lane group (both kinds) runs both tests on every lane
+// and keeps the one its slot needs -- no divergent branches.  Contacts are
+// compacted with a ballot per pass, in slot order, which is the canonical
+// pair order.
+template <int NA, int LPS, int S>
+__device__ __forceinline__ void ball_pass(const DevModel& M, WarpWS<NA>& w, const Lanes<LPS>& g,
+                                          float (&pa)[32 / LPS], float (&pbox)[32 / LPS], int& base,
+                                          unsigned& tbits) {
     using d = Dims<NA>;
+    static_assert(1 + 2 * MAXL <= 16 && MAXB <= 16, "ball pairs must fit their slot ranges");
+    constexpr int lo = S * LPS, hi = lo + LPS;            // the slots of this pass
+    constexpr bool has_link = lo < 1 + d::NL, has_box = hi > 16;
+    if constexpr (!has_link && !has_box) return;
     const int nb = M.nb;
-    const int nball = 1 + d::NL + nb;
+    if (!has_link && lo >= 16 + nb) return;  // no box slot in use (group-uniform)
+    const int slot = lo + g.sl;
     const float* pb = &w.q[d::B];
     const float rb = M.rb;
-    int base = 0, nsurv = 0;
-    unsigned tbits = 0u;  // blocks the stored contacts touch
-    // ball pairs in one pass (1 + 2 n_a + n_b <= 32): every lane runs the
-    // floor, capsule and (with boxes) box tests on its own or clamped
-    // operands and keeps the one its pair needs -- no divergent branches
-    static_assert(1 + 2 * MAXL + MAXB <= 32, "ball pairs must fit one warp");
-    {
-        const int p = lane;
-        const int l = min(max(p - 1, 0), d::NL - 1);
+    const bool isf = slot == 0, isc = slot >= 1 && slot <= d::NL, isb = slot >= 16 && slot < 16 + nb;
+    float dist = 1.0f, nn[3] = {0.0f, 0.0f, 1.0f}, cp[3] = {0.0f, 0.0f, 0.0f};
+    const int l = min(max(slot - 1, 0), d::NL - 1);
+    if constexpr (has_link) {  // ball - capsule, and the floor on slot 0
         const float* a0 = w.a0[l];
         const float* a1 = w.a1[l];
         float dd[3] = {a1[0] - a0[0], a1[1] - a0[1], a1[2] - a0[2]};
@@ -483,24 +550,23 @@ __device__ __forceinline__ int collide(const DevModel& M, WarpWS<NA>& w, int lan
         float df[3] = {pb[0] - sp[0], pb[1] - sp[1], pb[2] - sp[2]};
         const float len = sqrtf(dot3(df, df));
         const float il = 1.0f / len;
-        const bool isf = p == 0, isc = p >= 1 && p <= d::NL, isb = p > d::NL && p < nball;
-        float nn[3];
         nn[0] = !isf && len > 0.0f ? df[0] * il : 0.0f;
         nn[1] = !isf && len > 0.0f ? df[1] * il : 0.0f;
         nn[2] = !isf && len > 0.0f ? df[2] * il : 1.0f;
         const float rc = M.link[l / NA][l % NA].rcap;
-        float cp[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) cp[k] = 0.5f * ((pb[k] - rb * nn[k]) + (sp[k] + rc * nn[k]));
-        float dist = len - rb - rc;
+        dist = len - rb - rc;
         if (isf) {  // ball - floor
             dist = (pb[2] - M.floor_z) - rb;
             cp[0] = pb[0];
             cp[1] = pb[1];
             cp[2] = 0.5f * ((pb[2] - rb) + M.floor_z);
         }
-        if (nb > 0) {  // ball - box (warp-uniform test)
-            const float* box = M.box[min(max(p - 1 - d::NL, 0), nb - 1)];
+    }
+    if constexpr (has_box) {  // ball - box
+        if (nb > 0) {
+            const float* box = M.box[min(max(slot - 16, 0), nb - 1)];
             float nb3[3], surf[3];
             const float db = box_sdf(pb, box, nb3, surf) - rb;
             if (isb) {
@@ -512,33 +578,60 @@ __device__ __forceinline__ int collide(const DevModel& M, WarpWS<NA>& w, int lan
                 }
             }
         }
-        const int Bb = isc ? l : -1;
-        const bool active = (isf || isc || isb) && dist < 0.0f;
-        const unsigned mask = __ballot_sync(FULL, active);
-        const int pos = __popc(mask & ((1u << lane) - 1u));
-        const bool keep = active && pos < M.maxc;
-        pa += active ? -dist : 0.0f;
-        pbox += active && isb ? -dist : 0.0f;
-        tbits |= keep ? 4u | (Bb >= 0 ? 1u << (Bb / NA) : 0u) : 0u;
-        if (keep) {
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                w.cp[pos][k] = cp[k];
-                w.cn[pos][k] = nn[k];
-            }
-            w.cdep[pos] = -dist;
-            w.cA[pos] = d::B;
-            w.cB[pos] = Bb;
-        }
-        base = __popc(mask);
     }
-    // capsule-box: lanes l and 16 + l test link l's capsule against the first
-    // and the second half of the boxes (bounding sphere and axis-aligned
-    // overlap, both conservative); the survivors are placed link-major,
-    // box-minor by a prefix sum over the links
+    const int Bb = isc ? l : -1;
+    const bool active = (isf || isc || isb) && dist < 0.0f;
+    const unsigned mask = g.ballot(active);
+    const int pos = base + __popc(mask & ((1u << g.sl) - 1u));
+    const bool keep = active && pos < M.maxc;
+    pa[S] += active ? -dist : 0.0f;
+    pbox[S] += active && isb ? -dist : 0.0f;
+    tbits |= keep ? 4u | (Bb >= 0 ? 1u << (Bb / NA) : 0u) : 0u;
+    if (keep) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            w.cp[pos][k] = cp[k];
+            w.cn[pos][k] = nn[k];
+        }
+        w.cdep[pos] = -dist;
+        w.cA[pos] = d::B;
+        w.cB[pos] = Bb;
+    }
+    base += __popc(mask);
+}
+
+// Narrow phase in canonical pair order (ball-floor, ball-links, ball-boxes,
+// links x boxes).  Ball pairs: one lane per pair slot (above), exact,
+// compacted with a ballot.  Capsule-box pairs: a conservative
+// bounding-sphere cull per lane, then each surviving pair (in pair order) is
+// minimised by the whole group over the candidate set above.  Each lane adds
+// the depths of the contacts it found to pa (all) and pbox (against boxes),
+// per slot element; every lane gets the number of stored contacts (ncon) and
+// the blocks they touch (tb: 1 left arm, 2 right arm, 4 ball).  Returns the
+// number of exact capsule-box tests on group lane 0 (0 on the other lanes).
+template <int NA, int LPS>
+__device__ __forceinline__ int collide(const DevModel& M, WarpWS<NA>& w, const Lanes<LPS>& g,
+                                      float (&pa)[32 / LPS], float (&pbox)[32 / LPS], int& ncon, int& tb) {
+    using d = Dims<NA>;
+    const int nb = M.nb;
+    int base = 0, nsurv = 0;
+    unsigned tbits = 0u;  // blocks the stored contacts touch
+    ball_pass<NA, LPS, 0>(M, w, g, pa, pbox, base, tbits);
+    if constexpr (LPS <= 16) ball_pass<NA, LPS, 1>(M, w, g, pa, pbox, base, tbits);
+    if constexpr (LPS <= 8) {
+        ball_pass<NA, LPS, 2>(M, w, g, pa, pbox, base, tbits);
+        ball_pass<NA, LPS, 3>(M, w, g, pa, pbox, base, tbits);
+    }
+    // capsule-box: lane l (and, where a pass over the links fills half the
+    // group, lane CL + l) tests link l's capsule against the boxes (or one
+    // half of them each): bounding sphere and axis-aligned overlap, both
+    // conservative; the survivors are placed link-major, box-minor by a
+    // prefix sum over the links
     if (nb > 0) {
-        const int l = lane & 15, half = lane >> 4;
-        const int bsplit = (nb + 1) >> 1;
+        constexpr int CL = d::NL <= LPS / 2 ? LPS / 2 : LPS;  // lanes of one pass over the links
+        constexpr int NH = LPS / CL;                          // box halves
+        const int l = g.sl & (CL - 1), half = g.sl / CL;
+        const int bsplit = NH == 2 ? (nb + 1) >> 1 : nb;
         const int b0 = half ? bsplit : 0, b1 = half ? nb : bsplit;
         unsigned smask = 0u;
         if (l < d::NL) {
@@ -554,6 +647,9 @@ __device__ __forceinline__ int collide(const DevModel& M, WarpWS<NA>& w, int lan
             }
             const float dx = a1[0] - a0[0], dy = a1[1] - a0[1], dz = a1[2] - a0[2];
             const float rad = 0.5f * sqrtf(dx * dx + dy * dy + dz * dz) + rc;
+            // the boxes' tests are independent: unrolled, their loads and
+            // compare chains overlap
+#pragma unroll 4
             for (int bi = b0; bi < b1; ++bi) {
                 const float* box = M.box[bi];
                 float lb2 = 0.0f;
@@ -568,11 +664,11 @@ __device__ __forceinline__ int collide(const DevModel& M, WarpWS<NA>& w, int lan
             }
         }
         const int cnt = __popc(smask);
-        const int cnt_link = cnt + __shfl_xor_sync(FULL, cnt, 16);  // both halves of link l
-        int pre = cnt_link;  // inclusive prefix over the links (both half-warps alike)
+        const int cnt_link = NH == 2 ? cnt + g.xor_(cnt, CL) : cnt;  // both halves of link l
+        int pre = cnt_link;  // inclusive prefix over the links (both halves alike)
 #pragma unroll
-        for (int off = 1; off < 16; off <<= 1) {
-            const int o = __shfl_up_sync(FULL, pre, off, 16);
+        for (int off = 1; off < CL; off <<= 1) {
+            const int o = __shfl_up_sync(g.gm, pre, off, CL);
             if (l >= off) pre += o;
         }
         int pos = pre - cnt_link + (half ? cnt_link - cnt : 0);
@@ -581,9 +677,9 @@ __device__ __forceinline__ int collide(const DevModel& M, WarpWS<NA>& w, int lan
             smask &= smask - 1u;
             w.ph.col.surv[pos++] = (short)(l * nb + bi);
         }
-        nsurv = __shfl_sync(FULL, pre, 15);
+        nsurv = g.shfl(pre, CL - 1);
     }
-    __syncwarp();
+    g.sync();
     for (int si = 0; si < nsurv; ++si) {
         const int idx = w.ph.col.surv[si];
         const int l = idx / nb, bi = idx - l * nb;
@@ -592,7 +688,7 @@ __device__ __forceinline__ int collide(const DevModel& M, WarpWS<NA>& w, int lan
         const float rc = M.link[l / NA][l % NA].rcap;
         const float dd[3] = {w.a1[l][0] - a0[0], w.a1[l][1] - a0[1], w.a1[l][2] - a0[2]};
         float bf = INFINITY, bt = 0.0f;
-        for (int cid = lane; cid < CB_CANDIDATES; cid += 32) {
+        for (int cid = g.sl; cid < CB_CANDIDATES; cid += LPS) {
             const float t = capsule_box_candidate(cid, a0, dd, box);
             const float f = box_sdf_only(a0, dd, t, box);
             if (f < bf || (f == bf && t < bt)) {
@@ -600,10 +696,12 @@ __device__ __forceinline__ int collide(const DevModel& M, WarpWS<NA>& w, int lan
                 bt = t;
             }
         }
+        // the lexicographic minimum of (f, t) over all candidates: the same
+        // whichever lanes held them
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            const float of = __shfl_xor_sync(FULL, bf, off);
-            const float ot = __shfl_xor_sync(FULL, bt, off);
+        for (int off = LPS / 2; off > 0; off >>= 1) {
+            const float of = g.xor_(bf, off);
+            const float ot = g.xor_(bt, off);
             if (of < bf || (of == bf && ot < bt)) {
                 bf = of;
                 bt = ot;
@@ -613,9 +711,9 @@ __device__ __forceinline__ int collide(const DevModel& M, WarpWS<NA>& w, int lan
         float nn[3], surf[3];
         const float dist = box_sdf(x, box, nn, surf) - rc;
         if (dist < 0.0f) {
-            if (lane == 0) {
-                pa += -dist;
-                pbox += -dist;
+            if (g.sl == 0) {
+                pa[0] += -dist;
+                pbox[0] += -dist;
                 if (base < M.maxc) {
                     tbits |= 1u << (l / NA);
 #pragma unroll
@@ -631,37 +729,37 @@ __device__ __forceinline__ int collide(const DevModel& M, WarpWS<NA>& w, int lan
             ++base;
         }
     }
-    tb = (int)__reduce_or_sync(FULL, tbits);
+    tb = (int)__reduce_or_sync(g.gm, tbits);
     ncon = base < M.maxc ? base : M.maxc;
-    return lane == 0 ? nsurv : 0;
+    return g.sl == 0 ? nsurv : 0;
 }
 
 // ---------------------------------------------------------------------------
 // dynamics: free velocity vf = qd + dt (M + dt D)^-1 (tau_drive - c - D qd)
 // ---------------------------------------------------------------------------
-// Inclusive scans over the links of one arm (a 16-lane segment; lanes past
-// the last link hold zeros).  Suffix sums run towards the base, prefix sums
-// towards the tip.
-template <int N>
-__device__ __forceinline__ void seg_suffix_sum(float (&v)[N], int i, int nlinks) {
+// Inclusive scans over the links of one arm (the lane's arm segment; lanes
+// past the last link hold zeros).  Suffix sums run towards the base, prefix
+// sums towards the tip.
+template <int N, int LPS>
+__device__ __forceinline__ void seg_suffix_sum(const Lanes<LPS>& g, float (&v)[N], int i, int nlinks) {
 #pragma unroll
-    for (int off = 1; off < 16; off <<= 1) {
+    for (int off = 1; off < Lanes<LPS>::SEG; off <<= 1) {
         if (off >= nlinks) break;
 #pragma unroll
         for (int t = 0; t < N; ++t) {
-            const float o = __shfl_down_sync(FULL, v[t], off, 16);
+            const float o = g.down_seg(v[t], off);
             if (i + off < nlinks) v[t] += o;  // lanes past the last link never enter
         }
     }
 }
-template <int N>
-__device__ __forceinline__ void seg_prefix_sum(float (&v)[N], int i, int nlinks) {
+template <int N, int LPS>
+__device__ __forceinline__ void seg_prefix_sum(const Lanes<LPS>& g, float (&v)[N], int i, int nlinks) {
 #pragma unroll
-    for (int off = 1; off < 16; off <<= 1) {
+    for (int off = 1; off < Lanes<LPS>::SEG; off <<= 1) {
         if (off >= nlinks) break;
 #pragma unroll
         for (int t = 0; t < N; ++t) {
-            const float o = __shfl_up_sync(FULL, v[t], off, 16);
+            const float o = g.up_seg(v[t], off);
             if (i >= off) v[t] += o;
         }
     }
@@ -714,11 +812,12 @@ __device__ __forceinline__ void arm_solve(const WarpWS<NA>& w, int a, float (&A)
     }
 }
 
-template <int NA>
-__device__ __forceinline__ void dynamics(const DevModel& M, WarpWS<NA>& w, int lane, int* err, const float (&R)[9],
-                                         const float (&cl)[3], int tb, bool solve) {
+template <int NA, int LPS>
+__device__ __forceinline__ void dynamics(const DevModel& M, WarpWS<NA>& w, const Lanes<LPS>& g, int* err,
+                                         const float (&R)[9], const float (&cl)[3], int tb, bool solve) {
     using d = Dims<NA>;
-    const int a = lane >> 4, i = lane & 15;
+    constexpr int SEG = Lanes<LPS>::SEG;
+    const int a = g.a, i = g.i;
     const bool act = i < NA;
     const int l = a * NA + (act ? i : 0);
     // (1) per link (lane i): spatial inertia about the world origin
@@ -765,18 +864,18 @@ __device__ __forceinline__ void dynamics(const DevModel& M, WarpWS<NA>& w, int l
     float Ic[10];
 #pragma unroll
     for (int t = 0; t < 10; ++t) Ic[t] = Is[t];
-    seg_suffix_sum<10>(Ic, i, NA);
+    seg_suffix_sum<10>(g, Ic, i, NA);
     float F[6];
     spatial_inertia_apply(Ic, S, F);
     float V[6];
 #pragma unroll
     for (int t = 0; t < 6; ++t) V[t] = sq[t];
-    seg_prefix_sum<6>(V, i, NA);
+    seg_prefix_sum<6>(g, V, i, NA);
     // (3) velocity-product acceleration A_i = sum_{k<=i} V_{k-1} x (S_k qd_k)
     float Vp[6];
 #pragma unroll
     for (int t = 0; t < 6; ++t) {
-        Vp[t] = __shfl_up_sync(FULL, V[t], 1, 16);
+        Vp[t] = g.up_seg(V[t], 1);
         if (i == 0) Vp[t] = 0.0f;
     }
     float Aa[6];
@@ -792,7 +891,7 @@ __device__ __forceinline__ void dynamics(const DevModel& M, WarpWS<NA>& w, int l
         Aa[4] = t2[1] + t3[1];
         Aa[5] = t2[2] + t3[2];
     }
-    seg_prefix_sum<6>(Aa, i, NA);
+    seg_prefix_sum<6>(g, Aa, i, NA);
     // bias force of link i: I_i (A_i + a_g) + V_i x* (I_i V_i), gravity as a
     // base acceleration -g on links without compensation
     float f[6];
@@ -816,7 +915,7 @@ __device__ __forceinline__ void dynamics(const DevModel& M, WarpWS<NA>& w, int l
         f[5] = IA[5] + f1[2];
     }
     // (4) bias torque S_i . (subtree force); drive; implicit damping
-    seg_suffix_sum<6>(f, i, NA);
+    seg_suffix_sum<6>(g, f, i, NA);
     {  // every lane computes, the links' lanes store
         const float tb = S[0] * f[0] + S[1] * f[1] + S[2] * f[2] + S[3] * f[3] + S[4] * f[4] + S[5] * f[5];
         const DevLink& L = M.link[a][l - a * NA];
@@ -831,12 +930,12 @@ __device__ __forceinline__ void dynamics(const DevModel& M, WarpWS<NA>& w, int l
             }
         }
     }
-    __syncwarp();
+    g.sync();
     // (5) mass-matrix entries M[r][c] = S_r . F_c (r <= c), spread over the
-    //     16 lanes of the arm's half-warp; dt D on the diagonal
+    //     lanes of the arm's segment; dt D on the diagonal
     constexpr int NENT = NA * (NA + 1) / 2;
 #pragma unroll
-    for (int e0 = 0; e0 < NENT; e0 += 16) {
+    for (int e0 = 0; e0 < NENT; e0 += SEG) {
         const int e = e0 + i;
         {  // every lane computes (past the last entry on the last one), the entries' lanes store
             int c = 0, rem = e < NENT ? e : NENT - 1;
@@ -854,7 +953,7 @@ __device__ __forceinline__ void dynamics(const DevModel& M, WarpWS<NA>& w, int l
             if (e < NENT) w.L[a][c][r] = mv;
         }
     }
-    __syncwarp();
+    g.sync();
     // (6) Cholesky of each arm block (in registers), the free velocity; ball.
     //     The factor is kept only for arms a contact touches (the contact
     //     solve's rows need it there).  Skipped (solve = false) when the
@@ -877,14 +976,14 @@ __device__ __forceinline__ void dynamics(const DevModel& M, WarpWS<NA>& w, int l
         }
         if (!ok) atomicOr(err, ERRB_CHOLESKY);
     }
-    if (lane == 15) {
+    if (a == 0 && i == SEG - 1) {  // the ball's lane
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
             w.vf[d::B + r] = w.qd[d::B + r] + M.dt * M.g[r];
             w.vf[d::B + 3 + r] = w.qd[d::B + 3 + r];
         }
     }
-    __syncwarp();
+    g.sync();
 }
 
 // ---------------------------------------------------------------------------
@@ -1068,19 +1167,23 @@ __device__ __forceinline__ void ball_contact_dv(const DevModel& M, const WarpWS<
 }
 
 // v = v_f + M^-1 J^T lambda on the ball, v_f elsewhere.
-template <int NA, int NC>
-__device__ __forceinline__ void contacts_ball(const DevModel& M, WarpWS<NA>& w, int lane) {
+template <int NA, int NC, int LPS>
+__device__ __forceinline__ void contacts_ball(const DevModel& M, WarpWS<NA>& w, const Lanes<LPS>& g) {
     using d = Dims<NA>;
     float dv[6];
     ball_contact_dv<NA, NC, 0>(M, w, &w.vf[d::B], &w.vf[d::B + 3], dv);
-    if (lane < d::NV) {
-        float add = 0.0f;
 #pragma unroll
-        for (int k = 0; k < 6; ++k)
-            if (lane == d::B + k) add = dv[k];
-        w.v[lane] = w.vf[lane] + add;
+    for (int c0 = 0; c0 < d::NV; c0 += LPS) {
+        const int c = c0 + g.sl;
+        if (c < d::NV) {
+            float add = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 6; ++k)
+                if (c == d::B + k) add = dv[k];
+            w.v[c] = w.vf[c] + add;
+        }
     }
-    __syncwarp();
+    g.sync();
 }
 
 // The free velocity and a ball-only contact solve together (one or two
@@ -1090,10 +1193,12 @@ __device__ __forceinline__ void contacts_ball(const DevModel& M, WarpWS<NA>& w, 
 // the contact solve: with no divergence between them the two independent
 // chains share the issue slots.  Writes v: the arms' free velocities and the
 // ball's after the impulses (the values dynamics and contacts_ball give).
-template <int NA, int NC, int SW>
-__device__ __forceinline__ void solve_ball_contacts(const DevModel& M, WarpWS<NA>& w, int lane, int* err) {
+template <int NA, int NC, int SW, int LPS>
+__device__ __forceinline__ void solve_ball_contacts(const DevModel& M, WarpWS<NA>& w, const Lanes<LPS>& g,
+                                                    int* err) {
     using d = Dims<NA>;
-    const int a = lane >> 4, i = lane & 15;
+    constexpr int SEG = Lanes<LPS>::SEG;
+    const int a = g.a, i = g.i;
     float vb[6];
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
@@ -1106,32 +1211,27 @@ __device__ __forceinline__ void solve_ball_contacts(const DevModel& M, WarpWS<NA
     float dv[6];
     ball_contact_dv<NA, NC, SW>(M, w, vb, vb + 3, dv);
     if (i == 0 && !ok) atomicOr(err, ERRB_CHOLESKY);
-    // lane 16a + i < NA: the arm's velocity i; lanes NA..NA+5 of half 0: the
-    // ball's six (both values formed on every lane, one stored)
-    float yi = y[0], vk = vb[0], dk = dv[0];
-    const int k = i - NA;
+    // lane i < NA of segment a: the arm's velocity i (formed on every lane,
+    // one stored); the ball's lane stores the ball's six
+    float yi = y[0];
 #pragma unroll
     for (int r = 1; r < NA; ++r)
         if (i == r) yi = y[r];
-#pragma unroll
-    for (int r = 1; r < 6; ++r)
-        if (k == r) {
-            vk = vb[r];
-            dk = dv[r];
-        }
     const float vf = w.qd[a * NA + (i < NA ? i : 0)] + M.dt * yi;
-    const float va = vf + 0.0f, vbk = vk + dk;
-    if (i < NA) w.v[a * NA + i] = va;
-    else if (a == 0 && i < NA + 6) w.v[d::B + k] = vbk;
-    __syncwarp();
+    if (i < NA) w.v[a * NA + i] = vf;
+    if (a == 0 && i == SEG - 1) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) w.v[d::B + k] = vb[k] + dv[k];
+    }
+    g.sync();
 }
 
 // Projected Gauss-Seidel for one or two contacts with the Delassus block in
 // registers: every lane runs the same sweeps (no shuffles, no shared-memory
 // round trips), then lane r stores lambda_r.  The same iteration as the
 // lane-parallel path below, summed in a different order.
-template <int NA, int NC>
-__device__ __forceinline__ void pgs_small(const DevModel& M, WarpWS<NA>& w, int lane) {
+template <int NA, int NC, int LPS>
+__device__ __forceinline__ void pgs_small(const DevModel& M, WarpWS<NA>& w, const Lanes<LPS>& g) {
     constexpr int NR = 3 * NC;
     float G[NR][NR], bb[NR], R[NR], iA[NR], vs[NR], lam[NR];
 #pragma unroll
@@ -1173,9 +1273,10 @@ __device__ __forceinline__ void pgs_small(const DevModel& M, WarpWS<NA>& w, int 
             lam[rn + 2] = l2;
         }
     }
+    static_assert(NR <= LPS, "one lane per row");
 #pragma unroll
     for (int r = 0; r < NR; ++r)
-        if (lane == r) w.ph.con.lam[r] = lam[r];
+        if (g.sl == r) w.ph.con.lam[r] = lam[r];
 }
 
 // Soft contact by projected Gauss-Seidel in contact space.  With the
@@ -1183,25 +1284,28 @@ __device__ __forceinline__ void pgs_small(const DevModel& M, WarpWS<NA>& w, int 
 // G = Y Y^T and the unconstrained row velocities are b = Y z_f, z_f = L^T
 // v_f; after the sweeps v = L^-T (z_f + Y^T lambda).  This is the same
 // iteration as updating v row by row (J_r v = b_r + (G lambda)_r).
-template <int NA>
-__device__ __forceinline__ void contacts(const DevModel& M, WarpWS<NA>& w, int lane, int nc, int tb) {
+template <int NA, int LPS>
+__device__ __forceinline__ void contacts(const DevModel& M, WarpWS<NA>& w, const Lanes<LPS>& g, int nc, int tb) {
     using d = Dims<NA>;
+    constexpr int SEG = Lanes<LPS>::SEG;
     if (nc == 0) {
-        if (lane < d::NV) w.v[lane] = w.vf[lane];
-        __syncwarp();
+#pragma unroll
+        for (int c0 = 0; c0 < d::NV; c0 += LPS)
+            if (c0 + g.sl < d::NV) w.v[c0 + g.sl] = w.vf[c0 + g.sl];
+        g.sync();
         return;
     }
     const float ismb = rsqrtf(M.mb), isIb = rsqrtf(M.Ib);
     // tb: the blocks any contact touches (warp-uniform, from the narrow
     // phase).  Untouched blocks keep v = v_f and skip the z-space work.
     if (tb == 4 && nc <= 2) {  // ball against static geometry only
-        if (nc == 1) contacts_ball<NA, 1>(M, w, lane);
-        else contacts_ball<NA, 2>(M, w, lane);
+        if (nc == 1) contacts_ball<NA, 1>(M, w, g);
+        else contacts_ball<NA, 2>(M, w, g);
         return;
     }
-    // z_f = L^T v_f (one lane per arm coordinate; lane 15 the ball)
+    // z_f = L^T v_f (one lane per arm coordinate; the ball's lane the ball)
     {
-        const int a = lane >> 4, i = lane & 15;
+        const int a = g.a, i = g.i;
         if (i < NA && ((tb >> a) & 1)) {
             float sz = 0.0f;
 #pragma unroll
@@ -1209,7 +1313,7 @@ __device__ __forceinline__ void contacts(const DevModel& M, WarpWS<NA>& w, int l
                 if (k >= i) sz += w.L[a][k][i] * w.vf[a * NA + k];
             w.zz[a * NA + i] = sz;
         }
-        if (lane == 15 && (tb & 4)) {
+        if (a == 0 && i == SEG - 1 && (tb & 4)) {
             const float smb = M.mb * ismb, sIb = M.Ib * isIb;
 #pragma unroll
             for (int r = 0; r < 3; ++r) {
@@ -1221,7 +1325,7 @@ __device__ __forceinline__ void contacts(const DevModel& M, WarpWS<NA>& w, int l
     // rows: Jacobian of the touched bodies (in registers), half-solved by
     // the factor, one store per row
     const int nr = 3 * nc;
-    for (int r = lane; r < nr; r += 32) {
+    for (int r = g.sl; r < nr; r += LPS) {
         const int c = r / 3, k = r - 3 * (r / 3);
         float e[3];
         contact_frame_row<NA>(w.cn[c], k, e);
@@ -1299,12 +1403,12 @@ __device__ __forceinline__ void contacts(const DevModel& M, WarpWS<NA>& w, int l
         w.ph.con.rc4[r].w = (k == 0) ? (M.erp / M.dt) * w.cdep[c] : 0.0f;
         w.ph.con.lam[r] = 0.0f;
     }
-    __syncwarp();
+    g.sync();
     // Delassus block G = Y Y^T (nr x nr) and b = Y z_f, over the blocks rows
     // share
     const float regc = (1.0f - M.imp) / M.imp;
     const int npk = nr * (nr + 1) / 2;
-    for (int t = lane; t < npk + nr; t += 32) {
+    for (int t = g.sl; t < npk + nr; t += LPS) {
         if (t < npk) {
             // decode (r, s), r <= s, from the upper-triangle index
             int r = 0, rem = t;
@@ -1356,46 +1460,76 @@ __device__ __forceinline__ void contacts(const DevModel& M, WarpWS<NA>& w, int l
             w.ph.con.rc4[r].x = bb;
         }
     }
-    __syncwarp();
+    g.sync();
     // projected Gauss-Seidel sweeps (normal row, then the tangent pair with
     // the friction disk |lambda_t| <= mu lambda_n).  One or two contacts:
-    // registers.  More: lane q holds lambda_q; the three residuals of a
-    // contact are one butterfly reduction of G_rq lambda_q over the lanes,
-    // and the tangent residuals take the normal update through G's normal
-    // column.
+    // registers.  More: row q's lambda sits on group lane q % LPS as element
+    // q / LPS; the three residuals of a contact are one butterfly reduction
+    // of G_rq lambda_q over the rows (the order of a 32-lane butterfly with
+    // offsets 1, 2, 4, ..., in-lane folds past LPS), and the tangent
+    // residuals take the normal update through G's normal column.
     if (nc == 1) {
-        pgs_small<NA, 1>(M, w, lane);
+        pgs_small<NA, 1>(M, w, g);
     } else if (nc == 2) {
-        pgs_small<NA, 2>(M, w, lane);
+        pgs_small<NA, 2>(M, w, g);
     } else {
-        float lamA = 0.0f;  // lambda of row `lane` (nr <= 24 rows)
+        constexpr int RS = 32 / LPS;  // row slots per lane
+        float lamA[RS];
+#pragma unroll
+        for (int t = 0; t < RS; ++t) lamA[t] = 0.0f;
         int width = 1;
         while (width < nr && width < 32) width <<= 1;
         for (int sw = 0; sw < M.sweeps; ++sw) {
             for (int c = 0; c < nc; ++c) {
                 const int rn = 3 * c;
-                float p0 = 0.0f, p1 = 0.0f, p2 = 0.0f;
-                if (lane < nr) {
-                    p0 = w.ph.con.G[rn * nr + lane] * lamA;
-                    p1 = w.ph.con.G[(rn + 1) * nr + lane] * lamA;
-                    p2 = w.ph.con.G[(rn + 2) * nr + lane] * lamA;
+                float p0[RS], p1[RS], p2[RS];
+#pragma unroll
+                for (int t = 0; t < RS; ++t) {
+                    const int q = t * LPS + g.sl;
+                    p0[t] = p1[t] = p2[t] = 0.0f;
+                    if (q < nr) {
+                        p0[t] = w.ph.con.G[rn * nr + q] * lamA[t];
+                        p1[t] = w.ph.con.G[(rn + 1) * nr + q] * lamA[t];
+                        p2[t] = w.ph.con.G[(rn + 2) * nr + q] * lamA[t];
+                    }
                 }
                 const float4 cN = w.ph.con.rc4[rn], c1 = w.ph.con.rc4[rn + 1], c2 = w.ph.con.rc4[rn + 2];
                 const float g1n = w.ph.con.G[(rn + 1) * nr + rn];
                 const float g2n = w.ph.con.G[(rn + 2) * nr + rn];
-                for (int off = 1; off < width; off <<= 1) {
-                    p0 += __shfl_xor_sync(FULL, p0, off);
-                    p1 += __shfl_xor_sync(FULL, p1, off);
-                    p2 += __shfl_xor_sync(FULL, p2, off);
+                for (int off = 1; off < width && off < LPS; off <<= 1) {
+#pragma unroll
+                    for (int t = 0; t < RS; ++t) {
+                        p0[t] += g.xor_(p0[t], off);
+                        p1[t] += g.xor_(p1[t], off);
+                        p2[t] += g.xor_(p2[t], off);
+                    }
                 }
-                const float ln0 = __shfl_sync(FULL, lamA, rn);
-                const float l10 = __shfl_sync(FULL, lamA, rn + 1);
-                const float l20 = __shfl_sync(FULL, lamA, rn + 2);
-                const float res = cN.x + p0 + cN.y * ln0 - cN.w;
+#pragma unroll
+                for (int st = 1; st < RS; st <<= 1) {
+                    if (st * LPS >= width) break;
+#pragma unroll
+                    for (int t = 0; t + st < RS; t += 2 * st) {
+                        p0[t] += p0[t + st];
+                        p1[t] += p1[t + st];
+                        p2[t] += p2[t + st];
+                    }
+                }
+                // lambda of row r: element r / LPS on group lane r % LPS
+                auto lam_of = [&](int r) {
+                    float v = lamA[0];
+#pragma unroll
+                    for (int t = 1; t < RS; ++t)
+                        if (r / LPS == t) v = lamA[t];
+                    return g.shfl(v, r % LPS);
+                };
+                const float ln0 = lam_of(rn);
+                const float l10 = lam_of(rn + 1);
+                const float l20 = lam_of(rn + 2);
+                const float res = cN.x + p0[0] + cN.y * ln0 - cN.w;
                 const float ln = fmaxf(ln0 - res * cN.z, 0.0f);
                 const float dn = ln - ln0;
-                const float r1 = c1.x + p1 + g1n * dn + c1.y * l10;
-                const float r2 = c2.x + p2 + g2n * dn + c2.y * l20;
+                const float r1 = c1.x + p1[0] + g1n * dn + c1.y * l10;
+                const float r2 = c2.x + p2[0] + g2n * dn + c2.y * l20;
                 float l1 = l10 - r1 * c1.z;
                 float l2 = l20 - r2 * c2.z;
                 const float n2 = l1 * l1 + l2 * l2, lim = M.mu * ln;
@@ -1404,28 +1538,38 @@ __device__ __forceinline__ void contacts(const DevModel& M, WarpWS<NA>& w, int l
                     l1 *= sc;
                     l2 *= sc;
                 }
-                if (lane == rn) lamA = ln;
-                if (lane == rn + 1) lamA = l1;
-                if (lane == rn + 2) lamA = l2;
+#pragma unroll
+                for (int t = 0; t < RS; ++t) {
+                    const int q = t * LPS + g.sl;
+                    if (q == rn) lamA[t] = ln;
+                    if (q == rn + 1) lamA[t] = l1;
+                    if (q == rn + 2) lamA[t] = l2;
+                }
             }
         }
-        if (lane < nr) w.ph.con.lam[lane] = lamA;
+#pragma unroll
+        for (int t = 0; t < RS; ++t)
+            if (t * LPS + g.sl < nr) w.ph.con.lam[t * LPS + g.sl] = lamA[t];
     }
-    __syncwarp();
+    g.sync();
     // z = z_f + Y^T lambda, then v = L^-T z on the touched blocks
-    if (lane < d::NV) {
-        const int blk = lane < NA ? 1 : (lane < 2 * NA ? 2 : 4);
-        if (tb & blk) {
-            float zv = w.zz[lane];
-            for (int r = 0; r < nr; ++r) zv += w.ph.con.Y[r][lane] * w.ph.con.lam[r];
-            w.zz[lane] = zv;
-        } else {
-            w.v[lane] = w.vf[lane];
+#pragma unroll
+    for (int c0 = 0; c0 < d::NV; c0 += LPS) {
+        const int c = c0 + g.sl;
+        if (c < d::NV) {
+            const int blk = c < NA ? 1 : (c < 2 * NA ? 2 : 4);
+            if (tb & blk) {
+                float zv = w.zz[c];
+                for (int r = 0; r < nr; ++r) zv += w.ph.con.Y[r][c] * w.ph.con.lam[r];
+                w.zz[c] = zv;
+            } else {
+                w.v[c] = w.vf[c];
+            }
         }
     }
-    __syncwarp();
-    if ((lane & 15) == 0 && ((tb >> (lane >> 4)) & 1)) {
-        const int a = lane >> 4;
+    g.sync();
+    if (g.i == 0 && ((tb >> g.a) & 1)) {
+        const int a = g.a;
         float zl[NA], t[NA];
 #pragma unroll
         for (int ii = 0; ii < NA; ++ii) zl[ii] = w.zz[a * NA + ii];
@@ -1439,24 +1583,24 @@ __device__ __forceinline__ void contacts(const DevModel& M, WarpWS<NA>& w, int l
 #pragma unroll
         for (int ii = 0; ii < NA; ++ii) w.v[a * NA + ii] = t[ii];
     }
-    if (lane == 15 && (tb & 4)) {
+    if (g.a == 0 && g.i == SEG - 1 && (tb & 4)) {
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
             w.v[d::B + r] = w.zz[d::B + r] * ismb;
             w.v[d::B + 3 + r] = w.zz[d::B + 3 + r] * isIb;
         }
     }
-    __syncwarp();
+    g.sync();
 }
 
 // ---------------------------------------------------------------------------
 // semi-implicit Euler
 // ---------------------------------------------------------------------------
-template <int NA>
-__device__ __forceinline__ void integrate(const DevModel& M, WarpWS<NA>& w, int lane) {
+template <int NA, int LPS>
+__device__ __forceinline__ void integrate(const DevModel& M, WarpWS<NA>& w, const Lanes<LPS>& g) {
     using d = Dims<NA>;
     const float dt = M.dt;
-    {  // every lane forms the new orientation (no divergent branch); lane 31 stores it
+    {  // every lane forms the new orientation (no divergent branch); the group's last lane stores it
         const float* om = &w.v[d::B + 3];
         const float th[3] = {om[0] * dt, om[1] * dt, om[2] * dt};
         // dq = (cos x, th sin(x) / (2x)) with x = |th| / 2.  For x < 1/2 both
@@ -1482,17 +1626,21 @@ __device__ __forceinline__ void integrate(const DevModel& M, WarpWS<NA>& w, int 
         float ny = dq0 * y0 - dq1 * z0 + dq2 * w0 + dq3 * x0;
         float nz = dq0 * z0 + dq1 * y0 - dq2 * x0 + dq3 * w0;
         const float inv = rsqrtf(nw * nw + nx * nx + ny * ny + nz * nz);
-        __syncwarp();  // every lane has read the old orientation
-        if (lane == 31) {
+        g.sync();  // every lane has read the old orientation
+        if (g.sl == LPS - 1) {
             qq[0] = nw * inv;
             qq[1] = nx * inv;
             qq[2] = ny * inv;
             qq[3] = nz * inv;
         }
     }
-    if (lane < d::NV) w.qd[lane] = w.v[lane];
-    if (lane < d::B + 3) w.q[lane] += dt * w.v[lane];
-    __syncwarp();
+#pragma unroll
+    for (int c0 = 0; c0 < d::NV; c0 += LPS) {
+        const int c = c0 + g.sl;
+        if (c < d::NV) w.qd[c] = w.v[c];
+        if (c < d::B + 3) w.q[c] += dt * w.v[c];
+    }
+    g.sync();
 }
 
 // coordinate k of the grasp-maintenance error p_L + p_R - 2 p_ball, squared,

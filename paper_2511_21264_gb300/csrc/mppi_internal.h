@@ -31,7 +31,7 @@ struct HostModelInfo {
     std::vector<float> x0;
 };
 
-// Arguments of the rollout kernel (one warp per sample).
+// Arguments of the rollout kernel (one group of lanes per sample).
 struct RolloutArgs {
     const DevModel* model;
     int n;                       // samples
@@ -54,6 +54,8 @@ struct RolloutArgs {
     const float* Lfac;           // optional: covariance factors H x nu x nu (MODE 1), else diagonal sigma
     const DevTask* task;         // optional: the ball-task cost suite replaces the stage cost
     int pdl;                     // launch as a programmatic dependent of the previous kernel
+    int lps;                     // lanes per sample: 32, 16 or 8 (0 = 32)
+    int place;                   // lone ball contact solve: 0 fused with the arms' factor, 1 after it
 };
 
 // Arguments of the weighted-mean update (one CTA per horizon step).
@@ -120,10 +122,13 @@ struct BatchCtl {
 
 // launch shape of the persistent batched rollout
 struct BatchLaunch {
-    int na = 7, spc = 4, grid = 0, max_unom = 0;
+    int na = 7, spc = 4, lps = 32, place = 0, grid = 0, max_unom = 0;
     size_t smem = 0;
 };
-int batch_shape(int na, int spc, int max_h, BatchLaunch* L);
+// spc: samples per tile (rounded up to whole warps); lps: lanes per sample
+// (32, 16 or 8; 0 = 32); place: the lone ball contact's solve fused (0) or
+// after the arms' factor (1)
+int batch_shape(int na, int spc, int lps, int place, int max_h, BatchLaunch* L);
 int launch_batch_iteration(const BatchInst* insts, int n, int ntiles, int nrows, BatchCtl* ctl, const BatchLaunch& L,
                            cudaStream_t s);
 int launch_shift(float* u, int H, int nu, cudaStream_t s);
@@ -178,6 +183,5 @@ int parse_model_blob(const void* blob, size_t len, DevModel* out, HostModelInfo*
 int launch_rollout(int na, int mode, const RolloutArgs& a, int spc, cudaStream_t s);
 int launch_update(int nu, const UpdateArgs& a, int H, cudaStream_t s);
 int launch_noise(int nu, const NoiseArgs& a, cudaStream_t s);
-size_t rollout_smem_bytes(int na, int spc, int unom_floats);
 
 }  // namespace mppi

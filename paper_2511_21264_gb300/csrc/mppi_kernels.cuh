@@ -7,13 +7,13 @@
 
 namespace mppi {
 
-// Inputs of one sample's rollout (one warp).
+// Inputs of one sample's rollout (one lane group).
 struct SampleIO {
     const float* x;            // start state (nx)
     const float* U;            // explicit controls of this sample, row h at U + h * u_stride, MODE 0
     long long u_stride;
     const float* unom;         // nominal controls (H x nu, shared or global), MODE 1
-    float sig, lo, hi;         // this lane's sigma and control bounds (lane < nu), MODE 1
+    float sig, lo, hi;         // this lane's sigma and control bounds (group lane < nu), MODE 1
     uint2 key;                 // Philox key, MODE 1
     uint32_t iter;             // Philox iteration word, MODE 1
     int k, H;                  // sample index, horizon
@@ -36,20 +36,35 @@ __device__ __forceinline__ void stage_model(unsigned char* smem, const DevModel*
 }
 
 // H simulator steps of one sample with its stage costs (TASK: the ball-task
-// cost suite instead); the warp's state stays in shared memory throughout.
-// Returns the summed cost on every lane.
-template <int NA, int MODE, bool TASK = false>
-__device__ __forceinline__ float rollout_sample(const DevModel& M, WarpWS<NA>& w, int lane, const SampleIO& io) {
+// cost suite instead, 32 lanes per sample only); the group's state stays in
+// shared memory throughout.  PLACE selects where the lone ball contact's
+// solve runs: 0 fused with the arms' factorisation (every lane runs both
+// chains), 1 after it (the factor on one lane per arm, then the sweeps);
+// both give the same bits.  Returns the summed cost on every lane.
+template <int NA, int LPS, int MODE, bool TASK = false, int PLACE = 0>
+__device__ __forceinline__ float rollout_sample(const DevModel& M, WarpWS<NA>& w, const Lanes<LPS>& g,
+                                                const SampleIO& io) {
     using d = Dims<NA>;
+    static_assert(!TASK || LPS == 32, "the ball-task cost suite runs on 32 lanes per sample");
+    static_assert(d::NU <= LPS, "one lane per control");
+    constexpr int PS = 32 / LPS;  // pair slots per lane
+    constexpr int DS = LPS / 4;   // steps of normals per Philox draw (one block of 4 per lane)
     const int k = io.k;
-    if (lane < d::NQ) w.q[lane] = io.x[lane];
-    if (lane < d::NV) w.qd[lane] = io.x[d::NQ + lane];
-    __syncwarp();
+    const int sl = g.sl;
+#pragma unroll
+    for (int c0 = 0; c0 < d::NX; c0 += LPS) {
+        const int c = c0 + sl;
+        if (c < d::NQ) w.q[c] = io.x[c];
+        else if (c < d::NX) w.qd[c - d::NQ] = io.x[c];
+    }
+    g.sync();
     float cost = 0.0f;
     const float* gb = M.goal;
     unsigned n_exact = 0, n_con = 0, n_lone = 0;
     float uacc = 0.0f;  // this lane's control's sum of squares over the horizon
-    float pacc = 0.0f, pbacc = 0.0f;  // this lane's contacts' depths (all, against boxes) over the horizon
+    float pacc[PS], pbacc[PS];  // this lane's contacts' depths (all, against boxes) over the horizon, per slot
+#pragma unroll
+    for (int t = 0; t < PS; ++t) pacc[t] = pbacc[t] = 0.0f;
     float gacc = 0.0f;  // squared goal error of this lane's ball coordinate over the horizon
     float kacc = 0.0f;  // squared grasp error (p_L + p_R - 2 p_ball) of this lane's coordinate
     TaskAcc<NA> tacc;
@@ -61,118 +76,130 @@ __device__ __forceinline__ float rollout_sample(const DevModel& M, WarpWS<NA>& w
         tacc.c = tacc.th = tacc.yz = tacc.v2 = tacc.r = tacc.l = tacc.eo = tacc.ot = 0.0f;
     }
     float upre = 0.0f;  // explicit controls: the next step's value
-    if (MODE == 0 && lane < d::NU) upre = io.U[lane];
+    if (MODE == 0 && sl < d::NU) upre = io.U[sl];
     for (int h = 0; h < io.H; ++h) {
         if (MODE == 1) {
-            // every 8 steps the 32 lanes draw one Philox block each: 8 steps x
-            // 16 controls of standard normals, counter (j/4, h, k, iteration),
-            // Box-Muller on the word pairs (the values sample_row and the
-            // debug draw give)
-            if ((h & 7) == 0) {
-                const int jb = lane & 3, hs = h + (lane >> 2);
+            // every DS steps the group's lanes draw one Philox block each: DS
+            // steps x 16 controls of standard normals, counter (j/4, h, k,
+            // iteration), Box-Muller on the word pairs (the values sample_row
+            // and the debug draw give)
+            if ((h & (DS - 1)) == 0) {
+                const int jb = sl & 3, hs = h + (sl >> 2);
                 if (4 * jb < d::NU && hs < io.H) {
                     const uint4 wv = philox4x32_10(make_uint4((uint32_t)jb, (uint32_t)hs, (uint32_t)k, io.iter), io.key);
                     float z4[4];
                     block_normals4(wv, z4);
 #pragma unroll
-                    for (int t = 0; t < 4; ++t) w.zn[lane >> 2][4 * jb + t] = z4[t];
+                    for (int t = 0; t < 4; ++t) w.zn[sl >> 2][4 * jb + t] = z4[t];
                 }
-                __syncwarp();
+                g.sync();
             }
             {  // every lane computes (past the controls on the last one), the controls' lanes store
-                const int jc = lane < d::NU ? lane : d::NU - 1;
+                const int jc = sl < d::NU ? sl : d::NU - 1;
+                const float* zr = w.zn[h & (DS - 1)];
                 float acc = io.unom[h * d::NU + jc];
                 if (io.Lfac) {  // u = nu + L_h z, FMAs in the order sample_row uses
                     // (unrolled over the row so that its loads are issued together)
                     const float* Lr = io.Lfac + ((size_t)h * d::NU + jc) * d::NU;
 #pragma unroll
                     for (int i = 0; i < d::NU; ++i)
-                        if (i <= jc) acc = __fmaf_rn(Lr[i], w.zn[h & 7][i], acc);
+                        if (i <= jc) acc = __fmaf_rn(Lr[i], zr[i], acc);
                 } else {
-                    acc = __fmaf_rn(io.sig, w.zn[h & 7][jc], acc);
+                    acc = __fmaf_rn(io.sig, zr[jc], acc);
                 }
                 const float uv = fminf(fmaxf(acc, io.lo), io.hi);
-                if (lane < d::NU) {
-                    w.u[lane] = uv;
+                if (sl < d::NU) {
+                    w.u[sl] = uv;
                     uacc = __fmaf_rn(uv, uv, uacc);
-                    if (io.U_store) io.U_store[((size_t)h * io.Kn + k) * d::NU + lane] = uv;
+                    if (io.U_store) io.U_store[((size_t)h * io.Kn + k) * d::NU + sl] = uv;
                 }
             }
-        } else if (lane < d::NU) {
+        } else if (sl < d::NU) {
             const float uv = upre;  // read one step ahead: its latency overlaps the step
-            if (h + 1 < io.H) upre = io.U[(h + 1) * io.u_stride + lane];
-            w.u[lane] = uv;
+            if (h + 1 < io.H) upre = io.U[(h + 1) * io.u_stride + sl];
+            w.u[sl] = uv;
             uacc = __fmaf_rn(uv, uv, uacc);
         }
         float Rl[9], cl[3];  // this lane's link rotation and COM, kept for the dynamics
-        forward_kinematics<NA>(M, w, lane, Rl, cl);
-        __syncwarp();
+        forward_kinematics<NA>(M, w, g, Rl, cl);
+        g.sync();
         if constexpr (TASK) {
-            task_state<NA>(M, *io.task, w, lane, Rl, h == 0, tacc);
+            task_state<NA>(M, *io.task, w, sl, Rl, h == 0, tacc);
         } else {
-            if (h > 0 && lane < 3 && M.w_grasp != 0.0f) kacc += grasp_coord<NA>(w, lane);
+            if (h > 0 && sl < 3 && M.w_grasp != 0.0f) kacc += grasp_coord<NA>(w, sl);
         }
         int ncon, tb;
-        n_exact += collide<NA>(M, w, lane, pacc, pbacc, ncon, tb);
-        __syncwarp();
+        n_exact += collide<NA>(M, w, g, pacc, pbacc, ncon, tb);
+        g.sync();
         n_con += ncon;
-        // one ball contact with static geometry (the lift's common case):
-        // the arms' solve and the contact solve run side by side
-        const bool fast = tb == 4 && ncon == 1;
-        n_lone += fast ? 1u : 0u;
-        dynamics<NA>(M, w, lane, io.err, Rl, cl, tb, !fast);
-        if (fast) {
-            solve_ball_contacts<NA, 1, 0>(M, w, lane, io.err);
+        // one ball contact with static geometry (the lift's common case)
+        const bool lone = tb == 4 && ncon == 1;
+        n_lone += lone ? 1u : 0u;
+        if (PLACE == 0) {
+            // the arms' solve and the contact solve side by side
+            dynamics<NA>(M, w, g, io.err, Rl, cl, tb, !lone);
+            if (lone) {
+                solve_ball_contacts<NA, 1, 0>(M, w, g, io.err);
+            } else {
+                contacts<NA>(M, w, g, ncon, tb);
+            }
         } else {
-            contacts<NA>(M, w, lane, ncon, tb);
+            dynamics<NA>(M, w, g, io.err, Rl, cl, tb, true);
+            contacts<NA>(M, w, g, ncon, tb);
         }
-        integrate<NA>(M, w, lane);
-        if (!TASK && lane >= d::B && lane < d::B + 3) {  // the ball coordinate this lane integrated
-            const float e = w.q[lane] - gb[lane - d::B];
+        integrate<NA>(M, w, g);
+        if (!TASK && sl < 3) {  // the goal error of ball coordinate sl
+            const float e = w.q[d::B + sl] - gb[sl];
             gacc = __fmaf_rn(e, e, gacc);
         }
-        __syncwarp();
+        g.sync();
     }
     if constexpr (TASK) {
         float Rl[9], cl[3];
-        forward_kinematics<NA>(M, w, lane, Rl, cl);
-        __syncwarp();
-        task_state<NA>(M, *io.task, w, lane, Rl, false, tacc);
+        forward_kinematics<NA>(M, w, g, Rl, cl);
+        g.sync();
+        task_state<NA>(M, *io.task, w, sl, Rl, false, tacc);
         cost = task_total<NA>(*io.task, tacc);
     } else if (M.w_grasp != 0.0f) {
         float Rl[9], cl[3];
-        forward_kinematics<NA>(M, w, lane, Rl, cl);
-        __syncwarp();
-        if (lane < 3) kacc += grasp_coord<NA>(w, lane);
+        forward_kinematics<NA>(M, w, g, Rl, cl);
+        g.sync();
+        if (sl < 3) kacc += grasp_coord<NA>(w, sl);
     }
     if constexpr (!TASK) {
         // w_goal sum_h |p_ball - goal|^2 + w_u sum_h |u_h|^2 + w_pen sum_h pen_h
         // + w_obst sum_h pen_box_h + w_grasp sum_h |p_L + p_R - 2 p_ball|^2
-        // from the lanes' sums, each reduced in a fixed butterfly order
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            gacc += __shfl_xor_sync(FULL, gacc, off);
-            uacc += __shfl_xor_sync(FULL, uacc, off);
-            pacc += __shfl_xor_sync(FULL, pacc, off);
-            pbacc += __shfl_xor_sync(FULL, pbacc, off);
-            kacc += __shfl_xor_sync(FULL, kacc, off);
-        }
-        cost += M.w_goal * gacc + M.w_u * uacc + M.w_pen * pacc + M.w_obst * pbacc + M.w_grasp * kacc;
+        // from the lanes' sums, each reduced in the order of a 32-slot butterfly
+        gacc = group_sum(g, gacc);
+        uacc = group_sum(g, uacc);
+        const float ps = slot_sum(g, pacc);
+        const float pbs = slot_sum(g, pbacc);
+        kacc = group_sum(g, kacc);
+        cost += M.w_goal * gacc + M.w_u * uacc + M.w_pen * ps + M.w_obst * pbs + M.w_grasp * kacc;
     }
     // a non-finite state poisons the sample's cost (weight 0 in the update)
-    const bool bad = (lane < d::NQ && !isfinite(w.q[lane])) || (lane < d::NV && !isfinite(w.qd[lane]));
-    if (__any_sync(FULL, bad)) cost = __int_as_float(0x7fc00000);
-    cost = __shfl_sync(FULL, cost, 0);
-    if (lane == 0 && !isfinite(cost)) atomicOr(io.err, ERRB_NONFINITE);
-    if (io.stats && lane == 0) {
+    bool bad = false;
+#pragma unroll
+    for (int c0 = 0; c0 < d::NQ; c0 += LPS) {
+        const int c = c0 + sl;
+        bad = bad || (c < d::NQ && !isfinite(w.q[c])) || (c < d::NV && !isfinite(w.qd[c]));
+    }
+    if (g.any(bad)) cost = __int_as_float(0x7fc00000);
+    cost = g.shfl(cost, 0);
+    if (sl == 0 && !isfinite(cost)) atomicOr(io.err, ERRB_NONFINITE);
+    if (io.stats && sl == 0) {
         atomicAdd(&io.stats[0], (unsigned long long)io.H);
         atomicAdd(&io.stats[1], (unsigned long long)n_con);
         atomicAdd(&io.stats[2], (unsigned long long)n_exact);
         atomicAdd(&io.stats[3], (unsigned long long)n_lone);
     }
     if (io.x_out) {
-        if (lane < d::NQ) io.x_out[lane] = w.q[lane];
-        if (lane < d::NV) io.x_out[d::NQ + lane] = w.qd[lane];
+#pragma unroll
+        for (int c0 = 0; c0 < d::NX; c0 += LPS) {
+            const int c = c0 + sl;
+            if (c < d::NQ) io.x_out[c] = w.q[c];
+            else if (c < d::NX) io.x_out[c] = w.qd[c - d::NQ];
+        }
     }
     return cost;
 }

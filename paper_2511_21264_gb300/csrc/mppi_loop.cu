@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(32) probe_kernel(const DevModel* model, const 
     if (lane < d::NV) w.qd[lane] = x[d::NQ + lane];
     __syncwarp();
     float Rl[9], cl[3];
-    forward_kinematics<NA>(M, w, lane, Rl, cl);
+    forward_kinematics<NA>(M, w, Lanes<32>(lane), Rl, cl);
     __syncwarp();
     const int nlb = 2 * NA * M.nb, np = nlb + NA * NA;
     float mb = INFINITY, ma = INFINITY;

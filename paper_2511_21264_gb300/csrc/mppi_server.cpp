@@ -376,7 +376,7 @@ int srv_start(mppi_server* S) {
     if (!S || S->running.load() || S->scenes.empty()) return MPPI_ERR_INVALID_ARG;
     int max_h = 0;
     for (const Scene& sc : S->scenes) max_h = std::max(max_h, sc.H);
-    int rc = batch_shape(S->na, S->cfg.samples_per_cta, max_h, &S->L);
+    int rc = batch_shape(S->na, S->cfg.samples_per_cta, 0, 0, max_h, &S->L);
     if (rc != MPPI_OK) return rc;
     S->stop = false;
     S->running = true;

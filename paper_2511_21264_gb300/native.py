@@ -121,6 +121,8 @@ def lib():
     _decl(L, "mppi_set_iteration", i, [vp, u64, vp])
     _decl(L, "mppi_sync", i, [vp, vp])
     _decl(L, "mppi_set_launch", i, [vp, i])
+    _decl(L, "mppi_set_layout", i, [vp, i, i])
+    _decl(L, "mppi_get_layout", i, [vp, C.POINTER(i), C.POINTER(i), C.POINTER(i)])
     _decl(L, "mppi_set_update", i, [vp, i, C.c_float, i, C.c_float])
     _decl(L, "mppi_get_covariance", i, [vp, fp, vp])
     _decl(L, "mppi_set_covariance", i, [vp, fp, vp])
@@ -136,9 +138,11 @@ def lib():
     _decl(L, "mppi_batch_costs", C.c_void_p, [vp, i])
     _decl(L, "mppi_batch_set_launch", i, [vp, i, i])
     _decl(L, "mppi_batch_get_launch", i, [vp, C.POINTER(i), C.POINTER(i)])
+    _decl(L, "mppi_batch_set_layout", i, [vp, i, i])
+    _decl(L, "mppi_batch_get_layout", i, [vp, C.POINTER(i), C.POINTER(i)])
     _decl(L, "mppi_batch_autotune", i, [vp, vp, vp, i, vp, C.POINTER(C.c_float)])
-    _decl(L, "mppi_tune_store", i, [C.c_char_p, i, i, C.c_float])
-    _decl(L, "mppi_tune_lookup", i, [C.c_char_p, C.POINTER(i), C.POINTER(i)])
+    _decl(L, "mppi_tune_store", i, [C.c_char_p, i, i, i, i, C.c_float])
+    _decl(L, "mppi_tune_lookup", i, [C.c_char_p, C.POINTER(i), C.POINTER(i), C.POINTER(i), C.POINTER(i)])
     _decl(L, "srv_create", i, [C.POINTER(ServerConfig), C.POINTER(vp)])
     _decl(L, "srv_destroy", i, [vp])
     _decl(L, "srv_add_scene", i, [vp, vp, i, i, C.c_float, fp, u64, fp, C.POINTER(i)])
@@ -394,6 +398,14 @@ class Batch:
         _check(lib().mppi_batch_get_launch(self._h, C.byref(s), C.byref(o)), "mppi_batch_get_launch")
         return s.value, o.value
 
+    def set_layout(self, lanes_per_sample=32, placement=0):
+        _check(lib().mppi_batch_set_layout(self._h, int(lanes_per_sample), int(placement)), "mppi_batch_set_layout")
+
+    def get_layout(self):
+        l, p = C.c_int(), C.c_int()
+        _check(lib().mppi_batch_get_layout(self._h, C.byref(l), C.byref(p)), "mppi_batch_get_layout")
+        return l.value, p.value
+
     def autotune(self, states, us, reps=3, stream=None):
         ms = C.c_float()
         _check(lib().mppi_batch_autotune(self._h, self._ptrs(states), self._ptrs(us), reps, _stream(stream),
@@ -546,6 +558,16 @@ class Controller:
 
     def set_launch(self, samples_per_cta: int):
         _check(lib().mppi_set_launch(self._h, int(samples_per_cta)), "mppi_set_launch")
+
+    def set_layout(self, lanes_per_sample: int = 32, placement: int = 0):
+        """Rollout layout: lanes per sample (32, 16, or 8 for 3-link arms) and
+        the placement of a lone ball contact's solve (0 fused, 1 after)."""
+        _check(lib().mppi_set_layout(self._h, int(lanes_per_sample), int(placement)), "mppi_set_layout")
+
+    def get_layout(self):
+        l, p, s = C.c_int(), C.c_int(), C.c_int()
+        _check(lib().mppi_get_layout(self._h, C.byref(l), C.byref(p), C.byref(s)), "mppi_get_layout")
+        return l.value, p.value, s.value
 
     def set_projection(self, bounds, iters: int = 30, rho: float = 1.0, scales=None):
         """QP smoothing projection (Eq. 5) of every sample: bounds is nu x 8

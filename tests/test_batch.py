@@ -16,15 +16,18 @@ def test_tune_table_store_and_lookup(tmp_path, monkeypatch):
     L = native.lib()
     path = tmp_path / "sub" / "tune.txt"
     monkeypatch.setenv("MPPI_TUNE_FILE", str(path))
-    s, o = C.c_int(), C.c_int()
-    assert L.mppi_tune_lookup(b"nv20_nb8_n4_K100_H16", C.byref(s), C.byref(o)) != 0
-    assert L.mppi_tune_store(b"nv20_nb8_n4_K100_H16", 4, 1, C.c_float(1.5)) == 0
-    assert L.mppi_tune_store(b"other", 2, 0, C.c_float(0.5)) == 0
-    assert L.mppi_tune_store(b"nv20_nb8_n4_K100_H16", 8, 0, C.c_float(1.2)) == 0  # later entry wins
-    assert L.mppi_tune_lookup(b"nv20_nb8_n4_K100_H16", C.byref(s), C.byref(o)) == 0
-    assert (s.value, o.value) == (8, 0)
-    assert L.mppi_tune_store(b"bad key", 4, 1, C.c_float(1.0)) == 1
-    assert L.mppi_tune_store(b"k", 0, 1, C.c_float(1.0)) == 1
+    s, o, lp, pl = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+    look = lambda k: L.mppi_tune_lookup(k, C.byref(s), C.byref(o), C.byref(lp), C.byref(pl))
+    assert look(b"nv20_nb8_n4_K100_H16") != 0
+    assert L.mppi_tune_store(b"nv20_nb8_n4_K100_H16", 4, 1, 32, 0, C.c_float(1.5)) == 0
+    assert L.mppi_tune_store(b"other", 2, 0, 16, 1, C.c_float(0.5)) == 0
+    assert L.mppi_tune_store(b"nv20_nb8_n4_K100_H16", 8, 0, 16, 1, C.c_float(1.2)) == 0  # later entry wins
+    assert look(b"nv20_nb8_n4_K100_H16") == 0
+    assert (s.value, o.value, lp.value, pl.value) == (8, 0, 16, 1)
+    assert L.mppi_tune_store(b"bad key", 4, 1, 32, 0, C.c_float(1.0)) == 1
+    assert L.mppi_tune_store(b"k", 0, 1, 32, 0, C.c_float(1.0)) == 1
+    assert L.mppi_tune_store(b"k", 4, 1, 12, 0, C.c_float(1.0)) == 1
+    assert L.mppi_tune_store(b"k", 4, 1, 16, 2, C.c_float(1.0)) == 1
     assert len(path.read_text().splitlines()) == 3
 
 
@@ -60,18 +63,20 @@ def test_batch_matches_single_controllers_bitwise_under_every_shape(tmp_path, mo
         ref.append(u.clone())
     b = native.Batch([(m, K, H, lam, sig, key) for sc, m, K, H, lam, sig, key in inst])
     xs = [torch.tensor(m.home(), device="cuda") for sc, m, *_ in inst]
-    for spc in (1, 2, 4, 8):
-        for order in (0, 1):
-            b.set_launch(spc, order)
-            b.set_iteration(-1, 0)
-            us = [torch.zeros((H, sc.nu), device="cuda") for sc, m, K, H, *_ in inst]
-            b.step(xs, us)
-            b.step(xs, us)
-            rc, errs = b.sync()
-            assert rc == 0, errs
-            for i in range(len(inst)):
-                assert torch.equal(us[i], ref[i]), (spc, order, i)
-                assert b.iteration(i) == 2
+    for lps, place in ((32, 0), (32, 1), (16, 0), (16, 1)):
+        b.set_layout(lps, place)
+        for spc in (1, 2, 4, 8):
+            for order in (0, 1):
+                b.set_launch(spc, order)
+                b.set_iteration(-1, 0)
+                us = [torch.zeros((H, sc.nu), device="cuda") for sc, m, K, H, *_ in inst]
+                b.step(xs, us)
+                b.step(xs, us)
+                rc, errs = b.sync()
+                assert rc == 0, errs
+                for i in range(len(inst)):
+                    assert torch.equal(us[i], ref[i]), (lps, place, spc, order, i)
+                    assert b.iteration(i) == 2
 
 
 @pytest.mark.gpu
@@ -102,7 +107,9 @@ def test_batch_graph_replay_and_autotune(tmp_path, monkeypatch):
         assert ms > 0
         assert all(b.iteration(i, stream=s) == 3 for i in range(len(inst)))
     text = (tmp_path / "tune.txt").read_text().split()
-    assert text[0].startswith("nv20_") and int(text[1]) in (1, 2, 4, 8) and int(text[2]) in (0, 1)
+    assert text[0].startswith("nv20_") and int(text[1]) in (1, 2, 4, 8, 16) and int(text[2]) in (0, 1)
+    assert int(text[3]) in (16, 32) and int(text[4]) in (0, 1)
     # a new batch with the same key picks the stored shape up
     b2 = native.Batch([(m, K, H, lam, sig, key) for sc, m, K, H, lam, sig, key in inst])
     assert b2.get_launch() == (int(text[1]), int(text[2]))
+    assert b2.get_layout() == (int(text[3]), int(text[4]))

@@ -327,15 +327,17 @@ def test_step_with_host_buffers_matches_device_step(native):
 
 def test_launch_shape_does_not_change_results(native):
     # one sample per CTA (the default below 8 x the SM count, plain launches)
-    # and 2, 4 or 16 samples per CTA (programmatic dependent launches): the
-    # same iterations, bitwise, eager and from the captured graph
+    # and 2, 4 or 16 samples per CTA (programmatic dependent launches), one or
+    # two samples per warp: the same iterations, bitwise, eager and from the
+    # captured graph
     K, H = 1024, 32
     sc, gm, om, ctl, key = _setup(2, K=K, H=H)
     x = _t(_f32(sc.x0))
     s = torch.cuda.Stream()
     outs = []
     with torch.cuda.stream(s):
-        for spc in (0, 1, 2, 4, 16):
+        for lps, spc in ((32, 0), (32, 1), (32, 2), (32, 4), (32, 16), (16, 2), (16, 8), (16, 16)):
+            ctl.set_layout(lps, 0)
             ctl.set_launch(spc)
             for graph in (False, True):
                 ctl.set_iteration(0, stream=s)
@@ -350,6 +352,12 @@ def test_launch_shape_does_not_change_results(native):
     s.synchronize()
     assert all(torch.equal(outs[0], o) for o in outs[1:])
     assert float(outs[0].abs().max()) > 0.0
+    # a shape whose workspaces exceed one CTA's shared memory is refused
+    from paper_2511_21264_gb300.native import MPPIError
+    ctl.set_layout(16, 0)
+    ctl.set_launch(32)
+    with pytest.raises(MPPIError):
+        ctl.step(x, u, u)
 
 
 def test_edge_cases(native):
