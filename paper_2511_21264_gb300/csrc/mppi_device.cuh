@@ -424,6 +424,30 @@ __device__ __forceinline__ float box_sdf_only(const float* a, const float* d, fl
     return sqrtf(q2) + fminf(mx, 0.0f);
 }
 
+// Separating-axis test of the segment mid +- hv against the box inflated
+// by r on every side (half-extents h + r): the three box axes, then the
+// three products hv x e_k, onto which the segment projects to one point.
+// A capsule of radius r that touches the box lies in that inflated box, so
+// it always passes; the margin eps absorbs FP32 rounding.
+__device__ __forceinline__ bool segment_meets_inflated_box(const float* mid, const float* hv, const float* box,
+                                                           float r) {
+    constexpr float eps = 1e-5f;
+    float dc[3], e[3], ah[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        dc[k] = mid[k] - box[k];
+        e[k] = box[3 + k] + r + eps;
+        ah[k] = fabsf(hv[k]);
+    }
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) ok = ok && fabsf(dc[k]) <= e[k] + ah[k];
+    ok = ok && fabsf(dc[1] * hv[2] - dc[2] * hv[1]) <= e[1] * ah[2] + e[2] * ah[1] + eps;
+    ok = ok && fabsf(dc[2] * hv[0] - dc[0] * hv[2]) <= e[0] * ah[2] + e[2] * ah[0] + eps;
+    ok = ok && fabsf(dc[0] * hv[1] - dc[1] * hv[0]) <= e[0] * ah[1] + e[1] * ah[0] + eps;
+    return ok;
+}
+
 // Candidate minimisers of the box SDF along the segment a + t d, t in [0,1].
 // The SDF is convex along the segment and piecewise smooth; its minimum lies
 // at an end point, at a slab-plane or axis-centre crossing (kinks), at the
@@ -624,9 +648,9 @@ __device__ __forceinline__ int collide(const DevModel& M, WarpWS<NA>& w, const L
     }
     // capsule-box: lane l (and, where a pass over the links fills half the
     // group, lane CL + l) tests link l's capsule against the boxes (or one
-    // half of them each): bounding sphere and axis-aligned overlap, both
-    // conservative; the survivors are placed link-major, box-minor by a
-    // prefix sum over the links
+    // half of them each): the segment against the box inflated by the
+    // capsule radius (separating axes, conservative); the survivors are
+    // placed link-major, box-minor by a prefix sum over the links
     if (nb > 0) {
         constexpr int CL = d::NL <= LPS / 2 ? LPS / 2 : LPS;  // lanes of one pass over the links
         constexpr int NH = LPS / CL;                          // box halves
@@ -638,30 +662,17 @@ __device__ __forceinline__ int collide(const DevModel& M, WarpWS<NA>& w, const L
             const float* a0 = w.a0[l];
             const float* a1 = w.a1[l];
             const float rc = M.link[l / NA][l % NA].rcap;
-            float mid[3], lo[3], hi[3];
+            float mid[3], hv[3];
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 mid[k] = 0.5f * (a0[k] + a1[k]);
-                lo[k] = fminf(a0[k], a1[k]) - rc;
-                hi[k] = fmaxf(a0[k], a1[k]) + rc;
+                hv[k] = 0.5f * (a1[k] - a0[k]);
             }
-            const float dx = a1[0] - a0[0], dy = a1[1] - a0[1], dz = a1[2] - a0[2];
-            const float rad = 0.5f * sqrtf(dx * dx + dy * dy + dz * dz) + rc;
             // the boxes' tests are independent: unrolled, their loads and
             // compare chains overlap
 #pragma unroll 4
-            for (int bi = b0; bi < b1; ++bi) {
-                const float* box = M.box[bi];
-                float lb2 = 0.0f;
-                bool ov = true;
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    const float e = fmaxf(fabsf(mid[k] - box[k]) - box[3 + k], 0.0f);
-                    lb2 += e * e;
-                    ov = ov && (lo[k] <= box[k] + box[3 + k]) && (hi[k] >= box[k] - box[3 + k]);
-                }
-                if (ov && lb2 < rad * rad) smask |= 1u << bi;
-            }
+            for (int bi = b0; bi < b1; ++bi)
+                if (segment_meets_inflated_box(mid, hv, M.box[bi], rc)) smask |= 1u << bi;
         }
         const int cnt = __popc(smask);
         const int cnt_link = NH == 2 ? cnt + g.xor_(cnt, CL) : cnt;  // both halves of link l
@@ -938,14 +949,13 @@ __device__ __forceinline__ void dynamics(const DevModel& M, WarpWS<NA>& w, const
     for (int e0 = 0; e0 < NENT; e0 += SEG) {
         const int e = e0 + i;
         {  // every lane computes (past the last entry on the last one), the entries' lanes store
-            int c = 0, rem = e < NENT ? e : NENT - 1;
+            // entry ee = c (c + 1) / 2 + r, r <= c: c counts the triangular
+            // numbers 1, 3, 6, ... not above ee
+            const int ee = e < NENT ? e : NENT - 1;
+            int c = 0;
 #pragma unroll
-            for (int cc = 0; cc < NA; ++cc)
-                if (rem > c) {
-                    rem -= c + 1;
-                    ++c;
-                }
-            const int r = rem;
+            for (int cc = 1; cc < NA; ++cc) c += ee >= cc * (cc + 1) / 2 ? 1 : 0;
+            const int r = ee - c * (c + 1) / 2;
             const float* Sr = w.ph.dyn.S[a * NA + r];
             const float* Fc = w.ph.dyn.F[a * NA + c];
             float mv = Sr[0] * Fc[0] + Sr[1] * Fc[1] + Sr[2] * Fc[2] + Sr[3] * Fc[3] + Sr[4] * Fc[4] + Sr[5] * Fc[5];

@@ -150,3 +150,58 @@ def test_layout_arguments_are_checked(native):
         ctl.set_layout(8, 0)    # a 7-link arm does not fit 4 lanes per arm
     ctl.set_layout(16, 1)
     assert ctl.get_layout()[:2] == (16, 1)
+
+
+def _boxes_under_links(sc, links, half=0.04, pen=0.01):
+    """The scene with its first boxes moved under the given (arm, link)
+    segments of the home pose: a cube below the link's midpoint, lowered
+    until the oracle's capsule-box distance is -pen.  The tilted link meets
+    the cube's top edge, so every contact point is unique (a segment
+    parallel to a face would make the deepest point a flat minimum, where
+    the two sides may pick different points of the minimising interval)."""
+    import dataclasses
+    f = oracle.Model(sc.to_blob()).fk(sc.x0[:sc.nq])
+    bc, bh = np.array(sc.boxes_c), np.array(sc.boxes_h)
+    for j, (a, i) in enumerate(links):
+        a0, a1 = f["a0"][a, i], f["a1"][a, i]
+        mid = 0.5 * (a0 + a1)
+        rc = sc.links[a][i].radius
+        lo, hi = 0.0, 1.0
+        for _ in range(80):   # bisection on the drop of the cube's centre
+            dz = 0.5 * (lo + hi)
+            if oracle.capsule_box(a0, a1, rc, mid - np.array([0.0, 0.0, dz]), np.full(3, half))[0] < -pen:
+                lo = dz
+            else:
+                hi = dz
+        bc[j] = mid - np.array([0.0, 0.0, 0.5 * (lo + hi)])
+        bh[j] = half
+    return dataclasses.replace(sc, boxes_c=bc, boxes_h=bh)
+
+
+def test_link_box_contacts_single_step_every_layout(native):
+    # capsule-box contacts found through the cull (bounding spheres, overlap,
+    # the segment against the box inflated by the capsule radius) and the
+    # exact minimum: single steps against the oracle, same bits in every
+    # layout, with many link-box contacts among the oracle's contacts
+    sc = _boxes_under_links(scenes.config(3), [(0, 2), (0, 4), (1, 3), (1, 5)])
+    blob = sc.to_blob()
+    gm, om = native.Model(blob), oracle.Model(blob)
+    n = 101
+    X = _states(sc, om, n, seed=91, q_spread=0.15, v_spread=0.2)
+    U1 = _f32(np.random.default_rng(92).normal(scale=0.3, size=(n, sc.nu)))
+    ctl = native.Controller(gm, n, 1, sc.lam, sc.sigma_vec(), 9)
+    outs = []
+    for lps, place in _layouts(3):
+        ctl.set_layout(lps, place)
+        xs = _t(X)
+        ctl.sim_step(xs, _t(U1))
+        assert ctl.sync() == 0
+        outs.append(xs.cpu().numpy())
+    for g in outs[1:]:
+        np.testing.assert_array_equal(g, outs[0])
+    link_box = 0
+    for i in range(n):
+        xo, info, lam, cons = om.step(X[i], U1[i], want_contacts=True)
+        link_box += sum(1 for c in cons if c["box"] >= 0 and c["bodyA"] < 2 * sc.n_a)
+        assert np.abs(outs[0][i] - xo).max() <= 1e-4 * max(1.0, np.abs(xo).max()), i
+    assert link_box >= 30, link_box
