@@ -140,6 +140,17 @@ int mppi_debug_noise(mppi_ctx *c, uint64_t iteration, float *eps_out, void *stre
  * ctr (device, n x 4 uint32), key = the 64-bit key, out (device, n x 4). */
 int mppi_debug_philox(int n, const uint32_t *ctr, uint64_t key, uint32_t *out, void *stream);
 
+/* Bounds check.  In a library compiled with -DMPPI_BOUNDS_CHECK every index
+ * the rollout, update, elite-set and QP kernels use into shared memory, the
+ * staged model and the device buffers is compared with its extent; a failed
+ * check sets a bit in a device word (1: shared/workspace index, 2: device
+ * buffer index) and the access is diverted, with no trap.  This call
+ * synchronises the device, returns the word of every translation unit ORed
+ * (and clears it) and sets *checked to 1 in such a build, 0 (word 0)
+ * otherwise.  Either pointer may be NULL.  A stand-in for a memory checker
+ * on small cases. */
+int mppi_debug_bounds(unsigned *word, int *checked);
+
 /* Iteration counter (checkpoint / resume).  get synchronises `stream`. */
 int mppi_get_iteration(mppi_ctx *c, uint64_t *iteration, void *stream);
 int mppi_set_iteration(mppi_ctx *c, uint64_t iteration, void *stream);

@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(1024) elite_select_kernel(const float* costs, 
         unsigned long long x = ~0ull;
         bool fin = false;
         if (t < K) {
-            const float c = costs[t];
+            const float c = ld_checked(costs, t, K);
             x = cost_key(c, t);
             fin = isfinite(c);
         }
@@ -79,9 +79,9 @@ __global__ void __launch_bounds__(1024) elite_select_kernel(const float* costs, 
             for (int stride = size >> 1; stride > 0; stride >>= 1) {
                 unsigned long long y;
                 if (stride >= 32) {
-                    keys[buf * 1024 + t] = x;
+                    if (MPPI_IN_RANGE(buf * 1024 + t, 2048)) keys[buf * 1024 + t] = x;
                     __syncthreads();
-                    y = keys[buf * 1024 + (t ^ stride)];
+                    y = MPPI_IN_RANGE(buf * 1024 + (t ^ stride), 2048) ? keys[buf * 1024 + (t ^ stride)] : x;
                     buf ^= 1;
                 } else {
                     y = __shfl_xor_sync(0xffffffffu, x, stride);
@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(1024) elite_select_kernel(const float* costs, 
                 x = (lower == asc) ? (x < y ? x : y) : (x < y ? y : x);
             }
         const int ne = nf == 0 ? 0 : (n_elite < nf ? n_elite : nf);
-        if (t < ne) eidx[t] = (int)(x & 0xFFFFFFFFull);
+        if (t < ne && MPPI_IN_RANGE(t, K)) eidx[t] = (int)(x & 0xFFFFFFFFull);
         if (t == 0) {
             sel[1] = x;
             sel[2] = (unsigned long long)nf;
@@ -103,8 +103,8 @@ __global__ void __launch_bounds__(1024) elite_select_kernel(const float* costs, 
     __syncthreads();
     int mine = 0;
     for (int i = threadIdx.x; i < P; i += blockDim.x) {
-        const float c = i < K ? costs[i] : 0.0f;
-        keys[i] = i < K ? cost_key(c, i) : ~0ull;
+        const float c = i < K ? ld_checked(costs, i, K) : 0.0f;
+        if (MPPI_IN_RANGE(i, P)) keys[i] = i < K ? cost_key(c, i) : ~0ull;
         mine += (i < K && isfinite(c)) ? 1 : 0;
     }
     atomicAdd(&nfin, mine);
@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(1024) elite_select_kernel(const float* costs, 
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
             for (int i = threadIdx.x; i < P; i += blockDim.x) {
                 const int j = i ^ stride;
-                if (j > i) {
+                if (j > i && MPPI_IN_RANGE(j, P)) {
                     const bool asc = (i & size) == 0;
                     const unsigned long long x = keys[i], y = keys[j];
                     if ((x > y) == asc) {
@@ -126,7 +126,8 @@ __global__ void __launch_bounds__(1024) elite_select_kernel(const float* costs, 
         }
     const int nf = nfin;
     const int ne = nf == 0 ? 0 : (n_elite < nf ? n_elite : nf);
-    for (int e = threadIdx.x; e < ne; e += blockDim.x) eidx[e] = (int)(keys[e] & 0xFFFFFFFFull);
+    for (int e = threadIdx.x; e < ne; e += blockDim.x)
+        if (MPPI_IN_RANGE(e, K)) eidx[e] = (int)(keys[e] & 0xFFFFFFFFull);
     if (threadIdx.x == 0) {
         sel[0] = ne > 0 ? keys[ne - 1] : 0ull;
         sel[1] = keys[0];
@@ -202,7 +203,9 @@ int launch_rollout(int na, int mode, const RolloutArgs& a, int spc, cudaStream_t
     return MPPI_ERR_UNSUPPORTED;
 }
 
-int launch_update(int nu, const UpdateArgs& a, int H, cudaStream_t s) {
+int launch_update(int nu, const UpdateArgs& a_in, int H, cudaStream_t s) {
+    UpdateArgs a = a_in;
+    a.H = H;
     cudaError_t e;
     if (nu == 6) e = launch_kernel(update_kernel<6>, dim3(H), dim3(256), 0, s, a.pdl != 0, a);
     else if (nu == 14) e = launch_kernel(update_kernel<14>, dim3(H), dim3(256), 0, s, a.pdl != 0, a);
@@ -308,6 +311,8 @@ int parse_model_blob(const void* blob, size_t len, DevModel* out, HostModelInfo*
     return MPPI_OK;
 }
 
+MPPI_BOUNDS_READER(bounds_word_api)
+
 }  // namespace mppi
 
 // ---------------------------------------------------------------------------
@@ -325,6 +330,7 @@ struct mppi_ctx {
     int K = 0, H = 0, spc = 4;
     int lps = 32, place = 0;  // lanes per sample, placement of the lone ball contact's solve
     bool spc_auto = true;     // spc is the library's choice for the layout
+    int spc_alt = 0, spc_alt_lps = 0;  // the default shape of another layout (the task suite's)
     float lambda = 1.0f;
     uint64_t seed = 0;
     float* d_sigma = nullptr;
@@ -470,9 +476,26 @@ int mppi_destroy(mppi_ctx* c) {
 // Samples per rollout CTA when the caller sets none: the shape that puts
 // the K samples on the SMs in the fewest waves with the least load on the
 // busiest SM (occupancy of the sampling rollout kernel of the layout).
-static int default_spc(const mppi_ctx* c) {
+static int default_spc_for(const mppi_ctx* c, int lps) {
     const int unom = c->H * 2 * c->m->info.na <= 2048 ? c->H * 2 * c->m->info.na : 0;
-    return c->m->info.na == 3 ? choose_spc_na3(c->lps, c->K, unom) : choose_spc_na7(c->lps, c->K, unom);
+    return c->m->info.na == 3 ? choose_spc_na3(lps, c->K, unom) : choose_spc_na7(lps, c->K, unom);
+}
+static int default_spc(const mppi_ctx* c) { return default_spc_for(c, c->lps); }
+
+// Samples per CTA for a launch in layout lps: the handle's shape when lps is
+// its layout, else (the ball-task suite runs on 32 lanes per sample) the
+// default shape for lps, or the handle's shape capped at 512 threads when
+// the caller chose it.
+static int launch_spc(mppi_ctx* c, int lps) {
+    if (lps == c->lps) return c->spc;
+    if (c->spc_auto) {
+        if (c->spc_alt_lps != lps) {
+            c->spc_alt = default_spc_for(c, lps);
+            c->spc_alt_lps = lps;
+        }
+        return c->spc_alt;
+    }
+    return std::min(c->spc, 512 / lps);
 }
 
 int mppi_create(const mppi_model* m, int K, int H, float lambda, const float* sigma, uint64_t seed, mppi_ctx** out) {
@@ -789,6 +812,9 @@ static int launch_projection(mppi_ctx* c, const float* state, const float* u_nom
     q.o_a = nu;                        // member k
     q.o_b = 1;                         // class j
     q.o_h = (long long)c->K * nu;      // step h
+    q.n_cls = nu;
+    q.in_n = 0;
+    q.out_n = (long long)c->H * c->K * nu;
     return launch_qp(q, s);
 }
 
@@ -918,6 +944,7 @@ static int launch_elite(mppi_ctx* c, const float* costs, const float* u_nom, flo
     if (e != cudaSuccess) return cuda_fail(e);
     EliteArgs a{};
     a.K = c->K;
+    a.H = c->H;
     a.n_elite = c->n_elite;
     a.update_cov = c->update_cov;
     a.beta = c->lambda;
@@ -992,9 +1019,9 @@ static int enqueue_step(mppi_ctx* c, const float* state, const float* u_nom, flo
     // dependent CTAs cost more than the overlap saves (lift, K = 1024: 0.146
     // ms per iteration without, 0.168 with), so they are used with wider CTAs
     // only; event records between the kernels would break the overlap anyway.
-    const bool pdl = !prof && c->spc * a.lps > 32;
+    const bool pdl = !prof && launch_spc(c, a.lps) * a.lps > 32;
     a.pdl = pdl;
-    rc = launch_rollout(c->m->info.na, mode, a, c->spc, s);
+    rc = launch_rollout(c->m->info.na, mode, a, launch_spc(c, a.lps), s);
     if (rc != MPPI_OK) return rc;
     if (prof) cudaEventRecord(ev[2], s);
     if (elite_mode(c)) {
@@ -1116,7 +1143,7 @@ int rollout_batch(mppi_ctx* c, int n, const float* states, const float* U, float
     a.err = c->d_err;
     a.task = c->task_on ? c->d_task : nullptr;
     a.lps = a.task ? 32 : c->lps;
-    return launch_rollout(c->m->info.na, 0, a, c->spc, (cudaStream_t)stream);
+    return launch_rollout(c->m->info.na, 0, a, launch_spc(c, a.lps), (cudaStream_t)stream);
 }
 
 int sim_step(mppi_ctx* c, int n, float* states, const float* U1, void* stream) {
@@ -1132,7 +1159,7 @@ int sim_step(mppi_ctx* c, int n, float* states, const float* U1, void* stream) {
     a.states_out = states;  // each lane group reads its state before writing it back
     a.err = c->d_err;
     a.lps = c->lps;
-    return launch_rollout(c->m->info.na, 0, a, c->spc, (cudaStream_t)stream);
+    return launch_rollout(c->m->info.na, 0, a, launch_spc(c, a.lps), (cudaStream_t)stream);
 }
 
 int mppi_debug_noise(mppi_ctx* c, uint64_t iteration, float* eps, void* stream) {
@@ -1186,6 +1213,14 @@ int mppi_sync(mppi_ctx* c, void* stream) {
     if (err & ERRB_CHOLESKY) return MPPI_ERR_CHOLESKY;
     if (err & ERRB_NONFINITE) return MPPI_ERR_NONFINITE;
     return MPPI_OK;
+}
+
+int mppi_debug_bounds(unsigned* word, int* checked) {
+    unsigned w = bounds_word_api() | bounds_word_batch() | bounds_word_qp() | bounds_word_loop() |
+                 bounds_word_rollout7() | bounds_word_rollout3();
+    if (word) *word = w;
+    if (checked) *checked = kBoundsCheck ? 1 : 0;
+    return w == ~0u ? MPPI_ERR_CUDA : MPPI_OK;
 }
 
 }  // extern "C"

@@ -108,6 +108,7 @@ __global__ void __launch_bounds__(256) batch_update_kernel(const BatchInst* inst
     const int h = blockIdx.x - I.row0;
     UpdateArgs a{};
     a.K = I.K;
+    a.H = I.H;
     a.costs = I.costs;
     a.u_nom = I.u;
     a.u_out = I.u;
@@ -199,6 +200,8 @@ int launch_batch_iteration(const BatchInst* insts, int n, int ntiles, int nrows,
     else batch_update_kernel<14><<<nrows, 256, 0, s>>>(insts, n);
     return cudaGetLastError() == cudaSuccess ? MPPI_OK : MPPI_ERR_CUDA;
 }
+
+MPPI_BOUNDS_READER(bounds_word_batch)
 
 int launch_shift(float* u, int H, int nu, cudaStream_t s) {
     shift_kernel<<<1, 32, 0, s>>>(u, H, nu);

@@ -31,6 +31,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "mppi_check.cuh"
 #include "mppi_internal.h"
 
 namespace mppi {
@@ -42,14 +43,16 @@ constexpr int MAXR = 3 * MAXC;
 constexpr unsigned FULL = 0xffffffffu;
 
 
+// Arrays are CArr (mppi_check.cuh): plain arrays, range-checked in the
+// bounds-check build.
 struct __align__(16) DevLink {
-    float FR[9];
-    float Fp[3];
-    float com[3];
+    CArr<float, 9> FR;
+    CArr<float, 3> Fp;
+    CArr<float, 3> com;
     float mass;
-    float I[6];  // inertia about the COM in link axes: xx yy zz xy xz yz
-    float s0[3];
-    float s1[3];
+    CArr<float, 6> I;  // inertia about the COM in link axes: xx yy zz xy xz yz
+    CArr<float, 3> s0;
+    CArr<float, 3> s1;
     float rcap, D, gear, tau_max;  // D = joint damping + servo gain (implicit)
     float u_lo, u_hi, gravcomp, pad;
 };
@@ -57,14 +60,16 @@ struct __align__(16) DevLink {
 struct __align__(16) DevModel {
     int na, nb, maxc, sweeps;
     float dt, mu, imp, erp;
-    float g[3], floor_z;
+    CArr<float, 3> g;
+    float floor_z;
     float rb, mb, Ib, pad0;
-    float goal[3], w_goal;
+    CArr<float, 3> goal;
+    float w_goal;
     float w_u, w_pen, w_obst, w_grasp;
-    float baseR[2][9];
-    float basep[2][3];
-    float box[MAXB][6];  // centre, half-extents
-    DevLink link[2][MAXL];
+    CArr<CArr<float, 9>, 2> baseR;
+    CArr<CArr<float, 3>, 2> basep;
+    CArr<CArr<float, 6>, MAXB> box;  // centre, half-extents
+    CArr<CArr<DevLink, MAXL>, 2> link;
 };
 static_assert(sizeof(DevModel) % 16 == 0, "model must stage with 16-byte copies");
 
@@ -132,50 +137,50 @@ __device__ __forceinline__ float group_sum(const Lanes<LPS>& g, float v) {
     return v;
 }
 
-// Per-warp (per-sample) workspace in shared memory.  Scratch that lives in
+// Per-sample workspace in shared memory.  Scratch that lives in
 // one phase only shares storage: the capsule-box survivor list (collision),
 // the joint axes and subtree forces (dynamics) and the contact rows,
 // Delassus block and impulses (contacts).
 template <int NA>
 struct __align__(16) WarpWS {
     using d = Dims<NA>;
-    float q[d::NQ + 1];
-    float qd[d::NV];
-    float v[d::NV];
-    float vf[d::NV];
-    float zz[d::NV];
-    float rhs[d::NV];
-    float u[d::NU];
-    float zn[8][16];  // standard normals of the next 8 steps (Philox path)
+    CArr<float, d::NQ + 1> q;
+    CArr<float, d::NV> qd;
+    CArr<float, d::NV> v;
+    CArr<float, d::NV> vf;
+    CArr<float, d::NV> zz;
+    CArr<float, d::NV> rhs;
+    CArr<float, d::NU> u;
+    CArr<CArr<float, 16>, 8> zn;  // standard normals of the next steps (Philox path)
     // kinematics, per link (read across lanes)
-    float z[d::NL][3];
-    float o[d::NL][3];
-    float a0[d::NL][3];
-    float a1[d::NL][3];
+    CArr<CArr<float, 3>, d::NL> z;
+    CArr<CArr<float, 3>, d::NL> o;
+    CArr<CArr<float, 3>, d::NL> a0;
+    CArr<CArr<float, 3>, d::NL> a1;
     // factors of (M + dt D), per arm
-    float L[2][NA][NA];
-    float Ldi[2][NA];  // reciprocal diagonal of the factors
+    CArr<CArr<CArr<float, NA>, NA>, 2> L;
+    CArr<CArr<float, NA>, 2> Ldi;  // reciprocal diagonal of the factors
     // contacts of this step, canonical order
-    float cp[MAXC][3];
-    float cn[MAXC][3];
-    float cdep[MAXC];
-    int cA[MAXC];
-    int cB[MAXC];
-    float ee[2][6];   // task cost: end-effector position and velocity per arm
+    CArr<CArr<float, 3>, MAXC> cp;
+    CArr<CArr<float, 3>, MAXC> cn;
+    CArr<float, MAXC> cdep;
+    CArr<int, MAXC> cA;
+    CArr<int, MAXC> cB;
+    CArr<CArr<float, 6>, 2> ee;   // task cost: end-effector position and velocity per arm
     union Phase {
         struct {
-            short surv[2 * MAXL * MAXB];  // capsule-box pairs that pass the cull
+            CArr<short, 2 * MAXL * MAXB> surv;  // capsule-box pairs that pass the cull
         } col;
         struct {
-            float S[d::NL][6];
-            float F[d::NL][6];
+            CArr<CArr<float, 6>, d::NL> S;
+            CArr<CArr<float, 6>, d::NL> F;
         } dyn;
         struct {
-            float Y[MAXR][d::NV];
-            float G[MAXR * MAXR];  // Delassus block Y Y^T, nr x nr
-            float4 rc4[MAXR];      // per row: b = J v_f, R, 1/(A+R), reference velocity
-            float lam[MAXR];
-            int tmask[MAXR];       // blocks a row touches: 1 left arm, 2 right arm, 4 ball
+            CArr<CArr<float, d::NV>, MAXR> Y;
+            CArr<float, MAXR * MAXR> G;  // Delassus block Y Y^T, nr x nr
+            CArr<float4, MAXR> rc4;      // per row: b = J v_f, R, 1/(A+R), reference velocity
+            CArr<float, MAXR> lam;
+            CArr<int, MAXR> tmask;       // blocks a row touches: 1 left arm, 2 right arm, 4 ball
         } con;
     } ph;
 };

@@ -61,6 +61,7 @@ struct RolloutArgs {
 // Arguments of the weighted-mean update (one CTA per horizon step).
 struct UpdateArgs {
     int K;
+    int H;              // horizon (rows of u_nom / u_out); set by the launch
     const float* costs;
     const float* u_nom;
     float* u_out;
@@ -165,6 +166,9 @@ struct QPArgs {
     float* out;
     long long o_a, o_b, o_h;
     const float* minv;   // H <= 32: per class the 32 x 32 inverse (I + rho D^T D)^-1 in velocity coordinates
+    // extents, for the bounds-check build: classes, floats of vin and of out
+    int n_cls;
+    long long in_n, out_n;
 };
 constexpr int QP_WARP_MAX_H = 32;
 int qp_band_factor(int H, double rho, const double sc[4], float4* band);
@@ -178,6 +182,15 @@ int launch_best_average(const float* U, const float* best, const float* bestU, i
                         cudaStream_t s);
 int launch_shift_rows(float* u, int H, int row, int n, cudaStream_t s);
 int launch_probe(int na, const DevModel* model, const float* x, float* out, cudaStream_t s);
+
+// bounds words of the translation units with kernels (read and cleared;
+// always 0 unless built with -DMPPI_BOUNDS_CHECK)
+unsigned bounds_word_api();
+unsigned bounds_word_batch();
+unsigned bounds_word_qp();
+unsigned bounds_word_loop();
+unsigned bounds_word_rollout7();
+unsigned bounds_word_rollout3();
 
 int parse_model_blob(const void* blob, size_t len, DevModel* out, HostModelInfo* info);
 int launch_rollout(int na, int mode, const RolloutArgs& a, int spc, cudaStream_t s);

@@ -12,6 +12,7 @@ struct SampleIO {
     const float* x;            // start state (nx)
     const float* U;            // explicit controls of this sample, row h at U + h * u_stride, MODE 0
     long long u_stride;
+    long long u_ext;           // floats from U to the end of the caller's control buffer, MODE 0
     const float* unom;         // nominal controls (H x nu, shared or global), MODE 1
     float sig, lo, hi;         // this lane's sigma and control bounds (group lane < nu), MODE 1
     uint2 key;                 // Philox key, MODE 1
@@ -54,8 +55,8 @@ __device__ __forceinline__ float rollout_sample(const DevModel& M, WarpWS<NA>& w
 #pragma unroll
     for (int c0 = 0; c0 < d::NX; c0 += LPS) {
         const int c = c0 + sl;
-        if (c < d::NQ) w.q[c] = io.x[c];
-        else if (c < d::NX) w.qd[c - d::NQ] = io.x[c];
+        if (c < d::NQ) w.q[c] = ld_checked(io.x, c, d::NX);
+        else if (c < d::NX) w.qd[c - d::NQ] = ld_checked(io.x, c, d::NX);
     }
     g.sync();
     float cost = 0.0f;
@@ -76,7 +77,7 @@ __device__ __forceinline__ float rollout_sample(const DevModel& M, WarpWS<NA>& w
         tacc.c = tacc.th = tacc.yz = tacc.v2 = tacc.r = tacc.l = tacc.eo = tacc.ot = 0.0f;
     }
     float upre = 0.0f;  // explicit controls: the next step's value
-    if (MODE == 0 && sl < d::NU) upre = io.U[sl];
+    if (MODE == 0 && sl < d::NU) upre = ld_checked(io.U, sl, io.u_ext);
     for (int h = 0; h < io.H; ++h) {
         if (MODE == 1) {
             // every DS steps the group's lanes draw one Philox block each: DS
@@ -97,13 +98,13 @@ __device__ __forceinline__ float rollout_sample(const DevModel& M, WarpWS<NA>& w
             {  // every lane computes (past the controls on the last one), the controls' lanes store
                 const int jc = sl < d::NU ? sl : d::NU - 1;
                 const float* zr = w.zn[h & (DS - 1)];
-                float acc = io.unom[h * d::NU + jc];
+                float acc = ld_checked(io.unom, h * d::NU + jc, (long long)io.H * d::NU);
                 if (io.Lfac) {  // u = nu + L_h z, FMAs in the order sample_row uses
                     // (unrolled over the row so that its loads are issued together)
-                    const float* Lr = io.Lfac + ((size_t)h * d::NU + jc) * d::NU;
+                    const long long r0 = ((long long)h * d::NU + jc) * d::NU, n_l = (long long)io.H * d::NU * d::NU;
 #pragma unroll
                     for (int i = 0; i < d::NU; ++i)
-                        if (i <= jc) acc = __fmaf_rn(Lr[i], zr[i], acc);
+                        if (i <= jc) acc = __fmaf_rn(ld_checked(io.Lfac, r0 + i, n_l), zr[i], acc);
                 } else {
                     acc = __fmaf_rn(io.sig, zr[jc], acc);
                 }
@@ -111,12 +112,13 @@ __device__ __forceinline__ float rollout_sample(const DevModel& M, WarpWS<NA>& w
                 if (sl < d::NU) {
                     w.u[sl] = uv;
                     uacc = __fmaf_rn(uv, uv, uacc);
-                    if (io.U_store) io.U_store[((size_t)h * io.Kn + k) * d::NU + sl] = uv;
+                    const long long si = ((long long)h * io.Kn + k) * d::NU + sl;
+                    if (io.U_store && MPPI_IN_RANGE(si, (long long)io.H * io.Kn * d::NU)) io.U_store[si] = uv;
                 }
             }
         } else if (sl < d::NU) {
             const float uv = upre;  // read one step ahead: its latency overlaps the step
-            if (h + 1 < io.H) upre = io.U[(h + 1) * io.u_stride + sl];
+            if (h + 1 < io.H) upre = ld_checked(io.U, (h + 1) * io.u_stride + sl, io.u_ext);
             w.u[sl] = uv;
             uacc = __fmaf_rn(uv, uv, uacc);
         }
@@ -197,8 +199,8 @@ __device__ __forceinline__ float rollout_sample(const DevModel& M, WarpWS<NA>& w
 #pragma unroll
         for (int c0 = 0; c0 < d::NX; c0 += LPS) {
             const int c = c0 + sl;
-            if (c < d::NQ) io.x_out[c] = w.q[c];
-            else if (c < d::NX) io.x_out[c] = w.qd[c - d::NQ];
+            if (c < d::NQ && MPPI_IN_RANGE(c, d::NX)) io.x_out[c] = w.q[c];
+            else if (c < d::NX && MPPI_IN_RANGE(c, d::NX)) io.x_out[c] = w.qd[c - d::NQ];
         }
     }
     return cost;
@@ -207,9 +209,9 @@ __device__ __forceinline__ float rollout_sample(const DevModel& M, WarpWS<NA>& w
 // Shared memory of one update CTA.
 template <int NU>
 struct UpdateSmem {
-    float red[NU + 1][256];
-    float rmin[256];
-    int ridx[256];
+    CArr<CArr<float, 256>, NU + 1> red;
+    CArr<float, 256> rmin;
+    CArr<int, 256> ridx;
     int is_last;
 };
 
@@ -226,7 +228,7 @@ __device__ __forceinline__ void update_step(const UpdateArgs& a, int h, UpdateSm
     float cm = INFINITY;
     int ci = 0x7fffffff;
     for (int k = tid; k < a.K; k += T) {
-        const float c = a.costs[k];
+        const float c = ld_checked(a.costs, k, a.K);
         if (isfinite(c) && (c < cm)) {
             cm = c;
             ci = k;
@@ -267,22 +269,22 @@ __device__ __forceinline__ void update_step(const UpdateArgs& a, int h, UpdateSm
     float un[NU], sg[NU], lo[NU], hi[NU];
 #pragma unroll
     for (int j = 0; j < NU; ++j) {
-        un[j] = a.u_nom[h * NU + j];
-        sg[j] = a.sigma[j];
-        lo[j] = a.u_lo[j];
-        hi[j] = a.u_hi[j];
+        un[j] = ld_checked(a.u_nom, h * NU + j, (long long)a.H * NU);
+        sg[j] = ld_checked(a.sigma, j, NU);
+        lo[j] = ld_checked(a.u_lo, j, NU);
+        hi[j] = ld_checked(a.u_hi, j, NU);
     }
     if (any) {
         const float inv_lam = 1.0f / a.lambda;
         for (int k = tid; k < a.K; k += T) {
-            const float c = a.costs[k];
+            const float c = ld_checked(a.costs, k, a.K);
             const float wk = isfinite(c) ? expf(-(c - cmin) * inv_lam) : 0.0f;
             Z += wk;
             if (a.U_stored) {
                 // the rollout's own samples (bit-identical to regenerating them)
-                const float* uk = a.U_stored + ((size_t)h * a.K + k) * NU;
+                const long long u0 = ((long long)h * a.K + k) * NU, n_u = (long long)a.H * a.K * NU;
 #pragma unroll
-                for (int j = 0; j < NU; ++j) acc[j] += wk * uk[j];
+                for (int j = 0; j < NU; ++j) acc[j] += wk * ld_checked(a.U_stored, u0 + j, n_u);
             } else {
 #pragma unroll
                 for (int jb = 0; jb < (NU + 3) / 4; ++jb) {
@@ -321,7 +323,8 @@ __device__ __forceinline__ void update_step(const UpdateArgs& a, int h, UpdateSm
         sm.red[tid][0] = t;
     }
     __syncthreads();
-    if (tid < NU) a.u_out[h * NU + tid] = any ? sm.red[tid][0] / sm.red[NU][0] : un[tid];
+    if (tid < NU && MPPI_IN_RANGE(h * NU + tid, (long long)a.H * NU))
+        a.u_out[h * NU + tid] = any ? sm.red[tid][0] / sm.red[NU][0] : un[tid];
     if (h == 0 && tid == 0) {
         if (!any) atomicOr(a.err, ERRB_NONFINITE);
         if (a.best) {
@@ -396,7 +399,7 @@ __device__ __forceinline__ unsigned long long cost_key(float c, int k) {
 }
 
 struct EliteArgs {
-    int K, n_elite, update_cov;
+    int K, H, n_elite, update_cov;
     float beta, eta, cov_floor;
     const float* costs;
     const float* u_nom;
@@ -421,10 +424,10 @@ struct EliteArgs {
 
 template <int NU>
 struct EliteSmem {
-    float red[NU + 1][256];
-    float d[64][NU + 1];      // a chunk of weighted deviations
-    float cov[NU][NU];
-    float mean[NU];
+    CArr<CArr<float, 256>, NU + 1> red;
+    CArr<CArr<float, NU + 1>, 64> d;  // a chunk of weighted deviations
+    CArr<CArr<float, NU>, NU> cov;
+    CArr<float, NU> mean;
     int is_last;
 };
 
@@ -432,9 +435,9 @@ template <int NU>
 __device__ __forceinline__ void elite_row(const EliteArgs& a, int h, int k, uint2 key, uint32_t iter,
                                           const float* unom_h, float (&u)[NU]) {
     if (a.U_stored) {
-        const float* uk = a.U_stored + ((size_t)h * a.K + k) * NU;
+        const long long u0 = ((long long)h * a.K + k) * NU, n_u = (long long)a.H * a.K * NU;
 #pragma unroll
-        for (int j = 0; j < NU; ++j) u[j] = uk[j];
+        for (int j = 0; j < NU; ++j) u[j] = ld_checked(a.U_stored, u0 + j, n_u);
     } else {
         sample_row<NU>(key, iter, k, h, unom_h, a.sigma, a.Lfac ? a.Lfac + (size_t)h * NU * NU : nullptr, a.u_lo,
                        a.u_hi, u);
@@ -450,10 +453,10 @@ __device__ __forceinline__ void elite_update_step(const EliteArgs& a, int h, Eli
     const uint2 key = make_uint2((uint32_t)a.seed, (uint32_t)(a.seed >> 32));
     const unsigned long long bestk = a.sel[1];
     const bool any = a.sel[2] > 0;
-    const float cmin = any ? a.costs[(int)(bestk & 0xFFFFFFFFull)] : 0.0f;
+    const float cmin = any ? ld_checked(a.costs, (long long)(bestk & 0xFFFFFFFFull), a.K) : 0.0f;
     float unom_h[NU];
 #pragma unroll
-    for (int j = 0; j < NU; ++j) unom_h[j] = a.u_nom[h * NU + j];
+    for (int j = 0; j < NU; ++j) unom_h[j] = ld_checked(a.u_nom, h * NU + j, (long long)a.H * NU);
     const float inv_beta = 1.0f / a.beta;
     // (1) weighted elite mean over the elite list
     const int nfin = (int)a.sel[2];
@@ -464,8 +467,8 @@ __device__ __forceinline__ void elite_update_step(const EliteArgs& a, int h, Eli
     float Z = 0.0f;
     const bool cached = ne <= 64;  // the covariance pass then reuses the rows kept here
     for (int e = tid; e < ne; e += T) {
-        const int k = a.eidx[e];
-        const float wk = expf(-(a.costs[k] - cmin) * inv_beta);
+        const int k = ld_checked(a.eidx, e, a.K);
+        const float wk = expf(-(ld_checked(a.costs, k, a.K) - cmin) * inv_beta);
         float u[NU];
         elite_row<NU>(a, h, k, key, iter, unom_h, u);
         Z += wk;
@@ -507,7 +510,8 @@ __device__ __forceinline__ void elite_update_step(const EliteArgs& a, int h, Eli
         float u[NU];
         elite_row<NU>(a, h, (int)(bestk & 0xFFFFFFFFull), key, iter, unom_h, u);
 #pragma unroll
-        for (int j = 0; j < NU; ++j) a.best_U[h * NU + j] = u[j];
+        for (int j = 0; j < NU; ++j)
+            if (MPPI_IN_RANGE(h * NU + j, (long long)a.H * NU)) a.best_U[h * NU + j] = u[j];
     }
     __syncthreads();
     // (2) weighted covariance about the new mean, one block per step
@@ -536,8 +540,8 @@ __device__ __forceinline__ void elite_update_step(const EliteArgs& a, int h, Eli
                         for (int j = 0; j < NU; ++j) u[j] = sm.d[tid][j];
                         wk = sm.d[tid][NU];
                     } else {
-                        const int k = a.eidx[e];
-                        wk = expf(-(a.costs[k] - cmin) * inv_beta);
+                        const int k = ld_checked(a.eidx, e, a.K);
+                        wk = expf(-(ld_checked(a.costs, k, a.K) - cmin) * inv_beta);
                         elite_row<NU>(a, h, k, key, iter, unom_h, u);
                     }
                 }
@@ -554,14 +558,16 @@ __device__ __forceinline__ void elite_update_step(const EliteArgs& a, int h, Eli
             __syncthreads();
         }
         if (tid < NE) {
-            float* S = a.Sigma + (size_t)h * NU * NU;
-            float v = (1.0f - a.eta) * S[ci * NU + cj] + a.eta * (cv / Zs);
+            const long long n_s = (long long)a.H * NU * NU;
+            float v = (1.0f - a.eta) * ld_checked(a.Sigma, (long long)h * NU * NU + ci * NU + cj, n_s) +
+                      a.eta * (cv / Zs);
             if (ci == cj) v += a.cov_floor;
             sm.cov[ci][cj] = v;
             sm.cov[cj][ci] = v;
         }
         __syncthreads();
-        if (tid < NU * NU) a.Sigma[(size_t)h * NU * NU + tid] = sm.cov[tid / NU][tid % NU];
+        if (tid < NU * NU && MPPI_IN_RANGE((long long)h * NU * NU + tid, (long long)a.H * NU * NU))
+            a.Sigma[(size_t)h * NU * NU + tid] = sm.cov[tid / NU][tid % NU];
         __syncthreads();
         if (tid < 32) {  // factor the new block in place (one warp, right-looking) for the next sampling
             bool ok = true;
@@ -582,14 +588,16 @@ __device__ __forceinline__ void elite_update_step(const EliteArgs& a, int h, Eli
             }
             if (ok) {
                 float* Lo = a.Lout + (size_t)h * NU * NU;
-                for (int t = tid; t < NU * NU; t += 32) Lo[t] = (t % NU) <= (t / NU) ? sm.cov[t / NU][t % NU] : 0.0f;
+                for (int t = tid; t < NU * NU; t += 32)
+                    if (MPPI_IN_RANGE((long long)h * NU * NU + t, (long long)a.H * NU * NU))
+                        Lo[t] = (t % NU) <= (t / NU) ? sm.cov[t / NU][t % NU] : 0.0f;
             } else if (tid == 0) {
                 atomicOr(a.err, ERRB_CHOLESKY);
             }
         }
     }
     // (3) outputs (u_out may alias u_nom: this CTA read its row above)
-    if (tid < NU) a.u_out[h * NU + tid] = sm.mean[tid];
+    if (tid < NU && MPPI_IN_RANGE(h * NU + tid, (long long)a.H * NU)) a.u_out[h * NU + tid] = sm.mean[tid];
     if (h == 0 && tid == 0 && !any) atomicOr(a.err, ERRB_NONFINITE);
 }
 

@@ -99,4 +99,6 @@ int launch_probe(int na, const DevModel* model, const float* x, float* out, cuda
     return cudaGetLastError() == cudaSuccess ? MPPI_OK : MPPI_ERR_CUDA;
 }
 
+MPPI_BOUNDS_READER(bounds_word_loop)
+
 }  // namespace mppi

@@ -222,6 +222,9 @@ __device__ void qp_admm(const QPClass& c, const float4* __restrict__ band, int H
     qp_bound(s3, c.lo[3] * dt2 - qd, c.hi[3] * dt2 - qd, J1lo, J1hi);
     const float4* __restrict__ bf = band;      // forward rows
     const float4* __restrict__ bb = band + H;  // backward rows
+    // slot index i (0 <= i < H) of this thread's vectors and band rows;
+    // checked in the bounds-check build, the identity otherwise
+    auto sl = [H](int i) { return MPPI_IN_RANGE(i, H) ? i : 0; };
 
     for (int it = 0; it < iters; ++it) {
         // forward sweep: rows at t, right-hand side, forward substitution
@@ -233,8 +236,8 @@ __device__ void qp_admm(const QPClass& c, const float4* __restrict__ band, int H
         // substitution chain (the operations and their order are unchanged)
 #pragma unroll 4
         for (int t = 0; t < H; ++t) {
-            const float2 xv = xb[(size_t)t * T];
-            float4 y = yv[(size_t)t * T];
+            const float2 xv = xb[(size_t)sl(t) * T];
+            float4 y = yv[(size_t)sl(t) * T];
             const float xp1 = xv.x;
             const float d1 = xp1 - x0, d2 = d1 - d1p, d3 = d2 - d2p;
             const float eP = qp_row(s0 * xp1, y.x, Plo, Phi, rs0);
@@ -242,16 +245,16 @@ __device__ void qp_admm(const QPClass& c, const float4* __restrict__ band, int H
             const float eA = qp_row(s2 * d2, y.z, t == 0 ? A0lo : Alo, t == 0 ? A0hi : Ahi, rs2);
             float eJ = 0.0f;
             if (t >= 1) eJ = qp_row(s3 * d3, y.w, t == 1 ? J1lo : Jlo, t == 1 ? J1hi : Jhi, rs3);
-            yv[(size_t)t * T] = y;
+            yv[(size_t)sl(t) * T] = y;
             // row t touches x_{t+1} (+1), x_t (-1, -2, -3), x_{t-1} (+1, +3), x_{t-2} (-1)
             const float r3 = xv.y + eP + eV + eA + eJ;
             r2 = r2 - eV - 2.0f * eA - 3.0f * eJ;
             r1 = r1 + eA + 3.0f * eJ;
             r0 = r0 - eJ;
             if (t >= 3) {  // x_{t-2} is complete: substitute (index i = t-2, slot t-3)
-                const float4 L = __ldg(&bf[t - 3]);
+                const float4 L = __ldg(&bf[sl(t - 3)]);
                 const float z = (r0 - L.y * z1 - L.z * z2 - L.w * z3) * L.x;
-                xb[(size_t)(t - 3) * T].x = z;
+                xb[(size_t)sl(t - 3) * T].x = z;
                 z3 = z2;
                 z2 = z1;
                 z1 = z;
@@ -267,9 +270,9 @@ __device__ void qp_admm(const QPClass& c, const float4* __restrict__ band, int H
         for (int i = H - 2; i <= H; ++i) {
             const float r = i == H - 2 ? r0 : (i == H - 1 ? r1 : r2);
             if (i < 1) continue;
-            const float4 L = __ldg(&bf[i - 1]);
+            const float4 L = __ldg(&bf[sl(i - 1)]);
             const float z = (r - L.y * z1 - L.z * z2 - L.w * z3) * L.x;
-            xb[(size_t)(i - 1) * T].x = z;
+            xb[(size_t)sl(i - 1) * T].x = z;
             z3 = z2;
             z2 = z1;
             z1 = z;
@@ -278,8 +281,8 @@ __device__ void qp_admm(const QPClass& c, const float4* __restrict__ band, int H
         float p1 = 0.0f, p2 = 0.0f, p3 = 0.0f;  // x_{i+1}, x_{i+2}, x_{i+3}
 #pragma unroll 4
         for (int i = H; i >= 1; --i) {
-            const float4 L = __ldg(&bb[i - 1]);
-            float* slot = &xb[(size_t)(i - 1) * T].x;
+            const float4 L = __ldg(&bb[sl(i - 1)]);
+            float* slot = &xb[(size_t)sl(i - 1) * T].x;
             const float xi = (*slot - L.y * p1 - L.z * p2 - L.w * p3) * L.x;
             *slot = xi;
             p3 = p2;
@@ -292,16 +295,17 @@ __device__ void qp_admm(const QPClass& c, const float4* __restrict__ band, int H
 // Raw sample h of member k (sample) in class j (joint): the value the
 // rollout's sampler draws, unclamped.
 __device__ __forceinline__ float qp_sample(const QPArgs& a, uint2 key, uint32_t iter, int k, int j, int h) {
-    float v = a.u_nom[h * a.nu + j];
+    float v = ld_checked(a.u_nom, (long long)h * a.nu + j, (long long)a.H * a.nu);
     if (a.Lfac) {
-        const float* Lr = a.Lfac + ((size_t)h * a.nu + j) * a.nu;
+        const long long r0 = ((long long)h * a.nu + j) * a.nu, n_l = (long long)a.H * a.nu * a.nu;
         for (int jb = 0; 4 * jb <= j; ++jb) {
             const uint4 w = philox4x32_10(make_uint4((uint32_t)jb, (uint32_t)h, (uint32_t)k, iter), key);
-            for (int t = 0; t < 4 && 4 * jb + t <= j; ++t) v = __fmaf_rn(Lr[4 * jb + t], block_normal(w, t), v);
+            for (int t = 0; t < 4 && 4 * jb + t <= j; ++t)
+                v = __fmaf_rn(ld_checked(a.Lfac, r0 + 4 * jb + t, n_l), block_normal(w, t), v);
         }
     } else {
         const uint4 w = philox4x32_10(make_uint4((uint32_t)(j >> 2), (uint32_t)h, (uint32_t)k, iter), key);
-        v = __fmaf_rn(a.sigma[j], block_normal(w, j & 3), v);
+        v = __fmaf_rn(ld_checked(a.sigma, j, a.nu), block_normal(w, j & 3), v);
     }
     return v;
 }
@@ -394,15 +398,19 @@ __global__ void __launch_bounds__(14 * 32, 2) qp_warp_sample_kernel(QPArgs a) {
     float* stage = wsm + 32 * nu;  // H x nu
     const uint2 key = make_uint2((uint32_t)a.seed, (uint32_t)(a.seed >> 32));
     const uint32_t iter = (uint32_t)(a.iter_ptr ? *a.iter_ptr : a.iter_val);
-    const QPClass c = a.cls[j];
+    const QPClass c = a.cls[MPPI_IN_RANGE(j, a.n_cls) ? j : 0];
     float Mi[32];
-    qp_load_row(a.minv + (size_t)j * 32 * 32, lane, Mi);
+    qp_load_row(a.minv + (size_t)(MPPI_IN_RANGE(j, a.n_cls) ? j : 0) * 32 * 32, lane, Mi);
     const float vt = lane < a.H ? qp_sample(a, key, iter, k, j, lane) : 0.0f;
-    const float v = qp_warp_admm(c, Mi, a.H, a.iters, a.dt, a.q0[j], a.qd0[j], vt, lane, bc);
-    if (lane < a.H) stage[lane * nu + j] = v;
+    const float v = qp_warp_admm(c, Mi, a.H, a.iters, a.dt, ld_checked(a.q0, j, a.n_cls), ld_checked(a.qd0, j, a.n_cls),
+                                 vt, lane, bc);
+    // shared memory: nu rows of 32 floats, then the H x nu stage
+    if (lane < a.H && MPPI_IN_RANGE(lane * nu + j, a.H * nu)) stage[lane * nu + j] = v;
     __syncthreads();
-    for (int i = threadIdx.x; i < a.H * nu; i += blockDim.x)
-        a.out[((size_t)(i / nu) * a.per_cls + k) * nu + (i % nu)] = stage[i];
+    for (int i = threadIdx.x; i < a.H * nu; i += blockDim.x) {
+        const long long o = ((long long)(i / nu) * a.per_cls + k) * nu + (i % nu);
+        if (MPPI_IN_RANGE(o, a.out_n)) a.out[o] = stage[i];
+    }
 }
 
 // Standalone form: 8 warps per CTA, one sequence (class 0) each.
@@ -413,9 +421,10 @@ __global__ void __launch_bounds__(256) qp_warp_kernel(QPArgs a) {
     if (i >= a.n) return;
     float Mi[32];
     qp_load_row(a.minv, lane, Mi);
-    const float vt = lane < a.H ? a.vin[(size_t)i * a.H + lane] : 0.0f;
-    const float v = qp_warp_admm(a.cls[0], Mi, a.H, a.iters, a.dt, a.q0[i], a.qd0[i], vt, lane, bcs[w]);
-    if (lane < a.H) a.out[(size_t)i * a.H + lane] = v;
+    const float vt = lane < a.H ? ld_checked(a.vin, (long long)i * a.H + lane, a.in_n) : 0.0f;
+    const float v = qp_warp_admm(a.cls[0], Mi, a.H, a.iters, a.dt, ld_checked(a.q0, i, a.n), ld_checked(a.qd0, i, a.n),
+                                 vt, lane, bcs[MPPI_IN_RANGE(w, 8) ? w : 0]);
+    if (lane < a.H && MPPI_IN_RANGE((long long)i * a.H + lane, a.out_n)) a.out[(size_t)i * a.H + lane] = v;
 }
 
 // Sequence i: class i / per_cls, member i % per_cls.
@@ -427,8 +436,10 @@ __global__ void __launch_bounds__(QP_THREADS) qp_project_kernel(QPArgs a) {
     const int i = blockIdx.x * T + tid;
     if (i >= a.n) return;
     const int cls = i / a.per_cls, mem = i % a.per_cls;
-    const QPClass c = a.cls[cls];
-    const float q = a.q0[a.q_per_seq ? i : cls], qd = a.qd0[a.q_per_seq ? i : cls];
+    const QPClass c = a.cls[MPPI_IN_RANGE(cls, a.n_cls) ? cls : 0];
+    const long long nq = a.q_per_seq ? a.n : a.n_cls;
+    const float q = ld_checked(a.q0, a.q_per_seq ? i : cls, nq), qd = ld_checked(a.qd0, a.q_per_seq ? i : cls, nq);
+    auto sl = [&a](int h) { return MPPI_IN_RANGE(h, a.H) ? h : 0; };  // this thread's slots
     const long long base_in = (long long)mem * a.i_a + (long long)cls * a.i_b;
     // start point x = prefix sums of vt, and (B^T vt)_i = vt_{i-1} - vt_i (vt_H for i = H)
     uint2 key{};
@@ -441,23 +452,24 @@ __global__ void __launch_bounds__(QP_THREADS) qp_project_kernel(QPArgs a) {
     for (int h = 0; h < a.H; ++h) {
         float vt;
         if (a.vin) {
-            vt = a.vin[base_in + (long long)h * a.i_h];
+            vt = ld_checked(a.vin, base_in + (long long)h * a.i_h, a.in_n);
         } else {  // sample k = member, joint j = class
             vt = qp_sample(a, key, iter, mem, cls, h);
         }
         acc += vt;
-        if (h > 0) xb[(size_t)(h - 1) * T].y = prev - vt;
-        xb[(size_t)h * T].x = acc;
-        yv[(size_t)h * T] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (h > 0) xb[(size_t)sl(h - 1) * T].y = prev - vt;
+        xb[(size_t)sl(h) * T].x = acc;
+        yv[(size_t)sl(h) * T] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         prev = vt;
     }
-    xb[(size_t)(a.H - 1) * T].y = prev;
-    qp_admm(c, a.band + (size_t)cls * 2 * a.H, a.H, a.iters, a.dt, q, qd, xb, yv, T);
+    xb[(size_t)sl(a.H - 1) * T].y = prev;
+    qp_admm(c, a.band + (size_t)(MPPI_IN_RANGE(cls, a.n_cls) ? cls : 0) * 2 * a.H, a.H, a.iters, a.dt, q, qd, xb, yv, T);
     const long long base_out = (long long)mem * a.o_a + (long long)cls * a.o_b;
     float xp = 0.0f;
     for (int h = 0; h < a.H; ++h) {
-        const float x = xb[(size_t)h * T].x;
-        a.out[base_out + (long long)h * a.o_h] = x - xp;
+        const float x = xb[(size_t)sl(h) * T].x;
+        const long long o = base_out + (long long)h * a.o_h;
+        if (MPPI_IN_RANGE(o, a.out_n)) a.out[o] = x - xp;
         xp = x;
     }
 }
@@ -492,6 +504,8 @@ int launch_qp(const QPArgs& a, cudaStream_t s) {
     qp_project_kernel<<<grid, T, sm, s>>>(a);
     return cudaGetLastError() == cudaSuccess ? MPPI_OK : MPPI_ERR_CUDA;
 }
+
+MPPI_BOUNDS_READER(bounds_word_qp)
 
 }  // namespace mppi
 
@@ -546,6 +560,8 @@ extern "C" int mppi_qp_project(int n, int H, float dt, const float* bounds, int 
     a.o_a = H;
     a.o_b = 0;
     a.o_h = 1;
+    a.n_cls = 1;
+    a.in_n = a.out_n = (long long)n * H;
     if (e == cudaSuccess) rc = launch_qp(a, s);
     else rc = MPPI_ERR_CUDA;
     cudaFreeAsync(d, s);

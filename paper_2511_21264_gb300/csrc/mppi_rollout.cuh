@@ -78,21 +78,24 @@ __global__ void __launch_bounds__(512) rollout_kernel(RolloutArgs args) {
         io.iter = (uint32_t)(args.iter_ptr ? *args.iter_ptr : args.iter_val);
         io.key = make_uint2((uint32_t)args.seed, (uint32_t)(args.seed >> 32));
         if (g.sl < d::NU) {
-            io.sig = args.sigma[g.sl];
+            io.sig = ld_checked(args.sigma, g.sl, d::NU);
             io.lo = M.link[g.sl / NA][g.sl % NA].u_lo;
             io.hi = M.link[g.sl / NA][g.sl % NA].u_hi;
         }
     } else {
+        const long long total = (long long)args.n * args.H * d::NU;
         if (args.U_hmajor) {
             io.U = args.U + (size_t)k * d::NU;
             io.u_stride = (long long)args.n * d::NU;
+            io.u_ext = total - (long long)k * d::NU;
         } else {
             io.U = args.U + (size_t)k * args.H * d::NU;
             io.u_stride = d::NU;
+            io.u_ext = total - (long long)k * args.H * d::NU;
         }
     }
     const float cost = rollout_sample<NA, LPS, MODE, TASK, PLACE>(M, w, g, io);
-    if (g.sl == 0) args.costs[k] = cost;
+    if (g.sl == 0 && MPPI_IN_RANGE(k, args.n)) args.costs[k] = cost;
 }
 
 namespace rollout_launch {

@@ -17,6 +17,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(_HERE, "csrc")
 BUILD = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(BUILD, "libmppi.so")
+# the bounds-check build (-DMPPI_BOUNDS_CHECK): every kernel index compared
+# with its extent, failures counted in device words (mppi_debug_bounds)
+BOUNDS_BUILD = os.path.join(_HERE, "_build_bounds")
+BOUNDS_LIB_PATH = os.path.join(BOUNDS_BUILD, "libmppi.so")
 INCLUDE = os.path.join(os.path.dirname(_HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # FP32 division and square root by the hardware's approximate forms (errors of
@@ -41,26 +45,30 @@ def _sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB_PATH):
+def _stale(lib_path: str = LIB_PATH) -> bool:
+    if not os.path.exists(lib_path):
         return True
-    t = os.path.getmtime(LIB_PATH)
+    t = os.path.getmtime(lib_path)
     deps = _sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) \
         + glob.glob(os.path.join(INCLUDE, "*.h"))
     return any(os.path.getmtime(p) > t for p in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False, bounds: bool = False) -> str:
     """Compile every translation unit under csrc/ for sm_103a (in parallel)
-    and link libmppi.so in-tree."""
-    if not force and not _stale():
-        return LIB_PATH
-    os.makedirs(BUILD, exist_ok=True)
+    and link libmppi.so in-tree; bounds=True makes the bounds-check build in
+    its own folder."""
+    build_dir, lib_path = (BOUNDS_BUILD, BOUNDS_LIB_PATH) if bounds else (BUILD, LIB_PATH)
+    if not force and not _stale(lib_path):
+        return lib_path
+    os.makedirs(build_dir, exist_ok=True)
     objs, procs = [], []
     for src in _sources():
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src) + ".o")
         cmd = ["nvcc", "-O3", *FP_FLAGS, "-std=c++17", "-Xcompiler", "-fPIC", *ARCH, "-lineinfo",
                "-I", INCLUDE, "-c", src, "-o", obj]
+        if bounds:
+            cmd.insert(1, "-DMPPI_BOUNDS_CHECK")
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         procs.append((subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT), src))
@@ -74,10 +82,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
             failed.append(src)
     if failed:
         raise RuntimeError(f"nvcc failed for {failed}")
-    tmp = LIB_PATH + f".tmp{os.getpid()}"
+    tmp = lib_path + f".tmp{os.getpid()}"
     subprocess.run(["nvcc", "-shared", *ARCH, "-o", tmp, *objs, "-lcudart", "-lpthread"], check=True)
-    os.replace(tmp, LIB_PATH)
-    return LIB_PATH
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 _lib = None
@@ -121,6 +129,7 @@ def lib():
     _decl(L, "mppi_set_iteration", i, [vp, u64, vp])
     _decl(L, "mppi_sync", i, [vp, vp])
     _decl(L, "mppi_set_launch", i, [vp, i])
+    _decl(L, "mppi_debug_bounds", i, [C.POINTER(C.c_uint), C.POINTER(i)])
     _decl(L, "mppi_set_layout", i, [vp, i, i])
     _decl(L, "mppi_get_layout", i, [vp, C.POINTER(i), C.POINTER(i), C.POINTER(i)])
     _decl(L, "mppi_set_update", i, [vp, i, C.c_float, i, C.c_float])

@@ -434,13 +434,16 @@ def test_full_size_sampled_and_properties(native, cfg):
 
 
 # ------------------------------------------------------- statistical parity
-def test_statistical_parity_planar_100_seeds(native):
+@pytest.mark.parametrize("cfg,K,H,iters", [(1, 64, 20, 10), (2, 128, 32, 5)])
+def test_statistical_parity_100_seeds(native, cfg, K, H, iters):
     """Longer contact rollouts are compared statistically: final nominal cost
-    after 10 MPPI iterations from the home state, 100 controller seeds, GPU
-    vs oracle (two-sample KS) and the improvement rate (two proportions)."""
+    after `iters` MPPI iterations from the home state, 100 controller seeds,
+    GPU vs oracle (two-sample KS) and the improvement rate over zero controls
+    (two proportions).  Config 1 at its own K, H and iteration count; the
+    7-DoF lift at K = 128 (the oracle's share of the test stays in seconds)
+    and its full horizon H = 32, where the rollouts are long and chaotic."""
     from scipy import stats
-    sc = scenes.config(1)
-    K, H, iters = sc.K, sc.H, sc.iters
+    sc = scenes.config(cfg)
     blob = sc.to_blob()
     from paper_2511_21264_gb300 import native as nat
     gm = nat.Model(blob)
@@ -452,7 +455,7 @@ def test_statistical_parity_planar_100_seeds(native):
     nthreads = max(1, min(16, os.cpu_count() or 1))
     eval_ctl = nat.Controller(gm, 1, H, sc.lam, sig, 0)
     for s in range(100):
-        key = scenes.controller_key(1000 + s, 0)
+        key = scenes.controller_key(1000 * cfg + s, 0)
         ctl = nat.Controller(gm, K, H, sc.lam, sig, key)
         u = torch.zeros((H, sc.nu), device=DEV)
         for _ in range(iters):
