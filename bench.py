@@ -547,7 +547,7 @@ def run_serve(args):
     M = 10
 
     def serve(max_active, rate, seconds):
-        srv = native.Server(256 << 20, max_active, M)
+        srv = native.Server(256 << 20, max_active, M, lanes_per_sample=args.lps, size_classes=args.serve_classes)
         for m, sc in zip(models, pool):
             srv.add_scene(m, sc.K, sc.H, sc.lam, sc.sigma_vec(), scenes.controller_key(sc.seed, rank))
         srv.start()
@@ -568,12 +568,15 @@ def run_serve(args):
             b = serve(64, r, args.serve_seconds)
             entry = {"batched": {k: b[k] for k in ("p50_ms", "p99_ms", "mean_ms", "sample_steps_per_s", "completed",
                                                    "mean_active", "admission_waits", "wall_s")}}
-            # the one-request-at-a-time server on the same kind of trace: a
-            # shorter window above 200 req/s, where it saturates and its
-            # backlog drains after the window (throughput is then its capacity)
-            p = serve(1, r, min(args.serve_seconds, 5.0 if r <= 200 else 2.0))
+            # the one-request-at-a-time server on the same kind of trace and
+            # window; above 200 req/s, where it saturates and its backlog
+            # would drain long after the window, a 5 s window (its throughput
+            # is then its capacity)
+            p = serve(1, r, args.serve_seconds if r <= 200 else min(args.serve_seconds, 5.0))
             entry["one_at_a_time"] = {k: p[k] for k in ("p50_ms", "p99_ms", "mean_ms", "sample_steps_per_s",
                                                         "completed", "wall_s")}
+            entry["p99_one_at_a_time_over_batched"] = p["p99_ms"] / max(b["p99_ms"], 1e-9)
+            entry["throughput_batched_over_one_at_a_time"] = b["sample_steps_per_s"] / max(p["sample_steps_per_s"], 1e-9)
             out[f"{r:g}_req_per_s"] = entry
     if rank != 0:
         return 0
@@ -585,7 +588,8 @@ def run_serve(args):
         "data": "synthetic",
         "config": {"workload": "256 scenes (7-DoF arms, 0-16 boxes, K 512..4096, H 16..64), M=10 iterations per "
                                "request, Poisson arrivals", "rates_req_per_s": rates,
-                   "arrival_window_s": args.serve_seconds, "max_active": 64, "budget_bytes": 256 << 20},
+                   "arrival_window_s": args.serve_seconds, "max_active": 64, "budget_bytes": 256 << 20,
+                   "size_classes": args.serve_classes or 6, "lanes_per_sample": args.lps or 16},
         "latency": out,
         "clocks": clk.summary(),
     }
@@ -686,7 +690,9 @@ def main(argv=None):
     ap.add_argument("--qp", type=int, default=0, help="QP smoothing projection (Eq. 5) iterations (0 = off)")
     ap.add_argument("--task", type=int, choices=(0, 1), default=None,
                     help="the paper's ball-task cost suite in the given phase (0 pick, 1 move)")
-    ap.add_argument("--serve-seconds", type=float, default=10.0, help="arrival window per rate (serve)")
+    ap.add_argument("--serve-seconds", type=float, default=60.0, help="arrival window per rate (serve)")
+    ap.add_argument("--serve-classes", type=int, default=0,
+                    help="serve: size classes of the batched server (0 = 6; 1 = one batch of all requests)")
     ap.add_argument("--serve-rates", type=str, default="50,200,1000")
     ap.add_argument("--spc", type=int, default=0, help="samples per CTA (0 = library default)")
     ap.add_argument("--lps", type=int, default=0, help="lanes per sample: 32, 16 (0 = library default)")

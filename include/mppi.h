@@ -419,21 +419,29 @@ int mppi_tune_lookup(const char *key, int *samples_per_cta, int *order, int *lan
  * simulator state, warm-started nominal sequence and Philox counter on the
  * device (receding horizon with warm start, paper §III-A).  A request asks
  * for one replan of one scene: `iters_per_request` MPPI iterations (Alg. 1
- * with M = iters_per_request).  A scheduler thread works at iteration
- * boundaries: it admits waiting requests while there are free slots
- * (max_active), the scene has no request in flight and the request's
- * workspace (K sample costs) fits the device-memory budget; runs one
- * batched iteration of every active request; and retires those that
- * reached M iterations -- the plan is copied out, the scene's state
- * advances one simulator step under u_nom[0] and u_nom shifts by one step
- * (last step kept).  Latency = retirement time - submission time.
- * max_active = 1 serves one request at a time (no batching). */
+ * with M = iters_per_request).  Waiting requests are admitted while there
+ * are free slots (max_active), the scene has no request in flight and the
+ * request's workspace (K sample costs) fits the device-memory budget.
+ * Admitted requests join the size class of their work per iteration; each
+ * class runs on its own stream, one batched iteration of all its requests
+ * at a time, and takes newly admitted requests at its next iteration
+ * boundary, so classes overlap on the device and short requests do not wait
+ * for long ones.  A request that reached M iterations retires: the plan is
+ * copied out, the scene's state advances one simulator step under
+ * u_nom[0] and u_nom shifts by one step (last step kept).  Latency =
+ * retirement time - submission time.  max_active = 1 serves one request at
+ * a time (no batching). */
 typedef struct mppi_server mppi_server;
 typedef struct {
     size_t mem_budget_bytes; /* device arena for active requests' workspaces */
     int max_active;          /* 1..4096 */
     int iters_per_request;   /* M >= 1 */
     int samples_per_cta;     /* launch shape, 0 = default */
+    int lanes_per_sample;    /* rollout layout: 32, 16 (0 = 16 for 7-link
+                                arms, 32 for 3-link arms) */
+    int size_classes;        /* 1..8 streams of requests grouped by work per
+                                iteration (K x H in powers of two); 1 = one
+                                batch of every active request; 0 = 6 */
 } mppi_server_config;
 typedef struct {
     long long completed, iterations, waiting, active, admission_waits;

@@ -270,7 +270,7 @@ EPISODE_OUTCOMES = {0: "success", 1: "timeout", 2: "collision", 3: "dropped"}
 
 class ServerConfig(C.Structure):
     _fields_ = [("mem_budget_bytes", C.c_size_t), ("max_active", C.c_int), ("iters_per_request", C.c_int),
-                ("samples_per_cta", C.c_int)]
+                ("samples_per_cta", C.c_int), ("lanes_per_sample", C.c_int), ("size_classes", C.c_int)]
 
 
 class SrvStats(C.Structure):
@@ -281,8 +281,10 @@ class SrvStats(C.Structure):
 class Server:
     """Replan server with continuous batching (srv_*)."""
 
-    def __init__(self, mem_budget_bytes: int, max_active: int, iters_per_request: int, samples_per_cta: int = 0):
-        cfg = ServerConfig(int(mem_budget_bytes), int(max_active), int(iters_per_request), int(samples_per_cta))
+    def __init__(self, mem_budget_bytes: int, max_active: int, iters_per_request: int, samples_per_cta: int = 0,
+                 lanes_per_sample: int = 0, size_classes: int = 0):
+        cfg = ServerConfig(int(mem_budget_bytes), int(max_active), int(iters_per_request), int(samples_per_cta),
+                           int(lanes_per_sample), int(size_classes))
         h = C.c_void_p()
         _check(lib().srv_create(C.byref(cfg), C.byref(h)), "srv_create")
         self._h = h

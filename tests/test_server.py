@@ -42,11 +42,12 @@ def test_result_is_the_same_alone_and_in_the_mix():
     st, done, u_alone, lat = s1.poll(s1.submit(sid), sid, wait_ms=60000)
     assert done and st == 0 and lat > 0
     s1.stop()
-    # in a mix of 20 scenes of different K and H, submitted at once
+    # in a mix of 20 scenes of different K and H, submitted at once: three
+    # size classes, whose iterations overlap on their own streams
     s2 = native.Server(1 << 24, 64, M)
     models, ids = [], []
     for i in range(20):
-        sc = target if i == 3 else _scene(i, K=[64, 128, 256, 512][i % 4], H=[8, 16, 24][i % 3])
+        sc = target if i == 3 else _scene(i, K=[64, 128, 256, 512, 2048][i % 5], H=[8, 16, 24][i % 3])
         m = tm if i == 3 else native.Model(sc.to_blob())
         models.append(m)
         ids.append(s2.add_scene(m, sc.K, sc.H, sc.lam, sc.sigma_vec(), key if i == 3 else scenes.controller_key(i, 0)))
@@ -57,6 +58,18 @@ def test_result_is_the_same_alone_and_in_the_mix():
     np.testing.assert_array_equal(outs[3][2], u_alone)
     assert s2.stats()["mean_active"] > 1.0
     s2.stop()
+    # the same mix in one batch (a single size class)
+    s3 = native.Server(1 << 24, 64, M, size_classes=1)
+    ids3 = []
+    for i in range(20):
+        sc = target if i == 3 else _scene(i, K=[64, 128, 256, 512, 2048][i % 5], H=[8, 16, 24][i % 3])
+        ids3.append(s3.add_scene(models[i], sc.K, sc.H, sc.lam, sc.sigma_vec(),
+                                 key if i == 3 else scenes.controller_key(i, 0)))
+    s3.start()
+    outs3 = [s3.poll(t, i, wait_ms=60000) for t, i in zip([s3.submit(i) for i in ids3], ids3)]
+    s3.stop()
+    for a, b in zip(outs, outs3):
+        np.testing.assert_array_equal(a[2], b[2])
     # and both equal M iterations of the handle path
     ctl = native.Controller(tm, target.K, target.H, target.lam, target.sigma_vec(), key)
     x = torch.tensor(tm.home(), device="cuda")
