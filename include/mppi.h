@@ -407,6 +407,21 @@ int mppi_batch_get_layout(const mppi_batch *b, int *lanes_per_sample, int *place
  * iteration. */
 int mppi_batch_autotune(mppi_batch *b, const float *const *states, float *const *u, int reps, void *stream,
                         float *best_ms);
+/* The paper's full Eq. 8 for instance i (i = -1: every instance), as
+ * mppi_set_update does for one controller: elite set of n_elite samples
+ * (0 = all), learning rate eta, the covariance blocks updated (and sampled
+ * from) when update_cov, diagonal floor cov_floor.  Results stay bitwise
+ * those of a single controller with the same settings.  Errors as
+ * mppi_set_update. */
+int mppi_batch_set_update(mppi_batch *b, int i, int n_elite, float eta, int update_cov, float cov_floor);
+/* The QP smoothing projection (Eq. 5) of every instance's samples before its
+ * rollouts, as mppi_set_projection: bounds = n x nu x 8 floats (host; per
+ * instance and joint lo/hi of position, velocity, acceleration, jerk), the
+ * ADMM iterations (0 turns the projection off for the batch), rho and the
+ * row scales (NULL = defaults).  Allocates each instance's H x K x nu sample
+ * buffer.  MPPI_ERR_INVALID_ARG for bad bounds or instances of different
+ * time steps, MPPI_ERR_UNSUPPORTED for H above MPPI_QP_MAX_H. */
+int mppi_batch_set_projection(mppi_batch *b, const float *bounds, int iters, float rho, const float *scales);
 /* Tuning table: text file of "key spc order lps placement ms" lines at
  * $MPPI_TUNE_FILE (default ~/.cache/mppi_tune.txt); the last entry of a
  * key wins.  Host only; no GPU needed. */

@@ -54,85 +54,13 @@ __global__ void noise_kernel(NoiseArgs a) {
     }
 }
 
-// Elite threshold: bitonic sort of (cost, index) keys in shared memory (one
-// CTA, P = power of two >= K); sel = [key of the n_e-th elite, lowest key,
-// finite count].
+// Elite threshold of one controller (one CTA of 1024 threads; the sort in
+// mppi_kernels.cuh).
 __global__ void __launch_bounds__(1024) elite_select_kernel(const float* costs, int K, int P, int n_elite,
                                                             unsigned long long* sel, int* eidx) {
     extern __shared__ unsigned long long keys[];
     __shared__ int nfin;
-    if (P <= 1024) {
-        // one key per thread (padding keys sort last): the same bitonic
-        // network in registers, partners by shuffles below stride 32 and
-        // through a double-buffered shared array above
-        const int t = threadIdx.x;
-        unsigned long long x = ~0ull;
-        bool fin = false;
-        if (t < K) {
-            const float c = ld_checked(costs, t, K);
-            x = cost_key(c, t);
-            fin = isfinite(c);
-        }
-        const int nf = __syncthreads_count(fin);
-        int buf = 0;
-        for (int size = 2; size <= 1024; size <<= 1)
-            for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                unsigned long long y;
-                if (stride >= 32) {
-                    if (MPPI_IN_RANGE(buf * 1024 + t, 2048)) keys[buf * 1024 + t] = x;
-                    __syncthreads();
-                    y = MPPI_IN_RANGE(buf * 1024 + (t ^ stride), 2048) ? keys[buf * 1024 + (t ^ stride)] : x;
-                    buf ^= 1;
-                } else {
-                    y = __shfl_xor_sync(0xffffffffu, x, stride);
-                }
-                const bool asc = (t & size) == 0, lower = (t & stride) == 0;
-                x = (lower == asc) ? (x < y ? x : y) : (x < y ? y : x);
-            }
-        const int ne = nf == 0 ? 0 : (n_elite < nf ? n_elite : nf);
-        if (t < ne && MPPI_IN_RANGE(t, K)) eidx[t] = (int)(x & 0xFFFFFFFFull);
-        if (t == 0) {
-            sel[1] = x;
-            sel[2] = (unsigned long long)nf;
-            if (ne == 0) sel[0] = 0ull;
-        }
-        if (ne > 0 && t == ne - 1) sel[0] = x;
-        return;
-    }
-    if (threadIdx.x == 0) nfin = 0;
-    __syncthreads();
-    int mine = 0;
-    for (int i = threadIdx.x; i < P; i += blockDim.x) {
-        const float c = i < K ? ld_checked(costs, i, K) : 0.0f;
-        if (MPPI_IN_RANGE(i, P)) keys[i] = i < K ? cost_key(c, i) : ~0ull;
-        mine += (i < K && isfinite(c)) ? 1 : 0;
-    }
-    atomicAdd(&nfin, mine);
-    __syncthreads();
-    for (int size = 2; size <= P; size <<= 1)
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int i = threadIdx.x; i < P; i += blockDim.x) {
-                const int j = i ^ stride;
-                if (j > i && MPPI_IN_RANGE(j, P)) {
-                    const bool asc = (i & size) == 0;
-                    const unsigned long long x = keys[i], y = keys[j];
-                    if ((x > y) == asc) {
-                        keys[i] = y;
-                        keys[j] = x;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    const int nf = nfin;
-    const int ne = nf == 0 ? 0 : (n_elite < nf ? n_elite : nf);
-    for (int e = threadIdx.x; e < ne; e += blockDim.x)
-        if (MPPI_IN_RANGE(e, K)) eidx[e] = (int)(keys[e] & 0xFFFFFFFFull);
-    if (threadIdx.x == 0) {
-        sel[0] = ne > 0 ? keys[ne - 1] : 0ull;
-        sel[1] = keys[0];
-        sel[2] = (unsigned long long)nf;
-    }
+    elite_select_block(costs, K, P, n_elite, sel, eidx, keys, nfin);
 }
 
 template <int NU>
@@ -377,6 +305,7 @@ struct mppi_ctx {
 
 namespace mppi {
 const DevModel* model_device(const mppi_model* m) { return m ? m->dev : nullptr; }
+float model_dt(const mppi_model* m) { return m->host.dt; }
 void model_bounds(const mppi_model* m, int j, float* lo, float* hi) {
     const int na = m->info.na;
     *lo = m->host.link[j / na][j % na].u_lo;
@@ -788,15 +717,54 @@ static void drop_graph(mppi_ctx* c) {
 // joint, hence a band factor); output U[h][k][j] (h-major sample buffer).
 static int launch_projection(mppi_ctx* c, const float* state, const float* u_nom, cudaStream_t s) {
     const int na = c->m->info.na, nu = 2 * na, nq = 2 * na + 7;
+    const QPArgs q = qp_controller_args(nu, nq, c->K, c->H, c->qp_iters, c->qp_dt, c->d_qp, state, u_nom, c->d_sigma,
+                                        c->cov_sampling ? c->d_L : nullptr, c->seed, c->d_iter, c->d_U);
+    return launch_qp(q, s);
+}
+
+}  // extern "C"
+
+namespace mppi {
+// Per-joint projection data of one controller: nu class records, then per
+// joint the dense inverse (H <= 32, warp kernel) or the band factor rows.
+int qp_build(int nu, int H, const float* bounds, float rho, const float* scales, std::vector<unsigned char>& host) {
+    static const float kDefault[4] = {MPPI_QP_SCALE_POSITION, MPPI_QP_SCALE_VELOCITY, MPPI_QP_SCALE_ACCELERATION,
+                                      MPPI_QP_SCALE_JERK};
+    const float* sc = scales ? scales : kDefault;
+    for (int j = 0; j < nu; ++j) {
+        const int rc = qp_validate(bounds + 8 * j, sc, rho);
+        if (rc != MPPI_OK) return rc;
+    }
+    if (H > MPPI_QP_MAX_H) return MPPI_ERR_UNSUPPORTED;
+    const bool warp = H <= QP_WARP_MAX_H;
+    const size_t per = warp ? 32 * 32 * sizeof(float) : 2 * (size_t)H * sizeof(float4);
+    host.assign((size_t)nu * sizeof(QPClass) + (size_t)nu * per, 0);
+    QPClass* cls = reinterpret_cast<QPClass*>(host.data());
+    unsigned char* fac = host.data() + (size_t)nu * sizeof(QPClass);
+    for (int j = 0; j < nu; ++j) {
+        qp_make_class(bounds + 8 * j, sc, rho, &cls[j]);
+        const double scd[4] = {cls[j].s[0], cls[j].s[1], cls[j].s[2], cls[j].s[3]};
+        const int rc = warp ? qp_dense_inverse(H, rho, scd, reinterpret_cast<float*>(fac + j * per))
+                            : qp_band_factor(H, rho, scd, reinterpret_cast<float4*>(fac + j * per));
+        if (rc != MPPI_OK) return rc;
+    }
+    return MPPI_OK;
+}
+
+// Projection of the K x nu sampled sequences of one controller into its
+// h-major sample buffer U (Eq. 5).
+QPArgs qp_controller_args(int nu, int nq, int K, int H, int iters, float dt, const void* d_qp, const float* state,
+                          const float* u_nom, const float* sigma, const float* Lfac, uint64_t seed,
+                          const unsigned long long* iter_ptr, float* U) {
     QPArgs q{};
-    q.n = c->K * nu;
-    q.H = c->H;
-    q.iters = c->qp_iters;
-    q.per_cls = c->K;
-    q.dt = c->qp_dt;
-    q.cls = static_cast<const QPClass*>(c->d_qp);
-    const unsigned char* fac = static_cast<unsigned char*>(c->d_qp) + (size_t)nu * sizeof(QPClass);
-    if (c->H <= QP_WARP_MAX_H) q.minv = reinterpret_cast<const float*>(fac);
+    q.n = K * nu;
+    q.H = H;
+    q.iters = iters;
+    q.per_cls = K;
+    q.dt = dt;
+    q.cls = static_cast<const QPClass*>(d_qp);
+    const unsigned char* fac = static_cast<const unsigned char*>(d_qp) + (size_t)nu * sizeof(QPClass);
+    if (H <= QP_WARP_MAX_H) q.minv = reinterpret_cast<const float*>(fac);
     else q.band = reinterpret_cast<const float4*>(fac);
     q.q0 = state;
     q.qd0 = state + nq;
@@ -804,23 +772,24 @@ static int launch_projection(mppi_ctx* c, const float* state, const float* u_nom
     q.vin = nullptr;
     q.nu = nu;
     q.u_nom = u_nom;
-    q.sigma = c->d_sigma;
-    q.Lfac = c->cov_sampling ? c->d_L : nullptr;
-    q.seed = c->seed;
-    q.iter_ptr = c->d_iter;
-    q.out = c->d_U;
-    q.o_a = nu;                        // member k
-    q.o_b = 1;                         // class j
-    q.o_h = (long long)c->K * nu;      // step h
+    q.sigma = sigma;
+    q.Lfac = Lfac;
+    q.seed = seed;
+    q.iter_ptr = iter_ptr;
+    q.out = U;
+    q.o_a = nu;                  // member k
+    q.o_b = 1;                   // class j
+    q.o_h = (long long)K * nu;   // step h
     q.n_cls = nu;
     q.in_n = 0;
-    q.out_n = (long long)c->H * c->K * nu;
-    return launch_qp(q, s);
+    q.out_n = (long long)H * K * nu;
+    return q;
 }
+}  // namespace mppi
+
+extern "C" {
 
 int mppi_set_projection(mppi_ctx* c, const float* bounds, int iters, float rho, const float* scales) {
-    static const float kDefault[4] = {MPPI_QP_SCALE_POSITION, MPPI_QP_SCALE_VELOCITY, MPPI_QP_SCALE_ACCELERATION,
-                                      MPPI_QP_SCALE_JERK};
     if (!c || iters < 0) return MPPI_ERR_INVALID_ARG;
     if (iters == 0) {
         if (c->qp_iters) drop_graph(c);
@@ -828,28 +797,13 @@ int mppi_set_projection(mppi_ctx* c, const float* bounds, int iters, float rho, 
         return MPPI_OK;
     }
     if (!bounds) return MPPI_ERR_INVALID_ARG;
-    const float* sc = scales ? scales : kDefault;
     const int nu = 2 * c->m->info.na;
-    for (int j = 0; j < nu; ++j) {
-        const int rc = qp_validate(bounds + 8 * j, sc, rho);
-        if (rc != MPPI_OK) return rc;
-    }
-    if (c->H > MPPI_QP_MAX_H || !c->d_U) return MPPI_ERR_UNSUPPORTED;
+    std::vector<unsigned char> host;
+    const int brc = qp_build(nu, c->H, bounds, rho, scales, host);
+    if (brc != MPPI_OK) return brc;
+    if (!c->d_U) return MPPI_ERR_UNSUPPORTED;
     const float dt = c->m->host.dt;
-    // per joint: the dense inverse (H <= 32, warp kernel) or band factor rows
-    const bool warp = c->H <= QP_WARP_MAX_H;
-    const size_t per = warp ? 32 * 32 * sizeof(float) : 2 * (size_t)c->H * sizeof(float4);
-    const size_t bytes = (size_t)nu * sizeof(QPClass) + (size_t)nu * per;
-    std::vector<unsigned char> host(bytes);
-    QPClass* cls = reinterpret_cast<QPClass*>(host.data());
-    unsigned char* fac = host.data() + (size_t)nu * sizeof(QPClass);
-    for (int j = 0; j < nu; ++j) {
-        qp_make_class(bounds + 8 * j, sc, rho, &cls[j]);
-        const double scd[4] = {cls[j].s[0], cls[j].s[1], cls[j].s[2], cls[j].s[3]};
-        const int rc = warp ? qp_dense_inverse(c->H, rho, scd, reinterpret_cast<float*>(fac + j * per))
-                            : qp_band_factor(c->H, rho, scd, reinterpret_cast<float4*>(fac + j * per));
-        if (rc != MPPI_OK) return rc;
-    }
+    const size_t bytes = host.size();
     if (c->d_qp && c->qp_bytes != bytes) {
         cudaFree(c->d_qp);
         c->d_qp = nullptr;

@@ -41,7 +41,7 @@ __device__ __forceinline__ int owner(const BatchInst* insts, int n, int t, bool 
     return lo;
 }
 
-template <int NA, int LPS, int PLACE>
+template <int NA, int LPS, int PLACE, int MODE>
 __global__ void __launch_bounds__(256, 2) batch_rollout_kernel(const BatchInst* insts, int n, int ntiles, BatchCtl* ctl,
                                                              int max_unom) {
     using d = Dims<NA>;
@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(256, 2) batch_rollout_kernel(const BatchInst* 
         if (t >= ntiles) break;
         const int inst = owner(insts, n, t, false);
         const BatchInst& I = insts[inst];
-        const int unom_n = I.stage_unom ? I.H * d::NU : 0;
+        const int unom_n = (MODE == 1 && I.stage_unom) ? I.H * d::NU : 0;
         if (inst != staged) {
             stage_model(smem, I.model, unom_s, I.u, unom_n);
             staged = inst;
@@ -74,15 +74,22 @@ __global__ void __launch_bounds__(256, 2) batch_rollout_kernel(const BatchInst* 
             io.k = k;
             io.H = I.H;
             io.err = I.err;
-            io.unom = unom_n ? unom_s : I.u;
-            io.iter = (uint32_t)(*I.iter);
-            io.key = make_uint2((uint32_t)I.seed, (uint32_t)(I.seed >> 32));
-            if (g.sl < d::NU) {
-                io.sig = I.sigma[g.sl];
-                io.lo = I.u_lo[g.sl];
-                io.hi = I.u_hi[g.sl];
+            if (MODE == 1) {
+                io.unom = unom_n ? unom_s : I.u;
+                io.iter = (uint32_t)(*I.iter);
+                io.key = make_uint2((uint32_t)I.seed, (uint32_t)(I.seed >> 32));
+                io.Lfac = I.cov_sampling ? I.Lfac : nullptr;
+                if (g.sl < d::NU) {
+                    io.sig = I.sigma[g.sl];
+                    io.lo = I.u_lo[g.sl];
+                    io.hi = I.u_hi[g.sl];
+                }
+            } else {  // the instance's projected samples, h-major
+                io.U = I.U + (size_t)k * d::NU;
+                io.u_stride = (long long)I.K * d::NU;
+                io.u_ext = (long long)I.H * I.K * d::NU - (long long)k * d::NU;
             }
-            const float cost = rollout_sample<NA, LPS, 1, false, PLACE>(M, w, g, io);
+            const float cost = rollout_sample<NA, LPS, MODE, false, PLACE>(M, w, g, io);
             if (g.sl == 0) I.costs[k] = cost;
         }
         __syncthreads();
@@ -98,14 +105,71 @@ __global__ void __launch_bounds__(256, 2) batch_rollout_kernel(const BatchInst* 
     }
 }
 
-// One CTA per (instance, horizon step); each instance's last CTA advances
-// that instance's iteration counter.
+// Elite threshold of every instance that uses the full Eq. 8 (one CTA per
+// instance in execution order; the others exit).
+__global__ void __launch_bounds__(1024) batch_select_kernel(const BatchInst* insts, int n) {
+    extern __shared__ unsigned long long keys[];
+    __shared__ int nfin;
+    const BatchInst& I = insts[blockIdx.x];
+    if (!I.elite) return;
+    int P = 1;
+    while (P < I.K) P <<= 1;
+    elite_select_block(I.costs, I.K, P, I.n_elite, I.sel, I.eidx, keys, nfin);
+}
+
+// One CTA per (instance, horizon step): the plain update (Eq. 8a/8d with
+// eta = 1 over every sample) or the full Eq. 8 (elite set, learning rate,
+// covariance block) as the instance asks; each instance's last CTA
+// advances its iteration counter.
 template <int NU>
 __global__ void __launch_bounds__(256) batch_update_kernel(const BatchInst* insts, int n) {
-    __shared__ UpdateSmem<NU> sm;
+    __shared__ union {
+        UpdateSmem<NU> u;
+        EliteSmem<NU> e;
+    } sm;
     const int inst = owner(insts, n, blockIdx.x, true);
     const BatchInst& I = insts[inst];
     const int h = blockIdx.x - I.row0;
+    if (I.elite) {
+        EliteArgs a{};
+        a.K = I.K;
+        a.H = I.H;
+        a.n_elite = I.n_elite;
+        a.update_cov = I.update_cov;
+        a.beta = I.lambda;
+        a.eta = I.eta;
+        a.cov_floor = I.cov_floor;
+        a.costs = I.costs;
+        a.u_nom = I.u;
+        a.u_out = I.u;
+        a.sigma = I.sigma;
+        a.Lfac = I.cov_sampling ? I.Lfac : nullptr;
+        a.u_lo = I.u_lo;
+        a.u_hi = I.u_hi;
+        a.Sigma = I.Sigma;
+        a.Lout = I.Lfac;
+        a.seed = I.seed;
+        a.iter_ptr = I.iter;
+        a.U_stored = I.U;
+        a.sel = I.sel;
+        a.eidx = I.eidx;
+        a.best_U = nullptr;
+        a.err = I.err;
+        elite_update_step<NU>(a, h, sm.e);
+        __syncthreads();
+        if (threadIdx.x == 0) {  // the last CTA of the instance advances its counter (no waiting)
+            __threadfence();
+            const unsigned t = atomicAdd(I.done, 1u);
+            sm.e.is_last = (t == (unsigned)I.H - 1u);
+        }
+        __syncthreads();
+        if (sm.e.is_last && threadIdx.x == 0) {
+            *I.done = 0u;
+            *I.iter += 1ull;
+            __threadfence();
+        }
+        return;
+    }
     UpdateArgs a{};
     a.K = I.K;
     a.H = I.H;
@@ -122,8 +186,9 @@ __global__ void __launch_bounds__(256) batch_update_kernel(const BatchInst* inst
     a.best = I.best;
     a.advance = 1;
     a.done = I.done;
-    update_step<NU>(a, h, sm);
-    update_finish<NU>(a, I.H, sm);
+    a.U_stored = I.U;
+    update_step<NU>(a, h, sm.u);
+    update_finish<NU>(a, I.H, sm.u);
 }
 
 // Shift a nominal sequence one step: u[h] <- u[h+1], the last step kept.
@@ -135,12 +200,22 @@ __global__ void shift_kernel(float* u, int H, int nu) {
 
 using BatchFn = void (*)(const BatchInst*, int, int, BatchCtl*, int);
 
+// The persistent rollout of a layout: samples drawn in-kernel (mode 1, both
+// placements) or the instances' projected samples (mode 0, fused placement).
 template <int NA>
-BatchFn batch_fn(int lps, int place) {
-    if (lps == 32) return place ? batch_rollout_kernel<NA, 32, 1> : batch_rollout_kernel<NA, 32, 0>;
-    if (lps == 16) return place ? batch_rollout_kernel<NA, 16, 1> : batch_rollout_kernel<NA, 16, 0>;
+BatchFn batch_fn(int lps, int place, int mode = 1) {
+    if (mode == 0) {
+        if (lps == 32) return batch_rollout_kernel<NA, 32, 0, 0>;
+        if (lps == 16) return batch_rollout_kernel<NA, 16, 0, 0>;
+        if constexpr (Lanes<8>::SEG > NA) {
+            if (lps == 8) return batch_rollout_kernel<NA, 8, 0, 0>;
+        }
+        return nullptr;
+    }
+    if (lps == 32) return place ? batch_rollout_kernel<NA, 32, 1, 1> : batch_rollout_kernel<NA, 32, 0, 1>;
+    if (lps == 16) return place ? batch_rollout_kernel<NA, 16, 1, 1> : batch_rollout_kernel<NA, 16, 0, 1>;
     if constexpr (Lanes<8>::SEG > NA) {
-        if (lps == 8) return place ? batch_rollout_kernel<NA, 8, 1> : batch_rollout_kernel<NA, 8, 0>;
+        if (lps == 8) return place ? batch_rollout_kernel<NA, 8, 1, 1> : batch_rollout_kernel<NA, 8, 0, 1>;
     }
     return nullptr;
 }
@@ -165,6 +240,9 @@ int batch_shape_t(int spc, int lps, int place, int max_h, BatchLaunch* L) {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L->smem);
     if (e != cudaSuccess) return MPPI_ERR_CUDA;
     int per_sm = 0, dev = 0, sms = 0;
+    BatchFn fn0 = batch_fn<NA>(lps, 0, 0);  // the projected-sample form of the layout
+    if (fn0) e = cudaFuncSetAttribute(fn0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L->smem);
+    if (e != cudaSuccess) return MPPI_ERR_CUDA;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, spc * lps, L->smem);
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -191,11 +269,21 @@ int batch_shape(int na, int spc, int lps, int place, int max_h, BatchLaunch* L) 
 int launch_batch_iteration(const BatchInst* insts, int n, int ntiles, int nrows, BatchCtl* ctl, const BatchLaunch& L,
                            cudaStream_t s) {
     if (n <= 0) return MPPI_OK;
-    BatchFn fn = L.na == 3 ? batch_fn<3>(L.lps, L.place) : batch_fn<7>(L.lps, L.place);
+    BatchFn fn = L.na == 3 ? batch_fn<3>(L.lps, L.place, L.mode) : batch_fn<7>(L.lps, L.place, L.mode);
     if (!fn) return MPPI_ERR_UNSUPPORTED;
     fn<<<L.grid, L.spc * L.lps, L.smem, s>>>(insts, n, ntiles, ctl, L.max_unom);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return MPPI_ERR_CUDA;
+    if (L.sel_P > 0) {  // elite thresholds of the instances that use them
+        const size_t sm = (size_t)(L.sel_P <= 1024 ? 2048 : L.sel_P) * sizeof(unsigned long long);
+        if (sm > 48 * 1024) {
+            e = cudaFuncSetAttribute(batch_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e != cudaSuccess) return MPPI_ERR_CUDA;
+        }
+        batch_select_kernel<<<n, 1024, sm, s>>>(insts, n);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return MPPI_ERR_CUDA;
+    }
     if (L.na == 3) batch_update_kernel<6><<<nrows, 256, 0, s>>>(insts, n);
     else batch_update_kernel<14><<<nrows, 256, 0, s>>>(insts, n);
     return cudaGetLastError() == cudaSuccess ? MPPI_OK : MPPI_ERR_CUDA;
@@ -295,6 +383,13 @@ struct mppi_batch {
     cudaGraphExec_t gexec = nullptr;
     cudaGraph_t graph = nullptr;
     cudaStream_t gstream = nullptr;
+    // full Eq. 8 and the projection, per instance (user order)
+    std::vector<float*> d_eq8;       // Sigma, L (H x nu x nu each), then the elite indices
+    std::vector<unsigned long long*> d_sel;
+    std::vector<float*> d_Ubuf;      // H x K x nu projected samples
+    std::vector<void*> d_qp;         // projection classes and factors
+    int qp_iters = 0;
+    float qp_dt = 0.0f;
 };
 
 namespace {
@@ -346,7 +441,30 @@ int reshape(mppi_batch* b) {
 }
 
 int enqueue_batch(mppi_batch* b, cudaStream_t s) {
+    if (b->qp_iters > 0) {  // sample and project every instance's sequences (Eq. 5) into its buffer
+        const int nq = 2 * b->na + 7;
+        for (int i = 0; i < b->n; ++i) {
+            const BatchInst& I = b->inst[i];
+            const QPArgs q = qp_controller_args(b->nu, nq, I.K, I.H, b->qp_iters, b->qp_dt, b->d_qp[i], I.state, I.u,
+                                                I.sigma, I.cov_sampling ? I.Lfac : nullptr, I.seed, I.iter, I.U);
+            const int rc = launch_qp(q, s);
+            if (rc != MPPI_OK) return rc;
+        }
+    }
     return launch_batch_iteration(b->d_insts, b->n, b->ntiles, b->nrows, b->d_ctl, b->L, s);
+}
+
+// The elite sort's key count for the instances that use the elite set.
+void update_flags(mppi_batch* b) {
+    int P = 0;
+    for (const BatchInst& I : b->inst)
+        if (I.elite) {
+            int p = 1;
+            while (p < I.K) p <<= 1;
+            P = std::max(P, p);
+        }
+    b->L.sel_P = P;
+    b->L.mode = b->qp_iters > 0 ? 0 : 1;
 }
 
 // Write the caller's state and control pointers into the execution-order
@@ -369,6 +487,10 @@ int mppi_batch_destroy(mppi_batch* b) {
     if (!b) return MPPI_OK;
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     if (b->graph) cudaGraphDestroy(b->graph);
+    for (float* p : b->d_eq8) cudaFree(p);
+    for (unsigned long long* p : b->d_sel) cudaFree(p);
+    for (float* p : b->d_Ubuf) cudaFree(p);
+    for (void* p : b->d_qp) cudaFree(p);
     cudaFreeHost(b->h_pinned);
     cudaFree(b->d_insts);
     cudaFree(b->d_ctl);
@@ -476,6 +598,10 @@ int mppi_batch_create(const mppi_batch_desc* desc, int n, mppi_batch** out) {
         b->lps = lps;
         b->place = place;
     }
+    b->d_eq8.assign(n, nullptr);
+    b->d_sel.assign(n, nullptr);
+    b->d_Ubuf.assign(n, nullptr);
+    b->d_qp.assign(n, nullptr);
     int rc = reshape(b);
     if (rc != MPPI_OK) {
         mppi_batch_destroy(b);
@@ -483,6 +609,101 @@ int mppi_batch_create(const mppi_batch_desc* desc, int n, mppi_batch** out) {
     }
     *out = b;
     return MPPI_OK;
+}
+
+int mppi_batch_set_update(mppi_batch* b, int i, int n_elite, float eta, int update_cov, float cov_floor) {
+    if (!b || i < -1 || i >= b->n) return MPPI_ERR_INVALID_ARG;
+    if (i < 0) {
+        for (int q = 0; q < b->n; ++q) {
+            const int rc = mppi_batch_set_update(b, q, n_elite, eta, update_cov, cov_floor);
+            if (rc != MPPI_OK) return rc;
+        }
+        return MPPI_OK;
+    }
+    BatchInst& I = b->inst[i];
+    if (n_elite == 0) n_elite = I.K;
+    if (n_elite < 1 || n_elite > I.K || !(eta > 0.0f && eta <= 1.0f) || update_cov < 0 || update_cov > 1 ||
+        !(cov_floor >= 0.0f))
+        return MPPI_ERR_INVALID_ARG;
+    if (n_elite < I.K && I.K > 8192) return MPPI_ERR_UNSUPPORTED;  // the elite sort holds 8192 keys
+    const int nu = b->nu;
+    const size_t blk = (size_t)I.H * nu * nu;
+    if (!b->d_eq8[i]) {
+        float* p = nullptr;
+        unsigned long long* sp = nullptr;
+        cudaError_t e = cudaMalloc(&p, (2 * blk + (size_t)I.K) * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc(&sp, 3 * sizeof(unsigned long long));
+        if (e != cudaSuccess) {
+            cudaFree(p);
+            return cuda_rc(e);
+        }
+        // Sigma_0 = diag(sigma^2), its factor diag(sigma)
+        std::vector<float> sig(nu), S(2 * blk, 0.0f);
+        e = cudaMemcpy(sig.data(), I.sigma, nu * sizeof(float), cudaMemcpyDeviceToHost);
+        for (int h = 0; h < I.H; ++h)
+            for (int j = 0; j < nu; ++j) {
+                S[((size_t)h * nu + j) * nu + j] = sig[j] * sig[j];
+                S[blk + ((size_t)h * nu + j) * nu + j] = sig[j];
+            }
+        if (e == cudaSuccess) e = cudaMemcpy(p, S.data(), 2 * blk * sizeof(float), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(p);
+            cudaFree(sp);
+            return cuda_rc(e);
+        }
+        b->d_eq8[i] = p;
+        b->d_sel[i] = sp;
+    }
+    I.Sigma = b->d_eq8[i];
+    I.Lfac = b->d_eq8[i] + blk;
+    I.eidx = reinterpret_cast<int*>(b->d_eq8[i] + 2 * blk);
+    I.sel = b->d_sel[i];
+    I.n_elite = n_elite;
+    I.eta = eta;
+    I.update_cov = update_cov;
+    I.cov_floor = cov_floor;
+    if (update_cov) I.cov_sampling = 1;
+    I.elite = (n_elite != I.K || eta != 1.0f || update_cov || I.cov_sampling) ? 1 : 0;
+    update_flags(b);
+    return reshape(b);
+}
+
+int mppi_batch_set_projection(mppi_batch* b, const float* bounds, int iters, float rho, const float* scales) {
+    if (!b || iters < 0) return MPPI_ERR_INVALID_ARG;
+    if (iters == 0) {
+        b->qp_iters = 0;
+        for (BatchInst& I : b->inst) I.U = nullptr;
+        update_flags(b);
+        return reshape(b);
+    }
+    if (!bounds) return MPPI_ERR_INVALID_ARG;
+    const int nu = b->nu;
+    std::vector<std::vector<unsigned char>> host(b->n);
+    for (int i = 0; i < b->n; ++i) {
+        const int rc = qp_build(nu, b->inst[i].H, bounds + (size_t)i * nu * 8, rho, scales, host[i]);
+        if (rc != MPPI_OK) return rc;
+    }
+    float dt = 0.0f;
+    for (int i = 0; i < b->n; ++i) {
+        const float dti = model_dt(b->desc[i].model);
+        if (i > 0 && dti != dt) return MPPI_ERR_INVALID_ARG;  // one time step across the batch
+        dt = dti;
+    }
+    for (int i = 0; i < b->n; ++i) {
+        BatchInst& I = b->inst[i];
+        cudaFree(b->d_qp[i]);
+        b->d_qp[i] = nullptr;
+        cudaError_t e = cudaMalloc(&b->d_qp[i], host[i].size());
+        if (e == cudaSuccess) e = cudaMemcpy(b->d_qp[i], host[i].data(), host[i].size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && !b->d_Ubuf[i])
+            e = cudaMalloc(&b->d_Ubuf[i], (size_t)I.H * I.K * nu * sizeof(float));
+        if (e != cudaSuccess) return cuda_rc(e);
+        I.U = b->d_Ubuf[i];
+    }
+    b->qp_iters = iters;
+    b->qp_dt = dt;
+    update_flags(b);
+    return reshape(b);
 }
 
 int mppi_batch_set_launch(mppi_batch* b, int spc, int order) {

@@ -94,6 +94,7 @@ struct mppi_model;
 namespace mppi {
 const DevModel* model_device(const mppi_model* m);
 void model_bounds(const mppi_model* m, int j, float* lo, float* hi);
+float model_dt(const mppi_model* m);
 
 // descriptor of one controller in a batched iteration (device table)
 struct BatchInst {
@@ -114,6 +115,15 @@ struct BatchInst {
     int stage_unom;
     int tile0;  // first work item (tile of samples) of this instance
     int row0;   // first update CTA of this instance
+    // the full Eq. 8 update (elite != 0: elite set, learning rate,
+    // covariance blocks) and the projected samples (Eq. 5)
+    int elite, n_elite, update_cov, cov_sampling;
+    float eta, cov_floor;
+    float* Sigma;               // H x nu x nu
+    float* Lfac;                // H x nu x nu sampling factors (rewritten by the covariance update)
+    unsigned long long* sel;    // [threshold key, best key, finite count]
+    int* eidx;                  // K elite indices
+    float* U;                   // H x K x nu projected samples, or null (samples drawn in the rollout)
 };
 
 struct BatchCtl {
@@ -125,6 +135,8 @@ struct BatchCtl {
 struct BatchLaunch {
     int na = 7, spc = 4, lps = 32, place = 0, grid = 0, max_unom = 0;
     size_t smem = 0;
+    int mode = 1;       // 1: samples drawn in the rollout; 0: every instance's projected samples (BatchInst::U)
+    int sel_P = 0;      // > 0: some instance uses the elite set; its sort holds up to sel_P keys
 };
 // spc: samples per tile (rounded up to whole warps); lps: lanes per sample
 // (32, 16 or 8; 0 = 32); place: the lone ball contact's solve fused (0) or
@@ -176,6 +188,10 @@ int qp_dense_inverse(int H, double rho, const double sc[4], float* minv);
 void qp_make_class(const float b[8], const float sc[4], float rho, QPClass* c);
 int qp_validate(const float b[8], const float sc[4], float rho);
 int launch_qp(const QPArgs& a, cudaStream_t s);
+int qp_build(int nu, int H, const float* bounds, float rho, const float* scales, std::vector<unsigned char>& host);
+QPArgs qp_controller_args(int nu, int nq, int K, int H, int iters, float dt, const void* d_qp, const float* state,
+                          const float* u_nom, const float* sigma, const float* Lfac, uint64_t seed,
+                          const unsigned long long* iter_ptr, float* U);
 
 // closed-loop episode helpers
 int launch_best_average(const float* U, const float* best, const float* bestU, int K, int nu, int n, float* u1,

@@ -284,7 +284,7 @@ __device__ __forceinline__ void update_step(const UpdateArgs& a, int h, UpdateSm
                 // the rollout's own samples (bit-identical to regenerating them)
                 const long long u0 = ((long long)h * a.K + k) * NU, n_u = (long long)a.H * a.K * NU;
 #pragma unroll
-                for (int j = 0; j < NU; ++j) acc[j] += wk * ld_checked(a.U_stored, u0 + j, n_u);
+                for (int j = 0; j < NU; ++j) acc[j] = __fmaf_rn(wk, ld_checked(a.U_stored, u0 + j, n_u), acc[j]);
             } else {
 #pragma unroll
                 for (int jb = 0; jb < (NU + 3) / 4; ++jb) {
@@ -297,7 +297,7 @@ __device__ __forceinline__ void update_step(const UpdateArgs& a, int h, UpdateSm
                         if (j < NU) {
                             const float z = z4[t];
                             const float u = fminf(fmaxf(__fmaf_rn(sg[j], z, un[j]), lo[j]), hi[j]);
-                            acc[j] += wk * u;
+                            acc[j] = __fmaf_rn(wk, u, acc[j]);
                         }
                     }
                 }
@@ -472,8 +472,10 @@ __device__ __forceinline__ void elite_update_step(const EliteArgs& a, int h, Eli
         float u[NU];
         elite_row<NU>(a, h, k, key, iter, unom_h, u);
         Z += wk;
+        // products and sums with their rounding written out (explicit FMAs):
+        // every kernel that inlines this step computes the same bits
 #pragma unroll
-        for (int j = 0; j < NU; ++j) acc[j] += wk * u[j];
+        for (int j = 0; j < NU; ++j) acc[j] = __fmaf_rn(wk, u[j], acc[j]);
         if (cached) {
 #pragma unroll
             for (int j = 0; j < NU; ++j) sm.d[e][j] = u[j];
@@ -502,7 +504,7 @@ __device__ __forceinline__ void elite_update_step(const EliteArgs& a, int h, Eli
     const float Zs = sm.red[NU][0];
     if (tid < NU) {
         const float m = any ? sm.red[tid][0] / Zs : unom_h[tid];
-        sm.mean[tid] = any ? (1.0f - a.eta) * unom_h[tid] + a.eta * m : unom_h[tid];
+        sm.mean[tid] = any ? __fmaf_rn(a.eta, m, __fmul_rn(1.0f - a.eta, unom_h[tid])) : unom_h[tid];
     }
     // the lowest-cost sample's row, read before this CTA rewrites the block's
     // factor (regeneration samples through the current factor)
@@ -553,14 +555,14 @@ __device__ __forceinline__ void elite_update_step(const EliteArgs& a, int h, Eli
             if (tid < NE) {
                 const int nt = ne - e0 < 64 ? ne - e0 : 64;
 #pragma unroll 4
-                for (int t = 0; t < nt; ++t) cv += sm.d[t][NU] * sm.d[t][ci] * sm.d[t][cj];
+                for (int t = 0; t < nt; ++t) cv = __fmaf_rn(__fmul_rn(sm.d[t][NU], sm.d[t][ci]), sm.d[t][cj], cv);
             }
             __syncthreads();
         }
         if (tid < NE) {
             const long long n_s = (long long)a.H * NU * NU;
-            float v = (1.0f - a.eta) * ld_checked(a.Sigma, (long long)h * NU * NU + ci * NU + cj, n_s) +
-                      a.eta * (cv / Zs);
+            float v = __fmaf_rn(a.eta, cv / Zs,
+                                __fmul_rn(1.0f - a.eta, ld_checked(a.Sigma, (long long)h * NU * NU + ci * NU + cj, n_s)));
             if (ci == cj) v += a.cov_floor;
             sm.cov[ci][cj] = v;
             sm.cov[cj][ci] = v;
@@ -582,7 +584,7 @@ __device__ __forceinline__ void elite_update_step(const EliteArgs& a, int h, Eli
                 const int n = NU - j - 1;
                 for (int t = tid; t < n * n; t += 32) {
                     const int r = j + 1 + t / n, q = j + 1 + t % n;
-                    if (q <= r) sm.cov[r][q] -= sm.cov[r][j] * sm.cov[q][j];
+                    if (q <= r) sm.cov[r][q] = __fmaf_rn(-sm.cov[r][j], sm.cov[q][j], sm.cov[r][q]);
                 }
                 __syncwarp();
             }
@@ -599,6 +601,87 @@ __device__ __forceinline__ void elite_update_step(const EliteArgs& a, int h, Eli
     // (3) outputs (u_out may alias u_nom: this CTA read its row above)
     if (tid < NU && MPPI_IN_RANGE(h * NU + tid, (long long)a.H * NU)) a.u_out[h * NU + tid] = sm.mean[tid];
     if (h == 0 && tid == 0 && !any) atomicOr(a.err, ERRB_NONFINITE);
+}
+
+// Elite threshold: bitonic sort of (cost, index) keys in shared memory (one
+// CTA of 1024 threads, P = power of two >= K; keys holds 2048 keys when
+// P <= 1024, else P); sel = [key of the n_e-th elite, lowest key, finite
+// count], eidx = the elite indices in cost order.
+__device__ __forceinline__ void elite_select_block(const float* costs, int K, int P, int n_elite,
+                                                  unsigned long long* sel, int* eidx, unsigned long long* keys,
+                                                  int& nfin) {
+    if (P <= 1024) {
+        // one key per thread (padding keys sort last): the same bitonic
+        // network in registers, partners by shuffles below stride 32 and
+        // through a double-buffered shared array above
+        const int t = threadIdx.x;
+        unsigned long long x = ~0ull;
+        bool fin = false;
+        if (t < K) {
+            const float c = ld_checked(costs, t, K);
+            x = cost_key(c, t);
+            fin = isfinite(c);
+        }
+        const int nf = __syncthreads_count(fin);
+        int buf = 0;
+        for (int size = 2; size <= 1024; size <<= 1)
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                unsigned long long y;
+                if (stride >= 32) {
+                    if (MPPI_IN_RANGE(buf * 1024 + t, 2048)) keys[buf * 1024 + t] = x;
+                    __syncthreads();
+                    y = MPPI_IN_RANGE(buf * 1024 + (t ^ stride), 2048) ? keys[buf * 1024 + (t ^ stride)] : x;
+                    buf ^= 1;
+                } else {
+                    y = __shfl_xor_sync(0xffffffffu, x, stride);
+                }
+                const bool asc = (t & size) == 0, lower = (t & stride) == 0;
+                x = (lower == asc) ? (x < y ? x : y) : (x < y ? y : x);
+            }
+        const int ne = nf == 0 ? 0 : (n_elite < nf ? n_elite : nf);
+        if (t < ne && MPPI_IN_RANGE(t, K)) eidx[t] = (int)(x & 0xFFFFFFFFull);
+        if (t == 0) {
+            sel[1] = x;
+            sel[2] = (unsigned long long)nf;
+            if (ne == 0) sel[0] = 0ull;
+        }
+        if (ne > 0 && t == ne - 1) sel[0] = x;
+        return;
+    }
+    if (threadIdx.x == 0) nfin = 0;
+    __syncthreads();
+    int mine = 0;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const float c = i < K ? ld_checked(costs, i, K) : 0.0f;
+        if (MPPI_IN_RANGE(i, P)) keys[i] = i < K ? cost_key(c, i) : ~0ull;
+        mine += (i < K && isfinite(c)) ? 1 : 0;
+    }
+    atomicAdd(&nfin, mine);
+    __syncthreads();
+    for (int size = 2; size <= P; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                const int j = i ^ stride;
+                if (j > i && MPPI_IN_RANGE(j, P)) {
+                    const bool asc = (i & size) == 0;
+                    const unsigned long long x = keys[i], y = keys[j];
+                    if ((x > y) == asc) {
+                        keys[i] = y;
+                        keys[j] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    const int nf = nfin;
+    const int ne = nf == 0 ? 0 : (n_elite < nf ? n_elite : nf);
+    for (int e = threadIdx.x; e < ne; e += blockDim.x)
+        if (MPPI_IN_RANGE(e, K)) eidx[e] = (int)(keys[e] & 0xFFFFFFFFull);
+    if (threadIdx.x == 0) {
+        sel[0] = ne > 0 ? keys[ne - 1] : 0ull;
+        sel[1] = keys[0];
+        sel[2] = (unsigned long long)nf;
+    }
 }
 
 }  // namespace mppi

@@ -148,6 +148,8 @@ def lib():
     _decl(L, "mppi_batch_set_launch", i, [vp, i, i])
     _decl(L, "mppi_batch_get_launch", i, [vp, C.POINTER(i), C.POINTER(i)])
     _decl(L, "mppi_batch_set_layout", i, [vp, i, i])
+    _decl(L, "mppi_batch_set_update", i, [vp, i, i, C.c_float, i, C.c_float])
+    _decl(L, "mppi_batch_set_projection", i, [vp, fp, i, C.c_float, fp])
     _decl(L, "mppi_batch_get_layout", i, [vp, C.POINTER(i), C.POINTER(i)])
     _decl(L, "mppi_batch_autotune", i, [vp, vp, vp, i, vp, C.POINTER(C.c_float)])
     _decl(L, "mppi_tune_store", i, [C.c_char_p, i, i, i, i, C.c_float])
@@ -411,6 +413,22 @@ class Batch:
 
     def set_layout(self, lanes_per_sample=32, placement=0):
         _check(lib().mppi_batch_set_layout(self._h, int(lanes_per_sample), int(placement)), "mppi_batch_set_layout")
+
+    def set_update(self, i: int, n_elite: int, eta: float = 1.0, update_cov: bool = False, cov_floor: float = 0.0):
+        """The full Eq. 8 for instance i (-1: all); n_elite 0 = every sample."""
+        _check(lib().mppi_batch_set_update(self._h, int(i), int(n_elite), float(eta), int(bool(update_cov)),
+                                           float(cov_floor)), "mppi_batch_set_update")
+
+    def set_projection(self, bounds, iters: int = 30, rho: float = 1.0, scales=None):
+        """QP projection (Eq. 5) of every instance: bounds n x nu x 8 (host);
+        iters = 0 turns it off."""
+        if int(iters) == 0:
+            _check(lib().mppi_batch_set_projection(self._h, None, 0, 1.0, None), "mppi_batch_set_projection")
+            return
+        b = _host_f32(bounds)
+        sc = None if scales is None else _host_f32(scales, 4)
+        _check(lib().mppi_batch_set_projection(self._h, b.ctypes.data, int(iters), float(rho),
+                                               None if sc is None else sc.ctypes.data), "mppi_batch_set_projection")
 
     def get_layout(self):
         l, p = C.c_int(), C.c_int()

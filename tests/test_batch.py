@@ -113,3 +113,49 @@ def test_batch_graph_replay_and_autotune(tmp_path, monkeypatch):
     b2 = native.Batch([(m, K, H, lam, sig, key) for sc, m, K, H, lam, sig, key in inst])
     assert b2.get_launch() == (int(text[1]), int(text[2]))
     assert b2.get_layout() == (int(text[3]), int(text[4]))
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("proj", [False, True])
+def test_batch_full_eq8_and_projection_match_single_controllers(tmp_path, monkeypatch, proj):
+    # instances with the elite set, a learning rate and covariance blocks
+    # (and, with proj, the QP projection of every sample) give bitwise the
+    # iterations a single controller with the same settings gives
+    import torch
+    from paper_2511_21264_gb300 import native
+    monkeypatch.setenv("MPPI_TUNE_FILE", str(tmp_path / "tune.txt"))
+    native.build()
+    inst = _instances(native)
+    settings = [(16, 0.7, True), (0, 1.0, False), (40, 0.5, True), (8, 1.0, False), (10, 0.8, True), (0, 0.6, False)]
+    bounds = [scenes.projection_bounds(sc) for sc, *_ in inst]
+    ref = []
+    for (sc, m, K, H, lam, sig, key), (ne, eta, cov) in zip(inst, settings):
+        ctl = native.Controller(m, K, H, lam, sig, key)
+        ctl.set_update(ne or K, eta, cov, 1e-6)
+        if proj:
+            ctl.set_projection(scenes.projection_bounds(sc), iters=10)
+        x = torch.tensor(m.home(), device="cuda")
+        u = torch.zeros((H, sc.nu), device="cuda")
+        for _ in range(3):
+            ctl.step(x, u, u)
+        assert ctl.sync() == 0
+        ref.append(u.clone())
+    xs = [torch.tensor(m.home(), device="cuda") for sc, m, *_ in inst]
+    s = torch.cuda.Stream()
+    for lps, graph in ((32, False), (16, True)):
+        # a fresh batch per pass: the covariance blocks start from diag(sigma^2)
+        b = native.Batch([(m, K, H, lam, sig, key) for sc, m, K, H, lam, sig, key in inst])
+        for i, (ne, eta, cov) in enumerate(settings):
+            b.set_update(i, ne, eta, cov, 1e-6)
+        if proj:
+            b.set_projection(np.stack(bounds), iters=10)
+        b.set_layout(lps, 0)
+        us = [torch.zeros((H, sc.nu), device="cuda") for sc, m, K, H, *_ in inst]
+        with torch.cuda.stream(s):
+            for _ in range(3):
+                b.step(xs, us, stream=s, graph=graph)
+        rc, errs = b.sync(stream=s)
+        assert rc == 0, errs
+        for i in range(len(inst)):
+            assert torch.equal(us[i], ref[i]), (lps, graph, i)
+        b.close()
