@@ -457,6 +457,11 @@ typedef struct {
     int size_classes;        /* 1..8 streams of requests grouped by work per
                                 iteration (K x H in powers of two); 1 = one
                                 batch of every active request; 0 = 6 */
+    int qp_iters;            /* QP projection (Eq. 5) of every request's
+                                samples, ADMM iterations; 0 = off.  Every
+                                scene then needs srv_set_scene_projection and
+                                a request's workspace holds its H x K x nu
+                                projected samples besides the K costs */
 } mppi_server_config;
 typedef struct {
     long long completed, iterations, waiting, active, admission_waits;
@@ -475,6 +480,12 @@ int srv_start(mppi_server *s);
 /* Stop the scheduler thread (requests in flight are abandoned); returns the
  * first device or CUDA error the scheduler met. */
 int srv_stop(mppi_server *s);
+/* Before srv_start: the full Eq. 8 for a scene (as mppi_set_update; its
+ * covariance blocks stay resident and carry over to its next request, the
+ * warm start of Sigma of Sec. III-A), and a scene's projection bounds (nu x
+ * 8 floats, host; rho and scales as mppi_set_projection). */
+int srv_set_scene_update(mppi_server *s, int scene_id, int n_elite, float eta, int update_cov, float cov_floor);
+int srv_set_scene_projection(mppi_server *s, int scene_id, const float *bounds, float rho, const float *scales);
 int srv_submit(mppi_server *s, int scene_id, uint64_t *ticket);
 /* Withdraw a request that has not been admitted yet. */
 int srv_cancel(mppi_server *s, uint64_t ticket);

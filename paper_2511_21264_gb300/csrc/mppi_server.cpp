@@ -52,6 +52,13 @@ struct Scene {
     int* d_err = nullptr;
     float* d_best = nullptr;
     bool busy = false;  // a request of this scene is active
+    // the full Eq. 8 (elite != 0); the covariance blocks stay resident and
+    // warm-start the scene's next request
+    int elite = 0, n_elite = 0, update_cov = 0, cov_sampling = 0;
+    float eta = 1.0f, cov_floor = 0.0f;
+    float* d_eq8 = nullptr;              // Sigma, L (H x nu x nu each), elite indices (K)
+    unsigned long long* d_sel = nullptr;
+    void* d_qp = nullptr;                // projection classes and factors (server-wide projection)
 };
 
 struct Request {
@@ -103,7 +110,11 @@ struct Arena {
     }
 };
 
-size_t request_bytes(int K) { return ((size_t)K * sizeof(float) + 255) / 256 * 256; }
+// A request's device workspace: its K sample costs and, with the
+// projection on, its H x K x nu projected samples.
+size_t request_bytes(int K, int H = 0, int nu = 0) {
+    return ((size_t)K * sizeof(float) + 255) / 256 * 256 + ((size_t)H * K * nu * sizeof(float) + 255) / 256 * 256;
+}
 
 }  // namespace
 
@@ -186,7 +197,7 @@ void complete_lane(mppi_server* S, Lane& ln, cudaError_t e) {
             const int err = ln.h_err[q];
             r.status = (err & ERRB_CHOLESKY) ? MPPI_ERR_CHOLESKY : (err & ERRB_NONFINITE) ? MPPI_ERR_NONFINITE : S->error;
             r.latency_ms = std::chrono::duration<double, std::milli>(now - r.arrival).count();
-            S->arena.release(r.arena_off, request_bytes(sc.K));
+            S->arena.release(r.arena_off, request_bytes(sc.K, S->cfg.qp_iters ? sc.H : 0, sc.nu));
             sc.busy = false;
             S->lat.push_back(r.latency_ms);
             S->completed++;
@@ -239,6 +250,21 @@ int launch_lane(mppi_server* S, Lane& ln) {
         I.stage_unom = sc.H * sc.nu <= 2048;
         I.tile0 = t;
         I.row0 = row;
+        if (sc.d_eq8) {
+            const size_t blk = (size_t)sc.H * sc.nu * sc.nu;
+            I.elite = sc.elite;
+            I.n_elite = sc.n_elite;
+            I.update_cov = sc.update_cov;
+            I.cov_sampling = sc.cov_sampling;
+            I.eta = sc.eta;
+            I.cov_floor = sc.cov_floor;
+            I.Sigma = sc.d_eq8;
+            I.Lfac = sc.d_eq8 + blk;
+            I.eidx = reinterpret_cast<int*>(sc.d_eq8 + 2 * blk);
+            I.sel = sc.d_sel;
+        }
+        if (S->cfg.qp_iters)  // the projected samples follow the costs in the request's workspace
+            I.U = reinterpret_cast<float*>(S->d_arena + r.arena_off + ((size_t)sc.K * sizeof(float) + 255) / 256 * 256);
         t += (sc.K + S->L.spc - 1) / S->L.spc;
         row += sc.H;
     }
@@ -249,7 +275,23 @@ int launch_lane(mppi_server* S, Lane& ln) {
     NvtxRange range("srv_iteration");
     BatchLaunch L = S->L;
     L.grid = std::min(L.grid, t);  // CTAs past the work would only exit
+    L.mode = S->cfg.qp_iters ? 0 : 1;
+    L.sel_P = 0;
+    for (int e = 0; e < n; ++e)
+        if (ln.h_insts[e].elite) {
+            int p = 1;
+            while (p < ln.h_insts[e].K) p <<= 1;
+            L.sel_P = std::max(L.sel_P, p);
+        }
     int rc = cuda_rc(cudaMemcpyAsync(ln.d_insts, ln.h_insts, n * sizeof(BatchInst), cudaMemcpyHostToDevice, ln.stream));
+    for (int e = 0; e < n && rc == MPPI_OK && S->cfg.qp_iters; ++e) {  // sample and project (Eq. 5)
+        const BatchInst& I = ln.h_insts[e];
+        const Scene& sc = S->scenes[act[e]->scene];
+        const QPArgs q = qp_controller_args(sc.nu, 2 * S->na + 7, sc.K, sc.H, S->cfg.qp_iters, model_dt(sc.model),
+                                            sc.d_qp, I.state, I.u, I.sigma, I.cov_sampling ? I.Lfac : nullptr, I.seed,
+                                            I.iter, I.U);
+        rc = launch_qp(q, ln.stream);
+    }
     if (rc == MPPI_OK) rc = launch_batch_iteration(ln.d_insts, n, t, row, ln.d_ctl, L, ln.stream);
     for (size_t q = 0; q < ln.retiring.size() && rc == MPPI_OK; ++q) {
         Request& r = *ln.retiring[q];
@@ -314,7 +356,7 @@ bool scheduler_step(mppi_server* S) {
                 continue;
             }
             size_t off = 0;
-            if (!S->arena.alloc(request_bytes(sc.K), &off)) {
+            if (!S->arena.alloc(request_bytes(sc.K, S->cfg.qp_iters ? sc.H : 0, sc.nu), &off)) {
                 ++S->admission_waits;
                 ++it;
                 continue;
@@ -375,7 +417,7 @@ int srv_create(const mppi_server_config* cfg, mppi_server** out) {
     S->cfg = *cfg;
     if (S->cfg.samples_per_cta <= 0) S->cfg.samples_per_cta = 4;
     cudaGetDevice(&S->device);
-    if (cfg->size_classes < 0 || cfg->size_classes > MAX_CLASSES) {
+    if (cfg->size_classes < 0 || cfg->size_classes > MAX_CLASSES || cfg->qp_iters < 0) {
         delete S;
         return MPPI_ERR_INVALID_ARG;
     }
@@ -416,7 +458,8 @@ int srv_add_scene(mppi_server* S, const mppi_model* m, int K, int H, float lambd
     const int na = nu / 2;
     if (na != 3 && na != 7) return MPPI_ERR_UNSUPPORTED;
     if (S->na && S->na != na) return MPPI_ERR_INVALID_ARG;
-    if (request_bytes(K) > S->cfg.mem_budget_bytes) return MPPI_ERR_ADMISSION;
+    if (request_bytes(K, S->cfg.qp_iters ? H : 0, 2 * ((nq - 7) / 2)) > S->cfg.mem_budget_bytes)
+        return MPPI_ERR_ADMISSION;
     S->na = na;
     Scene sc;
     sc.model = m;
@@ -463,6 +506,9 @@ int srv_add_scene(mppi_server* S, const mppi_model* m, int K, int H, float lambd
 
 int srv_start(mppi_server* S) {
     if (!S || S->running.load() || S->scenes.empty()) return MPPI_ERR_INVALID_ARG;
+    if (S->cfg.qp_iters)
+        for (const Scene& sc : S->scenes)
+            if (!sc.d_qp) return MPPI_ERR_INVALID_ARG;  // every scene needs its projection bounds
     int max_h = 0;
     for (const Scene& sc : S->scenes) max_h = std::max(max_h, sc.H);
     // 16 lanes per sample for 7-link arms unless set: the mixes hold large K,
@@ -509,6 +555,9 @@ int srv_destroy(mppi_server* S) {
         cudaFree(sc.d_done);
         cudaFree(sc.d_err);
         cudaFree(sc.d_best);
+        cudaFree(sc.d_eq8);
+        cudaFree(sc.d_sel);
+        cudaFree(sc.d_qp);
     }
     for (int c = 0; c < MAX_CLASSES; ++c) {
         Lane& ln = S->lanes[c];
@@ -523,6 +572,57 @@ int srv_destroy(mppi_server* S) {
     cudaFree(S->d_arena);
     delete S;
     return MPPI_OK;
+}
+
+int srv_set_scene_update(mppi_server* S, int scene_id, int n_elite, float eta, int update_cov, float cov_floor) {
+    if (!S || scene_id < 0 || scene_id >= (int)S->scenes.size() || S->running.load()) return MPPI_ERR_INVALID_ARG;
+    Scene& sc = S->scenes[scene_id];
+    if (n_elite == 0) n_elite = sc.K;
+    if (n_elite < 1 || n_elite > sc.K || !(eta > 0.0f && eta <= 1.0f) || update_cov < 0 || update_cov > 1 ||
+        !(cov_floor >= 0.0f))
+        return MPPI_ERR_INVALID_ARG;
+    if (n_elite < sc.K && sc.K > 8192) return MPPI_ERR_UNSUPPORTED;  // the elite sort holds 8192 keys
+    const size_t blk = (size_t)sc.H * sc.nu * sc.nu;
+    if (!sc.d_eq8) {
+        cudaError_t e = cudaMalloc(&sc.d_eq8, (2 * blk + (size_t)sc.K) * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc(&sc.d_sel, 3 * sizeof(unsigned long long));
+        std::vector<float> sig(sc.nu), B(2 * blk, 0.0f);  // Sigma_0 = diag(sigma^2), its factor diag(sigma)
+        if (e == cudaSuccess) e = cudaMemcpy(sig.data(), sc.d_params, sc.nu * sizeof(float), cudaMemcpyDeviceToHost);
+        for (int h = 0; h < sc.H; ++h)
+            for (int j = 0; j < sc.nu; ++j) {
+                B[((size_t)h * sc.nu + j) * sc.nu + j] = sig[j] * sig[j];
+                B[blk + ((size_t)h * sc.nu + j) * sc.nu + j] = sig[j];
+            }
+        if (e == cudaSuccess) e = cudaMemcpy(sc.d_eq8, B.data(), 2 * blk * sizeof(float), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(sc.d_eq8);
+            cudaFree(sc.d_sel);
+            sc.d_eq8 = nullptr;
+            sc.d_sel = nullptr;
+            return cuda_rc(e);
+        }
+    }
+    sc.n_elite = n_elite;
+    sc.eta = eta;
+    sc.update_cov = update_cov;
+    sc.cov_floor = cov_floor;
+    if (update_cov) sc.cov_sampling = 1;
+    sc.elite = (n_elite != sc.K || eta != 1.0f || update_cov || sc.cov_sampling) ? 1 : 0;
+    return MPPI_OK;
+}
+
+int srv_set_scene_projection(mppi_server* S, int scene_id, const float* bounds, float rho, const float* scales) {
+    if (!S || !bounds || scene_id < 0 || scene_id >= (int)S->scenes.size() || S->running.load())
+        return MPPI_ERR_INVALID_ARG;
+    Scene& sc = S->scenes[scene_id];
+    std::vector<unsigned char> host;
+    const int rc = qp_build(sc.nu, sc.H, bounds, rho, scales, host);
+    if (rc != MPPI_OK) return rc;
+    cudaFree(sc.d_qp);
+    sc.d_qp = nullptr;
+    cudaError_t e = cudaMalloc(&sc.d_qp, host.size());
+    if (e == cudaSuccess) e = cudaMemcpy(sc.d_qp, host.data(), host.size(), cudaMemcpyHostToDevice);
+    return cuda_rc(e);
 }
 
 int srv_submit(mppi_server* S, int scene_id, uint64_t* ticket) {

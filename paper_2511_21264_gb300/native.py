@@ -159,6 +159,8 @@ def lib():
     _decl(L, "srv_add_scene", i, [vp, vp, i, i, C.c_float, fp, u64, fp, C.POINTER(i)])
     _decl(L, "srv_start", i, [vp])
     _decl(L, "srv_stop", i, [vp])
+    _decl(L, "srv_set_scene_update", i, [vp, i, i, C.c_float, i, C.c_float])
+    _decl(L, "srv_set_scene_projection", i, [vp, i, fp, C.c_float, fp])
     _decl(L, "srv_submit", i, [vp, i, C.POINTER(u64)])
     _decl(L, "srv_cancel", i, [vp, u64])
     _decl(L, "srv_poll", i, [vp, u64, fp, i, C.POINTER(C.c_double), C.POINTER(i), i])
@@ -272,7 +274,8 @@ EPISODE_OUTCOMES = {0: "success", 1: "timeout", 2: "collision", 3: "dropped"}
 
 class ServerConfig(C.Structure):
     _fields_ = [("mem_budget_bytes", C.c_size_t), ("max_active", C.c_int), ("iters_per_request", C.c_int),
-                ("samples_per_cta", C.c_int), ("lanes_per_sample", C.c_int), ("size_classes", C.c_int)]
+                ("samples_per_cta", C.c_int), ("lanes_per_sample", C.c_int), ("size_classes", C.c_int),
+                ("qp_iters", C.c_int)]
 
 
 class SrvStats(C.Structure):
@@ -284,9 +287,9 @@ class Server:
     """Replan server with continuous batching (srv_*)."""
 
     def __init__(self, mem_budget_bytes: int, max_active: int, iters_per_request: int, samples_per_cta: int = 0,
-                 lanes_per_sample: int = 0, size_classes: int = 0):
+                 lanes_per_sample: int = 0, size_classes: int = 0, qp_iters: int = 0):
         cfg = ServerConfig(int(mem_budget_bytes), int(max_active), int(iters_per_request), int(samples_per_cta),
-                           int(lanes_per_sample), int(size_classes))
+                           int(lanes_per_sample), int(size_classes), int(qp_iters))
         h = C.c_void_p()
         _check(lib().srv_create(C.byref(cfg), C.byref(h)), "srv_create")
         self._h = h
@@ -309,6 +312,17 @@ class Server:
 
     def stop(self) -> int:
         return lib().srv_stop(self._h)
+
+    def set_scene_update(self, scene: int, n_elite: int, eta: float = 1.0, update_cov: bool = False,
+                         cov_floor: float = 0.0):
+        _check(lib().srv_set_scene_update(self._h, int(scene), int(n_elite), float(eta), int(bool(update_cov)),
+                                          float(cov_floor)), "srv_set_scene_update")
+
+    def set_scene_projection(self, scene: int, bounds, rho: float = 1.0, scales=None):
+        b = _host_f32(bounds)
+        sc = None if scales is None else _host_f32(scales, 4)
+        _check(lib().srv_set_scene_projection(self._h, int(scene), b.ctypes.data, float(rho),
+                                              None if sc is None else sc.ctypes.data), "srv_set_scene_projection")
 
     def submit(self, scene: int) -> int:
         t = C.c_uint64()

@@ -148,3 +148,53 @@ def test_poisson_load_completes_and_reports_latency():
     assert s["completed"] > 20 and s["waiting"] == 0 and s["active"] == 0
     assert s["p99_ms"] >= s["p50_ms"] > 0 and s["sample_steps_per_s"] > 0
     srv.stop()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("qp", [0, 8])
+def test_server_full_eq8_and_projection(qp):
+    # scenes with the full Eq. 8 (elite set, eta, covariance blocks that carry
+    # over between requests) and, with qp, the projection of every request's
+    # samples: each result equals the same scene's controller run M
+    # iterations per request, bitwise, alone and in a mix of classes
+    from paper_2511_21264_gb300 import native
+    native.build()
+    M = 3
+    cfgs = [(256, 16, 32, 0.7, True), (512, 16, 0, 1.0, False), (128, 8, 16, 0.5, True), (2048, 16, 64, 0.8, True)]
+    mix = []
+    for i, (K, H, ne, eta, cov) in enumerate(cfgs):
+        sc = _scene(20 + i, K=K, H=H)
+        mix.append((sc, native.Model(sc.to_blob()), K, H, ne, eta, cov, scenes.controller_key(20 + i, 0)))
+    srv = native.Server(1 << 26, 16, M, qp_iters=qp)
+    ids = []
+    for sc, m, K, H, ne, eta, cov, key in mix:
+        sid = srv.add_scene(m, K, H, sc.lam, sc.sigma_vec(), key)
+        srv.set_scene_update(sid, ne, eta, cov, 1e-6)
+        if qp:
+            srv.set_scene_projection(sid, scenes.projection_bounds(sc))
+        ids.append(sid)
+    srv.start()
+    plans = []
+    for rnd in range(2):   # two requests per scene: the warm start (u_nom, Sigma) carries over
+        tickets = [srv.submit(i) for i in ids]
+        outs = [srv.poll(t, i, wait_ms=60000) for t, i in zip(tickets, ids)]
+        assert all(o[1] and o[0] == 0 for o in outs)
+        plans.append([o[2] for o in outs])
+    srv.stop()
+    for j, (sc, m, K, H, ne, eta, cov, key) in enumerate(mix):
+        ctl = native.Controller(m, K, H, sc.lam, sc.sigma_vec(), key)
+        ctl.set_update(ne or K, eta, cov, 1e-6)
+        if qp:
+            ctl.set_projection(scenes.projection_bounds(sc), iters=qp)
+        x = torch.tensor(m.home(), device="cuda")
+        u = torch.zeros((H, sc.nu), device="cuda")
+        for rnd in range(2):
+            for _ in range(M):
+                ctl.step(x, u, u)
+            assert ctl.sync() == 0
+            np.testing.assert_array_equal(u.cpu().numpy(), plans[rnd][j], err_msg=f"scene {j} request {rnd}")
+            # the server executes u_nom[0] and shifts the warm start
+            x1 = x[None].clone()
+            ctl.sim_step(x1, u[:1].contiguous())
+            x = x1[0].clone()
+            u = torch.cat([u[1:], u[-1:]], 0).contiguous()
