@@ -429,6 +429,12 @@ def run_batched(args):
             for m, sc in zip(models, pool)]
     units = sum(sc.K * sc.H for sc in pool)
     b = native.Batch(inst)
+    full = bool(args.elite or args.eta != 1.0 or args.cov or args.qp)
+    if full:  # the full Eq. 8 and/or the projection for every instance (and the sequential controllers)
+        if args.elite or args.eta != 1.0 or args.cov:
+            b.set_update(-1, args.elite, args.eta, args.cov, 1e-6)
+        if args.qp:
+            b.set_projection(np.stack([scenes.projection_bounds(sc) for sc in pool]), iters=args.qp)
     stream = torch.cuda.Stream(device=dev)
     xs = [torch.tensor(m.home(), device=dev) for m in models]
     us = [torch.zeros((sc.H, sc.nu), device=dev) for sc in pool]
@@ -447,6 +453,7 @@ def run_batched(args):
     with torch.cuda.stream(stream):
         tune_ms = b.autotune(xs, [u.clone() for u in us], reps=2, stream=stream)
         spc, order = b.get_launch()
+        lps, place = b.get_layout()
         for _ in range(args.warmup):
             b.step(xs, us, stream=stream, graph=True)
         stream.synchronize()
@@ -459,6 +466,11 @@ def run_batched(args):
             raise RuntimeError(f"device error {rc} in the batched steps")
         # sequential plain launches of the same controllers
         ctls = [native.Controller(m, K, H, lam, sig, key) for (m, K, H, lam, sig, key) in inst]
+        for c, sc in zip(ctls, pool):
+            if args.elite or args.eta != 1.0 or args.cov:
+                c.set_update(min(args.elite, sc.K) or sc.K, args.eta, args.cov, 1e-6)
+            if args.qp:
+                c.set_projection(scenes.projection_bounds(sc), iters=args.qp)
         useq = [torch.zeros_like(u) for u in us]
 
         def seq():
@@ -508,6 +520,8 @@ def run_batched(args):
                                "0..16 boxes (seeded), one persistent launch + update, graph replay",
                    "instances": 64, "sample_steps_per_iteration": units, "autotuned_samples_per_cta": spc,
                    "autotuned_order": "longest first" if order == 1 else "as given",
+                   "autotuned_lanes_per_sample": lps,
+                   "autotuned_placement": "fused" if place == 0 else "after the factor",
                    "autotune_ms": tune_ms, "parallelism": f"replicas x{world}",
                    "l2": "flushed between timed steps (256 MiB write)"},
         "iters_per_s": 64 * args.steps * world / (total * 1e-3),
@@ -524,6 +538,11 @@ def run_batched(args):
                                     "the whole iteration time"},
         "clocks": clocks,
     }
+    if full:
+        line["config"]["update"] = {"n_elite": args.elite or "K", "eta": args.eta, "covariance": bool(args.cov),
+                                    "projection_iters": args.qp}
+        line["metric"] = line["metric"].replace("controllers", "controllers, full Eq. 8" +
+                                                (" + QP projection" if args.qp else ""))
     print(json.dumps(line), flush=True)
     return 0
 
@@ -601,11 +620,15 @@ def run_closed_loop(args):
     """Closed-loop receding horizon as the paper evaluates it (Sec. IV-A):
     N_runs = args.runs episodes of the planar ball lift with randomised
     goals (ball start + (U(-0.1, 0.1), 0, U(0.15, 0.3)) m), K = args.k
-    samples, H = 16, M = 10 iterations per planning step, the first 4 steps
-    of the best sequence averaged and executed, 8 s of simulated time per
-    run.  Reports the success rate, task time (mean and standard deviation
-    over successful runs) and planning compute time (mean and standard
-    deviation over every planning step)."""
+    samples, H = args.cl_h, M = 10 iterations per planning step, the first 4
+    steps of the best sequence averaged and executed, 8 s of simulated time
+    per run.  Cost: the paper's ball-task suite (Sec. IV-B), pick phase then
+    move phase (switched when the end effectors' midpoint reaches the pick
+    point), end effectors l_ball apart and the pick point eps below the
+    ball's centre; --task -1 uses the scene's stage cost instead.  Reports
+    the success rate, task time (mean and standard deviation over
+    successful runs) and planning compute time (mean and standard deviation
+    over every planning step)."""
     import numpy as np
     import torch
     from paper_2511_21264_gb300 import native
@@ -615,7 +638,9 @@ def run_closed_loop(args):
     native.build() if rank == 0 and world == 1 else None
     native.lib()
     rng = np.random.default_rng(1000 + rank)
-    K, H, M, n_avg, max_steps = args.k, 16, 10, 4, 800
+    K, H, M, n_avg, max_steps = args.k, args.cl_h, 10, 4, 800
+    task = 0 if args.task is None else args.task
+    task = None if task < 0 else task
     results = []
     stream = torch.cuda.Stream(device=dev)
     with ClockSampler(local) as clk:
@@ -629,12 +654,12 @@ def run_closed_loop(args):
                 ctl.set_update(args.elite or K, args.eta, args.cov, 1e-6)
             if args.qp:
                 ctl.set_projection(scenes.projection_bounds(sc), iters=args.qp)
-            if args.task is not None:
-                ctl.set_task_cost(scenes.ball_task(sc, phase=args.task))
+            if task is not None:
+                ctl.set_task_cost(scenes.ball_task(sc, phase=task, eps=args.eps, l_ball=args.l_ball))
             u = torch.zeros((H, sc.nu), device=dev)
             with torch.cuda.stream(stream):
                 ep = ctl.run_episode(sc.x0, u, iters=M, n_avg=n_avg, max_steps=max_steps, goal_tol=0.03,
-                                     lift_dz=0.05, drop_dz=0.05, pick_tol=0.03 if args.task == 0 else 0.0,
+                                     lift_dz=0.05, drop_dz=0.05, pick_tol=0.03 if task == 0 else 0.0,
                                      record=True, stream=stream)
             results.append(ep)
             ctl.close()
@@ -657,8 +682,8 @@ def run_closed_loop(args):
                                f"{max_steps} world steps ({max_steps * 0.01:g} s) per run",
                    "update": {"n_elite": args.elite or K, "eta": args.eta, "covariance": bool(args.cov)},
                    "projection_iters": args.qp,
-                   "cost": "ball-task suite (Sec. IV-B), pick then move" if args.task == 0 else
-                           ("ball-task suite, move" if args.task == 1 else "scene stage cost")},
+                   "cost": (f"ball-task suite (Sec. IV-B), pick then move, l_ball={args.l_ball} m, eps={args.eps} m"
+                            if task == 0 else ("ball-task suite, move" if task == 1 else "scene stage cost"))},
         "task_time_s": {"mean": float(tt.mean()) if tt.size else None, "std": float(tt.std()) if tt.size else None,
                         "n_success": len(ok)},
         "comp_time_ms": {"mean": float(comp.mean()), "std": float(comp.std()), "n_plans": int(comp.size)},
@@ -688,8 +713,12 @@ def main(argv=None):
     ap.add_argument("--eta", type=float, default=1.0, help="learning rate of Eq. 8 (elite mode)")
     ap.add_argument("--cov", action="store_true", help="update the per-step covariance blocks (Eq. 8b/8c)")
     ap.add_argument("--qp", type=int, default=0, help="QP smoothing projection (Eq. 5) iterations (0 = off)")
-    ap.add_argument("--task", type=int, choices=(0, 1), default=None,
-                    help="the paper's ball-task cost suite in the given phase (0 pick, 1 move)")
+    ap.add_argument("--task", type=int, choices=(-1, 0, 1), default=None,
+                    help="the paper's ball-task cost suite in the given phase (0 pick, 1 move); closed_loop: "
+                         "default 0 (pick, then move), -1 = the scene's stage cost")
+    ap.add_argument("--cl-h", type=int, default=48, help="closed_loop: horizon (steps of 10 ms)")
+    ap.add_argument("--l-ball", type=float, default=0.25, help="closed_loop: end-effector distance of the grasp (m)")
+    ap.add_argument("--eps", type=float, default=0.02, help="closed_loop: pick point below the ball's centre (m)")
     ap.add_argument("--serve-seconds", type=float, default=60.0, help="arrival window per rate (serve)")
     ap.add_argument("--serve-classes", type=int, default=0,
                     help="serve: size classes of the batched server (0 = 6; 1 = one batch of all requests)")
@@ -711,6 +740,8 @@ def main(argv=None):
         return run_serve(args)
     if args.workload == "closed_loop":
         return run_closed_loop(args)
+    if args.task is not None and args.task < 0:
+        args.task = None
     return run_ours(args)
 
 
