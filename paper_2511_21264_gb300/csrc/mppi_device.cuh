@@ -138,9 +138,8 @@ __device__ __forceinline__ float group_sum(const Lanes<LPS>& g, float v) {
 }
 
 // Per-sample workspace in shared memory.  Scratch that lives in
-// one phase only shares storage: the capsule-box survivor list (collision),
-// the joint axes and subtree forces (dynamics) and the contact rows,
-// Delassus block and impulses (contacts).
+// one phase only shares storage: the capsule-box survivor list (collision)
+// and the contact rows, Delassus block and impulses (contacts).
 template <int NA>
 struct __align__(16) WarpWS {
     using d = Dims<NA>;
@@ -171,10 +170,6 @@ struct __align__(16) WarpWS {
         struct {
             CArr<short, 2 * MAXL * MAXB> surv;  // capsule-box pairs that pass the cull
         } col;
-        struct {
-            CArr<CArr<float, 6>, d::NL> S;
-            CArr<CArr<float, 6>, d::NL> F;
-        } dyn;
         struct {
             CArr<CArr<float, d::NV>, MAXR> Y;
             CArr<float, MAXR * MAXR> G;  // Delassus block Y Y^T, nr x nr
@@ -673,8 +668,6 @@ __device__ __forceinline__ int collide(const DevModel& M, WarpWS<NA>& w, const L
                 mid[k] = 0.5f * (a0[k] + a1[k]);
                 hv[k] = 0.5f * (a1[k] - a0[k]);
             }
-            // the boxes' tests are independent: unrolled, their loads and
-            // compare chains overlap
 #pragma unroll 4
             for (int bi = b0; bi < b1; ++bi)
                 if (segment_meets_inflated_box(mid, hv, M.box[bi], rc)) smask |= 1u << bi;
@@ -937,35 +930,24 @@ __device__ __forceinline__ void dynamics(const DevModel& M, WarpWS<NA>& w, const
         const DevLink& L = M.link[a][l - a * NA];
         const float td = fminf(fmaxf(L.gear * w.u[l], -L.tau_max), L.tau_max);
         const float rhs = td - tb - L.D * qdi;
-        if (act) {
-            w.rhs[l] = rhs;
-#pragma unroll
-            for (int t = 0; t < 6; ++t) {
-                w.ph.dyn.S[l][t] = S[t];
-                w.ph.dyn.F[l][t] = F[t];
-            }
-        }
+        if (act) w.rhs[l] = rhs;
     }
-    g.sync();
-    // (5) mass-matrix entries M[r][c] = S_r . F_c (r <= c), spread over the
-    //     lanes of the arm's segment; dt D on the diagonal
-    constexpr int NENT = NA * (NA + 1) / 2;
+    // (5) mass-matrix column c = i, M[r][c] = S_r . F_c (r <= c), on lane c
+    //     of the arm's segment: S_r comes from lane r by shuffles, F_c is the
+    //     lane's own; dt D on the diagonal.  The dot product's rounding is
+    //     written out (explicit FMAs) so that every layout forms the same bits.
+    {
+        const float dtD = M.dt * M.link[a][l - a * NA].D;
 #pragma unroll
-    for (int e0 = 0; e0 < NENT; e0 += SEG) {
-        const int e = e0 + i;
-        {  // every lane computes (past the last entry on the last one), the entries' lanes store
-            // entry ee = c (c + 1) / 2 + r, r <= c: c counts the triangular
-            // numbers 1, 3, 6, ... not above ee
-            const int ee = e < NENT ? e : NENT - 1;
-            int c = 0;
+        for (int r = 0; r < NA; ++r) {
+            float sr[6];
 #pragma unroll
-            for (int cc = 1; cc < NA; ++cc) c += ee >= cc * (cc + 1) / 2 ? 1 : 0;
-            const int r = ee - c * (c + 1) / 2;
-            const float* Sr = w.ph.dyn.S[a * NA + r];
-            const float* Fc = w.ph.dyn.F[a * NA + c];
-            float mv = Sr[0] * Fc[0] + Sr[1] * Fc[1] + Sr[2] * Fc[2] + Sr[3] * Fc[3] + Sr[4] * Fc[4] + Sr[5] * Fc[5];
-            if (r == c) mv += M.dt * M.link[a][c].D;
-            if (e < NENT) w.L[a][c][r] = mv;
+            for (int t = 0; t < 6; ++t) sr[t] = __shfl_sync(g.gm, S[t], r, Lanes<LPS>::SEG);
+            float mv = __fmul_rn(sr[0], F[0]);
+#pragma unroll
+            for (int t = 1; t < 6; ++t) mv = __fmaf_rn(sr[t], F[t], mv);
+            if (r == i) mv = __fadd_rn(mv, dtD);
+            if (act && r <= i) w.L[a][i][r] = mv;
         }
     }
     g.sync();
