@@ -591,9 +591,19 @@ def run_serve(args):
             # window; above 200 req/s, where it saturates and its backlog
             # would drain long after the window, a 5 s window (its throughput
             # is then its capacity)
-            p = serve(1, r, args.serve_seconds if r <= 200 else min(args.serve_seconds, 5.0))
+            short = args.serve_seconds if r <= 200 else min(args.serve_seconds, 5.0)
+            p = serve(1, r, short)
             entry["one_at_a_time"] = {k: p[k] for k in ("p50_ms", "p99_ms", "mean_ms", "sample_steps_per_s",
                                                         "completed", "wall_s")}
+            entry["one_at_a_time"]["arrival_window_s"] = short
+            if short < args.serve_seconds:
+                # saturated: latency grows with the window (the backlog), so
+                # the batched server also runs the one-at-a-time window
+                bs = serve(64, r, short)
+                entry["batched_same_window"] = {k: bs[k] for k in ("p50_ms", "p99_ms", "mean_ms",
+                                                                   "sample_steps_per_s", "completed", "wall_s")}
+                entry["batched_same_window"]["arrival_window_s"] = short
+                b = bs
             entry["p99_one_at_a_time_over_batched"] = p["p99_ms"] / max(b["p99_ms"], 1e-9)
             entry["throughput_batched_over_one_at_a_time"] = b["sample_steps_per_s"] / max(p["sample_steps_per_s"], 1e-9)
             out[f"{r:g}_req_per_s"] = entry
