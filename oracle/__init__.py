@@ -102,6 +102,9 @@ def lib():
         L.or_task_cost.restype = d
         L.or_rollout_task.argtypes = [vp, dp, dp, dp, i, dp, dp]
         L.or_rollout_task.restype = d
+        L.or_rollout_task_many.argtypes = [vp, dp, dp, dp, i, i, dp, i]
+        L.or_mppi_iteration_task.argtypes = [vp, dp, dp, dp, i, i, d, dp, C.c_uint64, C.c_uint64, dp, dp, dp, i]
+        L.or_mppi_iteration_task.restype = i
         _lib = L
     return _lib
 
@@ -238,21 +241,127 @@ class Model:
             raise FloatingPointError("oracle: covariance block not positive definite")
         return U
 
+    def rollout_task_many(self, x, U, task, nthreads=1):
+        """Ball-task-suite costs of K sequences U (K x H x nu) from x."""
+        U = _f64(U)
+        K, H = U.shape[0], U.shape[1]
+        costs = np.zeros(K)
+        lib().or_rollout_task_many(self.ptr, _dp(_f64(task)), _dp(_f64(x)), _dp(U), K, H, _dp(costs), nthreads)
+        return costs
+
     def mppi_iteration(self, x, u_nom, K, lam, sigma, seed, iteration, nthreads=1,
-                       want_samples=False):
+                       want_samples=False, task=None):
+        """One iteration; task (the suite's parameter array) replaces the
+        scene's stage cost by the ball-task suite."""
         u_nom = _f64(u_nom)
         H = u_nom.shape[0]
         u_out = np.zeros_like(u_nom)
         costs = np.zeros(K)
         U = np.zeros((K, H, self.nu)) if want_samples else None
-        st = lib().or_mppi_iteration(self.ptr, _dp(_f64(x)), _dp(u_nom), K, H, float(lam),
-                                     _dp(_f64(sigma)), C.c_uint64(seed), C.c_uint64(iteration),
-                                     _dp(u_out), _dp(costs), _dp(U) if want_samples else None,
-                                     nthreads)
+        tail = (float(lam), _dp(_f64(sigma)), C.c_uint64(seed), C.c_uint64(iteration),
+                _dp(u_out), _dp(costs), _dp(U) if want_samples else None, nthreads)
+        if task is None:
+            st = lib().or_mppi_iteration(self.ptr, _dp(_f64(x)), _dp(u_nom), K, H, *tail)
+        else:
+            st = lib().or_mppi_iteration_task(self.ptr, _dp(_f64(task)), _dp(_f64(x)), _dp(u_nom), K, H, *tail)
         out = dict(u_nom=u_out, costs=costs, status=st)
         if want_samples:
             out["U"] = U
         return out
+
+
+# -- closed-loop receding horizon (Sec. III-A; metrics of Sec. IV-A) --------
+EPISODE_OUTCOMES = ("success", "timeout", "collision", "dropped")
+
+
+def probe(model: Model, x):
+    """(smallest link-box distance, smallest left-right link distance, ball
+    centre, end-effector midpoint) at state x, from the collision pairs'
+    signed distances and the end effectors' positions."""
+    d = model.pair_distances(x, 1)
+    na = model.na
+    nlb = len(d) - na * na                 # every link against every box, then left x right links
+    link_box = d[:nlb].min() if nlb else np.inf
+    arm_arm = d[nlb:].min()
+    ball = _f64(x)[2 * na:2 * na + 3]
+    mid = model.ee_state(x)["p"].mean(axis=0)
+    return link_box, arm_arm, ball, mid
+
+
+def run_episode(model: Model, x0, K, H, lam, sigma, seed, iters, n_avg, max_steps, goal_tol, lift_dz,
+                drop_dz, pick_tol=0.0, task=None, goal=None, nthreads=1):
+    """Receding-horizon control with the simulator as the world (Sec. III-A,
+    Alg. 1 and the paragraph after Eq. 8).
+
+    Each planning step runs `iters` MPPI iterations from the world state on
+    the warm-started nominal sequence (iteration counter running on across
+    planning steps, so iteration i draws the i-th noise block of `seed`),
+    takes the lowest-cost sample of the last iteration, averages its first
+    n_avg controls, applies the average for n_avg world steps and shifts the
+    nominal sequence by n_avg steps (the last step repeated).  After every
+    world step: collision (a link inside a box, or the two arms' links
+    touching when they were apart at the start), success (the ball centre
+    within goal_tol of the goal: the task's target with the ball-task suite,
+    else `goal`), drop (the ball more than drop_dz below the highest point
+    it reached after rising lift_dz above its start), in that order; a
+    timeout after max_steps world steps.  With the suite in its pick phase
+    and pick_tol > 0 the task switches to the move phase once the end
+    effectors' midpoint is within pick_tol of the pick point (eps below the
+    ball's start).  Returns outcome, steps, plans, switch_step, the world
+    trajectory and the executed controls."""
+    x = _f64(x0).copy()
+    nu = model.nu
+    task = None if task is None else _f64(task).copy()
+    goal = _f64(task[15:18] if task is not None else goal)
+    switching = task is not None and task[0] == 0.0 and pick_tol > 0.0
+    pick_point = task[12:15] - np.array([0.0, 0.0, task[11]]) if task is not None else None
+    u = np.zeros((H, nu))
+    it = 0
+    lb0, aa0, ball0, _ = probe(model, x)
+    z0 = ball0[2]
+    zmax, lifted = z0, False
+    out = dict(outcome="timeout", steps=0, plans=0, switch_step=-1)
+    traj, uex = [x.copy()], []
+    done = False
+    while not done and out["steps"] < max_steps:
+        for _ in range(iters):
+            r = model.mppi_iteration(x, u, K, lam, sigma, seed, it, nthreads=nthreads, want_samples=True,
+                                     task=task)
+            it += 1
+            u = r["u_nom"]
+        costs = np.where(np.isfinite(r["costs"]), r["costs"], np.inf)
+        best = int(np.argmin(costs))           # lowest index among equal costs
+        u1 = r["U"][best, :n_avg].mean(axis=0)
+        for _ in range(n_avg):
+            if out["steps"] >= max_steps:
+                break
+            x, _info = model.step(x, u1)
+            out["steps"] += 1
+            traj.append(x.copy())
+            uex.append(u1.copy())
+            lb, aa, ball, mid = probe(model, x)
+            if not lifted and ball[2] > z0 + lift_dz:
+                lifted = True
+            zmax = max(zmax, ball[2])
+            if lb < 0.0 or (aa0 >= 0.0 and aa < 0.0):
+                out["outcome"], done = "collision", True
+            elif np.linalg.norm(ball - goal) < goal_tol:
+                out["outcome"], done = "success", True
+            elif lifted and ball[2] < zmax - drop_dz:
+                out["outcome"], done = "dropped", True
+            if done:
+                break
+            if switching and np.linalg.norm(mid - pick_point) < pick_tol:
+                task[0] = 1.0
+                switching = False
+                out["switch_step"] = out["steps"]
+        out["plans"] += 1
+        if done:
+            break
+        u = np.concatenate([u[n_avg:], np.repeat(u[-1:], min(n_avg, H), axis=0)])[:H]
+    out["traj"] = np.array(traj)
+    out["u_exec"] = np.array(uex).reshape(-1, nu)
+    return out
 
 
 # -- narrow phase (module level, for brute-force tests) --------------------

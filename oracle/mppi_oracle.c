@@ -965,8 +965,12 @@ int or_mppi_update(int K, int H, int nu, const double *costs, const double *U, d
     return 0;
 }
 
+double or_rollout_task(const or_model *m, const double *task, const double *x, const double *U, int H,
+                       double *traj_out, double *terms);
+
 typedef struct {
     const or_model *m;
+    const double *task; /* NULL: the scene's stage cost; else the ball-task suite */
     const double *x;
     const double *U;
     int H, k0, k1;
@@ -976,8 +980,35 @@ typedef struct {
 static void *rollout_worker(void *arg) {
     rollout_job *j = (rollout_job *)arg;
     size_t stride = (size_t)j->H * j->m->nu;
-    for (int k = j->k0; k < j->k1; k++) j->costs[k] = or_rollout(j->m, j->x, j->U + (size_t)k * stride, j->H, NULL);
+    for (int k = j->k0; k < j->k1; k++) {
+        const double *Uk = j->U + (size_t)k * stride;
+        j->costs[k] = j->task ? or_rollout_task(j->m, j->task, j->x, Uk, j->H, NULL, NULL)
+                              : or_rollout(j->m, j->x, Uk, j->H, NULL);
+    }
     return NULL;
+}
+
+/* K rollouts from one state, samples split into contiguous chunks over
+ * `nthreads` host threads (each cost is computed alone, so the split does
+ * not change any result). */
+static void rollout_many_from(const or_model *m, const double *task, const double *x, const double *U, int K,
+                              int H, double *costs, int nthreads) {
+    pthread_t th[256];
+    rollout_job jobs[256];
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    int per = (K + nthreads - 1) / nthreads;
+    int started = 0;
+    for (int t = 0; t < nthreads; t++) {
+        jobs[t].m = m; jobs[t].task = task; jobs[t].x = x; jobs[t].U = U; jobs[t].H = H;
+        jobs[t].k0 = t * per; jobs[t].k1 = (t + 1) * per < K ? (t + 1) * per : K;
+        jobs[t].costs = costs;
+        if (jobs[t].k0 >= jobs[t].k1) break;
+        if (nthreads == 1) { rollout_worker(&jobs[t]); started = 0; break; }
+        pthread_create(&th[t], NULL, rollout_worker, &jobs[t]);
+        started++;
+    }
+    for (int t = 0; t < started; t++) pthread_join(th[t], NULL);
 }
 
 /* Roll out K control sequences from one state (or from K states when
@@ -991,30 +1022,23 @@ void or_rollout_many(const or_model *m, const double *x, int per_sample_state, c
         for (int k = 0; k < K; k++) costs[k] = or_rollout(m, x + (size_t)k * nx, U + (size_t)k * H * m->nu, H, NULL);
         return;
     }
-    pthread_t th[256];
-    rollout_job jobs[256];
-    if (nthreads > 256) nthreads = 256;
-    int per = (K + nthreads - 1) / nthreads;
-    int started = 0;
-    for (int t = 0; t < nthreads; t++) {
-        jobs[t].m = m; jobs[t].x = x; jobs[t].U = U; jobs[t].H = H;
-        jobs[t].k0 = t * per; jobs[t].k1 = (t + 1) * per < K ? (t + 1) * per : K;
-        jobs[t].costs = costs;
-        if (jobs[t].k0 >= jobs[t].k1) break;
-        if (nthreads == 1) { rollout_worker(&jobs[t]); started = 0; break; }
-        pthread_create(&th[t], NULL, rollout_worker, &jobs[t]);
-        started++;
-    }
-    for (int t = 0; t < started; t++) pthread_join(th[t], NULL);
+    rollout_many_from(m, NULL, x, U, K, H, costs, nthreads);
+}
+
+/* The same K rollouts costed by the ball-task suite (Sec. IV-B) instead of
+ * the scene's stage cost. */
+void or_rollout_task_many(const or_model *m, const double *task, const double *x, const double *U, int K, int H,
+                          double *costs, int nthreads) {
+    rollout_many_from(m, task, x, U, K, H, costs, nthreads);
 }
 
 /* One MPPI iteration (Alg. 1, one pass of the loop without the QP and with
  * the full sample set as elite set): samples U_k = clamp(u_nom + eps_k),
  * roll out, cost, update.  Writes the K costs, the new nominal sequence and
  * optionally the samples.  Returns the update's status. */
-int or_mppi_iteration(const or_model *m, const double *x, const double *u_nom, int K, int H, double lambda,
-                      const double *sigma, uint64_t seed, uint64_t iteration, double *u_out, double *costs,
-                      double *U_out, int nthreads) {
+static int mppi_iteration_with(const or_model *m, const double *task, const double *x, const double *u_nom, int K,
+                               int H, double lambda, const double *sigma, uint64_t seed, uint64_t iteration,
+                               double *u_out, double *costs, double *U_out, int nthreads) {
     int nu = m->nu;
     size_t n = (size_t)K * H * nu;
     double *eps = (double *)malloc(sizeof(double) * n);
@@ -1030,11 +1054,27 @@ int or_mppi_iteration(const or_model *m, const double *x, const double *u_nom, i
                 if (val > L->u_hi) val = L->u_hi;
                 U[i] = val;
             }
-    or_rollout_many(m, x, 0, U, K, H, costs, nthreads);
+    rollout_many_from(m, task, x, U, K, H, costs, nthreads);
     int st = or_mppi_update(K, H, nu, costs, U, lambda, u_nom, u_out, NULL);
     free(eps);
     if (!U_out) free(U);
     return st;
+}
+
+int or_mppi_iteration(const or_model *m, const double *x, const double *u_nom, int K, int H, double lambda,
+                      const double *sigma, uint64_t seed, uint64_t iteration, double *u_out, double *costs,
+                      double *U_out, int nthreads) {
+    return mppi_iteration_with(m, NULL, x, u_nom, K, H, lambda, sigma, seed, iteration, u_out, costs, U_out,
+                               nthreads);
+}
+
+/* The same iteration with every sample costed by the ball-task suite
+ * (Sec. IV-B): the optimiser step of the closed-loop task runs. */
+int or_mppi_iteration_task(const or_model *m, const double *task, const double *x, const double *u_nom, int K,
+                           int H, double lambda, const double *sigma, uint64_t seed, uint64_t iteration,
+                           double *u_out, double *costs, double *U_out, int nthreads) {
+    return mppi_iteration_with(m, task, x, u_nom, K, H, lambda, sigma, seed, iteration, u_out, costs, U_out,
+                               nthreads);
 }
 
 /* --------------------------------------------------------------------- */

@@ -11,7 +11,7 @@ divisions, trigonometric, exponential and logarithmic functions run on the
 special-function units and are not FP32 FLOPs; Philox is integer work.
 
 The data-dependent terms (active contacts per step, capsule-box pairs that
-pass the bounding-sphere cull, steps whose only contact is the ball against
+pass the separating-axis cull, steps whose only contact is the ball against
 static geometry) are measured on the device during the timed run
 (mppi_profile_read, mppi_profile_lone_contacts).
 """
@@ -36,9 +36,16 @@ def per_sample_step(scene, contacts: float, box_tests: float, lone: float = 0.0,
     # a3 broad + narrow phase
     sphere_capsule = 53
     sphere_box = 25
-    cull = 28
-    golden = 37 * 20 + 34 * 3 + 40 + 25 + 12   # SDF evaluations, bookkeeping, refinement, witness
-    parts["collide"] = 4 + sphere_capsule * nl + sphere_box * nb + cull * nl * nb + golden * box_tests
+    cull = 28  # segment against the inflated box: centre offset, three box axes, three cross axes
+    # exact capsule-box distance of a pair that passes the cull: the 43
+    # candidate parameters along the segment (the two ends 0, the nine slab
+    # and centre crossings 3 each, the twelve edge-region stationary points
+    # 18, the eight vertex-region ones 22, the twelve face-distance crossings
+    # 14), each clamped (2), the box SDF there (26: the point 6, per axis 6,
+    # root and sum 2) and the running minimum (2); at the minimiser the SDF
+    # with normal and surface point (30) and the contact point (12)
+    exact = (3 * 9 + 18 * 12 + 22 * 8 + 14 * 12) + 43 * (2 + 26 + 2) + 30 + 12
+    parts["collide"] = 4 + sphere_capsule * nl + sphere_box * nb + cull * nl * nb + exact * box_tests
     # a4/a5 per link: world inertia (R I R^T 75, params 26), axis 6, composite 10,
     #    F = I^c S 42, velocity 12, velocity-product acceleration 42, gravity 6,
     #    I a and I v 84, force cross product 36, subtree force 6, S.F 11, drive 7

@@ -438,6 +438,14 @@ def served_pool(n_scenes=256, seed=0, k_choices=(512, 1024, 2048, 4096),
     return batched_pool(n_scenes, seed=seed + 77, k_choices=k_choices, h_choices=h_choices)
 
 
+def lift_goal(scene: Scene, seed: int) -> tuple:
+    """A randomised lift goal for closed-loop runs (seeded): the ball's start
+    moved by U(-0.1, 0.1) m sideways and U(0.15, 0.3) m up."""
+    rng = np.random.default_rng(5000 + seed)
+    start = np.array(scene.x0[scene.nu:scene.nu + 3])
+    return tuple(start + np.array([rng.uniform(-0.1, 0.1), 0.0, rng.uniform(0.15, 0.3)]))
+
+
 def controller_key(scene_seed: int, instance: int) -> int:
     """64-bit Philox key for one controller instance (splitmix64 of the pair)."""
     z = (scene_seed * 0x9E3779B97F4A7C15 + instance * 0xBF58476D1CE4E5B9 + 0x94D049BB133111EB)

@@ -1,7 +1,13 @@
 """Closed-loop receding horizon (mppi_run_episode) on the GPU: the driver's
 steps against the same steps made through the C ABI by hand (bitwise), the
 world steps against the FP64 oracle's simulator (single-step tolerance
-1e-4 max(1, |x|)), outcomes, statistics and determinism."""
+1e-4 max(1, |x|)), outcomes, statistics and determinism; the first planning
+step's executed control and the outcome rates of 100 runs against the
+oracle's closed loop."""
+import json
+import math
+import os
+
 import numpy as np
 import pytest
 
@@ -11,6 +17,10 @@ from paper_2511_21264_gb300 import scenes
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 DEV = "cuda:0"
+
+
+def _f32(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float32))
 
 
 @pytest.fixture(scope="module")
@@ -127,3 +137,78 @@ def test_episode_with_projection_and_full_update(native):
     assert np.all(np.isfinite(ep["traj"]))
     # executed controls respect the projection's velocity bounds (to the ADMM tolerance)
     assert np.abs(ep["u_exec"]).max() <= np.pi * 1.05
+
+
+# -- closed-loop outcomes against the oracle's (Sec. IV-A metrics) ---------
+GOLDEN_CL = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                         "closed_loop_outcomes_config1.json")
+
+
+def _cl_controller(native, s, seed, key_instance):
+    sc = scenes.config(1, seed=seed)
+    sc.goal = scenes.lift_goal(sc, seed)
+    gm = native.Model(sc.to_blob())
+    ctl = native.Controller(gm, s["K"], s["H"], sc.lam, sc.sigma_vec(), scenes.controller_key(seed, key_instance))
+    ctl.set_task_cost(scenes.ball_task(sc, phase=0, eps=s["eps"], l_ball=s["l_ball"]))
+    return sc, gm, ctl
+
+
+def _cl_episode(native, s, seed, key_instance, max_steps):
+    sc, gm, ctl = _cl_controller(native, s, seed, key_instance)
+    u = torch.zeros((s["H"], sc.nu), device=DEV)
+    ep = ctl.run_episode(sc.x0, u, iters=s["iters"], n_avg=s["n_avg"], max_steps=max_steps,
+                         goal_tol=s["goal_tol"], lift_dz=s["lift_dz"], drop_dz=s["drop_dz"],
+                         pick_tol=s["pick_tol"], record=True)
+    ctl.close()
+    gm.close()
+    return ep
+
+
+def test_first_plan_executes_the_oracles_control(native):
+    # Same noise key as the oracle's stored single plans.  The lowest-cost
+    # sample of the plan's last iteration is unique unless two costs are
+    # within the FP32 rollouts' tolerance (1e-3 relative): where the GPU
+    # picks the oracle's sample, the executed control (mean of its first
+    # n_avg rows) must match; where it picks another, that sample's oracle
+    # cost must tie with the lowest.
+    doc = json.load(open(GOLDEN_CL))
+    s = doc["setting"]
+    same = 0
+    for rec in doc["first_plan"]:
+        sc, gm, ctl = _cl_controller(native, s, rec["seed"], doc["first_plan_key_instance"])
+        u = torch.zeros((s["H"], sc.nu), device=DEV)
+        best = torch.zeros(2, device=DEV)
+        ctl.solve(torch.tensor(_f32(sc.x0), device=DEV), u, s["iters"], best=best)
+        assert ctl.sync() == 0
+        k = int(best[1].item())
+        ctl.close()
+        gm.close()
+        costs = np.array(rec["costs"])
+        if k == rec["best"]:
+            ep = _cl_episode(native, s, rec["seed"], doc["first_plan_key_instance"], s["n_avg"])
+            np.testing.assert_allclose(ep["u_exec"][0], np.array(rec["u_exec0"]), atol=1e-3, rtol=0)
+            same += 1
+        else:
+            cmin = costs[rec["best"]]
+            assert costs[k] - cmin <= 1e-3 * abs(cmin), (rec["seed"], k, rec["best"])
+    assert same >= len(doc["first_plan"]) // 2
+
+
+def test_closed_loop_outcome_rates_match_the_oracle(native):
+    # 100 closed-loop runs of the planar ball lift on the GPU against the
+    # oracle's 100 (same scenes and goals, independent noise keys): for each
+    # outcome a two-proportion z test, |z| < 2.576 (two-sided, alpha = 0.01).
+    doc = json.load(open(GOLDEN_CL))
+    s = doc["setting"]
+    n = len(doc["runs"])
+    gpu = [_cl_episode(native, s, r["seed"], 0, s["max_steps"])["outcome_name"] for r in doc["runs"]]
+    ora = [r["outcome"] for r in doc["runs"]]
+    for outcome in oracle.EPISODE_OUTCOMES:
+        x1, x2 = gpu.count(outcome), ora.count(outcome)
+        p = (x1 + x2) / (2 * n)
+        if p in (0.0, 1.0):
+            continue
+        z = (x1 / n - x2 / n) / math.sqrt(p * (1 - p) * 2 / n)
+        assert abs(z) < 2.576, (outcome, x1, x2, z)
+    # the comparison has power only if some outcome is neither rare nor certain
+    assert any(10 <= ora.count(o) <= n - 10 for o in oracle.EPISODE_OUTCOMES)

@@ -434,14 +434,16 @@ def test_full_size_sampled_and_properties(native, cfg):
 
 
 # ------------------------------------------------------- statistical parity
-@pytest.mark.parametrize("cfg,K,H,iters", [(1, 64, 20, 10), (2, 128, 32, 5)])
-def test_statistical_parity_100_seeds(native, cfg, K, H, iters):
+@pytest.mark.parametrize("cfg,K,H,iters,lps", [(1, 64, 20, 10, 0), (2, 128, 32, 5, 0), (3, 64, 16, 5, 16)])
+def test_statistical_parity_100_seeds(native, cfg, K, H, iters, lps):
     """Longer contact rollouts are compared statistically: final nominal cost
     after `iters` MPPI iterations from the home state, 100 controller seeds,
     GPU vs oracle (two-sample KS) and the improvement rate over zero controls
     (two proportions).  Config 1 at its own K, H and iteration count; the
     7-DoF lift at K = 128 (the oracle's share of the test stays in seconds)
-    and its full horizon H = 32, where the rollouts are long and chaotic."""
+    and its full horizon H = 32, where the rollouts are long and chaotic; the
+    8-box transfer at K = 64, H = 16 on the 16-lane layout its full size
+    runs on."""
     from scipy import stats
     sc = scenes.config(cfg)
     blob = sc.to_blob()
@@ -457,6 +459,8 @@ def test_statistical_parity_100_seeds(native, cfg, K, H, iters):
     for s in range(100):
         key = scenes.controller_key(1000 * cfg + s, 0)
         ctl = nat.Controller(gm, K, H, sc.lam, sig, key)
+        if lps:
+            ctl.set_layout(lps, 0)
         u = torch.zeros((H, sc.nu), device=DEV)
         for _ in range(iters):
             ctl.step(_t(x), u, u)
