@@ -324,7 +324,9 @@ def _measure(args, workload, steps, dev, stream, flush, world, local, rank):
     # from the committed ncu summary of the workload, taken at the current
     # kernel sources; null when there is none or it is stale
     traffic, exec_flops, source = profile_counters(workload) if plain else (None, None, "not captured")
-    roof = {"bound": "alu", "kernel": "rollout_kernel<7,1>", "achieved": achieved, "peak": peak,
+    lay = ctl.get_layout()
+    kname = f"rollout_kernel<{sc.n_a},{lay[0]},1,{int(args.task is not None)},{lay[1]}>"
+    roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
             "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic, "traffic_source": source,
             "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (median SM clock "
                           f"sampled during the timed steps)",
@@ -339,7 +341,6 @@ def _measure(args, workload, steps, dev, stream, flush, world, local, rank):
             "flops_per_launch": exec_flops, "achieved": ex, "frac": ex / peak,
             "per_sample_step": exec_flops / (K * H),
             "basis": "ncu FP32 thread instructions of one launch (2 x FFMA + FADD + FMUL) / live mean duration"}
-    lay = ctl.get_layout()
     roof["layout"] = {"lanes_per_sample": lay[0], "placement": "fused" if lay[1] == 0 else "after the factor",
                       "samples_per_cta": lay[2]}
     return {"sc": sc, "value": units / (total_ms * 1e-3), "e2e": units / (e2e_ms * 1e-3),
