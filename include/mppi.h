@@ -162,7 +162,7 @@ int mppi_sync(mppi_ctx *c, void *stream);
 /* Profiling.  mppi_profile(c, n) records CUDA events around the rollout
  * and update kernels of the next n iterations (mppi_step / mppi_solve
  * eager path) on the launching stream and counts, on the device, the active
- * contacts and the capsule-box pairs that pass the bounding-sphere cull;
+ * contacts and the capsule-box pairs that pass the separating-axis cull;
  * n = 0 turns it off.  mppi_profile_read synchronises the recorded events
  * and returns: iterations recorded, total rollout and update kernel time
  * (ms), mean active contacts per sample-step and mean exact capsule-box
