@@ -627,8 +627,9 @@ __device__ __forceinline__ void ball_pass(const DevModel& M, WarpWS<NA>& w, cons
 // Narrow phase in canonical pair order (ball-floor, ball-links, ball-boxes,
 // links x boxes).  Ball pairs: one lane per pair slot (above), exact,
 // compacted with a ballot.  Capsule-box pairs: a conservative
-// bounding-sphere cull per lane, then each surviving pair (in pair order) is
-// minimised by the whole group over the candidate set above.  Each lane adds
+// separating-axis cull per lane (segment_meets_inflated_box), then each
+// surviving pair (in pair order) is minimised by the whole group over the
+// candidate set above.  Each lane adds
 // the depths of the contacts it found to pa (all) and pbox (against boxes),
 // per slot element; every lane gets the number of stored contacts (ncon) and
 // the blocks they touch (tb: 1 left arm, 2 right arm, 4 ball).  Returns the
