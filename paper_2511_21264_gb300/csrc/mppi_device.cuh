@@ -454,83 +454,78 @@ __device__ __forceinline__ bool segment_meets_inflated_box(const float* mid, con
 // stationary point of the squared distance to an edge or vertex region (for
 // every set of >= 2 exceeded slabs and sign pattern), or inside the box where
 // two face distances cross.  43 candidates in all; each is clamped to [0,1].
+//
+// Every candidate is t = num / den with, per axis k and for a sign s_k,
+//   al_k = s_k (a_k - c_k) - Z_k h_k,   be_k = s_k d_k,
+//   num  = sum_k al_k (b_k - p_k be_k),  den = sum_k be_k (p_k be_k - b_k):
+//   - ends (ids 0, 1): no axis terms, t = 0 or 1;
+//   - slab planes x_k = c_k + s h_k (ids 2-7) and axis centres x_k = c_k
+//     (ids 8-10, Z_k = 0): b_k = -1 on that axis, t = -al_k / be_k;
+//   - edge (ids 11-22, two axes) and vertex (ids 23-30, three axes) regions:
+//     p_k = 1 on the exceeded slabs, t = -sum al_k be_k / sum be_k^2, the
+//     stationary point of the squared distance to that edge or vertex;
+//   - two face distances crossing inside the box (ids 31-42): b = -1 on the
+//     lower axis j and +1 on the higher one k, t = (al_k - al_j) / (be_j - be_k).
+// One arithmetic path for all of them (no branches on the candidate's kind);
+// the table holds (s_k, Z_k, p_k, b_k) per candidate and axis.
 constexpr int CB_CANDIDATES = 43;
+static __device__ const float4 CB_TABLE[CB_CANDIDATES][3] = {
+    {{1.0f, 1.0f, 0.0f, 0.0f}, {1.0f, 1.0f, 0.0f, 0.0f}, {1.0f, 1.0f, 0.0f, 0.0f}},
+    {{1.0f, 1.0f, 0.0f, 0.0f}, {1.0f, 1.0f, 0.0f, 0.0f}, {1.0f, 1.0f, 0.0f, 0.0f}},
+    {{1.0f, 1.0f, 0.0f, -1.0f}, {1.0f, 1.0f, 0.0f, 0.0f}, {1.0f, 1.0f, 0.0f, 0.0f}},
+    {{-1.0f, 1.0f, 0.0f, -1.0f}, {1.0f, 1.0f, 0.0f, 0.0f}, {1.0f, 1.0f, 0.0f, 0.0f}},
+    {{1.0f, 1.0f, 0.0f, 0.0f}, {1.0f, 1.0f, 0.0f, -1.0f}, {1.0f, 1.0f, 0.0f, 0.0f}},
+    {{1.0f, 1.0f, 0.0f, 0.0f}, {-1.0f, 1.0f, 0.0f, -1.0f}, {1.0f, 1.0f, 0.0f, 0.0f}},
+    {{1.0f, 1.0f, 0.0f, 0.0f}, {1.0f, 1.0f, 0.0f, 0.0f}, {1.0f, 1.0f, 0.0f, -1.0f}},
+    {{1.0f, 1.0f, 0.0f, 0.0f}, {1.0f, 1.0f, 0.0f, 0.0f}, {-1.0f, 1.0f, 0.0f, -1.0f}},
+    {{1.0f, 0.0f, 0.0f, -1.0f}, {1.0f, 1.0f, 0.0f, 0.0f}, {1.0f, 1.0f, 0.0f, 0.0f}},
+    {{1.0f, 1.0f, 0.0f, 0.0f}, {1.0f, 0.0f, 0.0f, -1.0f}, {1.0f, 1.0f, 0.0f, 0.0f}},
+    {{1.0f, 1.0f, 0.0f, 0.0f}, {1.0f, 1.0f, 0.0f, 0.0f}, {1.0f, 0.0f, 0.0f, -1.0f}},
+    {{1.0f, 1.0f, 1.0f, 0.0f}, {1.0f, 1.0f, 1.0f, 0.0f}, {1.0f, 1.0f, 0.0f, 0.0f}},
+    {{-1.0f, 1.0f, 1.0f, 0.0f}, {1.0f, 1.0f, 1.0f, 0.0f}, {1.0f, 1.0f, 0.0f, 0.0f}},
+    {{1.0f, 1.0f, 1.0f, 0.0f}, {-1.0f, 1.0f, 1.0f, 0.0f}, {1.0f, 1.0f, 0.0f, 0.0f}},
+    {{-1.0f, 1.0f, 1.0f, 0.0f}, {-1.0f, 1.0f, 1.0f, 0.0f}, {1.0f, 1.0f, 0.0f, 0.0f}},
+    {{1.0f, 1.0f, 1.0f, 0.0f}, {1.0f, 1.0f, 0.0f, 0.0f}, {1.0f, 1.0f, 1.0f, 0.0f}},
+    {{-1.0f, 1.0f, 1.0f, 0.0f}, {1.0f, 1.0f, 0.0f, 0.0f}, {1.0f, 1.0f, 1.0f, 0.0f}},
+    {{1.0f, 1.0f, 1.0f, 0.0f}, {1.0f, 1.0f, 0.0f, 0.0f}, {-1.0f, 1.0f, 1.0f, 0.0f}},
+    {{-1.0f, 1.0f, 1.0f, 0.0f}, {1.0f, 1.0f, 0.0f, 0.0f}, {-1.0f, 1.0f, 1.0f, 0.0f}},
+    {{1.0f, 1.0f, 0.0f, 0.0f}, {1.0f, 1.0f, 1.0f, 0.0f}, {1.0f, 1.0f, 1.0f, 0.0f}},
+    {{1.0f, 1.0f, 0.0f, 0.0f}, {-1.0f, 1.0f, 1.0f, 0.0f}, {1.0f, 1.0f, 1.0f, 0.0f}},
+    {{1.0f, 1.0f, 0.0f, 0.0f}, {1.0f, 1.0f, 1.0f, 0.0f}, {-1.0f, 1.0f, 1.0f, 0.0f}},
+    {{1.0f, 1.0f, 0.0f, 0.0f}, {-1.0f, 1.0f, 1.0f, 0.0f}, {-1.0f, 1.0f, 1.0f, 0.0f}},
+    {{1.0f, 1.0f, 1.0f, 0.0f}, {1.0f, 1.0f, 1.0f, 0.0f}, {1.0f, 1.0f, 1.0f, 0.0f}},
+    {{-1.0f, 1.0f, 1.0f, 0.0f}, {1.0f, 1.0f, 1.0f, 0.0f}, {1.0f, 1.0f, 1.0f, 0.0f}},
+    {{1.0f, 1.0f, 1.0f, 0.0f}, {-1.0f, 1.0f, 1.0f, 0.0f}, {1.0f, 1.0f, 1.0f, 0.0f}},
+    {{-1.0f, 1.0f, 1.0f, 0.0f}, {-1.0f, 1.0f, 1.0f, 0.0f}, {1.0f, 1.0f, 1.0f, 0.0f}},
+    {{1.0f, 1.0f, 1.0f, 0.0f}, {1.0f, 1.0f, 1.0f, 0.0f}, {-1.0f, 1.0f, 1.0f, 0.0f}},
+    {{-1.0f, 1.0f, 1.0f, 0.0f}, {1.0f, 1.0f, 1.0f, 0.0f}, {-1.0f, 1.0f, 1.0f, 0.0f}},
+    {{1.0f, 1.0f, 1.0f, 0.0f}, {-1.0f, 1.0f, 1.0f, 0.0f}, {-1.0f, 1.0f, 1.0f, 0.0f}},
+    {{-1.0f, 1.0f, 1.0f, 0.0f}, {-1.0f, 1.0f, 1.0f, 0.0f}, {-1.0f, 1.0f, 1.0f, 0.0f}},
+    {{1.0f, 1.0f, 0.0f, -1.0f}, {1.0f, 1.0f, 0.0f, 1.0f}, {1.0f, 1.0f, 0.0f, 0.0f}},
+    {{-1.0f, 1.0f, 0.0f, -1.0f}, {1.0f, 1.0f, 0.0f, 1.0f}, {1.0f, 1.0f, 0.0f, 0.0f}},
+    {{1.0f, 1.0f, 0.0f, -1.0f}, {-1.0f, 1.0f, 0.0f, 1.0f}, {1.0f, 1.0f, 0.0f, 0.0f}},
+    {{-1.0f, 1.0f, 0.0f, -1.0f}, {-1.0f, 1.0f, 0.0f, 1.0f}, {1.0f, 1.0f, 0.0f, 0.0f}},
+    {{1.0f, 1.0f, 0.0f, -1.0f}, {1.0f, 1.0f, 0.0f, 0.0f}, {1.0f, 1.0f, 0.0f, 1.0f}},
+    {{-1.0f, 1.0f, 0.0f, -1.0f}, {1.0f, 1.0f, 0.0f, 0.0f}, {1.0f, 1.0f, 0.0f, 1.0f}},
+    {{1.0f, 1.0f, 0.0f, -1.0f}, {1.0f, 1.0f, 0.0f, 0.0f}, {-1.0f, 1.0f, 0.0f, 1.0f}},
+    {{-1.0f, 1.0f, 0.0f, -1.0f}, {1.0f, 1.0f, 0.0f, 0.0f}, {-1.0f, 1.0f, 0.0f, 1.0f}},
+    {{1.0f, 1.0f, 0.0f, 0.0f}, {1.0f, 1.0f, 0.0f, -1.0f}, {1.0f, 1.0f, 0.0f, 1.0f}},
+    {{1.0f, 1.0f, 0.0f, 0.0f}, {-1.0f, 1.0f, 0.0f, -1.0f}, {1.0f, 1.0f, 0.0f, 1.0f}},
+    {{1.0f, 1.0f, 0.0f, 0.0f}, {1.0f, 1.0f, 0.0f, -1.0f}, {-1.0f, 1.0f, 0.0f, 1.0f}},
+    {{1.0f, 1.0f, 0.0f, 0.0f}, {-1.0f, 1.0f, 0.0f, -1.0f}, {-1.0f, 1.0f, 0.0f, 1.0f}},
+};
 __device__ __forceinline__ float capsule_box_candidate(int id, const float* a, const float* d, const float* box) {
-    // per-lane axis choices are applied by selects over the three axes, so
-    // that the caller's small arrays stay in registers
-    float t = 0.0f;
-    if (id == 1) {
-        t = 1.0f;
-    } else if (id >= 2 && id < 11) {  // slab planes x_k = c_k +- h_k, axis centres x_k = c_k
-        const int k = id < 8 ? (id - 2) >> 1 : id - 8;
-        const float sg = id >= 8 ? 0.0f : ((id & 1) ? -1.0f : 1.0f);
-        float ak = a[0], dk = d[0], ck = box[0], hk = box[3];
+    float num = id == 1 ? 1.0f : 0.0f, den = id < 2 ? 1.0f : 0.0f;
 #pragma unroll
-        for (int q = 1; q < 3; ++q)
-            if (k == q) {
-                ak = a[q];
-                dk = d[q];
-                ck = box[q];
-                hk = box[3 + q];
-            }
-        t = (ck + sg * hk - ak) / dk;
-    } else if (id >= 11) {
-        float al[3], be[3];
-        int use = 7;
-        bool cross = false;
-        float sgn[3] = {1.0f, 1.0f, 1.0f};
-        if (id < 31 && id >= 23) {  // three exceeded slabs (vertex regions)
-            const int q = id - 23;
-            sgn[0] = (q & 1) ? -1.0f : 1.0f;
-            sgn[1] = (q & 2) ? -1.0f : 1.0f;
-            sgn[2] = (q & 4) ? -1.0f : 1.0f;
-        } else {  // two exceeded slabs (edge regions, id < 23), or two face
-                  // distances equal inside the box (id >= 31)
-            const int q = id < 23 ? id - 11 : id - 31;
-            const int pair = q >> 2;
-            use = pair == 0 ? 3 : (pair == 1 ? 5 : 6);
-            const int first = pair == 2 ? 1 : 0;
-            const int second = pair == 0 ? 1 : 2;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                if (k == first) sgn[k] = (q & 1) ? -1.0f : 1.0f;
-                if (k == second) sgn[k] = (q & 2) ? -1.0f : 1.0f;
-            }
-            cross = id >= 31;
-        }
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            al[k] = sgn[k] * (a[k] - box[k]) - box[3 + k];
-            be[k] = sgn[k] * d[k];
-        }
-        if (!cross) {
-            float num = 0.0f, den = 0.0f;
-#pragma unroll
-            for (int k = 0; k < 3; ++k)
-                if (use & (1 << k)) {
-                    num += al[k] * be[k];
-                    den += be[k] * be[k];
-                }
-            t = -num / den;
-        } else {
-            // the two axes in use, lower (j) and higher (k2)
-            float alj = 0.0f, bej = 0.0f, alk = 0.0f, bek = 0.0f;
-            bool seen = false;
-#pragma unroll
-            for (int k = 0; k < 3; ++k)
-                if (use & (1 << k)) {
-                    if (!seen) {
-                        alj = al[k];
-                        bej = be[k];
-                    } else {
-                        alk = al[k];
-                        bek = be[k];
-                    }
-                    seen = true;
-                }
-            t = (alk - alj) / (bej - bek);
-        }
+    for (int k = 0; k < 3; ++k) {
+        const float4 c = __ldg(&CB_TABLE[id][k]);  // s, Z, p, b
+        const float al = fmaf(c.x, a[k] - box[k], -(c.y * box[3 + k]));
+        const float be = c.x * d[k];
+        const float t1 = fmaf(-c.z, be, c.w);
+        num = fmaf(al, t1, num);
+        den = fmaf(be, -t1, den);
     }
+    float t = num / den;
     if (!(t >= 0.0f)) t = 0.0f;  // also maps NaN from degenerate directions
     if (t > 1.0f) t = 1.0f;
     return t;
