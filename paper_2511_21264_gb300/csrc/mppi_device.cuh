@@ -818,10 +818,12 @@ __device__ __forceinline__ void arm_solve(const WarpWS<NA>& w, int a, float (&A)
 }
 
 template <int NA, int LPS>
+__device__ __forceinline__ void arm_factor_step(const DevModel& M, WarpWS<NA>& w, const Lanes<LPS>& g, int* err,
+                                                int tb);
+
+template <int NA, int LPS>
 __device__ __forceinline__ void dynamics(const DevModel& M, WarpWS<NA>& w, const Lanes<LPS>& g, int* err,
                                          const float (&R)[9], const float (&cl)[3], int tb, bool solve) {
-    using d = Dims<NA>;
-    constexpr int SEG = Lanes<LPS>::SEG;
     const int a = g.a, i = g.i;
     const bool act = i < NA;
     const int l = a * NA + (act ? i : 0);
@@ -951,7 +953,18 @@ __device__ __forceinline__ void dynamics(const DevModel& M, WarpWS<NA>& w, const
     //     The factor is kept only for arms a contact touches (the contact
     //     solve's rows need it there).  Skipped (solve = false) when the
     //     caller solves the arms together with a ball-only contact problem.
-    if (!solve) return;
+    if (solve) arm_factor_step<NA, LPS>(M, w, g, err, tb);
+}
+
+// (6) of dynamics on its own: the Cholesky factor of each arm block (in
+// registers) and the free velocity; the ball's free velocity.  The factor is
+// kept for the arms a contact touches (tb), whose contact rows need it.
+template <int NA, int LPS>
+__device__ __forceinline__ void arm_factor_step(const DevModel& M, WarpWS<NA>& w, const Lanes<LPS>& g, int* err,
+                                                int tb) {
+    using d = Dims<NA>;
+    constexpr int SEG = Lanes<LPS>::SEG;
+    const int a = g.a, i = g.i;
     const int armc = tb & 3;
     if (i == 0) {
         float A[NA][NA], di[NA], y[NA];

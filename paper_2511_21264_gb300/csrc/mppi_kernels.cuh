@@ -130,6 +130,10 @@ __device__ __forceinline__ float rollout_sample(const DevModel& M, WarpWS<NA>& w
         } else {
             if (h > 0 && sl < 3 && M.w_grasp != 0.0f) kacc += grasp_coord<NA>(w, sl);
         }
+        // the mass matrix and bias forces do not depend on the contacts:
+        // formed before the collision phase, so that the link frames kept
+        // from the kinematics are no longer live across it
+        dynamics<NA>(M, w, g, io.err, Rl, cl, 0, false);
         int ncon, tb;
         n_exact += collide<NA>(M, w, g, pacc, pbacc, ncon, tb);
         g.sync();
@@ -139,14 +143,14 @@ __device__ __forceinline__ float rollout_sample(const DevModel& M, WarpWS<NA>& w
         n_lone += lone ? 1u : 0u;
         if (PLACE == 0) {
             // the arms' solve and the contact solve side by side
-            dynamics<NA>(M, w, g, io.err, Rl, cl, tb, !lone);
             if (lone) {
                 solve_ball_contacts<NA, 1, 0>(M, w, g, io.err);
             } else {
+                arm_factor_step<NA, LPS>(M, w, g, io.err, tb);
                 contacts<NA>(M, w, g, ncon, tb);
             }
         } else {
-            dynamics<NA>(M, w, g, io.err, Rl, cl, tb, true);
+            arm_factor_step<NA, LPS>(M, w, g, io.err, tb);
             contacts<NA>(M, w, g, ncon, tb);
         }
         integrate<NA>(M, w, g);
