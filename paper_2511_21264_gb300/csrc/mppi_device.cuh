@@ -1618,9 +1618,12 @@ __device__ __forceinline__ void integrate(const DevModel& M, WarpWS<NA>& w, cons
             dq0 = 1.0f + x2 * (-0.5f + x2 * (1.0f / 24.0f + x2 * (-1.0f / 720.0f + x2 * (1.0f / 40320.0f))));
             kq = 0.5f + x2 * (-1.0f / 12.0f + x2 * (1.0f / 240.0f + x2 * (-1.0f / 10080.0f + x2 * (1.0f / 725760.0f))));
         } else {
+            // the sine and cosine of x from the argument in half-turns,
+            // x / pi, whose reduction is exact (no slow path for large
+            // arguments); the division by pi adds one rounding of x
             const float ang = sqrtf(a2);
             float s, c;
-            sincosf(0.5f * ang, &s, &c);
+            sincospif(0.5f * ang * 0.318309886183790672f, &s, &c);
             dq0 = c;
             kq = s / ang;
         }
