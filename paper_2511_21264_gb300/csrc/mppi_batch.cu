@@ -89,7 +89,8 @@ __global__ void __launch_bounds__(256, 2) batch_rollout_kernel(const BatchInst* 
                 io.u_stride = (long long)I.K * d::NU;
                 io.u_ext = (long long)I.H * I.K * d::NU - (long long)k * d::NU;
             }
-            const float cost = rollout_sample<NA, LPS, MODE, false, PLACE>(M, w, g, io);
+            // drawn samples: the covariance-capable draw (instances may mix)
+            const float cost = rollout_sample<NA, LPS, MODE == 1 ? 2 : 0, false, PLACE>(M, w, g, io);
             if (g.sl == 0) I.costs[k] = cost;
         }
         __syncthreads();

@@ -13,15 +13,15 @@ struct SampleIO {
     const float* U;            // explicit controls of this sample, row h at U + h * u_stride, MODE 0
     long long u_stride;
     long long u_ext;           // floats from U to the end of the caller's control buffer, MODE 0
-    const float* unom;         // nominal controls (H x nu, shared or global), MODE 1
-    float sig, lo, hi;         // this lane's sigma and control bounds (group lane < nu), MODE 1
-    uint2 key;                 // Philox key, MODE 1
-    uint32_t iter;             // Philox iteration word, MODE 1
+    const float* unom;         // nominal controls (H x nu, shared or global), MODE 1 and 2
+    float sig, lo, hi;         // this lane's sigma and control bounds (group lane < nu), MODE 1 and 2
+    uint2 key;                 // Philox key, MODE 1 and 2
+    uint32_t iter;             // Philox iteration word, MODE 1 and 2
     int k, H;                  // sample index, horizon
     float* x_out;              // optional final state (nx)
     float* U_store;            // optional: sampled controls out, H x Kn x nu (h-major)
     int Kn;                    // sample count of U_store
-    const float* Lfac;         // optional: H x nu x nu factors of the sampling covariance blocks
+    const float* Lfac;         // optional (MODE 2): H x nu x nu factors of the sampling covariance blocks
     int* err;                  // error word
     unsigned long long* stats; // optional [sample-steps, contacts, exact box tests]
     const DevTask* task;       // ball-task cost suite (TASK rollouts), in place of the stage cost
@@ -79,7 +79,7 @@ __device__ __forceinline__ float rollout_sample(const DevModel& M, WarpWS<NA>& w
     float upre = 0.0f;  // explicit controls: the next step's value
     if (MODE == 0 && sl < d::NU) upre = ld_checked(io.U, sl, io.u_ext);
     for (int h = 0; h < io.H; ++h) {
-        if (MODE == 1) {
+        if (MODE >= 1) {
             // every DS steps the group's lanes draw one Philox block each: DS
             // steps x 16 controls of standard normals, counter (j/4, h, k,
             // iteration), Box-Muller on the word pairs (the values sample_row
@@ -99,7 +99,7 @@ __device__ __forceinline__ float rollout_sample(const DevModel& M, WarpWS<NA>& w
                 const int jc = sl < d::NU ? sl : d::NU - 1;
                 const float* zr = w.zn[h & (DS - 1)];
                 float acc = ld_checked(io.unom, h * d::NU + jc, (long long)io.H * d::NU);
-                if (io.Lfac) {  // u = nu + L_h z, FMAs in the order sample_row uses
+                if (MODE == 2 && io.Lfac) {  // u = nu + L_h z, FMAs in the order sample_row uses
                     // (unrolled over the row so that its loads are issued together)
                     const long long r0 = ((long long)h * d::NU + jc) * d::NU, n_l = (long long)io.H * d::NU * d::NU;
 #pragma unroll

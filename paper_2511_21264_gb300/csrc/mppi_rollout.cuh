@@ -1,7 +1,9 @@
 // The rollout kernel (sampling + H-step contact rollout + stage cost of K
 // samples, Alg. 1) and its launch: template over the arm size NA, the lanes
 // per sample LPS (32, 16 or 8 -- one, two or four samples per warp), the
-// control source MODE (0 explicit, 1 Philox), the ball-task cost suite and
+// control source MODE (0 explicit, 1 Philox with the diagonal sigma, 2
+// Philox through the covariance factors when they are given: the draw's
+// covariance branch stays out of the plain kernel), the ball-task cost suite and
 // the placement of the lone ball contact's solve.  Each arm size is
 // instantiated in a translation unit of its own (mppi_rollout_dh7.cu,
 // mppi_rollout_planar3.cu) so that they compile in parallel.
@@ -47,7 +49,7 @@ __global__ void __launch_bounds__(512) rollout_kernel(RolloutArgs args) {
     constexpr size_t task_b = TASK ? sizeof(DevTask) : 0;
     DevTask* task_s = reinterpret_cast<DevTask*>(smem + sizeof(DevModel));
     float* unom_s = reinterpret_cast<float*>(smem + sizeof(DevModel) + task_b);
-    const int unom_n = (MODE == 1 && args.stage_unom) ? args.H * d::NU : 0;
+    const int unom_n = (MODE >= 1 && args.stage_unom) ? args.H * d::NU : 0;
     const size_t ws_off = sizeof(DevModel) + task_b + ((size_t)unom_n * sizeof(float) + 15) / 16 * 16;
     stage_model(smem, args.model, unom_s, args.u_nom, unom_n);
     if constexpr (TASK) {
@@ -70,10 +72,10 @@ __global__ void __launch_bounds__(512) rollout_kernel(RolloutArgs args) {
     io.stats = args.stats;
     io.task = TASK ? task_s : nullptr;
     io.x_out = args.states_out ? args.states_out + (size_t)k * d::NX : nullptr;
-    io.U_store = MODE == 1 ? args.U_store : nullptr;
+    io.U_store = MODE >= 1 ? args.U_store : nullptr;
     io.Kn = args.n;
-    io.Lfac = MODE == 1 ? args.Lfac : nullptr;
-    if (MODE == 1) {
+    io.Lfac = MODE == 2 ? args.Lfac : nullptr;
+    if (MODE >= 1) {
         io.unom = unom_n ? unom_s : args.u_nom;
         io.iter = (uint32_t)(args.iter_ptr ? *args.iter_ptr : args.iter_val);
         io.key = make_uint2((uint32_t)args.seed, (uint32_t)(args.seed >> 32));
@@ -108,7 +110,7 @@ inline int cuda_fail(cudaError_t e) {
 
 template <int NA, int LPS, int MODE, bool TASK, int PLACE>
 int launch_t(const RolloutArgs& a, int spc, cudaStream_t s) {
-    const int unom = (MODE == 1 && a.stage_unom) ? a.H * Dims<NA>::NU : 0;
+    const int unom = (MODE >= 1 && a.stage_unom) ? a.H * Dims<NA>::NU : 0;
     const size_t sm = rollout_smem<NA, LPS>(spc, unom, TASK);
     auto fn = rollout_kernel<NA, LPS, MODE, TASK, PLACE>;
     int dev = 0, max_sm = 0;
@@ -138,6 +140,7 @@ int launch_t(const RolloutArgs& a, int spc, cudaStream_t s) {
 template <int NA, int LPS>
 int launch_lps(int mode, const RolloutArgs& a, int spc, cudaStream_t s) {
     if (mode == 0) return launch_t<NA, LPS, 0, false, 0>(a, spc, s);
+    if (a.Lfac) return a.place ? launch_t<NA, LPS, 2, false, 1>(a, spc, s) : launch_t<NA, LPS, 2, false, 0>(a, spc, s);
     return a.place ? launch_t<NA, LPS, 1, false, 1>(a, spc, s) : launch_t<NA, LPS, 1, false, 0>(a, spc, s);
 }
 
@@ -158,7 +161,8 @@ int dispatch_rollout(int mode, const RolloutArgs& a, int spc, cudaStream_t s) {
     if (spc * lps > 512) return MPPI_ERR_INVALID_ARG;
     if (a.task) {
         if (lps != 32 || a.place != 0) return MPPI_ERR_UNSUPPORTED;
-        return mode ? launch_t<NA, 32, 1, true, 0>(a, spc, s) : launch_t<NA, 32, 0, true, 0>(a, spc, s);
+        if (mode == 0) return launch_t<NA, 32, 0, true, 0>(a, spc, s);
+        return a.Lfac ? launch_t<NA, 32, 2, true, 0>(a, spc, s) : launch_t<NA, 32, 1, true, 0>(a, spc, s);
     }
     if (lps == 32) return launch_lps<NA, 32>(mode, a, spc, s);
     if (lps == 16) return launch_lps<NA, 16>(mode, a, spc, s);
