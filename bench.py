@@ -228,9 +228,16 @@ def run_reference(args):
     om = oracle.Model(sc.to_blob())
     x = sc.x0.astype(np.float32).astype(np.float64)
     u = np.zeros((sc.H, sc.nu))
-    Kp = max(2 * nthreads, 16)   # bounded sample per step
+    # bounded sample per step: the warm-up steps measure the oracle's rate on
+    # a small sample, then each timed step takes as many samples (a multiple
+    # of the thread count, at most K) as keep the timed steps near a minute
+    Kp = max(2 * nthreads, 16)
+    tw = time.perf_counter()
     for w in range(args.warmup):
         om.mppi_iteration(x, u, Kp, sc.lam, sc.sigma_vec(), 1, w, nthreads=nthreads)
+    rate = Kp * sc.H * args.warmup / max(time.perf_counter() - tw, 1e-9)
+    want = int(rate * 60.0 / (sc.H * max(args.steps, 1)))
+    Kp = int(min(sc.K, max(Kp, want // nthreads * nthreads)))
     t0 = time.perf_counter()
     for s in range(args.steps):
         om.mppi_iteration(x, u, Kp, sc.lam, sc.sigma_vec(), 1, args.warmup + s, nthreads=nthreads)
